@@ -1,0 +1,97 @@
+"""Seeded synthetic workloads: parameter sets and random perturbations.
+
+This module holds no arithmetic of the method.  It names the workloads by what
+they are (disc, order, mesh) with the parameters of the paper's planet-disc
+runs (Sec. 5.1: G = M_* = 1, planet on a fixed circular orbit at r_p = 1 with
+Omega_p = 1, smoothing eps = 0.6 H with H = h r_p, h = 0.05) and supplies seeded
+random modal perturbations that the tests feed to both the CUDA path and the
+oracle.  Both sides read these dicts; neither side's arithmetic lives here.
+"""
+import copy
+
+import numpy as np
+
+H_ASPECT = 0.05
+
+
+def _disc_base(n, order, seed, planet_q=None, damping=False, bc=1):
+    cfg = {
+        "order": order,
+        "mesh": {"nx": n, "ny": n, "x0": -2.5, "x1": 2.5, "y0": -2.5, "y1": 2.5, "bc": bc},
+        "eos": {"kind": 0, "gamma": 1.4, "h": H_ASPECT},
+        "planet": {"q": 0.0, "r_p": 1.0, "eps": 0.6 * H_ASPECT * 1.0, "omega_p": 1.0,
+                   "phi0": 0.0, "enabled": 0},
+        "disc": {"ic": 0, "star": 1, "r_soft": 0.2, "sigma_slope": -0.5, "sigma_floor": 1e-4,
+                 "noise_amp": 1e-4, "seed": seed, "rdamp_in": 0.0, "rdamp_out": 0.0,
+                 "cfl": 0.1, "rk": 3, "prec": 0, "amp": 0.0, "vx0": 0.0, "vy0": 0.0},
+    }
+    if planet_q is not None:
+        cfg["planet"]["q"] = planet_q
+        cfg["planet"]["enabled"] = 1
+    if damping:
+        cfg["disc"]["rdamp_in"] = 0.4
+        cfg["disc"]["rdamp_out"] = 2.1
+    return cfg
+
+
+def disc_small(n=64, order=2, seed=1):
+    """Locally isothermal Keplerian disc, P2 on 64x64, no planet, 50 steps."""
+    return _disc_base(n, order, seed)
+
+
+def disc_planet(n=256, order=4, seed=2, q=1e-5):
+    """Planet-disc, P4 on 256x256, q = 1e-5, damping zones r < 0.4 and r > 2.1, 200 steps."""
+    return _disc_base(n, order, seed, planet_q=q, damping=True)
+
+
+def disc_planet_512(n=512, order=4, seed=3, q=3e-5):
+    """Planet-disc, P4 on 512x512, q = 3e-5, damping zones, 1000 steps (precision form)."""
+    return _disc_base(n, order, seed, planet_q=q, damping=True)
+
+
+def density_wave(n=32, order=2, amp=0.2):
+    """Adiabatic density wave rho = 1 + amp sin(2 pi (x + y)), v = (1, 1), p = 1 on the
+    periodic unit square: an exact translating solution of Eq. 1 without gravity."""
+    return {
+        "order": order,
+        "mesh": {"nx": n, "ny": n, "x0": 0.0, "x1": 1.0, "y0": 0.0, "y1": 1.0, "bc": 0},
+        "eos": {"kind": 1, "gamma": 1.4, "h": 0.0},
+        "planet": {"q": 0.0, "r_p": 1.0, "eps": 0.03, "omega_p": 1.0, "phi0": 0.0, "enabled": 0},
+        "disc": {"ic": 1, "star": 0, "r_soft": 0.2, "sigma_slope": -0.5, "sigma_floor": 1e-4,
+                 "noise_amp": 0.0, "seed": 0, "rdamp_in": 0.0, "rdamp_out": 0.0, "cfl": 0.1,
+                 "rk": 3, "prec": 0, "amp": amp, "vx0": 1.0, "vy0": 1.0},
+    }
+
+
+def uniform_state(n=8, order=2, kind=1, vx0=0.0, vy0=0.0, bc=0, h=0.0):
+    """Uniform state rho = 1, v = (vx0, vy0), p = 1 on the unit square."""
+    cfg = density_wave(n, order, amp=0.0)
+    cfg["disc"]["ic"] = 2
+    cfg["disc"]["vx0"] = vx0
+    cfg["disc"]["vy0"] = vy0
+    cfg["eos"]["kind"] = kind
+    cfg["eos"]["h"] = h
+    cfg["mesh"]["bc"] = bc
+    return cfg
+
+
+WORKLOADS = {
+    "disc_p2_64": disc_small,
+    "disc_p4_256": disc_planet,
+    "disc_p4_512": disc_planet_512,
+}
+
+
+def workload(name, **kw):
+    return copy.deepcopy(WORKLOADS[name](**kw))
+
+
+def modal_perturbation(shape, seed, amp=1e-3, decay=0.5):
+    """Seeded uniform random modal coefficients of shape (nv, m*m, ny, nx) with
+    amplitude amp * decay**(a + b) for mode (a, b): a rough but resolved field."""
+    nv, M, ny, nx = shape
+    m = int(round(M ** 0.5))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = rng.uniform(-1.0, 1.0, size=shape)
+    scale = np.array([amp * decay ** (k // m + k % m) for k in range(M)])
+    return out * scale[None, :, None, None]

@@ -1,0 +1,425 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed forms
+(Gauss-Legendre tables, Legendre polynomials, spherical-Bessel projections,
+RK stability polynomials), published generator vectors, invariants (constant
+states, conservation, mirror symmetry), exact weak forms of polynomial states
+computed here with numpy quadrature, and measured convergence order p+1
+(Sec. 4.1).  None of these tests needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import spherical_jn
+
+import oracle
+from paper_1805_01443_gb300 import inputs
+
+# ----------------------------------------------------------------------------
+# independent helpers (numpy only)
+
+
+def np_basis(p, x):
+    """sqrt(2a+1) P_a(x) for a = 0..p via numpy's Legendre Vandermonde matrix."""
+    V = np.polynomial.legendre.legvander(np.asarray(x, dtype=float), p)
+    return V * np.sqrt(2 * np.arange(p + 1) + 1.0)
+
+
+def np_project(fun, xc, yc, dx, dy, p, npts=12):
+    """Mean-normalised L2 projection on one element by an npts^2 numpy GL rule."""
+    xg, wg = np.polynomial.legendre.leggauss(npts)
+    X = xc + 0.5 * dx * xg[:, None]
+    Y = yc + 0.5 * dy * xg[None, :]
+    F = fun(X, Y)
+    B = np_basis(p, xg)
+    return 0.25 * np.einsum("q,r,qr,qa,rb->ab", wg, wg, F, B, B).reshape(-1)
+
+
+def project_field(fun, cfg, npts=12):
+    mesh = cfg["mesh"]
+    p = cfg["order"]
+    nx, ny = mesh["nx"], mesh["ny"]
+    dx = (mesh["x1"] - mesh["x0"]) / nx
+    dy = (mesh["y1"] - mesh["y0"]) / ny
+    out = np.zeros(((p + 1) ** 2, ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            xc = mesh["x0"] + (i + 0.5) * dx
+            yc = mesh["y0"] + (j + 0.5) * dy
+            out[:, j, i] = np_project(fun, xc, yc, dx, dy, p, npts)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# tables
+
+
+def test_gauss_legendre_closed_forms():
+    s = math.sqrt
+    ref = {
+        1: ([0.0], [2.0]),
+        2: ([-1 / s(3), 1 / s(3)], [1.0, 1.0]),
+        3: ([-s(3 / 5), 0.0, s(3 / 5)], [5 / 9, 8 / 9, 5 / 9]),
+        4: ([-s(3 / 7 + 2 / 7 * s(6 / 5)), -s(3 / 7 - 2 / 7 * s(6 / 5)),
+             s(3 / 7 - 2 / 7 * s(6 / 5)), s(3 / 7 + 2 / 7 * s(6 / 5))],
+            [(18 - s(30)) / 36, (18 + s(30)) / 36, (18 + s(30)) / 36, (18 - s(30)) / 36]),
+        5: ([-s(5 + 2 * s(10 / 7)) / 3, -s(5 - 2 * s(10 / 7)) / 3, 0.0,
+             s(5 - 2 * s(10 / 7)) / 3, s(5 + 2 * s(10 / 7)) / 3],
+            [(322 - 13 * s(70)) / 900, (322 + 13 * s(70)) / 900, 128 / 225,
+             (322 + 13 * s(70)) / 900, (322 - 13 * s(70)) / 900]),
+    }
+    for m, (xr, wr) in ref.items():
+        x, w = oracle.gauss_legendre(m)
+        np.testing.assert_allclose(x, xr, rtol=0, atol=4e-16)
+        np.testing.assert_allclose(w, wr, rtol=4e-15, atol=0)
+
+
+def test_gauss_legendre_m6_matches_numpy():
+    x, w = oracle.gauss_legendre(6)
+    xr, wr = np.polynomial.legendre.leggauss(6)
+    np.testing.assert_allclose(x, xr, atol=1e-15)
+    np.testing.assert_allclose(w, wr, rtol=1e-14)
+
+
+def test_legendre_closed_forms():
+    for x in [-1.0, -0.7, -0.1, 0.0, 0.35, 0.9, 1.0]:
+        P, dP = oracle.legendre(5, x)
+        exact = [1, x, (3 * x**2 - 1) / 2, (5 * x**3 - 3 * x) / 2,
+                 (35 * x**4 - 30 * x**2 + 3) / 8, (63 * x**5 - 70 * x**3 + 15 * x) / 8]
+        dexact = [0, 1, 3 * x, (15 * x**2 - 3) / 2, (140 * x**3 - 60 * x) / 8,
+                  (315 * x**4 - 210 * x**2 + 15) / 8]
+        np.testing.assert_allclose(P, exact, atol=1e-15)
+        np.testing.assert_allclose(dP, dexact, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_basis_orthonormal_under_mean_inner_product(p):
+    m = p + 1
+    x, w = oracle.gauss_legendre(m)
+    phi = np.array([[math.sqrt(2 * a + 1) * oracle.legendre(p, xq)[0][a] for a in range(m)]
+                    for xq in x])
+    G1 = 0.5 * np.einsum("q,qa,qb->ab", w, phi, phi)
+    np.testing.assert_allclose(G1, np.eye(m), atol=2e-15)
+
+
+def test_splitmix64_published_vectors():
+    # first three outputs of SplitMix64 started from state 0 (Steele et al. 2014;
+    # the widely reproduced reference vector 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4,
+    # 0x06c45d188009454f); the oracle exposes the top 53 bits as a double in [0, 1)
+    ref = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    for c, v in enumerate(ref):
+        assert oracle.splitmix64_uniform(0, c) == (v >> 11) * 2.0**-53
+    u = np.array([oracle.splitmix64_uniform(12345, c) for c in range(20000)])
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.003
+
+
+# ----------------------------------------------------------------------------
+# Runge-Kutta tableaux (Appendix A) on u' = lambda u
+
+
+@pytest.mark.parametrize("z", [0.3 + 0.0j, -0.5 + 0.2j, 0.1 + 0.9j, -1.2 - 0.7j])
+def test_rk_ssp33_and_ssp22_stability_polynomials(z):
+    R3 = oracle.rk_linear(3, z.real, z.imag, 1.0)
+    assert abs(R3 - (1 + z + z**2 / 2 + z**3 / 6)) < 1e-15
+    R2 = oracle.rk_linear(2, z.real, z.imag, 1.0)
+    assert abs(R2 - (1 + z + z**2 / 2)) < 1e-15
+
+
+@pytest.mark.parametrize("rk,order", [(2, 2), (3, 3), (4, 4), (5, 5)])
+def test_rk_order_of_accuracy(rk, order):
+    lam = -0.8 + 1.1j
+    errs = []
+    for h in [0.1, 0.05]:
+        errs.append(abs(oracle.rk_linear(rk, lam.real, lam.imag, h) - np.exp(lam * h)))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > order + 1 - 0.2, (rk, rate)
+
+
+# ----------------------------------------------------------------------------
+# projection of initial data (Eq. 2, first line)
+
+
+def test_wave_projection_matches_spherical_bessel_closed_form():
+    # rho = 1 + A sin(k(x + y)) on element [xc +- dx/2] x [yc +- dy/2]:
+    # (1/2) int e^{i w xi} sqrt(2n+1) P_n(xi) dxi = sqrt(2n+1) i^n j_n(w)
+    # n = 16 keeps the (m+1)-point rule's error (~w^(2m+2)/(2m+2)!) below 1e-13
+    p, n = 3, 16
+    cfg = inputs.density_wave(n, p, amp=0.2)
+    o = oracle.Oracle(cfg)
+    u = o.fetch()
+    k = 2 * math.pi
+    dx = 1.0 / n
+    w = k * dx / 2
+    for (i, j) in [(0, 0), (5, 3), (15, 15)]:
+        xc, yc = (i + 0.5) * dx, (j + 0.5) * dx
+        ex = np.array([math.sqrt(2 * a + 1) * (1j**a) * spherical_jn(a, w) for a in range(p + 1)])
+        # sin(k(xc+yc) + w xi + w eta) = Im(e^{i k(xc+yc)} e^{i w xi} e^{i w eta})
+        ph = np.exp(1j * k * (xc + yc))
+        coef = 0.2 * np.imag(ph * np.outer(ex, ex)).reshape(-1)
+        coef[0] += 1.0
+        np.testing.assert_allclose(u[0, :, j, i], coef, atol=1e-12)
+
+
+def test_disc_ic_noise_statistics_and_seed():
+    cfg = inputs.disc_small(16, 2, seed=7)
+    a = oracle.Oracle(cfg).fetch()
+    b = oracle.Oracle(cfg).fetch()
+    assert np.array_equal(a, b)
+    cfg0 = inputs.disc_small(16, 2, seed=7)
+    cfg0["disc"]["noise_amp"] = 0.0
+    c = oracle.Oracle(cfg0).fetch()
+    d = a[0, 0] - c[0, 0]
+    # element average of (m+1)^2 uniform(-1e-4, 1e-4) node draws
+    assert np.abs(d).max() < 1e-4 and 0 < np.std(d) < 1e-4
+    # the noise is on Sigma at fixed velocity, so momentum moves by at most |v| 1e-4
+    assert np.abs(a[1:, 0] - c[1:, 0]).max() < 1e-4 * 5.0
+
+
+# ----------------------------------------------------------------------------
+# the spatial operator (Eq. 2)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", [1, 2])
+def test_constant_state_is_steady(p, kind):
+    cfg = inputs.uniform_state(5, p, kind=kind, vx0=0.3, vy0=-0.2, h=0.6)
+    o = oracle.Oracle(cfg)
+    L = o.rhs()
+    assert np.abs(L).max() < 1e-13
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_polynomial_state_exact_weak_form(p):
+    """Isothermal gas with constant c and uniform velocity: the flux is linear in a
+    degree-p polynomial density, every quadrature in Eq. 2 is exact and the traces
+    are continuous, so L(u) must equal the L2 projection of -div f exactly."""
+    c, v0x, v0y = 0.7, 0.45, -0.3
+    cfg = inputs.uniform_state(3, p, kind=2, h=c, bc=2)
+    cfg["mesh"].update({"nx": 3, "ny": 2, "x0": 0.0, "x1": 1.5, "y0": 0.0, "y1": 0.8})
+    rng = np.random.default_rng(p)
+    C = rng.uniform(-0.3, 0.3, size=(p + 1, p + 1))
+
+    def rho(X, Y):
+        return 2.0 + sum(C[a, b] * X**a * Y**b for a in range(p + 1) for b in range(p + 1))
+
+    def drho_dx(X, Y):
+        return sum(a * C[a, b] * X**(a - 1) * Y**b for a in range(1, p + 1) for b in range(p + 1))
+
+    def drho_dy(X, Y):
+        return sum(b * C[a, b] * X**a * Y**(b - 1) for a in range(p + 1) for b in range(1, p + 1))
+
+    state = np.stack([project_field(rho, cfg),
+                      project_field(lambda X, Y: v0x * rho(X, Y), cfg),
+                      project_field(lambda X, Y: v0y * rho(X, Y), cfg)])
+    expect = np.stack([
+        project_field(lambda X, Y: -(v0x * drho_dx(X, Y) + v0y * drho_dy(X, Y)), cfg),
+        project_field(lambda X, Y: -((v0x**2 + c**2) * drho_dx(X, Y) + v0x * v0y * drho_dy(X, Y)), cfg),
+        project_field(lambda X, Y: -(v0x * v0y * drho_dx(X, Y) + (v0y**2 + c**2) * drho_dy(X, Y)), cfg),
+    ])
+    o = oracle.Oracle(cfg)
+    o.set_state(state)
+    L = o.rhs()
+    np.testing.assert_allclose(L, expect, atol=1e-12 * np.abs(expect).max())
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_gravity_source_matches_exact_integral(p):
+    """Resting cold gas (c = 0, v = 0): L(u) is the projected gravity source
+    -rho grad(Phi_* + Phi_p); compared with a 20-point integral, the m-point rule
+    of Eq. 2 is exact to within its (dx/d)^(2m) error on these small elements."""
+    cfg = inputs.uniform_state(6, p, kind=2, h=0.0, bc=2)
+    cfg["mesh"].update({"x0": 0.8, "x1": 1.1, "y0": 0.1, "y1": 0.4})
+    cfg["disc"].update({"star": 1, "r_soft": 0.2})
+    cfg["planet"].update({"enabled": 1, "q": 1e-3, "eps": 0.03, "phi0": math.pi})
+    xp, yp = -1.0, 0.0
+
+    def rho(X, Y):
+        return 1.0 + 0.3 * X - 0.2 * Y + 0.1 * X * Y
+
+    def gphi(X, Y):
+        r3 = (X**2 + Y**2) ** 1.5
+        d2 = (X - xp) ** 2 + (Y - yp) ** 2 + 0.03**2
+        f = 1e-3 / d2**1.5
+        return X / r3 + f * (X - xp), Y / r3 + f * (Y - yp)
+
+    state = np.stack([project_field(rho, cfg), 0 * project_field(rho, cfg),
+                      0 * project_field(rho, cfg)])
+    expect = np.stack([0 * state[0],
+                       project_field(lambda X, Y: -rho(X, Y) * gphi(X, Y)[0], cfg, npts=20),
+                       project_field(lambda X, Y: -rho(X, Y) * gphi(X, Y)[1], cfg, npts=20)])
+    o = oracle.Oracle(cfg)
+    o.set_state(state)
+    L = o.rhs()
+    scale = np.abs(expect).max()
+    # the exact integral, within the m-point rule's error on these elements
+    np.testing.assert_allclose(L, expect, atol={3: 1e-8, 4: 1e-10}[p] * scale)
+    # and the m-point Gauss rule itself (numpy's nodes), to round-off
+    same_rule = np.stack([0 * state[0],
+                          project_field(lambda X, Y: -rho(X, Y) * gphi(X, Y)[0], cfg, npts=p + 1),
+                          project_field(lambda X, Y: -rho(X, Y) * gphi(X, Y)[1], cfg, npts=p + 1)])
+    np.testing.assert_allclose(L, same_rule, atol=1e-14 * scale)
+
+
+def test_conservation_periodic():
+    """Periodic adiabatic gas without gravity: total mass, momentum and energy
+    (sum of element averages times |K|) are constant to round-off."""
+    cfg = inputs.density_wave(12, 2)
+    o = oracle.Oracle(cfg)
+    u0 = o.fetch() + inputs.modal_perturbation(o.shape, seed=3, amp=1e-2)
+    o.set_state(u0)
+    tot0 = u0[:, 0].sum(axis=(1, 2))
+    o.step(20)
+    tot = o.fetch()[:, 0].sum(axis=(1, 2))
+    np.testing.assert_allclose(tot, tot0, rtol=0, atol=1e-13 * np.abs(tot0).max())
+
+
+@pytest.mark.parametrize("p,grids,cfl,min_rate", [
+    (1, [8, 16, 32], 0.5, 1.7),
+    (2, [8, 16, 32], 0.5, 2.7),
+    (3, [4, 8, 16], 0.1, 3.7),
+    (4, [4, 8, 16], 0.1, 4.7),
+])
+def test_wave_convergence_order(p, grids, cfl, min_rate):
+    """Sec. 4.1: L1 error of the translated density wave converges at order p+1
+    (bar: p + 0.7 on the finest pair of these coarse grids)."""
+    T = 0.25
+    errs = []
+    for n in grids:
+        cfg = inputs.density_wave(n, p)
+        cfg["disc"]["cfl"] = cfl
+        o = oracle.Oracle(cfg)
+        while True:
+            t = o.get_time()[0]
+            dt = o.cfl_dt()
+            if t + dt >= T - 1e-14:
+                o.step_dt(1, T - t)
+                break
+            o.step(1)
+        assert abs(o.get_time()[0] - T) < 1e-14
+        errs.append(o.l1_wave(T, 0))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > min_rate, rates
+
+
+def test_l1_norm_formula():
+    """Sec. 4.1 quadrature L1 norm: uniform rho = 1 against rho = 1 + A sin(2 pi (x + y))
+    gives A * 2/pi on the unit square (to quadrature accuracy)."""
+    cfg = inputs.uniform_state(16, 4, kind=1)
+    cfg["disc"]["amp"] = 0.2
+    o = oracle.Oracle(cfg)
+    assert abs(o.l1_wave(0.0, 0) - 0.2 * 2 / math.pi) < 1e-4
+
+
+def test_well_balance_residual_converges():
+    """The discrete residual L(u_bg) of the projected rotational equilibrium disc
+    (no planet, no noise) shrinks under refinement in the smooth annulus."""
+    res = []
+    for n in [16, 32, 64]:
+        cfg = inputs.disc_small(n, 2)
+        cfg["disc"]["noise_amp"] = 0.0
+        o = oracle.Oracle(cfg)
+        L = o.rhs()
+        dx = 5.0 / n
+        xc = -2.5 + (np.arange(n) + 0.5) * dx
+        R = np.hypot(xc[None, :], xc[:, None])
+        mask = (R > 0.6) & (R < 1.8)
+        res.append(np.sqrt(np.mean(L[:, :, mask] ** 2)))
+    rates = np.log2(np.array(res[:-1]) / np.array(res[1:]))
+    assert rates.min() > 1.8, (res, rates)
+
+
+# ----------------------------------------------------------------------------
+# time step, damping, torque
+
+
+def test_cfl_closed_form():
+    cfg = inputs.uniform_state(10, 3, kind=1, vx0=0.3, vy0=-0.2)
+    cfg["mesh"].update({"x1": 2.0})
+    o = oracle.Oracle(cfg)
+    c = math.sqrt(1.4)
+    dx, dy = 0.2, 0.1
+    expect = 0.1 / 7 / ((0.3 + c) / dx + (0.2 + c) / dy)
+    assert abs(o.cfl_dt() - expect) < 1e-16
+
+
+def test_damping_relaxes_towards_equilibrium_at_nodes():
+    cfg = inputs.disc_planet(16, 2, seed=1)
+    cfg["disc"]["noise_amp"] = 0.0
+    o = oracle.Oracle(cfg)
+    u_bg = o.fetch()
+    # a perturbed state relaxes towards the analytic equilibrium Q0 at each damped
+    # node by (dt Q0 + tau Q) / (tau + dt); undamped nodes are left alone
+    pert = u_bg.copy()
+    pert[0] *= 1.01
+    pert[1] *= 1.01
+    pert[2] *= 1.01
+    o.set_state(pert)
+    n0 = o.nodal()
+    dt = 0.05
+    o.damp(dt)
+    n1 = o.nodal()
+    p = cfg["order"]
+    x, _ = oracle.gauss_legendre(p + 1)
+    n = 16
+    dx = 5.0 / n
+    f = 1.15**1.5
+    for (i, j) in [(0, 0), (7, 7), (3, 8), (15, 2)]:
+        for q in range(p + 1):
+            for r in range(p + 1):
+                X = -2.5 + (i + 0.5) * dx + 0.5 * dx * x[q]
+                Y = -2.5 + (j + 0.5) * dx + 0.5 * dx * x[r]
+                rr = math.hypot(X, Y)
+                if rr < 0.4:
+                    rd, rb = 0.4, 0.4 / f
+                elif rr > 2.1:
+                    rd, rb = 2.1, 2.1 * f
+                else:
+                    rd = None
+                k = q * (p + 1) + r
+                if rd is None:
+                    assert abs(n1[0, k, j, i] - n0[0, k, j, i]) < 1e-13
+                    continue
+                R = min(((rr - rd) / (rb - rd)) ** 2, 1.0)
+                tau = 2 * math.pi * math.sqrt(rd**3) / R
+                sig0 = rr ** -0.5
+                expect = (dt * sig0 + tau * n0[0, k, j, i]) / (tau + dt)
+                assert abs(n1[0, k, j, i] - expect) < 1e-12
+                # velocity is damped towards the rotational equilibrium too
+                vphi = math.sqrt((1 - 1.5 * 0.05**2) / rr) if rr >= 0.2 else \
+                    math.sqrt((1 + 1.5 * 0.05**2) * rr**2 / 0.2**3)
+                vx0 = -vphi * Y / rr
+                vx = n0[1, k, j, i] / n0[0, k, j, i]
+                vexp = (dt * vx0 + tau * vx) / (tau + dt)
+                assert abs(n1[1, k, j, i] / n1[0, k, j, i] - vexp) < 1e-12
+
+
+def test_torque_mirror_symmetry_vanishes():
+    """Planet on the +x axis and a y-mirror-symmetric disc: Gamma_z = 0."""
+    cfg = inputs.disc_planet(32, 3, seed=1)
+    cfg["disc"]["noise_amp"] = 0.0
+    o = oracle.Oracle(cfg)
+    gz, ab = o.torque_now(0.0)
+    assert ab > 0 and abs(gz) < 1e-14 * ab
+    # with noise the symmetry is broken and the torque is no longer zero
+    cfg["disc"]["noise_amp"] = 1e-4
+    gz2, ab2 = oracle.Oracle(cfg).torque_now(0.0)
+    assert abs(gz2) > 1e-12 * ab2
+
+
+def test_torque_point_mass_far_field():
+    """A single small uniform element far from the planet acts as a point mass:
+    Gamma_z = x_p g_y - y_p g_x with g = M (r_c - r_p) / (d^2 + eps^2)^(3/2)."""
+    cfg = inputs.uniform_state(1, 2, kind=2, h=0.1)
+    cfg["mesh"].update({"x0": 2.0, "x1": 2.01, "y0": 1.0, "y1": 1.01})
+    cfg["planet"].update({"eps": 0.03, "r_p": 1.0, "phi0": 0.3})
+    o = oracle.Oracle(cfg)
+    t = 0.2
+    xp, yp = math.cos(0.5), math.sin(0.5)
+    gz, _ = o.torque_now(t)
+    M = 1.0 * 0.01 * 0.01
+    dxp, dyp = 2.005 - xp, 1.005 - yp
+    d2 = dxp**2 + dyp**2 + 0.03**2
+    g = M / d2**1.5
+    expect = xp * g * dyp - yp * g * dxp
+    assert abs(gz - expect) < 1e-4 * abs(expect)
