@@ -1,0 +1,183 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) discontinuous-Galerkin operator for the
+ * 2D Euler equations with star + planet gravity on a Cartesian mesh of
+ * rectangular elements, tensor-product Legendre modal basis of degree p <= 4
+ * (Velasco Romero et al., arXiv:1805.01443).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   dg_init   -- mesh, order, EOS and planet of Sec. 5.1; initial nodes of the
+ *                primitive variables -> conserved -> modes (Sec. 3.1 step i,
+ *                Eq. 2 first line: L2 projection of the initial data)
+ *   dg_step   -- CFL step (Sec. 2.3) + SSP Runge-Kutta stages (Algorithm 1,
+ *                Appendix A) of the semi-discrete operator of Eq. 2, damping
+ *                zones (Sec. 5.1) and the torque on the planet (Sec. 5.2)
+ *   dg_torque -- specific torque Gamma_z on the planet (Sec. 5.2 torque equation)
+ *   dg_fetch  -- copy of the modes to the host (Sec. 3.1 step iv)
+ *
+ * Conventions.
+ *   Mode (a, b) of variable v in element (i, j) -- a the degree in x, b in y,
+ *   m = p + 1 -- is element [v][a*m + b][j][i] of every canonical coefficient
+ *   array (FP64, C order, nv*m*m*ny*nx doubles; nv = 3 for the isothermal
+ *   kinds (Sigma, Sigma vx, Sigma vy), 4 for the adiabatic kind (+ E)).
+ *   The basis sqrt(2a+1) P_a(xi) sqrt(2b+1) P_b(eta) is orthonormal under the
+ *   mean inner product over the element, so mode 0 is the element average
+ *   (Sec. 3.1 computes the time step from mode 0 as the average).
+ *   Units: G = M_* = 1 (Sec. 5.1).
+ *
+ * Ownership.  The library owns all device memory of a handle (allocated by
+ * dg_init, or carved from a caller-provided workspace by dg_init_ex).  Host
+ * buffers passed in are owned by the caller and only read or written during
+ * the call.  A handle is not thread safe; distinct handles are independent.
+ *
+ * Asynchrony.  dg_step/dg_step_dt only enqueue work on the handle's stream and
+ * return; errors found on the device (non-finite or non-positive state or time
+ * step) are reported by the next synchronising call (dg_torque,
+ * dg_torque_series, dg_fetch, dg_get_time, dg_conserved, dg_rhs, dg_sync), and
+ * after such an error every later step is a no-op so that the state stays at
+ * the last good step.
+ *
+ * Errors.  Every call returns DG_OK (0) or a negative DG_ERR_* code; a
+ * description of the last error of a handle is returned by dg_last_error(h)
+ * (or of the last failed dg_init by dg_last_error(NULL)).
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_ERR_ARG (-1)         /* invalid argument (null pointer, bad size, bad enum) */
+#define DG_ERR_UNSUPPORTED (-2) /* order, EOS, RK scheme or precision not built */
+#define DG_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define DG_ERR_NUMERIC (-4)     /* non-finite or non-positive state or time step on the device */
+#define DG_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define DG_ERR_NOMEM (-6)       /* device allocation failed or workspace too small */
+
+typedef struct dg_handle dg_handle;
+
+/* Mesh of nx x ny rectangular elements on [x0,x1] x [y0,y1] (Sec. 2.2). */
+typedef struct {
+  int nx, ny;
+  double x0, x1, y0, y1;
+  int bc; /* 0 periodic; 1 ghost elements holding the projected background
+             state of the initial condition (fixed); 2 transmissive (exterior
+             trace = interior trace) */
+} dg_mesh;
+
+/* Equation of state (Sec. 2.1). */
+typedef struct {
+  int kind;     /* 0 locally isothermal, c_s = h v_K(r), 3 variables;
+                   1 adiabatic ideal gas p = (gamma - 1) e, 4 variables;
+                   2 isothermal with constant c_s = h, 3 variables */
+  double gamma; /* adiabatic index (kind 1) */
+  double h;     /* disc aspect ratio (kind 0) or sound speed (kind 2) */
+} dg_eos;
+
+/* Planet on a fixed circular orbit (Sec. 5.1) with Plummer-softened potential
+   Phi_p = -q / sqrt(d^2 + eps^2) (the smoothing of the torque equation, Sec. 5.2). */
+typedef struct {
+  double q;       /* planet / star mass ratio */
+  double r_p;     /* orbital radius */
+  double eps;     /* smoothing length (0.6 H in the planet-disc workloads) */
+  double omega_p; /* orbital frequency: position r_p (cos, sin)(omega_p t + phi0) */
+  double phi0;
+  int enabled;    /* 1: planet potential in the gravity source */
+} dg_planet;
+
+/* Initial condition, star potential, damping zones and numerics. */
+typedef struct {
+  int ic;             /* 0 rotational-equilibrium disc Sigma = max(r^slope, floor)
+                         (Sec. 5.1 equilibrium with c_s = h v_K); 1 density wave
+                         rho = 1 + amp sin(2 pi (x~ + y~)), v = (vx0, vy0), p = 1;
+                         2 uniform rho = 1, v = (vx0, vy0), p = 1 */
+  int star;           /* 1: softened point-mass star at the origin in the source;
+                         Phi_* = -1/r for r >= r_soft, solid-body core inside */
+  double r_soft;      /* star softening radius (> 0 for kind 0, star or ic 0) */
+  double sigma_slope; /* disc Sigma ~ r^slope */
+  double sigma_floor;
+  double noise_amp;   /* additive U(-a, a) noise on Sigma at the projection nodes
+                         (SplitMix64 keyed by seed, element and node) */
+  unsigned long long seed;
+  double rdamp_in;    /* inner damping radius r_d (Sec. 5.1), <= 0 disables */
+  double rdamp_out;   /* outer damping radius r_d, <= 0 disables */
+  double cfl;         /* Courant number C of Sec. 2.3 */
+  int rk;             /* 3: SSP(3,3) (Appendix A); 2: SSP(2,2) */
+  int prec;           /* 0: FP64 operator */
+  double amp, vx0, vy0;
+} dg_disc;
+
+/* Create a handle: validates the arguments, allocates device memory with
+   cudaMalloc on the current device, evaluates the initial condition on the
+   device and computes the first CFL step.  Synchronises before returning. */
+int dg_init(dg_handle **h, const dg_mesh *mesh, int order, const dg_eos *eos,
+            const dg_planet *planet, const dg_disc *disc);
+
+/* Bytes of device workspace that dg_init_ex needs for these arguments. */
+int dg_workspace_bytes(const dg_mesh *mesh, int order, const dg_eos *eos, const dg_disc *disc,
+                       size_t *bytes);
+
+/* As dg_init, but all device memory of the handle is carved out of the
+   caller's device buffer `workspace` (>= dg_workspace_bytes, 256-byte aligned,
+   owned by the caller and valid until dg_destroy), and work is issued on
+   `stream` (a cudaStream_t, NULL for the legacy default stream). */
+int dg_init_ex(dg_handle **h, const dg_mesh *mesh, int order, const dg_eos *eos,
+               const dg_planet *planet, const dg_disc *disc, void *workspace,
+               size_t workspace_bytes, void *stream);
+
+/* Advance n >= 0 full time steps, each with the CFL step of the current state
+   (Sec. 2.3), the RK stages with the planet at t^n + c_i dt, damping (Sec. 5.1)
+   and the torque on the new state at t^{n+1}.  Asynchronous. */
+int dg_step(dg_handle *h, int n);
+
+/* As dg_step with a fixed time step dt > 0 instead of the CFL step. */
+int dg_step_dt(dg_handle *h, int n, double dt);
+
+/* Wait for the handle's stream; returns the device status. */
+int dg_sync(dg_handle *h);
+
+/* Evaluate the operator L(u^n, t^n) of Eq. 2 (right-hand side divided by |K|)
+   into the caller's canonical host array.  Synchronises. */
+int dg_rhs(dg_handle *h, double *out);
+
+/* Specific torque Gamma_z (Sec. 5.2) of the last completed step; 0 before the
+   first step.  Synchronises. */
+int dg_torque(dg_handle *h, double *gamma_z);
+
+/* Per-step torque series since the previous call (at most cap values, oldest
+   first; the device keeps the last 65536).  *n receives the count.  Synchronises. */
+int dg_torque_series(dg_handle *h, double *out, int cap, int *n);
+
+/* Copy the current modes to the caller's canonical host array.  Synchronises. */
+int dg_fetch(dg_handle *h, double *coeffs);
+
+/* Replace the modes (canonical host array), the time and the step counter,
+   clear the device status and recompute the CFL step.  Synchronises. */
+int dg_set_state(dg_handle *h, const double *coeffs, double t, long step);
+
+/* Current time, the time step of the next step, and the step counter. */
+int dg_get_time(dg_handle *h, double *t, double *dt, long *step);
+
+/* FP64 sums over the elements of (element average x |K|) for each variable:
+   total mass, momentum (and energy).  out has nv doubles.  Synchronises. */
+int dg_conserved(dg_handle *h, double *out);
+
+/* Issue later work on `stream` (cudaStream_t; NULL = legacy default stream). */
+int dg_set_stream(dg_handle *h, void *stream);
+
+/* Number of variables (3 or 4) and of modes per variable (m*m) of a handle. */
+int dg_shape(dg_handle *h, int *nv, int *nmodes, int *nx, int *ny);
+
+/* Release the handle and the device memory it allocated. */
+int dg_destroy(dg_handle *h);
+
+/* Static description of the last error of h (or of the last failed dg_init for NULL). */
+const char *dg_last_error(dg_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

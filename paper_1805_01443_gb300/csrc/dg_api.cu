@@ -1,0 +1,583 @@
+// dg_api.cu -- host implementation of the C ABI declared in include/dg.h.
+//
+// A handle owns (or carves from the caller's workspace) three tiled state
+// buffers B0, B1, Z, a canonical staging buffer, the ghost strips, the device
+// time state, the per-CTA torque partials and the torque ring.  One SSP(3,3)
+// step with u^n in B[c] runs
+//   B[1-c] = u^n + dt L(u^n)                          (stage 1, c_1 = 0)
+//   Z      = 3/4 u^n + 1/4 (B[1-c] + dt L(B[1-c]))    (stage 2, c_2 = 1)
+//   B[1-c] = 1/3 u^n + 2/3 (Z + dt L(Z))              (stage 3, c_3 = 1/2)
+// followed by the finish kernel, and the roles of B0 and B1 swap.  The step
+// counter on the device decides which buffer holds the last good state.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "dg_internal.cuh"
+
+using namespace dg;
+
+struct dg_handle {
+  dg_mesh mesh;
+  dg_eos eos;
+  dg_planet planet;
+  dg_disc disc;
+  int p, m, M, nv;
+  Mesh dm;
+  Phys ph;
+  double* B[2];
+  double* Z;
+  double* S;
+  double *GL, *GR, *GB, *GT;
+  DevState* ts;
+  double* part;
+  double* series;
+  double* cpart;
+  double* csum;
+  void* ws;
+  bool owns;
+  cudaStream_t stream;
+  int cur, cur0;
+  long long step0;
+  long long series_read;
+  int nparts;
+  char err[256];
+};
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+int fail(dg_handle* h, int code, const char* fmt, ...) {
+  char* dst = h ? h->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 256, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CU(h, call)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(h, DG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Legendre P_n and P'_n at x (three-term recurrence; derivative from the
+// identity (x^2 - 1) P'_n = n (x P_n - P_{n-1}), with the endpoint limits).
+void leg(int n, double x, double* Pn, double* dPn, double* Pn1) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    *Pn = 1.0;
+    *dPn = 0.0;
+    *Pn1 = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; k++) {
+    double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  *Pn = p1;
+  *Pn1 = p0;
+  if (fabs(x) == 1.0)
+    *dPn = (x > 0 ? 1.0 : ((n % 2) ? 1.0 : -1.0)) * 0.5 * n * (n + 1);
+  else
+    *dPn = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+// Gauss-Legendre rule with m points on [-1, 1], ascending nodes.
+void gauss(int m, double* x, double* w) {
+  for (int k = 0; k < (m + 1) / 2; k++) {
+    double z = -cos(M_PI * (4.0 * k + 3.0) / (4.0 * m + 2.0));
+    for (int it = 0; it < 60; it++) {
+      double P, dP, P1;
+      leg(m, z, &P, &dP, &P1);
+      double dz = P / dP;
+      z -= dz;
+      if (fabs(dz) <= 1e-17) break;
+    }
+    double P, dP, P1;
+    leg(m, z, &P, &dP, &P1);
+    x[k] = z;
+    x[m - 1 - k] = -z;
+    w[k] = w[m - 1 - k] = 2.0 / ((1.0 - z * z) * dP * dP);
+  }
+  if (m % 2) x[m / 2] = 0.0;
+}
+
+double basis(int a, double x) {
+  double P, dP, P1;
+  leg(a, x, &P, &dP, &P1);
+  return sqrt(2.0 * a + 1.0) * P;
+}
+
+double dbasis(int a, double x) {
+  double P, dP, P1;
+  leg(a, x, &P, &dP, &P1);
+  return sqrt(2.0 * a + 1.0) * dP;
+}
+
+void make_tables(int p, Tables* t) {
+  memset(t, 0, sizeof(*t));
+  const int m = p + 1;
+  double x[MAXM], w[MAXM];
+  gauss(m, x, w);
+  for (int q = 0; q < m; q++) {
+    t->xi[q] = x[q];
+    t->wh[q] = 0.5 * w[q];
+    for (int a = 0; a < m; a++) {
+      t->phi[q][a] = basis(a, x[q]);
+      t->dphi[q][a] = dbasis(a, x[q]);
+    }
+  }
+  for (int a = 0; a < m; a++) {
+    t->pp[a] = sqrt(2.0 * a + 1.0);
+    t->pm[a] = (a % 2 ? -1.0 : 1.0) * sqrt(2.0 * a + 1.0);
+  }
+}
+
+bool g_tables_ready = false;
+int g_tables_dev = -1;
+
+cudaError_t upload_all_tables() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (g_tables_ready && g_tables_dev == dev) return cudaSuccess;
+  Tables t;
+  make_tables(1, &t);
+  if ((e = upload_tables_p1(t)) != cudaSuccess) return e;
+  make_tables(2, &t);
+  if ((e = upload_tables_p2(t)) != cudaSuccess) return e;
+  make_tables(3, &t);
+  if ((e = upload_tables_p3(t)) != cudaSuccess) return e;
+  make_tables(4, &t);
+  if ((e = upload_tables_p4(t)) != cudaSuccess) return e;
+  g_tables_ready = true;
+  g_tables_dev = dev;
+  return cudaSuccess;
+}
+
+cudaError_t launch_stage(const StageArgs& a, int p, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_stage_p1(a, s);
+    case 2: return launch_stage_p2(a, s);
+    case 3: return launch_stage_p3(a, s);
+    case 4: return launch_stage_p4(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t state, canon, gcol, grow, tsb, part, series, cpart, csum, total;
+};
+
+int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* disc) {
+  if (!mesh || !eos || !disc) return fail(nullptr, DG_ERR_ARG, "null argument");
+  if (mesh->nx < 1 || mesh->ny < 1 || mesh->nx > 65535 || mesh->ny > 65535)
+    return fail(nullptr, DG_ERR_ARG, "mesh size %d x %d outside 1..65535", mesh->nx, mesh->ny);
+  if ((long long)mesh->nx * mesh->ny > (1LL << 28))
+    return fail(nullptr, DG_ERR_ARG, "mesh has more than 2^28 elements");
+  if (!(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0) || !isfinite(mesh->x1 - mesh->x0) ||
+      !isfinite(mesh->y1 - mesh->y0))
+    return fail(nullptr, DG_ERR_ARG, "empty or non-finite box");
+  if (mesh->bc < 0 || mesh->bc > 2) return fail(nullptr, DG_ERR_ARG, "bc %d not in 0..2", mesh->bc);
+  if (order < 1 || order > MAXP) return fail(nullptr, DG_ERR_UNSUPPORTED, "order %d not in 1..4", order);
+  if (eos->kind < 0 || eos->kind > 2) return fail(nullptr, DG_ERR_UNSUPPORTED, "eos kind %d", eos->kind);
+  if (eos->kind == 1 && !(eos->gamma > 1.0)) return fail(nullptr, DG_ERR_ARG, "gamma must be > 1");
+  if ((eos->kind == 0 || disc->star || disc->ic == 0) && !(disc->r_soft > 0.0))
+    return fail(nullptr, DG_ERR_ARG, "r_soft must be > 0");
+  if (disc->ic < 0 || disc->ic > 2) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
+  if (disc->rk != 2 && disc->rk != 3) return fail(nullptr, DG_ERR_UNSUPPORTED, "rk %d", disc->rk);
+  if (disc->prec != 0) return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form %d", disc->prec);
+  if (!(disc->cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "cfl must be > 0");
+  return DG_OK;
+}
+
+Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos) {
+  Layout L;
+  const int m = order + 1, M = m * m, nv = eos->kind == 1 ? 4 : 3;
+  const size_t ntx = (mesh->nx + TILE - 1) / TILE;
+  const size_t nvm = (size_t)nv * M;
+  L.state = align256((size_t)mesh->ny * ntx * nvm * TILE * sizeof(double));
+  L.canon = align256((size_t)mesh->nx * mesh->ny * nvm * sizeof(double));
+  L.gcol = align256((size_t)mesh->ny * nvm * sizeof(double));
+  L.grow = align256(ntx * nvm * TILE * sizeof(double));
+  L.tsb = align256(sizeof(DevState));
+  L.part = align256(2 * ntx * (size_t)mesh->ny * sizeof(double));
+  L.series = align256((size_t)SERIES_CAP * sizeof(double));
+  L.cpart = align256(4 * (((size_t)mesh->nx * mesh->ny + 255) / 256) * sizeof(double));
+  L.csum = align256(4 * sizeof(double));
+  L.total = 3 * L.state + L.canon + 2 * L.gcol + 2 * L.grow + L.tsb + L.part + L.series + L.cpart + L.csum;
+  return L;
+}
+
+int read_state(dg_handle* h, DevState* out) {
+  CU(h, cudaMemcpyAsync(out, h->ts, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  // the device step counter decides which buffer holds the last good state
+  h->cur = h->cur0 ^ (int)((out->step - h->step0) & 1);
+  if (out->status != 0) return fail(h, out->status, "device status %d (non-finite or non-positive state or time step)", out->status);
+  return DG_OK;
+}
+
+int launch_cfl_and_dt(dg_handle* h) {
+  CU(h, launch_cfl(h->B[h->cur], h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
+  CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, h->ph.r_p, h->ph.omega_p,
+                      h->ph.phi0, h->stream));
+  return DG_OK;
+}
+
+int do_steps(dg_handle* h, int n, double fixed_dt) {
+  if (!h || n < 0) return fail(h, DG_ERR_ARG, "bad argument");
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  a.GL = h->GL;
+  a.GR = h->GR;
+  a.GB = h->GB;
+  a.GT = h->GT;
+  a.ts = h->ts;
+  a.part = h->part;
+  a.mesh = h->dm;
+  a.phys = h->ph;
+  a.fixed_dt = fixed_dt;
+  for (int s = 0; s < n; s++) {
+    double* un = h->B[h->cur];
+    double* nx = h->B[1 - h->cur];
+    a.Un = un;
+    if (h->disc.rk == 3) {
+      a.U = un; a.Out = nx; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
+      CU(h, launch_stage(a, h->p, h->stream));
+      a.U = nx; a.Out = h->Z; a.alpha = 0.75; a.beta = 0.25; a.cstage = 1.0; a.mode = 1;
+      CU(h, launch_stage(a, h->p, h->stream));
+      a.U = h->Z; a.Out = nx; a.alpha = 1.0 / 3.0; a.beta = 2.0 / 3.0; a.cstage = 0.5; a.mode = 2;
+      CU(h, launch_stage(a, h->p, h->stream));
+    } else {
+      a.U = un; a.Out = h->Z; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
+      CU(h, launch_stage(a, h->p, h->stream));
+      a.U = h->Z; a.Out = nx; a.alpha = 0.5; a.beta = 0.5; a.cstage = 1.0; a.mode = 2;
+      CU(h, launch_stage(a, h->p, h->stream));
+    }
+    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, h->ph.r_p,
+                        h->ph.omega_p, h->ph.phi0, h->stream));
+    h->cur = 1 - h->cur;
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_last_error(dg_handle* h) { return h ? h->err : g_err; }
+
+int dg_workspace_bytes(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* disc,
+                       size_t* bytes) {
+  int rc = validate(mesh, order, eos, disc);
+  if (rc) return rc;
+  if (!bytes) return fail(nullptr, DG_ERR_ARG, "null bytes");
+  *bytes = layout_of(mesh, order, eos).total;
+  return DG_OK;
+}
+
+int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eos,
+               const dg_planet* planet, const dg_disc* disc, void* workspace,
+               size_t workspace_bytes, void* stream) {
+  if (!out || !planet) return fail(nullptr, DG_ERR_ARG, "null argument");
+  *out = nullptr;
+  int rc = validate(mesh, order, eos, disc);
+  if (rc) return rc;
+  if (planet->enabled && !(planet->eps > 0.0)) return fail(nullptr, DG_ERR_ARG, "planet eps must be > 0");
+  const Layout L = layout_of(mesh, order, eos);
+  if (workspace && ((uintptr_t)workspace & 255))
+    return fail(nullptr, DG_ERR_ARG, "workspace must be 256-byte aligned");
+  if (workspace && workspace_bytes < L.total)
+    return fail(nullptr, DG_ERR_NOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, L.total);
+  dg_handle* h = new (std::nothrow) dg_handle;
+  if (!h) return fail(nullptr, DG_ERR_NOMEM, "host allocation failed");
+  memset(h, 0, sizeof(*h));
+  h->mesh = *mesh;
+  h->eos = *eos;
+  h->planet = *planet;
+  h->disc = *disc;
+  h->p = order;
+  h->m = order + 1;
+  h->M = h->m * h->m;
+  h->nv = eos->kind == 1 ? 4 : 3;
+  h->stream = (cudaStream_t)stream;
+  Mesh& dm = h->dm;
+  dm.nx = mesh->nx;
+  dm.ny = mesh->ny;
+  dm.ntx = (mesh->nx + TILE - 1) / TILE;
+  dm.bc = mesh->bc;
+  dm.x0 = mesh->x0;
+  dm.y0 = mesh->y0;
+  dm.x1 = mesh->x1;
+  dm.y1 = mesh->y1;
+  dm.dx = (mesh->x1 - mesh->x0) / mesh->nx;
+  dm.dy = (mesh->y1 - mesh->y0) / mesh->ny;
+  Phys& ph = h->ph;
+  ph.kind = eos->kind;
+  ph.gamma = eos->gamma;
+  ph.h = eos->h;
+  ph.star = disc->star;
+  ph.rs = disc->r_soft;
+  ph.planet = planet->enabled;
+  ph.q = planet->q;
+  ph.eps2 = planet->eps * planet->eps;
+  ph.r_p = planet->r_p;
+  ph.omega_p = planet->omega_p;
+  ph.phi0 = planet->phi0;
+  ph.rd_in = disc->rdamp_in;
+  ph.rd_out = disc->rdamp_out;
+  ph.damp_ratio = pow(1.15, 1.5);
+  ph.ic = disc->ic;
+  ph.slope = disc->sigma_slope;
+  ph.sig_floor = disc->sigma_floor;
+  ph.amp = disc->amp;
+  ph.vx0 = disc->vx0;
+  ph.vy0 = disc->vy0;
+  ph.cfl = disc->cfl;
+  h->nparts = dm.ntx * dm.ny;
+
+  char* base;
+  if (workspace) {
+    base = (char*)workspace;
+    h->owns = false;
+  } else {
+    cudaError_t e = cudaMalloc((void**)&base, L.total);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(nullptr, DG_ERR_NOMEM, "cudaMalloc of %zu bytes: %s", L.total, cudaGetErrorString(e));
+    }
+    h->owns = true;
+  }
+  h->ws = base;
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    char* p = base + off;
+    off += n;
+    return p;
+  };
+  h->B[0] = (double*)take(L.state);
+  h->B[1] = (double*)take(L.state);
+  h->Z = (double*)take(L.state);
+  h->S = (double*)take(L.canon);
+  h->GL = (double*)take(L.gcol);
+  h->GR = (double*)take(L.gcol);
+  h->GB = (double*)take(L.grow);
+  h->GT = (double*)take(L.grow);
+  h->ts = (DevState*)take(L.tsb);
+  h->part = (double*)take(L.part);
+  h->series = (double*)take(L.series);
+  h->cpart = (double*)take(L.cpart);
+  h->csum = (double*)take(L.csum);
+
+  auto bail = [&](int code) {
+    snprintf(g_err, sizeof(g_err), "%s", h->err);
+    if (h->owns) cudaFree(h->ws);
+    delete h;
+    return code;
+  };
+  cudaError_t e = upload_all_tables();
+  if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, L.total, h->stream);
+  if (e == cudaSuccess) e = launch_reset_state(h->ts, 0.0, 0, h->stream);
+  if (e != cudaSuccess) {
+    fail(h, DG_ERR_CUDA, "init: %s", cudaGetErrorString(e));
+    return bail(DG_ERR_CUDA);
+  }
+  // initial condition: nodes of the primitive variables -> conserved -> modes
+  InitArgs ia;
+  memset(&ia, 0, sizeof(ia));
+  ia.p = order;
+  ia.nv = h->nv;
+  ia.mesh = dm;
+  ia.phys = ph;
+  ia.seed = disc->seed;
+  ia.noise_amp = disc->noise_amp;
+  gauss(h->m + 1, ia.xq, ia.wq);
+  for (int q = 0; q <= h->m; q++)
+    for (int a = 0; a < h->m; a++) ia.phq[q][a] = basis(a, ia.xq[q]);
+  ia.out = h->B[0];
+  ia.target = 0;
+  e = launch_init(ia, mesh->nx * mesh->ny, h->stream);
+  if (e == cudaSuccess && mesh->bc == 1) {
+    ia.out = h->GL; ia.target = 1; e = launch_init(ia, mesh->ny, h->stream);
+    if (e == cudaSuccess) { ia.out = h->GR; ia.target = 2; e = launch_init(ia, mesh->ny, h->stream); }
+    if (e == cudaSuccess) { ia.out = h->GB; ia.target = 3; e = launch_init(ia, mesh->nx, h->stream); }
+    if (e == cudaSuccess) { ia.out = h->GT; ia.target = 4; e = launch_init(ia, mesh->nx, h->stream); }
+  }
+  if (e != cudaSuccess) {
+    fail(h, DG_ERR_CUDA, "init kernels: %s", cudaGetErrorString(e));
+    return bail(DG_ERR_CUDA);
+  }
+  h->cur = h->cur0 = 0;
+  h->step0 = 0;
+  rc = launch_cfl_and_dt(h);
+  DevState st;
+  if (rc == DG_OK) rc = read_state(h, &st);
+  if (rc != DG_OK) return bail(rc);
+  *out = h;
+  return DG_OK;
+}
+
+int dg_init(dg_handle** h, const dg_mesh* mesh, int order, const dg_eos* eos, const dg_planet* planet,
+            const dg_disc* disc) {
+  return dg_init_ex(h, mesh, order, eos, planet, disc, nullptr, 0, nullptr);
+}
+
+int dg_step(dg_handle* h, int n) { return do_steps(h, n, 0.0); }
+
+int dg_step_dt(dg_handle* h, int n, double dt) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(h, DG_ERR_ARG, "dt must be finite and > 0");
+  return do_steps(h, n, dt);
+}
+
+int dg_sync(dg_handle* h) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  DevState st;
+  return read_state(h, &st);
+}
+
+int dg_rhs(dg_handle* h, double* out) {
+  if (!h || !out) return fail(h, DG_ERR_ARG, "null argument");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc) return rc;
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  a.U = a.Un = h->B[h->cur];
+  a.Out = h->Z;
+  a.GL = h->GL;
+  a.GR = h->GR;
+  a.GB = h->GB;
+  a.GT = h->GT;
+  a.ts = h->ts;
+  a.part = h->part;
+  a.mesh = h->dm;
+  a.phys = h->ph;
+  a.mode = 0;
+  CU(h, launch_stage(a, h->p, h->stream));
+  CU(h, launch_to_canon(h->Z, h->S, h->dm, h->nv, h->M, h->stream));
+  const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
+  CU(h, cudaMemcpyAsync(out, h->S, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+int dg_torque(dg_handle* h, double* gz) {
+  if (!h || !gz) return fail(h, DG_ERR_ARG, "null argument");
+  DevState st;
+  int rc = read_state(h, &st);
+  *gz = st.torque;
+  return rc;
+}
+
+int dg_torque_series(dg_handle* h, double* out, int cap, int* n) {
+  if (!h || !n || cap < 0 || (cap > 0 && !out)) return fail(h, DG_ERR_ARG, "bad argument");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc && rc != DG_ERR_NUMERIC) return rc;
+  long long avail = st.series_count - h->series_read;
+  if (avail > SERIES_CAP) {
+    h->series_read = st.series_count - SERIES_CAP;
+    avail = SERIES_CAP;
+  }
+  int k = (int)(avail < cap ? avail : cap);
+  int done = 0;
+  while (done < k) {
+    long long idx = (h->series_read + done) % SERIES_CAP;
+    int chunk = (int)((SERIES_CAP - idx) < (k - done) ? (SERIES_CAP - idx) : (k - done));
+    CU(h, cudaMemcpyAsync(out + done, h->series + idx, chunk * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    done += chunk;
+  }
+  CU(h, cudaStreamSynchronize(h->stream));
+  h->series_read += k;
+  *n = k;
+  return rc;
+}
+
+int dg_fetch(dg_handle* h, double* coeffs) {
+  if (!h || !coeffs) return fail(h, DG_ERR_ARG, "null argument");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc && rc != DG_ERR_NUMERIC) return rc;
+  CU(h, launch_to_canon(h->B[h->cur], h->S, h->dm, h->nv, h->M, h->stream));
+  const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
+  CU(h, cudaMemcpyAsync(coeffs, h->S, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int dg_set_state(dg_handle* h, const double* coeffs, double t, long step) {
+  if (!h || !coeffs) return fail(h, DG_ERR_ARG, "null argument");
+  if (!isfinite(t)) return fail(h, DG_ERR_ARG, "t must be finite");
+  const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
+  CU(h, cudaStreamSynchronize(h->stream));
+  CU(h, cudaMemcpyAsync(h->S, coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CU(h, launch_to_tiled(h->S, h->B[0], h->dm, h->nv, h->M, h->stream));
+  CU(h, launch_reset_state(h->ts, t, step, h->stream));
+  h->cur = h->cur0 = 0;
+  h->step0 = step;
+  h->series_read = 0;
+  int rc = launch_cfl_and_dt(h);
+  if (rc) return rc;
+  DevState st;
+  return read_state(h, &st);
+}
+
+int dg_get_time(dg_handle* h, double* t, double* dt, long* step) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (t) *t = st.t;
+  if (dt) *dt = st.dt;
+  if (step) *step = (long)st.step;
+  return rc;
+}
+
+int dg_conserved(dg_handle* h, double* out) {
+  if (!h || !out) return fail(h, DG_ERR_ARG, "null argument");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc && rc != DG_ERR_NUMERIC) return rc;
+  CU(h, launch_conserved(h->B[h->cur], h->cpart, h->csum, h->dm, h->nv, h->M, h->stream));
+  CU(h, cudaMemcpyAsync(out, h->csum, h->nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int dg_set_stream(dg_handle* h, void* stream) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  CU(h, cudaStreamSynchronize(h->stream));
+  h->stream = (cudaStream_t)stream;
+  return DG_OK;
+}
+
+int dg_shape(dg_handle* h, int* nv, int* nmodes, int* nx, int* ny) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  if (nv) *nv = h->nv;
+  if (nmodes) *nmodes = h->M;
+  if (nx) *nx = h->mesh.nx;
+  if (ny) *ny = h->mesh.ny;
+  return DG_OK;
+}
+
+int dg_destroy(dg_handle* h) {
+  if (!h) return DG_OK;
+  cudaStreamSynchronize(h->stream);
+  if (h->owns) cudaFree(h->ws);
+  delete h;
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+// dg_aux.cu -- initial-condition projection, CFL reduction, per-step finish,
+// layout transforms and conserved sums.
+#include <math.h>
+
+#include "dg_internal.cuh"
+
+namespace dg {
+
+namespace {
+
+constexpr unsigned long long INF_BITS = 0x7ff0000000000000ULL;
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator:
+// value(c) = mix(seed + (c + 1) * 0x9E3779B97F4A7C15), top 53 bits -> [0, 1).
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long c) {
+  unsigned long long z = seed + (c + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+__device__ double vk2_of(const Phys& ph, double r) {
+  return (r >= ph.rs) ? 1.0 / r : r * r / (ph.rs * ph.rs * ph.rs);
+}
+
+// primitive (rho, vx, vy, p) of the initial condition (no noise)
+__device__ void ic_prim(const Phys& ph, const Mesh& ms, double x, double y, double* w) {
+  if (ph.ic == 0) {
+    // rotational equilibrium of Sec. 5.1 for Sigma ~ r^slope and c_s = h v_K
+    double r = fmax(sqrt(x * x + y * y), 1e-12);
+    double h2 = ph.h * ph.h, rs3 = ph.rs * ph.rs * ph.rs;
+    double sig = fmax(pow(r, ph.slope), ph.sig_floor);
+    double vphi2 = (r >= ph.rs) ? (1.0 + (ph.slope - 1.0) * h2) / r
+                                : (1.0 + (ph.slope + 2.0) * h2) * r * r / rs3;
+    double vphi = sqrt(fmax(vphi2, 0.0));
+    w[0] = sig;
+    w[1] = -vphi * y / r;
+    w[2] = vphi * x / r;
+    w[3] = h2 * vk2_of(ph, r) * sig;
+  } else if (ph.ic == 1) {
+    double lx = ms.x1 - ms.x0, ly = ms.y1 - ms.y0;
+    w[0] = 1.0 + ph.amp * sin(6.283185307179586476925286766559 * ((x - ms.x0) / lx + (y - ms.y0) / ly));
+    w[1] = ph.vx0;
+    w[2] = ph.vy0;
+    w[3] = 1.0;
+  } else {
+    w[0] = 1.0;
+    w[1] = ph.vx0;
+    w[2] = ph.vy0;
+    w[3] = 1.0;
+  }
+}
+
+// L2 projection of the initial data onto the modes (Eq. 2, first line) with
+// the (m+1)-point Gauss-Legendre rule; one thread per element.
+__global__ void k_init(const InitArgs a, int count) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const Mesh& ms = a.mesh;
+  int i, j;
+  switch (a.target) {
+    case 0: i = e % ms.nx; j = e / ms.nx; break;
+    case 1: i = -1; j = e; break;
+    case 2: i = ms.nx; j = e; break;
+    case 3: i = e; j = -1; break;
+    default: i = e; j = ms.ny; break;
+  }
+  const int m = a.p + 1, mq = m + 1, M = m * m, nv = a.nv;
+  double c[4][MAXM * MAXM];
+  for (int v = 0; v < 4; v++)
+    for (int k = 0; k < M; k++) c[v][k] = 0.0;
+  const double xc = ms.x0 + (i + 0.5) * ms.dx, yc = ms.y0 + (j + 0.5) * ms.dy;
+  for (int q = 0; q < mq; q++)
+    for (int r = 0; r < mq; r++) {
+      const double x = xc + 0.5 * ms.dx * a.xq[q], y = yc + 0.5 * ms.dy * a.xq[r];
+      double w[4], u[4];
+      ic_prim(a.phys, ms, x, y, w);
+      if (a.target == 0 && a.phys.ic == 0 && a.noise_amp > 0.0) {
+        const unsigned long long ctr =
+            ((unsigned long long)j * ms.nx + i) * (unsigned long long)(mq * mq) + q * mq + r;
+        w[0] += a.noise_amp * (2.0 * splitmix_uniform(a.seed, ctr) - 1.0);
+      }
+      u[0] = w[0];
+      u[1] = w[0] * w[1];
+      u[2] = w[0] * w[2];
+      u[3] = w[3] / (a.phys.gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2]);
+      const double wt = 0.25 * a.wq[q] * a.wq[r];
+      for (int aa = 0; aa < m; aa++)
+        for (int b = 0; b < m; b++) {
+          const double f = wt * a.phq[q][aa] * a.phq[r][b];
+          for (int v = 0; v < nv; v++) c[v][aa * m + b] += f * u[v];
+        }
+    }
+  const size_t NVM = (size_t)nv * M;
+  for (int v = 0; v < nv; v++)
+    for (int k = 0; k < M; k++) {
+      const double val = c[v][k];
+      size_t o;
+      if (a.target == 0)
+        o = (((size_t)j * ms.ntx + (i >> 5)) * NVM + v * M + k) * TILE + (i & 31);
+      else if (a.target <= 2)
+        o = (size_t)j * NVM + v * M + k;
+      else
+        o = (((size_t)(i >> 5)) * NVM + v * M + k) * TILE + (i & 31);
+      a.out[o] = val;
+    }
+}
+
+// CFL time step of Sec. 2.3 from the element averages; block minimum folded
+// into the device slot with an atomic minimum on the (positive) bit pattern.
+__global__ void k_cfl(const double* U, DevState* ts, const Mesh ms, const Phys ph, int p, int nv) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int M = (p + 1) * (p + 1);
+  double dtk = __longlong_as_double((long long)INF_BITS);
+  int bad = 0;
+  if (e < ms.nx * ms.ny) {
+    const int i = e % ms.nx, j = e / ms.nx;
+    const size_t base = (((size_t)j * ms.ntx + (i >> 5)) * nv * M) * TILE + (i & 31);
+    const double rho = U[base], mx = U[base + (size_t)M * TILE], my = U[base + (size_t)2 * M * TILE];
+    const double vx = mx / rho, vy = my / rho;
+    double c;
+    if (ph.kind == 1) {
+      const double E = U[base + (size_t)3 * M * TILE];
+      const double pr = (ph.gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy));
+      c = sqrt(ph.gamma * pr / rho);
+    } else if (ph.kind == 2) {
+      c = ph.h;
+    } else {
+      const double xc = ms.x0 + (i + 0.5) * ms.dx, yc = ms.y0 + (j + 0.5) * ms.dy;
+      c = ph.h * sqrt(vk2_of(ph, sqrt(xc * xc + yc * yc)));
+    }
+    dtk = ph.cfl / (2.0 * p + 1.0) / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
+    bad = !(rho > 0.0) || !(dtk > 0.0) || !isfinite(dtk);
+    if (bad) dtk = __longlong_as_double((long long)INF_BITS);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dtk = fmin(dtk, __shfl_xor_sync(0xffffffffu, dtk, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(&ts->pending, 1);
+    atomicMin(&ts->dt_bits, (unsigned long long)__double_as_longlong(dtk));
+  }
+}
+
+// End of a step: fixed-order sum of the per-CTA torque partials, torque on the
+// planet at t^{n+1} (Sec. 5.2), time advance, and the next CFL step.  With
+// advance = 0 only the CFL slot is turned into ts->dt.
+__global__ void k_finish(DevState* ts, const double* part, int nparts, double* series,
+                         double fixed_dt, int advance, double r_p, double omega_p, double phi0) {
+  __shared__ double sx[256], sy[256];
+  const int tid = threadIdx.x;
+  if (ts->status != 0) return;
+  if (advance) {
+    double gx = 0.0, gy = 0.0;
+    for (int k = tid; k < nparts; k += 256) {
+      gx += part[2 * k];
+      gy += part[2 * k + 1];
+    }
+    sx[tid] = gx;
+    sy[tid] = gy;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s) {
+        sx[tid] += sx[tid + s];
+        sy[tid] += sy[tid + s];
+      }
+      __syncthreads();
+    }
+  }
+  if (tid != 0) return;
+  if (ts->pending) {
+    ts->status = DG_ERR_NUMERIC;
+    return;
+  }
+  if (advance) {
+    const double dt = fixed_dt > 0.0 ? fixed_dt : ts->dt;
+    const double tn1 = ts->t + dt;
+    double sn, cs;
+    sincos(omega_p * tn1 + phi0, &sn, &cs);
+    const double xp = r_p * cs, yp = r_p * sn;
+    const double gz = xp * sy[0] - yp * sx[0];
+    series[ts->series_count % SERIES_CAP] = gz;
+    ts->series_count += 1;
+    ts->torque = gz;
+    ts->t = tn1;
+    ts->step += 1;
+  }
+  const double dtn = __longlong_as_double((long long)ts->dt_bits);
+  if (!(dtn > 0.0) || !isfinite(dtn)) {
+    if (fixed_dt <= 0.0) ts->status = DG_ERR_NUMERIC;
+  } else {
+    ts->dt = dtn;
+  }
+  ts->dt_bits = INF_BITS;
+}
+
+__global__ void k_reset(DevState* ts, double t, long long step) {
+  ts->t = t;
+  ts->dt = 0.0;
+  ts->torque = 0.0;
+  ts->step = step;
+  ts->status = 0;
+  ts->pending = 0;
+  ts->dt_bits = INF_BITS;
+  ts->series_count = 0;
+}
+
+__global__ void k_to_tiled(const double* canon, double* tiled, const Mesh ms, int nv, int M) {
+  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ms.nx);
+    const size_t r1 = e / ms.nx;
+    const int j = (int)(r1 % ms.ny);
+    const size_t vk = r1 / ms.ny;
+    tiled[(((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31)] = canon[e];
+  }
+}
+
+__global__ void k_to_canon(const double* tiled, double* canon, const Mesh ms, int nv, int M) {
+  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ms.nx);
+    const size_t r1 = e / ms.nx;
+    const int j = (int)(r1 % ms.ny);
+    const size_t vk = r1 / ms.ny;
+    canon[e] = tiled[(((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31)];
+  }
+}
+
+// FP64 sums of element average x |K| per variable: per-block partials in a
+// fixed order, then one block sums the partials in a fixed order.
+__global__ void k_conserved_part(const double* U, double* part, const Mesh ms, int nv, int M) {
+  __shared__ double s[4][256];
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x * 256 + tid;
+  for (int v = 0; v < 4; v++) s[v][tid] = 0.0;
+  if (e < ms.nx * ms.ny) {
+    const int i = e % ms.nx, j = e / ms.nx;
+    const size_t base = (((size_t)j * ms.ntx + (i >> 5)) * nv * M) * TILE + (i & 31);
+    for (int v = 0; v < nv; v++) s[v][tid] = U[base + (size_t)v * M * TILE] * ms.dx * ms.dy;
+  }
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st)
+      for (int v = 0; v < 4; v++) s[v][tid] += s[v][tid + st];
+    __syncthreads();
+  }
+  if (tid == 0)
+    for (int v = 0; v < nv; v++) part[(size_t)blockIdx.x * 4 + v] = s[v][0];
+}
+
+__global__ void k_conserved_final(const double* part, int nblk, double* out, int nv) {
+  __shared__ double s[4][256];
+  const int tid = threadIdx.x;
+  for (int v = 0; v < 4; v++) {
+    double acc = 0.0;
+    for (int b = tid; b < nblk; b += 256) acc += part[(size_t)b * 4 + v];
+    s[v][tid] = acc;
+  }
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st)
+      for (int v = 0; v < 4; v++) s[v][tid] += s[v][tid + st];
+    __syncthreads();
+  }
+  if (tid == 0)
+    for (int v = 0; v < nv; v++) out[v] = s[v][0];
+}
+
+}  // namespace
+
+cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_init<<<(count + 127) / 128, 128, 0, s>>>(a, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
+                       int nv, cudaStream_t s) {
+  const int n = mesh.nx * mesh.ny;
+  k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, ts, mesh, phys, p, nv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
+                          double fixed_dt, int advance, double r_p, double omega_p, double phi0,
+                          cudaStream_t s) {
+  k_finish<<<1, 256, 0, s>>>(ts, part, nparts, series, fixed_dt, advance, r_p, omega_p, phi0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s) {
+  k_reset<<<1, 1, 0, s>>>(ts, t, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_tiled(const double* canon, double* tiled, const Mesh& mesh, int nv, int M,
+                            cudaStream_t s) {
+  k_to_tiled<<<1216, 256, 0, s>>>(canon, tiled, mesh, nv, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
+                            cudaStream_t s) {
+  k_to_canon<<<1216, 256, 0, s>>>(tiled, canon, mesh, nv, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,
+                             int M, cudaStream_t s) {
+  const int n = mesh.nx * mesh.ny, nblk = (n + 255) / 256;
+  k_conserved_part<<<nblk, 256, 0, s>>>(U, part, mesh, nv, M);
+  k_conserved_final<<<1, 256, 0, s>>>(part, nblk, out, nv);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

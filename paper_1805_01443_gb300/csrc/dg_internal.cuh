@@ -1,0 +1,123 @@
+// dg_internal.cuh -- declarations shared by the CUDA translation units of libdg.
+//
+// Device data layout ("element-blocked SoA"): elements are grouped in tiles of
+// 32 consecutive elements along x (one warp lane per element).  Tile (it, j)
+// holds element i = 32*it + lane of row j; inside a tile the layout is
+// [var][mode][lane], so the 32 lanes of a warp read one (var, mode) row of 32
+// elements as one coalesced 256-byte (FP64) transaction.  A state buffer is
+// [j][it][var][mode][32] doubles; lanes past nx in the last tile are padding.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int TILE = 32;
+constexpr int MAXP = 4;
+constexpr int MAXM = MAXP + 1;
+constexpr int SERIES_CAP = 65536;
+
+// Device-resident time state of one handle (no host round trip per step).
+struct DevState {
+  double t;                    // current time t^n
+  double dt;                   // CFL step of the current state (next step's dt)
+  double torque;               // Gamma_z of the last completed step
+  long long step;              // completed steps
+  int status;                  // 0 or a DG_ERR_* code; set => every kernel is a no-op
+  int pending;                 // error flagged by a stage kernel, promoted by finish
+  unsigned long long dt_bits;  // atomicMin slot for the next CFL step (bits of a double > 0)
+  long long series_count;      // torque values written to the ring so far
+};
+
+// Physical parameters shared by all kernels of a handle.
+struct Phys {
+  int kind;          // EOS kind (dg_eos.kind)
+  double gamma;
+  double h;          // aspect ratio or constant sound speed
+  int star;          // star potential on
+  double rs;         // star softening radius
+  int planet;        // planet potential on
+  double q, eps2;    // planet mass ratio, smoothing^2
+  double r_p, omega_p, phi0;
+  double rd_in, rd_out;   // damping radii (<= 0: off)
+  double damp_ratio;      // 1.15^(3/2)
+  int ic;
+  double slope, sig_floor, amp, vx0, vy0;
+  double cfl;
+};
+
+struct Mesh {
+  int nx, ny, ntx, bc;
+  double x0, y0, dx, dy, x1, y1;
+};
+
+// Arguments of one RK stage launch.
+struct StageArgs {
+  const double* U;    // u^(s): the state L is evaluated on (tiled)
+  const double* Un;   // u^n for the Shu-Osher combination (tiled)
+  double* Out;        // output (tiled)
+  const double* GL;   // ghosts (bc 1): left/right columns [j][var][mode]
+  const double* GR;
+  const double* GB;   // bottom/top rows, tiled [it][var][mode][32]
+  const double* GT;
+  DevState* ts;
+  double* part;       // per-CTA torque partials (gx, gy), last stage only
+  Mesh mesh;
+  Phys phys;
+  double alpha, beta; // Out = alpha u^n + beta (u^(s) + dt L(u^(s)))
+  double cstage;      // stage time t^n + cstage dt
+  double fixed_dt;    // > 0: use instead of ts->dt
+  int mode;           // 0: Out = L(U); 1: RK stage; 2: last RK stage (+ damping, torque, CFL)
+};
+
+// Constant tables of the m-point Gauss-Legendre rule for degree p.
+struct Tables {
+  double phi[MAXM][MAXM];   // [q][a] = sqrt(2a+1) P_a(xi_q)
+  double dphi[MAXM][MAXM];  // [q][a] = d/dxi of the above
+  double wh[MAXM];          // w_q / 2 (weights normalised to sum 1 on [-1,1])
+  double pp[MAXM];          // sqrt(2a+1) P_a(+1)
+  double pm[MAXM];          // sqrt(2a+1) P_a(-1)
+  double xi[MAXM];          // nodes
+};
+
+// per-order entry points (dg_stage_p{1..4}.cu)
+#define DG_DECLARE_ORDER(P)                                                        \
+  cudaError_t launch_stage_p##P(const StageArgs& a, cudaStream_t s);              \
+  cudaError_t upload_tables_p##P(const Tables& t);                                 \
+  size_t stage_smem_p##P(int kind);
+DG_DECLARE_ORDER(1)
+DG_DECLARE_ORDER(2)
+DG_DECLARE_ORDER(3)
+DG_DECLARE_ORDER(4)
+#undef DG_DECLARE_ORDER
+
+// auxiliary kernels (dg_aux.cu)
+struct InitArgs {
+  double* out;       // target buffer
+  int target;        // 0 interior (tiled), 1 left ghosts, 2 right, 3 bottom (tiled), 4 top (tiled)
+  int p, nv;
+  Mesh mesh;
+  Phys phys;
+  unsigned long long seed;
+  double noise_amp;
+  double xq[MAXM + 1], wq[MAXM + 1];   // (m+1)-point GL rule
+  double phq[MAXM + 1][MAXM];          // basis at those nodes
+};
+
+cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s);
+cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
+                       int nv, cudaStream_t s);
+cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
+                          double fixed_dt, int advance, double r_p, double omega_p, double phi0,
+                          cudaStream_t s);
+cudaError_t launch_to_tiled(const double* canon, double* tiled, const Mesh& mesh, int nv, int M,
+                            cudaStream_t s);
+cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
+                            cudaStream_t s);
+cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,
+                             int M, cudaStream_t s);
+cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s);
+
+}  // namespace dg

@@ -1,0 +1,288 @@
+"""ctypes binding of libdg (include/dg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of libdg.so.  The functions keep the C names (dg_init, dg_step, dg_torque,
+dg_fetch, ...); `Disc` bundles them around one handle.  Device memory comes
+from PyTorch's caching allocator (one workspace tensor handed to
+dg_init_ex) and work is issued on PyTorch's current CUDA stream, unless the
+caller asks otherwise.  There is no CPU fallback: without the built library or
+a CUDA device every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DG_OK = 0
+DG_ERR_ARG = -1
+DG_ERR_UNSUPPORTED = -2
+DG_ERR_CUDA = -3
+DG_ERR_NUMERIC = -4
+DG_ERR_TIMEOUT = -5
+DG_ERR_NOMEM = -6
+
+EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_dt", "dg_sync",
+            "dg_rhs", "dg_torque", "dg_torque_series", "dg_fetch", "dg_set_state", "dg_get_time",
+            "dg_conserved", "dg_set_stream", "dg_shape", "dg_destroy", "dg_last_error"]
+
+
+class DgMesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x0", ctypes.c_double),
+                ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("bc", ctypes.c_int)]
+
+
+class DgEos(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("gamma", ctypes.c_double), ("h", ctypes.c_double)]
+
+
+class DgPlanet(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double), ("r_p", ctypes.c_double), ("eps", ctypes.c_double),
+                ("omega_p", ctypes.c_double), ("phi0", ctypes.c_double), ("enabled", ctypes.c_int)]
+
+
+class DgDisc(ctypes.Structure):
+    _fields_ = [("ic", ctypes.c_int), ("star", ctypes.c_int), ("r_soft", ctypes.c_double),
+                ("sigma_slope", ctypes.c_double), ("sigma_floor", ctypes.c_double),
+                ("noise_amp", ctypes.c_double), ("seed", ctypes.c_ulonglong),
+                ("rdamp_in", ctypes.c_double), ("rdamp_out", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("rk", ctypes.c_int), ("prec", ctypes.c_int),
+                ("amp", ctypes.c_double), ("vx0", ctypes.c_double), ("vy0", ctypes.c_double)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib(build_if_missing=True):
+    """Load libdg.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libdg.so is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        P = ctypes.POINTER
+        L.dg_init.argtypes = [P(_VP), P(DgMesh), ctypes.c_int, P(DgEos), P(DgPlanet), P(DgDisc)]
+        L.dg_init_ex.argtypes = [P(_VP), P(DgMesh), ctypes.c_int, P(DgEos), P(DgPlanet), P(DgDisc),
+                                 _VP, ctypes.c_size_t, _VP]
+        L.dg_workspace_bytes.argtypes = [P(DgMesh), ctypes.c_int, P(DgEos), P(DgDisc),
+                                         P(ctypes.c_size_t)]
+        L.dg_step.argtypes = [_VP, ctypes.c_int]
+        L.dg_step_dt.argtypes = [_VP, ctypes.c_int, ctypes.c_double]
+        L.dg_sync.argtypes = [_VP]
+        L.dg_rhs.argtypes = [_VP, _DP]
+        L.dg_torque.argtypes = [_VP, _DP]
+        L.dg_torque_series.argtypes = [_VP, _DP, ctypes.c_int, P(ctypes.c_int)]
+        L.dg_fetch.argtypes = [_VP, _DP]
+        L.dg_set_state.argtypes = [_VP, _DP, ctypes.c_double, ctypes.c_long]
+        L.dg_get_time.argtypes = [_VP, _DP, _DP, P(ctypes.c_long)]
+        L.dg_conserved.argtypes = [_VP, _DP]
+        L.dg_set_stream.argtypes = [_VP, _VP]
+        L.dg_shape.argtypes = [_VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                               P(ctypes.c_int)]
+        L.dg_destroy.argtypes = [_VP]
+        L.dg_last_error.argtypes = [_VP]
+        L.dg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+class DgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc, h=None):
+    if rc != DG_OK:
+        raise DgError(rc, (lib().dg_last_error(h) or b"").decode())
+    return rc
+
+
+def _fill(cls, d):
+    s = cls()
+    for name, _ in cls._fields_:
+        if name in d:
+            setattr(s, name, d[name])
+    return s
+
+
+def _ptr(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def structs(cfg):
+    return (_fill(DgMesh, cfg["mesh"]), int(cfg["order"]), _fill(DgEos, cfg["eos"]),
+            _fill(DgPlanet, cfg["planet"]), _fill(DgDisc, cfg["disc"]))
+
+
+def dg_workspace_bytes(cfg):
+    mesh, order, eos, _, disc = structs(cfg)
+    n = ctypes.c_size_t()
+    _check(lib().dg_workspace_bytes(ctypes.byref(mesh), order, ctypes.byref(eos), ctypes.byref(disc),
+                                    ctypes.byref(n)))
+    return n.value
+
+
+class Disc:
+    """One DG problem on the GPU (a dg_handle)."""
+
+    def __init__(self, cfg, torch_memory=True, stream=None):
+        L = lib()
+        self.cfg = cfg
+        mesh, order, eos, planet, disc = structs(cfg)
+        self._structs = (mesh, eos, planet, disc)
+        self.order = order
+        self.nv = 4 if eos.kind == 1 else 3
+        self.m = order + 1
+        self.M = self.m * self.m
+        self.nx, self.ny = mesh.nx, mesh.ny
+        self.shape = (self.nv, self.M, self.ny, self.nx)
+        h = _VP()
+        self._ws = None
+        if torch_memory:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: libdg has no CPU path")
+            nbytes = dg_workspace_bytes(cfg)
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+            _check(L.dg_init_ex(ctypes.byref(h), ctypes.byref(mesh), order, ctypes.byref(eos),
+                                ctypes.byref(planet), ctypes.byref(disc),
+                                ctypes.c_void_p(self._ws.data_ptr()), nbytes,
+                                ctypes.c_void_p(stream or 0)))
+        else:
+            _check(L.dg_init(ctypes.byref(h), ctypes.byref(mesh), order, ctypes.byref(eos),
+                             ctypes.byref(planet), ctypes.byref(disc)))
+        self.h = h
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ---------------------------------------------------------------
+    def step(self, n=1):
+        _check(lib().dg_step(self.h, n), self.h)
+
+    def step_dt(self, n, dt):
+        _check(lib().dg_step_dt(self.h, n, dt), self.h)
+
+    def sync(self):
+        _check(lib().dg_sync(self.h), self.h)
+
+    def rhs(self):
+        out = np.empty(self.shape)
+        _check(lib().dg_rhs(self.h, _ptr(out)), self.h)
+        return out
+
+    def torque(self):
+        g = ctypes.c_double()
+        _check(lib().dg_torque(self.h, ctypes.byref(g)), self.h)
+        return g.value
+
+    def torque_series(self, cap=65536):
+        out = np.empty(cap)
+        n = ctypes.c_int()
+        _check(lib().dg_torque_series(self.h, _ptr(out), cap, ctypes.byref(n)), self.h)
+        return out[:n.value].copy()
+
+    def fetch(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        _check(lib().dg_fetch(self.h, _ptr(out)), self.h)
+        return out
+
+    def set_state(self, coeffs, t=0.0, step=0):
+        c = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(self.shape)
+        _check(lib().dg_set_state(self.h, _ptr(c), t, step), self.h)
+
+    def get_time(self):
+        t = ctypes.c_double()
+        dt = ctypes.c_double()
+        st = ctypes.c_long()
+        _check(lib().dg_get_time(self.h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(st)),
+               self.h)
+        return t.value, dt.value, st.value
+
+    def conserved(self):
+        out = np.empty(self.nv)
+        _check(lib().dg_conserved(self.h, _ptr(out)), self.h)
+        return out
+
+    def set_stream(self, stream):
+        _check(lib().dg_set_stream(self.h, ctypes.c_void_p(stream or 0)), self.h)
+
+
+# C-named entry points
+def dg_init(cfg, **kw):
+    return Disc(cfg, **kw)
+
+
+def dg_step(d, n=1):
+    d.step(n)
+
+
+def dg_step_dt(d, n, dt):
+    d.step_dt(n, dt)
+
+
+def dg_torque(d):
+    return d.torque()
+
+
+def dg_torque_series(d, cap=65536):
+    return d.torque_series(cap)
+
+
+def dg_fetch(d, out=None):
+    return d.fetch(out)
+
+
+def dg_set_state(d, coeffs, t=0.0, step=0):
+    d.set_state(coeffs, t, step)
+
+
+def dg_get_time(d):
+    return d.get_time()
+
+
+def dg_conserved(d):
+    return d.conserved()
+
+
+def dg_rhs(d):
+    return d.rhs()
+
+
+def dg_sync(d):
+    d.sync()
+
+
+def dg_destroy(d):
+    d.close()
