@@ -1,0 +1,281 @@
+"""Benchmark: DOF-updates/s per RK stage of the DG operator on the P4 512x512
+planet-disc workload (locally isothermal Keplerian disc, q = 3e-5, damping
+zones r < 0.4 and r > 2.1, SSP(3,3), torque on the planet every step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One timed step = one full RK step of the hot path (3 fused stage kernels +
+the finish kernel: damping, torque, CFL) on device-resident inputs.  The state
+buffers (157 MB each, 3 of them) are larger than the 129 MB L2, so no flush is
+needed between steps.  DOF = nx * ny * (p+1)^2 per stage (Sec. 3.1).
+For N > 1 (torchrun) every rank advances an independent replica (no data-path
+collective); value = DOF-updates of all ranks / max-over-ranks time.
+`--impl reference` times the FP64 CPU oracle (the reference arm of this
+project) on this host's cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s per RK stage, P4 512² disc: FP32-TC vs FP64 at stated error"
+UNIT = "DOF/s"
+WORKLOAD = "planet-disc P4 512x512 (q=3e-5, damping 0.4/2.1, SSP(3,3), torque every step)"
+# algorithmic work per element per RK stage, P4, 3 variables, FP64 (sum-factorised
+# contractions + pointwise flux, gravity and Riemann terms; u^n and u^(s) read,
+# u^(s+1) written on average over the 3 SSP(3,3) stages)
+FLOP_PER_ELEM_STAGE = 10.0e3
+BYTES_PER_ELEM_STAGE_FP64 = 1600.0
+# FP64 peak of GB300 derived from unit counts and clock: 2 FP64 FMA / clk / SM
+# x 152 SMs x 2 flop x 2.07 GHz = 1.26 TFLOP/s
+FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_sample(cfg, seconds=15.0):
+    """FP64 oracle on this host's cores over a bounded sample of the same
+    workload: whole steps of the full mesh until ~`seconds` of CPU work."""
+    import oracle
+
+    o = oracle.Oracle(cfg)
+    n_el = cfg["mesh"]["nx"] * cfg["mesh"]["ny"]
+    dof = n_el * (cfg["order"] + 1) ** 2
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    nsteps = max(1, min(50, int(seconds / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    el = time.perf_counter() - t0
+    return {"value": dof * 3 * nsteps / el, "unit": UNIT, "cores": oracle.nthreads(),
+            "kind": "oracle",
+            "sample": "%d SSP(3,3) steps (%d stages) of the full %dx%d P%d workload, FP64, "
+                      "OpenMP over elements" % (nsteps, 3 * nsteps, cfg["mesh"]["nx"],
+                                                cfg["mesh"]["ny"], cfg["order"])}
+
+
+def run_reference(args, cfg):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    o = oracle.Oracle(cfg)
+    n_el = cfg["mesh"]["nx"] * cfg["mesh"]["ny"]
+    dof = n_el * (cfg["order"] + 1) ** 2
+    o.step(max(args.warmup, 0))
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = dof * 3 * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.nthreads(), "kind": "oracle",
+                         "sample": "%d SSP(3,3) steps of the full workload per timed run"
+                                   % args.steps},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--n", type=int, default=512, help="mesh size (profiling cases only)")
+    args = ap.parse_args()
+
+    from paper_1805_01443_gb300 import inputs
+
+    world, rank, local = dist_env()
+    cfg = inputs.disc_planet_512(n=args.n, seed=3 + rank)
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+
+    from paper_1805_01443_gb300 import dg
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        pg = tdist
+    dg.lib()
+    n_el = cfg["mesh"]["nx"] * cfg["mesh"]["ny"]
+    dof = n_el * (cfg["order"] + 1) ** 2
+    stages_per_step = 3
+
+    disc = dg.Disc(cfg)
+    stream = torch.cuda.current_stream()
+    disc.step(args.warmup)
+    disc.sync()
+    disc.set_timing(True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        ev0.record(stream)
+        disc.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, nstage = disc.timing()
+    disc.set_timing(False)
+    disc.sync()
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * dof * stages_per_step * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # state from pinned host memory, advances one step and reads the torque back
+    host = torch.empty(disc.shape, dtype=torch.float64, pin_memory=True).numpy()
+    disc.fetch(host)
+    t_now, _, st = disc.get_time()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        disc.set_state(host, t=t_now, step=st)
+        disc.step(1)
+        disc.torque()
+    e2e_s = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * dof * stages_per_step / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": 8}
+
+    peaks = load_peaks()
+    stage_s = stage_ms / max(nstage, 1) / 1e3
+    flops = FLOP_PER_ELEM_STAGE * n_el
+    achieved_tflops = flops / stage_s / 1e12
+    hbm_gbs = BYTES_PER_ELEM_STAGE_FP64 * n_el / stage_s / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                "traffic": None, "kernel": "k_stage<4,0> (FP64 fused RK stage)",
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
+                "hbm_achieved_gbs": hbm_gbs,
+                "hbm_frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0),
+                "hbm_peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "stage_us": stage_s * 1e6}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "FP64 operator", "elements": n_el,
+                   "dof_per_stage": dof, "stages_per_step": stages_per_step,
+                   "l2": "inputs larger than L2 (3 state buffers of %.0f MB)"
+                         % (host.nbytes / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(cfg)
+    disc.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

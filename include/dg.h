@@ -171,6 +171,16 @@ int dg_set_stream(dg_handle *h, void *stream);
 /* Number of variables (3 or 4) and of modes per variable (m*m) of a handle. */
 int dg_shape(dg_handle *h, int *nv, int *nmodes, int *nx, int *ny);
 
+/* Kernel timing for benchmarks: while enabled, every RK-stage kernel launch of
+   the handle is bracketed by a pair of CUDA events recorded on the handle's
+   stream (no extra synchronisation).  Enabling or disabling synchronises and
+   discards earlier records. */
+int dg_set_timing(dg_handle *h, int enable);
+
+/* Sum of the recorded stage-kernel durations in milliseconds and the number of
+   recorded launches since the previous call; synchronises and clears the records. */
+int dg_timing(dg_handle *h, double *stage_ms, long long *nstage);
+
 /* Release the handle and the device memory it allocated. */
 int dg_destroy(dg_handle *h);
 

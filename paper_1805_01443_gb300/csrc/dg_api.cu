@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "dg_internal.cuh"
 
@@ -45,6 +46,9 @@ struct dg_handle {
   long long step0;
   long long series_read;
   int nparts;
+  int timing;                                   // bracket stage launches with events
+  std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
+  size_t ev_used;
   char err[256];
 };
 
@@ -163,7 +167,7 @@ cudaError_t upload_all_tables() {
   return cudaSuccess;
 }
 
-cudaError_t launch_stage(const StageArgs& a, int p, cudaStream_t s) {
+cudaError_t launch_stage_raw(const StageArgs& a, int p, cudaStream_t s) {
   switch (p) {
     case 1: return launch_stage_p1(a, s);
     case 2: return launch_stage_p2(a, s);
@@ -171,6 +175,24 @@ cudaError_t launch_stage(const StageArgs& a, int p, cudaStream_t s) {
     case 4: return launch_stage_p4(a, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// stage launch, bracketed by a pair of events when timing is on
+cudaError_t launch_stage_h(dg_handle* h, const StageArgs& a) {
+  if (!h->timing) return launch_stage_raw(a, h->p, h->stream);
+  if (!h->ev) h->ev = new std::vector<cudaEvent_t>();
+  std::vector<cudaEvent_t>& ev = *h->ev;
+  while (ev.size() < 2 * (h->ev_used + 1)) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+  }
+  cudaError_t r = cudaEventRecord(ev[2 * h->ev_used], h->stream);
+  if (r == cudaSuccess) r = launch_stage_raw(a, h->p, h->stream);
+  if (r == cudaSuccess) r = cudaEventRecord(ev[2 * h->ev_used + 1], h->stream);
+  h->ev_used++;
+  return r;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -254,16 +276,16 @@ int do_steps(dg_handle* h, int n, double fixed_dt) {
     a.Un = un;
     if (h->disc.rk == 3) {
       a.U = un; a.Out = nx; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
-      CU(h, launch_stage(a, h->p, h->stream));
+      CU(h, launch_stage_h(h, a));
       a.U = nx; a.Out = h->Z; a.alpha = 0.75; a.beta = 0.25; a.cstage = 1.0; a.mode = 1;
-      CU(h, launch_stage(a, h->p, h->stream));
+      CU(h, launch_stage_h(h, a));
       a.U = h->Z; a.Out = nx; a.alpha = 1.0 / 3.0; a.beta = 2.0 / 3.0; a.cstage = 0.5; a.mode = 2;
-      CU(h, launch_stage(a, h->p, h->stream));
+      CU(h, launch_stage_h(h, a));
     } else {
       a.U = un; a.Out = h->Z; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
-      CU(h, launch_stage(a, h->p, h->stream));
+      CU(h, launch_stage_h(h, a));
       a.U = h->Z; a.Out = nx; a.alpha = 0.5; a.beta = 0.5; a.cstage = 1.0; a.mode = 2;
-      CU(h, launch_stage(a, h->p, h->stream));
+      CU(h, launch_stage_h(h, a));
     }
     CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, h->ph.r_p,
                         h->ph.omega_p, h->ph.phi0, h->stream));
@@ -465,7 +487,7 @@ int dg_rhs(dg_handle* h, double* out) {
   a.mesh = h->dm;
   a.phys = h->ph;
   a.mode = 0;
-  CU(h, launch_stage(a, h->p, h->stream));
+  CU(h, launch_stage_h(h, a));
   CU(h, launch_to_canon(h->Z, h->S, h->dm, h->nv, h->M, h->stream));
   const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
   CU(h, cudaMemcpyAsync(out, h->S, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -572,9 +594,36 @@ int dg_shape(dg_handle* h, int* nv, int* nmodes, int* nx, int* ny) {
   return DG_OK;
 }
 
+int dg_set_timing(dg_handle* h, int enable) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  CU(h, cudaStreamSynchronize(h->stream));
+  h->timing = enable ? 1 : 0;
+  h->ev_used = 0;
+  return DG_OK;
+}
+
+int dg_timing(dg_handle* h, double* stage_ms, long long* nstage) {
+  if (!h || !stage_ms || !nstage) return fail(h, DG_ERR_ARG, "null argument");
+  CU(h, cudaStreamSynchronize(h->stream));
+  double tot = 0.0;
+  for (size_t k = 0; k < h->ev_used; k++) {
+    float ms = 0.0f;
+    CU(h, cudaEventElapsedTime(&ms, (*h->ev)[2 * k], (*h->ev)[2 * k + 1]));
+    tot += ms;
+  }
+  *stage_ms = tot;
+  *nstage = (long long)h->ev_used;
+  h->ev_used = 0;
+  return DG_OK;
+}
+
 int dg_destroy(dg_handle* h) {
   if (!h) return DG_OK;
   cudaStreamSynchronize(h->stream);
+  if (h->ev) {
+    for (cudaEvent_t e : *h->ev) cudaEventDestroy(e);
+    delete h->ev;
+  }
   if (h->owns) cudaFree(h->ws);
   delete h;
   return DG_OK;

@@ -25,7 +25,8 @@ DG_ERR_NOMEM = -6
 
 EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_dt", "dg_sync",
             "dg_rhs", "dg_torque", "dg_torque_series", "dg_fetch", "dg_set_state", "dg_get_time",
-            "dg_conserved", "dg_set_stream", "dg_shape", "dg_destroy", "dg_last_error"]
+            "dg_conserved", "dg_set_stream", "dg_shape", "dg_destroy", "dg_last_error",
+            "dg_set_timing", "dg_timing"]
 
 
 class DgMesh(ctypes.Structure):
@@ -90,6 +91,8 @@ def lib(build_if_missing=True):
         L.dg_shape.argtypes = [_VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                                P(ctypes.c_int)]
         L.dg_destroy.argtypes = [_VP]
+        L.dg_set_timing.argtypes = [_VP, ctypes.c_int]
+        L.dg_timing.argtypes = [_VP, _DP, P(ctypes.c_longlong)]
         L.dg_last_error.argtypes = [_VP]
         L.dg_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -235,6 +238,16 @@ class Disc:
         _check(lib().dg_conserved(self.h, _ptr(out)), self.h)
         return out
 
+    def set_timing(self, enable=True):
+        _check(lib().dg_set_timing(self.h, 1 if enable else 0), self.h)
+
+    def timing(self):
+        """(sum of stage-kernel milliseconds, number of stage launches) since the last call."""
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(lib().dg_timing(self.h, ctypes.byref(ms), ctypes.byref(n)), self.h)
+        return ms.value, n.value
+
     def set_stream(self, stream):
         _check(lib().dg_set_stream(self.h, ctypes.c_void_p(stream or 0)), self.h)
 
@@ -282,6 +295,14 @@ def dg_rhs(d):
 
 def dg_sync(d):
     d.sync()
+
+
+def dg_set_timing(d, enable=True):
+    d.set_timing(enable)
+
+
+def dg_timing(d):
+    return d.timing()
 
 
 def dg_destroy(d):
