@@ -181,6 +181,40 @@ int dg_set_timing(dg_handle *h, int enable);
    recorded launches since the previous call; synchronises and clears the records. */
 int dg_timing(dg_handle *h, double *stage_ms, long long *nstage);
 
+/* Largest input of dg_conserved_static, in elements (nx * ny). */
+#define DG_STATIC_MAX_ELEMENTS 1048576
+
+/* dg_conserved_static -- the totals of dg_conserved (per variable, the sum over
+   the elements of the element average times |K|, in FP64) for a canonical
+   coefficient array that the caller already holds in device memory, computed
+   without allocating any device memory.  The paper has no counterpart to this
+   call: it serves callers that cannot call cudaMalloc when they need the sums,
+   such as host codes that reserve all GPU memory for their own pool or arena
+   at start-up (a further allocation would fail or break their budget) and
+   time-critical loops that must not take the device-wide synchronisation that
+   cudaMalloc and cudaFree may cause.
+     coeffs  device pointer, FP64, layout [var][mode][ny][nx] (nv*nmodes*ny*nx
+             doubles), read only; mode 0 of each variable must be the element
+             average, as in every canonical array of this library
+     nv      variables (1..4), nmodes modes per variable, nx*ny elements of
+             size dx*dy
+     out     device pointer to nv doubles, written
+     stream  cudaStream_t the two kernels are launched on (NULL: legacy default)
+   Its scratch space is a fixed array of 4096 x 4 doubles (128 KiB) inside
+   libdg.so, held by every GPU that loads the library until the process exits;
+   it limits nx*ny to DG_STATIC_MAX_ELEMENTS, and larger inputs return
+   DG_ERR_ARG without launching anything.  The first call on a device, with that
+   device current, looks up the array's device address (cudaGetSymbolAddress);
+   make that first call before any stream capture.  All calls share the one
+   array and each call overwrites every slot it later reads, so nothing needs
+   clearing between calls, but calls whose kernels overlap on the GPU (on
+   different streams or from different host threads) race on it and return
+   wrong sums: serialise them.  Asynchronous: returns once the kernels are
+   enqueued.  Errors: DG_ERR_ARG for a null pointer or a bad size, DG_ERR_CUDA
+   if the address lookup or a launch fails. */
+int dg_conserved_static(const double *coeffs, int nv, int nmodes, int nx, int ny, double dx,
+                        double dy, double *out, void *stream);
+
 /* Release the handle and the device memory it allocated. */
 int dg_destroy(dg_handle *h);
 

@@ -26,7 +26,7 @@ DG_ERR_NOMEM = -6
 EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_dt", "dg_sync",
             "dg_rhs", "dg_torque", "dg_torque_series", "dg_fetch", "dg_set_state", "dg_get_time",
             "dg_conserved", "dg_set_stream", "dg_shape", "dg_destroy", "dg_last_error",
-            "dg_set_timing", "dg_timing"]
+            "dg_set_timing", "dg_timing", "dg_conserved_static"]
 
 
 class DgMesh(ctypes.Structure):
@@ -93,6 +93,8 @@ def lib(build_if_missing=True):
         L.dg_destroy.argtypes = [_VP]
         L.dg_set_timing.argtypes = [_VP, ctypes.c_int]
         L.dg_timing.argtypes = [_VP, _DP, P(ctypes.c_longlong)]
+        L.dg_conserved_static.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, _VP, _VP]
         L.dg_last_error.argtypes = [_VP]
         L.dg_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -303,6 +305,23 @@ def dg_set_timing(d, enable=True):
 
 def dg_timing(d):
     return d.timing()
+
+
+def dg_conserved_static(coeffs, dx, dy, out, stream=None):
+    """Allocation-free conserved sums of a canonical FP64 device tensor `coeffs`
+    of shape (nv, nmodes, ny, nx) into the FP64 device tensor `out` (nv values),
+    enqueued on `stream` (default: PyTorch's current stream).  Raises DgError
+    on a bad argument or a CUDA failure."""
+    import torch
+    nv, nmodes, ny, nx = coeffs.shape
+    assert coeffs.dtype == torch.float64 and coeffs.is_cuda and coeffs.is_contiguous()
+    assert out.dtype == torch.float64 and out.is_cuda and out.numel() >= nv
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib().dg_conserved_static(ctypes.c_void_p(coeffs.data_ptr()), nv, nmodes, nx, ny, dx, dy,
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
+    if rc != DG_OK:
+        raise DgError(rc, "dg_conserved_static")
 
 
 def dg_destroy(d):
