@@ -34,6 +34,12 @@ WORKLOAD = "planet-disc P4 512x512 (q=3e-5, damping 0.4/2.1, SSP(3,3), torque ev
 # u^(s+1) written on average over the 3 SSP(3,3) stages)
 FLOP_PER_ELEM_STAGE = 10.0e3
 BYTES_PER_ELEM_STAGE_FP64 = 1600.0
+# precision form (FP32 delta, 75 floats = 300 B per element and array): reads
+# delta^(s), delta^n (stages 2, 3) and R_b, writes delta^(s+1); the last stage
+# also reads the nodal background density (100 B), the background averages
+# (12 B) and, in damped elements (47 % at 512^2), the damping offsets (300 B):
+# (900 + 1200 + 1200 + 100 + 12 + 141) / 3 = 1184 B per element per stage
+BYTES_PER_ELEM_STAGE_PREC = 1184.0
 # FP64 peak of GB300 derived from unit counts and clock: 2 FP64 FMA / clk / SM
 # x 152 SMs x 2 flop x 2.07 GHz = 1.26 TFLOP/s
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
@@ -158,16 +164,74 @@ def run_reference(args, cfg):
     return 0
 
 
+def timed_run(dg, torch, cfg, steps, warmup, local, pg):
+    """Advance one handle `warmup` untimed steps, then time `steps` steps with CUDA
+    events on its stream (barrier + synchronize on both sides) and the stage
+    kernels with dg_set_timing; returns (handle, ms, mean stage seconds, clocks)."""
+    disc = dg.Disc(cfg)
+    stream = torch.cuda.current_stream()
+    disc.step(warmup)
+    disc.sync()
+    disc.set_timing(True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        ev0.record(stream)
+        disc.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, nstage = disc.timing()
+    disc.set_timing(False)
+    disc.sync()
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    return disc, ms, stage_ms / max(nstage, 1) / 1e3, clk.summary()
+
+
+def error_vs_fp64(dg, cfg, cfg32, nsteps):
+    """Precision form against the FP64 operator from the same initial state:
+    relative L2 of Sigma, of Sigma - Sigma_bg and of the torque series."""
+    bg = dict(cfg, disc=dict(cfg["disc"], noise_amp=0.0))
+    with dg.Disc(bg) as b:
+        sig_bg = b.fetch()[0]
+    with dg.Disc(cfg) as a, dg.Disc(cfg32) as p:
+        a.step(nsteps)
+        p.step(nsteps)
+        ua, up = a.fetch(), p.fetch()
+        ta, tp = a.torque_series(), p.torque_series()
+    rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
+    return {"steps": nsteps, "rel_l2_sigma": rel(up[0], ua[0]),
+            "rel_l2_sigma_minus_bg": rel(up[0] - sig_bg, ua[0] - sig_bg),
+            "rel_l2_momentum": max(rel(up[1], ua[1]), rel(up[2], ua[2])),
+            "rel_l2_torque_series": rel(tp, ta),
+            "bounds": {"sigma": 1e-5, "torque": 1e-4}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--form", default="prec", choices=["prec", "fp64"],
+                    help="prec: the precision form is the headline, FP64 alongside")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--err-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--n", type=int, default=512, help="mesh size (profiling cases only)")
     args = ap.parse_args()
+
+    import copy
 
     from paper_1805_01443_gb300 import inputs
 
@@ -190,33 +254,15 @@ def main():
     n_el = cfg["mesh"]["nx"] * cfg["mesh"]["ny"]
     dof = n_el * (cfg["order"] + 1) ** 2
     stages_per_step = 3
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    cfg32 = copy.deepcopy(cfg)
+    cfg32["disc"]["prec"] = 1
+    head_cfg = cfg32 if args.form == "prec" else cfg
 
-    disc = dg.Disc(cfg)
-    stream = torch.cuda.current_stream()
-    disc.step(args.warmup)
-    disc.sync()
-    disc.set_timing(True)
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        time.sleep(0.3)
-        ev0.record(stream)
-        disc.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    ms = ev0.elapsed_time(ev1)
-    stage_ms, nstage = disc.timing()
-    disc.set_timing(False)
-    disc.sync()
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    # headline form
+    disc, ms, stage_s, clocks = timed_run(dg, torch, head_cfg, args.steps, args.warmup, local, pg)
     value = world * dof * stages_per_step * args.steps / (ms / 1e3)
 
     # end to end through the C ABI with host buffers: every step uploads the
@@ -231,6 +277,7 @@ def main():
         disc.step(1)
         disc.torque()
     e2e_s = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
+    disc.close()
     if pg:
         t = torch.tensor([e2e_s], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -238,37 +285,56 @@ def main():
     e2e = {"value": world * dof * stages_per_step / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": 8}
 
-    peaks = load_peaks()
-    stage_s = stage_ms / max(nstage, 1) / 1e3
-    flops = FLOP_PER_ELEM_STAGE * n_el
-    achieved_tflops = flops / stage_s / 1e12
-    hbm_gbs = BYTES_PER_ELEM_STAGE_FP64 * n_el / stage_s / 1e9
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                "traffic": None, "kernel": "k_stage<4,0> (FP64 fused RK stage)",
+    def fp64_roofline(stage64):
+        tf = FLOP_PER_ELEM_STAGE * n_el / stage64 / 1e12
+        gbs = BYTES_PER_ELEM_STAGE_FP64 * n_el / stage64 / 1e9
+        return {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_stage<4,0> (FP64 fused RK stage)",
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz",
-                "hbm_achieved_gbs": hbm_gbs,
-                "hbm_frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0),
-                "hbm_peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "stage_us": stage_s * 1e6}
+                "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                "hbm_peak_source": hbm_src, "stage_us": stage64 * 1e6}
+
+    if args.form == "prec":
+        gbs = BYTES_PER_ELEM_STAGE_PREC * n_el / stage_s / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak, "traffic": None,
+                    "kernel": "k_stage32<4> (precision-form fused RK stage)",
+                    "peak_source": hbm_src, "stage_us": stage_s * 1e6,
+                    "algorithmic_bytes_per_element": BYTES_PER_ELEM_STAGE_PREC}
+        d64, ms64, stage64, clocks64 = timed_run(dg, torch, cfg, args.fp64_steps, 2, local, pg)
+        d64.close()
+        fp64 = {"value": world * dof * stages_per_step * args.fp64_steps / (ms64 / 1e3),
+                "unit": UNIT, "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps,
+                "dtype": "f64", "roofline": fp64_roofline(stage64), "clocks": clocks64}
+        err = error_vs_fp64(dg, cfg, cfg32, args.err_steps) if args.err_steps > 0 else None
+        dtype = "f32"
+        form = ("precision form: FP32 operator on the perturbation about the projected "
+                "equilibrium; FP64 background residual, torque reduction and sums")
+    else:
+        roofline = fp64_roofline(stage_s)
+        fp64, err, dtype, form = None, None, "f64", "FP64 operator"
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "FP64 operator", "elements": n_el,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": form, "elements": n_el,
                    "dof_per_stage": dof, "stages_per_step": stages_per_step,
-                   "l2": "inputs larger than L2 (3 state buffers of %.0f MB)"
-                         % (host.nbytes / 1e6),
+                   "l2": "inputs larger than L2 (state buffers of %.0f MB FP64 / %.0f MB FP32)"
+                         % (host.nbytes / 1e6, host.nbytes / 2e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
+    if fp64 is not None:
+        line["fp64"] = fp64
+    if err is not None:
+        line["error_vs_fp64"] = err
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(cfg)
-    disc.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

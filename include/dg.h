@@ -106,7 +106,11 @@ typedef struct {
   double rdamp_out;   /* outer damping radius r_d, <= 0 disables */
   double cfl;         /* Courant number C of Sec. 2.3 */
   int rk;             /* 3: SSP(3,3) (Appendix A); 2: SSP(2,2) */
-  int prec;           /* 0: FP64 operator */
+  int prec;           /* 0: FP64 operator.  1: precision form (locally isothermal
+                         disc only): FP32 operator on delta = u - u_b about the
+                         projected equilibrium u_b, with R_b = L(u_b) evaluated
+                         in FP64 once, FP64 torque reduction and sums; the
+                         state is exchanged as FP64 u = u_b + delta */
   double amp, vx0, vy0;
 } dg_disc;
 

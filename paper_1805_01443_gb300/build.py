@@ -73,5 +73,5 @@ def build(force=False, verbose=False, extra_flags=()):
 
 
 if __name__ == "__main__":
-    flags = [a for a in sys.argv[1:] if a.startswith("-X") or a.startswith("--")]
+    flags = [a for a in sys.argv[1:] if a.startswith(("-X", "-D", "--"))]
     print(build(force=True, verbose=True, extra_flags=[f for f in flags if f != "--force"]))

@@ -46,6 +46,20 @@ struct dg_handle {
   long long step0;
   long long series_read;
   int nparts;
+  // precision form (disc.prec == 1): FP32 delta = u - u_b about the FP64 background
+  int prec;
+  Prec32 pc;
+  double* BG;          // projected background u_b, FP64 tiled
+  float* D[2];         // delta state buffers (FP32 tiled)
+  float* DZ;
+  float* Rb;           // R_b = L(u_b) from the FP64 kernel, stored FP32
+  float* SigbN;
+  float* Db;
+  float* Bm0;
+  float* Bmodes;       // u_b modes in FP32 (exact-background tiles)
+  float* Disc;         // per-element projected-vs-analytic background discrepancy
+  int* TileFlag;
+  Tables tab;
   int timing;                                   // bracket stage launches with events
   std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
   size_t ev_used;
@@ -155,13 +169,13 @@ cudaError_t upload_all_tables() {
   if (g_tables_ready && g_tables_dev == dev) return cudaSuccess;
   Tables t;
   make_tables(1, &t);
-  if ((e = upload_tables_p1(t)) != cudaSuccess) return e;
+  if ((e = upload_tables_p1(t)) != cudaSuccess || (e = upload_tables32_p1(t)) != cudaSuccess) return e;
   make_tables(2, &t);
-  if ((e = upload_tables_p2(t)) != cudaSuccess) return e;
+  if ((e = upload_tables_p2(t)) != cudaSuccess || (e = upload_tables32_p2(t)) != cudaSuccess) return e;
   make_tables(3, &t);
-  if ((e = upload_tables_p3(t)) != cudaSuccess) return e;
+  if ((e = upload_tables_p3(t)) != cudaSuccess || (e = upload_tables32_p3(t)) != cudaSuccess) return e;
   make_tables(4, &t);
-  if ((e = upload_tables_p4(t)) != cudaSuccess) return e;
+  if ((e = upload_tables_p4(t)) != cudaSuccess || (e = upload_tables32_p4(t)) != cudaSuccess) return e;
   g_tables_ready = true;
   g_tables_dev = dev;
   return cudaSuccess;
@@ -175,6 +189,42 @@ cudaError_t launch_stage_raw(const StageArgs& a, int p, cudaStream_t s) {
     case 4: return launch_stage_p4(a, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stage32_raw(const StageArgs32& a, int p, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_stage32_p1(a, s);
+    case 2: return launch_stage32_p2(a, s);
+    case 3: return launch_stage32_p3(a, s);
+    case 4: return launch_stage32_p4(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t record_start(dg_handle* h) {
+  if (!h->ev) h->ev = new std::vector<cudaEvent_t>();
+  std::vector<cudaEvent_t>& ev = *h->ev;
+  while (ev.size() < 2 * (h->ev_used + 1)) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+  }
+  return cudaEventRecord(ev[2 * h->ev_used], h->stream);
+}
+
+cudaError_t record_end(dg_handle* h) {
+  cudaError_t r = cudaEventRecord((*h->ev)[2 * h->ev_used + 1], h->stream);
+  h->ev_used++;
+  return r;
+}
+
+cudaError_t launch_stage32_h(dg_handle* h, const StageArgs32& a) {
+  if (!h->timing) return launch_stage32_raw(a, h->p, h->stream);
+  cudaError_t r = record_start(h);
+  if (r == cudaSuccess) r = launch_stage32_raw(a, h->p, h->stream);
+  if (r == cudaSuccess) r = record_end(h);
+  return r;
 }
 
 // stage launch, bracketed by a pair of events when timing is on
@@ -198,7 +248,9 @@ cudaError_t launch_stage_h(dg_handle* h, const StageArgs& a) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t state, canon, gcol, grow, tsb, part, series, cpart, csum, total;
+  size_t state, canon, gcol, grow, tsb, part, series, cpart, csum;
+  size_t state32, nodes32, db32, bm032, disc32, flags;  // precision form only (0 otherwise)
+  size_t total;
 };
 
 int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* disc) {
@@ -218,12 +270,15 @@ int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* d
     return fail(nullptr, DG_ERR_ARG, "r_soft must be > 0");
   if (disc->ic < 0 || disc->ic > 2) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
   if (disc->rk != 2 && disc->rk != 3) return fail(nullptr, DG_ERR_UNSUPPORTED, "rk %d", disc->rk);
-  if (disc->prec != 0) return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form %d", disc->prec);
+  if (disc->prec != 0 && disc->prec != 1)
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form %d", disc->prec);
+  if (disc->prec == 1 && (eos->kind != 0 || disc->ic != 0))
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form 1 needs the locally isothermal disc (eos 0, ic 0)");
   if (!(disc->cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "cfl must be > 0");
   return DG_OK;
 }
 
-Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos) {
+Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec) {
   Layout L;
   const int m = order + 1, M = m * m, nv = eos->kind == 1 ? 4 : 3;
   const size_t ntx = (mesh->nx + TILE - 1) / TILE;
@@ -237,7 +292,17 @@ Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos) {
   L.series = align256((size_t)SERIES_CAP * sizeof(double));
   L.cpart = align256(4 * (((size_t)mesh->nx * mesh->ny + 255) / 256) * sizeof(double));
   L.csum = align256(4 * sizeof(double));
+  L.state32 = L.nodes32 = L.db32 = L.bm032 = L.disc32 = L.flags = 0;
+  if (prec == 1) {
+    L.state32 = align256((size_t)mesh->ny * ntx * nvm * TILE * sizeof(float));
+    L.nodes32 = align256((size_t)mesh->ny * ntx * M * TILE * sizeof(float));
+    L.db32 = align256((size_t)mesh->ny * ntx * 3 * M * TILE * sizeof(float));
+    L.bm032 = align256((size_t)mesh->ny * ntx * 3 * TILE * sizeof(float));
+    L.disc32 = align256((size_t)mesh->ny * ntx * TILE * sizeof(float));
+    L.flags = align256((size_t)mesh->ny * ntx * sizeof(int));
+  }
   L.total = 3 * L.state + L.canon + 2 * L.gcol + 2 * L.grow + L.tsb + L.part + L.series + L.cpart + L.csum;
+  if (prec == 1) L.total += L.state + 5 * L.state32 + L.nodes32 + L.db32 + L.bm032 + L.disc32 + L.flags;
   return L;
 }
 
@@ -250,15 +315,70 @@ int read_state(dg_handle* h, DevState* out) {
   return DG_OK;
 }
 
-int launch_cfl_and_dt(dg_handle* h) {
-  CU(h, launch_cfl(h->B[h->cur], h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
+// CFL step of a full FP64 tiled state into the device time state
+int launch_cfl_and_dt(dg_handle* h, const double* full) {
+  CU(h, launch_cfl(full, h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
   CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, h->ph.r_p, h->ph.omega_p,
                       h->ph.phi0, h->stream));
   return DG_OK;
 }
 
+size_t tiled_count(const dg_handle* h) { return (size_t)h->dm.ny * h->dm.ntx * h->nv * h->M * TILE; }
+
+// full FP64 tiled state of the current buffer: the state itself (FP64 form) or
+// u_b + delta written into Z (precision form)
+int full_state(dg_handle* h, const double** out) {
+  if (h->prec == 0) {
+    *out = h->B[h->cur];
+    return DG_OK;
+  }
+  CU(h, launch_full_from_delta(h->BG, h->D[h->cur], h->Z, tiled_count(h), h->stream));
+  *out = h->Z;
+  return DG_OK;
+}
+
+int do_steps32(dg_handle* h, int n, double fixed_dt) {
+  StageArgs32 a;
+  memset(&a, 0, sizeof(a));
+  a.Rb = h->Rb;
+  a.SigbN = h->SigbN;
+  a.Db = h->Db;
+  a.Bm0 = h->Bm0;
+  a.Bmodes = h->Bmodes;
+  a.TileFlag = h->TileFlag;
+  a.BG64 = h->BG;
+  a.ts = h->ts;
+  a.part = h->part;
+  a.mesh = h->dm;
+  a.pc = h->pc;
+  a.fixed_dt = fixed_dt;
+  for (int s = 0; s < n; s++) {
+    float* un = h->D[h->cur];
+    float* nx = h->D[1 - h->cur];
+    a.Dn = un;
+    if (h->disc.rk == 3) {
+      a.D = un; a.Out = nx; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
+      CU(h, launch_stage32_h(h, a));
+      a.D = nx; a.Out = h->DZ; a.alpha = 0.75; a.beta = 0.25; a.cstage = 1.0; a.mode = 1;
+      CU(h, launch_stage32_h(h, a));
+      a.D = h->DZ; a.Out = nx; a.alpha = 1.0 / 3.0; a.beta = 2.0 / 3.0; a.cstage = 0.5; a.mode = 2;
+      CU(h, launch_stage32_h(h, a));
+    } else {
+      a.D = un; a.Out = h->DZ; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
+      CU(h, launch_stage32_h(h, a));
+      a.D = h->DZ; a.Out = nx; a.alpha = 0.5; a.beta = 0.5; a.cstage = 1.0; a.mode = 2;
+      CU(h, launch_stage32_h(h, a));
+    }
+    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, h->ph.r_p,
+                        h->ph.omega_p, h->ph.phi0, h->stream));
+    h->cur = 1 - h->cur;
+  }
+  return DG_OK;
+}
+
 int do_steps(dg_handle* h, int n, double fixed_dt) {
   if (!h || n < 0) return fail(h, DG_ERR_ARG, "bad argument");
+  if (h->prec == 1) return do_steps32(h, n, fixed_dt);
   StageArgs a;
   memset(&a, 0, sizeof(a));
   a.GL = h->GL;
@@ -305,7 +425,7 @@ int dg_workspace_bytes(const dg_mesh* mesh, int order, const dg_eos* eos, const 
   int rc = validate(mesh, order, eos, disc);
   if (rc) return rc;
   if (!bytes) return fail(nullptr, DG_ERR_ARG, "null bytes");
-  *bytes = layout_of(mesh, order, eos).total;
+  *bytes = layout_of(mesh, order, eos, disc->prec).total;
   return DG_OK;
 }
 
@@ -317,7 +437,7 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   int rc = validate(mesh, order, eos, disc);
   if (rc) return rc;
   if (planet->enabled && !(planet->eps > 0.0)) return fail(nullptr, DG_ERR_ARG, "planet eps must be > 0");
-  const Layout L = layout_of(mesh, order, eos);
+  const Layout L = layout_of(mesh, order, eos, disc->prec);
   if (workspace && ((uintptr_t)workspace & 255))
     return fail(nullptr, DG_ERR_ARG, "workspace must be 256-byte aligned");
   if (workspace && workspace_bytes < L.total)
@@ -368,6 +488,47 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   ph.vy0 = disc->vy0;
   ph.cfl = disc->cfl;
   h->nparts = dm.ntx * dm.ny;
+  h->prec = disc->prec;
+  make_tables(order, &h->tab);
+  if (h->prec == 1) {
+    Prec32& pc = h->pc;
+    const double h2 = eos->h * eos->h, rs = disc->r_soft, s = disc->sigma_slope;
+    pc.rs = (float)rs;
+    pc.irs3 = (float)(1.0 / (rs * rs * rs));
+    pc.h2 = (float)h2;
+    pc.sqk_out = (float)sqrt(fmax(1.0 + (s - 1.0) * h2, 0.0));
+    pc.om_in = (float)sqrt(fmax(1.0 + (s + 2.0) * h2, 0.0) / (rs * rs * rs));
+    pc.slope = (float)s;
+    pc.sig_floor = (float)disc->sigma_floor;
+    pc.slope_half = (s == -0.5);
+    pc.star = disc->star;
+    pc.planet = planet->enabled;
+    pc.q = (float)planet->q;
+    pc.eps2 = (float)(planet->eps * planet->eps);
+    pc.r_p = planet->r_p;
+    pc.omega_p = planet->omega_p;
+    pc.phi0 = planet->phi0;
+    pc.rd_in = (float)disc->rdamp_in;
+    pc.rd_out = (float)disc->rdamp_out;
+    pc.damp_ratio = (float)pow(1.15, 1.5);
+    pc.cfl_fac = (float)(disc->cfl / (2.0 * order + 1.0));
+    pc.x0 = (float)dm.x0;
+    pc.y0 = (float)dm.y0;
+    pc.dx = (float)dm.dx;
+    pc.dy = (float)dm.dy;
+    pc.hdx = (float)(0.5 * dm.dx);
+    pc.hdy = (float)(0.5 * dm.dy);
+    pc.s2x = (float)(2.0 / dm.dx);
+    pc.s2y = (float)(2.0 / dm.dy);
+    pc.idx = (float)(1.0 / dm.dx);
+    pc.idy = (float)(1.0 / dm.dy);
+    pc.area = (float)(dm.dx * dm.dy);
+#ifndef DG_TORQUE_NEAR2
+#define DG_TORQUE_NEAR2 0.25f
+#endif
+    pc.near2 = DG_TORQUE_NEAR2;  // FP64 torque terms within sqrt(near2) of the planet
+    pc.eps2_d = planet->eps * planet->eps;
+  }
 
   char* base;
   if (workspace) {
@@ -401,6 +562,19 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   h->series = (double*)take(L.series);
   h->cpart = (double*)take(L.cpart);
   h->csum = (double*)take(L.csum);
+  if (h->prec == 1) {
+    h->BG = (double*)take(L.state);
+    h->D[0] = (float*)take(L.state32);
+    h->D[1] = (float*)take(L.state32);
+    h->DZ = (float*)take(L.state32);
+    h->Rb = (float*)take(L.state32);
+    h->SigbN = (float*)take(L.nodes32);
+    h->Db = (float*)take(L.db32);
+    h->Bm0 = (float*)take(L.bm032);
+    h->Bmodes = (float*)take(L.state32);
+    h->Disc = (float*)take(L.disc32);
+    h->TileFlag = (int*)take(L.flags);
+  }
 
   auto bail = [&](int code) {
     snprintf(g_err, sizeof(g_err), "%s", h->err);
@@ -440,9 +614,42 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     fail(h, DG_ERR_CUDA, "init kernels: %s", cudaGetErrorString(e));
     return bail(DG_ERR_CUDA);
   }
+  if (h->prec == 1) {
+    // background u_b (the initial condition without noise), its FP64 operator
+    // R_b = L(u_b) without the planet, the static node fields, and delta
+    ia.out = h->BG;
+    ia.target = 0;
+    ia.noise_amp = 0.0;
+    e = launch_init(ia, mesh->nx * mesh->ny, h->stream);
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.U = a.Un = h->BG;
+    a.Out = h->Z;
+    a.GL = h->GL;
+    a.GR = h->GR;
+    a.GB = h->GB;
+    a.GT = h->GT;
+    a.ts = h->ts;
+    a.part = h->part;
+    a.mesh = dm;
+    a.phys = ph;
+    a.phys.planet = 0;
+    a.mode = 0;
+    if (e == cudaSuccess) e = launch_stage_raw(a, h->p, h->stream);
+    if (e == cudaSuccess) e = launch_f64_to_f32(h->Z, h->Rb, tiled_count(h), h->stream);
+    if (e == cudaSuccess)
+      e = launch_bg_nodes(h->BG, h->SigbN, h->Db, h->Bm0, h->Disc, dm, ph, h->tab, order, h->stream);
+    if (e == cudaSuccess) e = launch_f64_to_f32(h->BG, h->Bmodes, tiled_count(h), h->stream);
+    if (e == cudaSuccess) e = launch_tile_flags(h->Disc, h->TileFlag, dm, 1e-6f, h->stream);
+    if (e == cudaSuccess) e = launch_delta_from_full(h->B[0], h->BG, h->D[0], tiled_count(h), h->stream);
+    if (e != cudaSuccess) {
+      fail(h, DG_ERR_CUDA, "precision-form setup: %s", cudaGetErrorString(e));
+      return bail(DG_ERR_CUDA);
+    }
+  }
   h->cur = h->cur0 = 0;
   h->step0 = 0;
-  rc = launch_cfl_and_dt(h);
+  rc = launch_cfl_and_dt(h, h->B[0]);
   DevState st;
   if (rc == DG_OK) rc = read_state(h, &st);
   if (rc != DG_OK) return bail(rc);
@@ -474,20 +681,42 @@ int dg_rhs(dg_handle* h, double* out) {
   DevState st;
   int rc = read_state(h, &st);
   if (rc) return rc;
-  StageArgs a;
-  memset(&a, 0, sizeof(a));
-  a.U = a.Un = h->B[h->cur];
-  a.Out = h->Z;
-  a.GL = h->GL;
-  a.GR = h->GR;
-  a.GB = h->GB;
-  a.GT = h->GT;
-  a.ts = h->ts;
-  a.part = h->part;
-  a.mesh = h->dm;
-  a.phys = h->ph;
-  a.mode = 0;
-  CU(h, launch_stage_h(h, a));
+  if (h->prec == 1) {
+    // R_b + [L(u_b + delta) - L(u_b)] from the FP32 kernel
+    StageArgs32 a;
+    memset(&a, 0, sizeof(a));
+    a.D = a.Dn = h->D[h->cur];
+    a.Out = h->DZ;
+    a.Rb = h->Rb;
+    a.SigbN = h->SigbN;
+    a.Db = h->Db;
+    a.Bm0 = h->Bm0;
+    a.Bmodes = h->Bmodes;
+    a.TileFlag = h->TileFlag;
+    a.BG64 = h->BG;
+    a.ts = h->ts;
+    a.part = h->part;
+    a.mesh = h->dm;
+    a.pc = h->pc;
+    a.mode = 0;
+    CU(h, launch_stage32_h(h, a));
+    CU(h, launch_f32_to_f64(h->DZ, h->Z, tiled_count(h), h->stream));
+  } else {
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.U = a.Un = h->B[h->cur];
+    a.Out = h->Z;
+    a.GL = h->GL;
+    a.GR = h->GR;
+    a.GB = h->GB;
+    a.GT = h->GT;
+    a.ts = h->ts;
+    a.part = h->part;
+    a.mesh = h->dm;
+    a.phys = h->ph;
+    a.mode = 0;
+    CU(h, launch_stage_h(h, a));
+  }
   CU(h, launch_to_canon(h->Z, h->S, h->dm, h->nv, h->M, h->stream));
   const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
   CU(h, cudaMemcpyAsync(out, h->S, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -533,7 +762,10 @@ int dg_fetch(dg_handle* h, double* coeffs) {
   DevState st;
   int rc = read_state(h, &st);
   if (rc && rc != DG_ERR_NUMERIC) return rc;
-  CU(h, launch_to_canon(h->B[h->cur], h->S, h->dm, h->nv, h->M, h->stream));
+  const double* full = nullptr;
+  int rc2 = full_state(h, &full);
+  if (rc2) return rc2;
+  CU(h, launch_to_canon(full, h->S, h->dm, h->nv, h->M, h->stream));
   const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
   CU(h, cudaMemcpyAsync(coeffs, h->S, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
@@ -546,12 +778,14 @@ int dg_set_state(dg_handle* h, const double* coeffs, double t, long step) {
   const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
   CU(h, cudaStreamSynchronize(h->stream));
   CU(h, cudaMemcpyAsync(h->S, coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  CU(h, launch_to_tiled(h->S, h->B[0], h->dm, h->nv, h->M, h->stream));
+  double* full = h->prec == 1 ? h->Z : h->B[0];
+  CU(h, launch_to_tiled(h->S, full, h->dm, h->nv, h->M, h->stream));
+  if (h->prec == 1) CU(h, launch_delta_from_full(full, h->BG, h->D[0], tiled_count(h), h->stream));
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
   h->cur = h->cur0 = 0;
   h->step0 = step;
   h->series_read = 0;
-  int rc = launch_cfl_and_dt(h);
+  int rc = launch_cfl_and_dt(h, full);
   if (rc) return rc;
   DevState st;
   return read_state(h, &st);
@@ -572,7 +806,10 @@ int dg_conserved(dg_handle* h, double* out) {
   DevState st;
   int rc = read_state(h, &st);
   if (rc && rc != DG_ERR_NUMERIC) return rc;
-  CU(h, launch_conserved(h->B[h->cur], h->cpart, h->csum, h->dm, h->nv, h->M, h->stream));
+  const double* full = nullptr;
+  int rc2 = full_state(h, &full);
+  if (rc2) return rc2;
+  CU(h, launch_conserved(full, h->cpart, h->csum, h->dm, h->nv, h->M, h->stream));
   CU(h, cudaMemcpyAsync(out, h->csum, h->nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   return rc;

@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "dg_internal.cuh"
+#include "dg_physics.cuh"
 
 namespace dg {
 
@@ -18,38 +19,6 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsi
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   z ^= z >> 31;
   return (double)(z >> 11) * 0x1.0p-53;
-}
-
-__device__ double vk2_of(const Phys& ph, double r) {
-  return (r >= ph.rs) ? 1.0 / r : r * r / (ph.rs * ph.rs * ph.rs);
-}
-
-// primitive (rho, vx, vy, p) of the initial condition (no noise)
-__device__ void ic_prim(const Phys& ph, const Mesh& ms, double x, double y, double* w) {
-  if (ph.ic == 0) {
-    // rotational equilibrium of Sec. 5.1 for Sigma ~ r^slope and c_s = h v_K
-    double r = fmax(sqrt(x * x + y * y), 1e-12);
-    double h2 = ph.h * ph.h, rs3 = ph.rs * ph.rs * ph.rs;
-    double sig = fmax(pow(r, ph.slope), ph.sig_floor);
-    double vphi2 = (r >= ph.rs) ? (1.0 + (ph.slope - 1.0) * h2) / r
-                                : (1.0 + (ph.slope + 2.0) * h2) * r * r / rs3;
-    double vphi = sqrt(fmax(vphi2, 0.0));
-    w[0] = sig;
-    w[1] = -vphi * y / r;
-    w[2] = vphi * x / r;
-    w[3] = h2 * vk2_of(ph, r) * sig;
-  } else if (ph.ic == 1) {
-    double lx = ms.x1 - ms.x0, ly = ms.y1 - ms.y0;
-    w[0] = 1.0 + ph.amp * sin(6.283185307179586476925286766559 * ((x - ms.x0) / lx + (y - ms.y0) / ly));
-    w[1] = ph.vx0;
-    w[2] = ph.vy0;
-    w[3] = 1.0;
-  } else {
-    w[0] = 1.0;
-    w[1] = ph.vx0;
-    w[2] = ph.vy0;
-    w[3] = 1.0;
-  }
 }
 
 // L2 projection of the initial data onto the modes (Eq. 2, first line) with

@@ -72,6 +72,45 @@ struct StageArgs {
   int mode;           // 0: Out = L(U); 1: RK stage; 2: last RK stage (+ damping, torque, CFL)
 };
 
+// Parameters of the precision form (FP32 operator on delta = u - u_b).
+struct Prec32 {
+  float rs, irs3, h2;      // star softening radius, 1/r_s^3, aspect ratio^2
+  float sqk_out, om_in;    // sqrt(1 + (s-1) h^2), sqrt((1 + (s+2) h^2) / r_s^3)
+  float slope, sig_floor;
+  int slope_half;          // slope == -1/2: Sigma_b = r^-1/2 by rsqrt
+  int star, planet;
+  float q, eps2;
+  double r_p, omega_p, phi0;
+  float rd_in, rd_out, damp_ratio;
+  float cfl_fac;           // C / (2p + 1)
+  // mesh geometry in FP32 (coefficients only; offsets from the planet are
+  // formed per CTA in FP64 and then rounded)
+  float x0, y0, dx, dy, hdx, hdy, s2x, s2y, idx, idy, area;
+  float near2;             // torque terms within sqrt(near2) of the planet use FP64
+  double eps2_d;           // planet smoothing^2 in FP64 (near-planet torque terms)
+};
+
+// Arguments of one precision-form stage launch (tiled FP32 arrays).
+struct StageArgs32 {
+  const float* D;      // delta^(s)
+  const float* Dn;     // delta^n
+  float* Out;
+  const float* Rb;     // R_b = L(u_b), evaluated in FP64, stored FP32 [tile][var][mode][32]
+  const float* SigbN;  // Sigma_b at the m x m nodes [tile][node][32] (torque)
+  const float* Db;     // Q0 - Q_b at the nodes for (Sigma, vx, vy) [tile][3][node][32] (damping)
+  const float* Bm0;    // element averages of u_b [tile][3][32] (CFL)
+  const float* Bmodes; // u_b modes in FP32 [tile][var][mode][32] (exact-background tiles)
+  const int* TileFlag; // 1: the tile uses the exact projected background
+  const double* BG64;  // u_b modes in FP64, tiled (torque near the planet)
+  DevState* ts;
+  double* part;
+  Mesh mesh;
+  Prec32 pc;
+  double cstage, fixed_dt;
+  float alpha, beta;
+  int mode;
+};
+
 // Constant tables of the m-point Gauss-Legendre rule for degree p.
 struct Tables {
   double phi[MAXM][MAXM];   // [q][a] = sqrt(2a+1) P_a(xi_q)
@@ -86,7 +125,9 @@ struct Tables {
 #define DG_DECLARE_ORDER(P)                                                        \
   cudaError_t launch_stage_p##P(const StageArgs& a, cudaStream_t s);              \
   cudaError_t upload_tables_p##P(const Tables& t);                                 \
-  size_t stage_smem_p##P(int kind);
+  size_t stage_smem_p##P(int kind);                                                \
+  cudaError_t launch_stage32_p##P(const StageArgs32& a, cudaStream_t s);          \
+  cudaError_t upload_tables32_p##P(const Tables& t);
 DG_DECLARE_ORDER(1)
 DG_DECLARE_ORDER(2)
 DG_DECLARE_ORDER(3)
@@ -119,5 +160,18 @@ cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,
                              int M, cudaStream_t s);
 cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s);
+
+// precision-form setup and conversions (dg_prec.cu)
+cudaError_t launch_delta_from_full(const double* full, const double* bg, float* d, size_t n,
+                                   cudaStream_t s);
+cudaError_t launch_full_from_delta(const double* bg, const float* d, double* full, size_t n,
+                                   cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double* x, float* y, size_t n, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* x, double* y, size_t n, cudaStream_t s);
+cudaError_t launch_bg_nodes(const double* bg, float* sigbn, float* db, float* bm0, float* disc,
+                            const Mesh& mesh, const Phys& phys, const Tables& tab, int p,
+                            cudaStream_t s);
+cudaError_t launch_tile_flags(const float* disc, int* flags, const Mesh& mesh, float threshold,
+                              cudaStream_t s);
 
 }  // namespace dg

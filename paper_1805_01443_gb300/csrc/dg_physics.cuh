@@ -1,0 +1,46 @@
+// dg_physics.cuh -- device definitions of the initial/background state shared
+// by the initial projection, the FP64 damping target and the precision-form
+// setup (one definition, so the three agree to the last bit).
+#pragma once
+#include "dg_internal.cuh"
+
+namespace dg {
+
+// r dPhi_*/dr of the softened star: 1/r outside r_s, r^2/r_s^3 in the
+// solid-body core (Sec. 5.1).
+__device__ __forceinline__ double vk2_of(const Phys& ph, double r) {
+  return (r >= ph.rs) ? 1.0 / r : r * r / (ph.rs * ph.rs * ph.rs);
+}
+
+// Primitive state (rho, vx, vy, p) of the initial condition without noise:
+// ic 0 the rotational-equilibrium disc Sigma = max(r^s, floor),
+// v_phi^2 = (1 + (s-1) h^2)/r outside r_s and (1 + (s+2) h^2) r^2/r_s^3
+// inside, p = h^2 v_K^2 Sigma; ic 1 the density wave; ic 2 a uniform state.
+__device__ __forceinline__ void ic_prim(const Phys& ph, const Mesh& ms, double x, double y,
+                                        double* w) {
+  if (ph.ic == 0) {
+    double r = fmax(sqrt(x * x + y * y), 1e-12);
+    double h2 = ph.h * ph.h, rs3 = ph.rs * ph.rs * ph.rs;
+    double sig = fmax(pow(r, ph.slope), ph.sig_floor);
+    double vphi2 = (r >= ph.rs) ? (1.0 + (ph.slope - 1.0) * h2) / r
+                                : (1.0 + (ph.slope + 2.0) * h2) * r * r / rs3;
+    double vphi = sqrt(fmax(vphi2, 0.0));
+    w[0] = sig;
+    w[1] = -vphi * y / r;
+    w[2] = vphi * x / r;
+    w[3] = h2 * vk2_of(ph, r) * sig;
+  } else if (ph.ic == 1) {
+    double lx = ms.x1 - ms.x0, ly = ms.y1 - ms.y0;
+    w[0] = 1.0 + ph.amp * sin(6.283185307179586476925286766559 * ((x - ms.x0) / lx + (y - ms.y0) / ly));
+    w[1] = ph.vx0;
+    w[2] = ph.vy0;
+    w[3] = 1.0;
+  } else {
+    w[0] = 1.0;
+    w[1] = ph.vx0;
+    w[2] = ph.vy0;
+    w[3] = 1.0;
+  }
+}
+
+}  // namespace dg

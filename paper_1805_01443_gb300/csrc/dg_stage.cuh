@@ -21,6 +21,7 @@
 //       partial on the new state (Sec. 5.2), per-CTA CFL minimum (Sec. 2.3)
 #pragma once
 #include "dg_internal.cuh"
+#include "dg_physics.cuh"
 
 #ifndef DG_P
 #error "define DG_P before including dg_stage.cuh"
@@ -135,38 +136,6 @@ __device__ __forceinline__ void grad_phi(const Phys& ph, double x, double y, dou
     double f = ph.q * id * id * id;
     gx = fma(f, ddx, gx);
     gy = fma(f, ddy, gy);
-  }
-}
-
-// Background primitive state (rho, vx, vy, p) of the initial condition at
-// (x, y) without noise: the damping target Q0 (Sec. 5.1).
-__device__ __forceinline__ void bg_prim(const Phys& ph, const Mesh& ms, double x, double y,
-                                        double* w) {
-  if (ph.ic == 0) {
-    double r = sqrt(x * x + y * y);
-    r = fmax(r, 1e-12);
-    double sig = fmax(pow(r, ph.slope), ph.sig_floor);
-    double h2 = ph.h * ph.h, rs3 = ph.rs * ph.rs * ph.rs;
-    double vphi2 = (r >= ph.rs) ? (1.0 + (ph.slope - 1.0) * h2) / r
-                                : (1.0 + (ph.slope + 2.0) * h2) * r * r / rs3;
-    double vphi = sqrt(fmax(vphi2, 0.0));
-    double vk2 = (r >= ph.rs) ? 1.0 / r : r * r / rs3;
-    w[0] = sig;
-    w[1] = -vphi * y / r;
-    w[2] = vphi * x / r;
-    w[3] = h2 * vk2 * sig;
-  } else if (ph.ic == 1) {
-    double lx = ms.x1 - ms.x0, ly = ms.y1 - ms.y0;
-    double phs = 6.283185307179586476925286766559 * ((x - ms.x0) / lx + (y - ms.y0) / ly);
-    w[0] = 1.0 + ph.amp * sin(phs);
-    w[1] = ph.vx0;
-    w[2] = ph.vy0;
-    w[3] = 1.0;
-  } else {
-    w[0] = 1.0;
-    w[1] = ph.vx0;
-    w[2] = ph.vy0;
-    w[3] = 1.0;
   }
 }
 
@@ -608,7 +577,7 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
           damped = 1;
           const double tau = 6.283185307179586476925286766559 * sqrt(rd * rd * rd) / R;
           double w0[4];
-          bg_prim(ph, ms, xq, y, w0);
+          ic_prim(ph, ms, xq, y, w0);
           const double rho = u[0][r];
           double Q[4] = {rho, u[1][r] / rho, u[2][r] / rho, 0.0};
           double Q0[4] = {w0[0], w0[1], w0[2], 0.0};

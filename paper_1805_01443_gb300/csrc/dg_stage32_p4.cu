@@ -1,0 +1,8 @@
+// dg_stage32_p4.cu -- precision-form stage kernel for polynomial degree p = 4.
+#define DG_P 4
+#include "dg_stage32.cuh"
+
+namespace dg {
+cudaError_t launch_stage32_p4(const StageArgs32& a, cudaStream_t s) { return launch_stage32_impl<4>(a, s); }
+cudaError_t upload_tables32_p4(const Tables& t) { return upload_tables32_impl<4>(t); }
+}  // namespace dg
