@@ -524,9 +524,9 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     pc.idy = (float)(1.0 / dm.dy);
     pc.area = (float)(dm.dx * dm.dy);
 #ifndef DG_TORQUE_NEAR2
-#define DG_TORQUE_NEAR2 0.25f
+#define DG_TORQUE_NEAR2 0.04f
 #endif
-    pc.near2 = DG_TORQUE_NEAR2;  // FP64 torque terms within sqrt(near2) of the planet
+    pc.near2 = DG_TORQUE_NEAR2;  // FP64 torque terms within 0.2 of the planet
     pc.eps2_d = planet->eps * planet->eps;
   }
 

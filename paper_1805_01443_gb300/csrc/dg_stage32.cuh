@@ -13,12 +13,17 @@
 // The background coefficients come from the analytic equilibrium at the point,
 // except in tiles flagged at set-up (the singular centre Sigma ~ r^-1/2 and the
 // solid-body-core edge), where the analytic and projected backgrounds differ
-// and the projected one is contracted from its FP32 modes.  Same CTA structure
-// as dg_stage.cuh (one 32-element tile, m warps).  The last stage adds damping
-// in delta form, the torque (FP64 terms within a radius of the planet, FP32
-// terms beyond, FP64 reduction) and the CFL minimum.  All mesh geometry is
-// passed as FP32 scalars; offsets from the planet are formed once per CTA in
-// FP64 and rounded, so the FP64 pipe is left to the near-planet torque.
+// and the projected one is contracted from its FP32 modes.
+//
+// Work decomposition: one CTA per 32-element tile of one mesh row, three warps;
+// thread (v, e) owns variable v of element e.  Its m*m modes, nodal values and
+// volume/lift accumulators stay in registers (sum-factorised contractions with
+// no shared-memory operand); shared memory only exchanges the nodal values,
+// face traces, pointwise fluxes and face fluxes between the three variable
+// threads of an element.  Pointwise and face work is dealt round-robin over
+// the three threads.  The last stage adds damping in delta form, the torque
+// (FP64 terms within a radius of the planet, compensated FP32 terms beyond,
+// FP64 weights and reduction) and the CFL minimum.
 #pragma once
 #include "dg_internal.cuh"
 
@@ -39,16 +44,22 @@ struct Bg32 {
   float sig, vx, vy, mx, my, c2;
 };
 
+// The background enters only as coefficients of perturbation terms, so the
+// hardware approximations (a few ulp) of reciprocal and square root serve; the
+// correctly rounded library forms run partly on this part's narrow FP64 unit.
+__device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrtf(x); }
+
 __device__ __forceinline__ Bg32 bg32_at(const Prec32& pc, float x, float y) {
   Bg32 b;
   const float r2 = fmaf(x, x, y * y);
   const float ir = rsqrtf(r2);
   const float r = r2 * ir;
-  float sig = pc.slope_half ? sqrtf(ir) : exp2f(pc.slope * __log2f(r));
+  const float sir = sqrt_fast(ir);  // r^-1/2
+  float sig = pc.slope_half ? sir : exp2f(pc.slope * __log2f(r));
   sig = fmaxf(sig, pc.sig_floor);
   float om, vk2;
   if (r >= pc.rs) {
-    om = pc.sqk_out * ir * sqrtf(ir);  // v_phi / r = sqrt((1 + (s-1) h^2) / r) / r
+    om = pc.sqk_out * ir * sir;        // v_phi / r = sqrt((1 + (s-1) h^2) / r) / r
     vk2 = ir;
   } else {
     om = pc.om_in;                     // solid-body core
@@ -67,7 +78,7 @@ __device__ __forceinline__ Bg32 bg32_at(const Prec32& pc, float x, float y) {
 __device__ __forceinline__ void dflux32(const Bg32& b, const float* d, float* fx, float* fy,
                                         float& vx, float& vy) {
   const float sg = b.sig + d[0];
-  const float is = __frcp_rn(sg);
+  const float is = __fdividef(1.0f, sg);
   const float dvx = (d[1] - b.vx * d[0]) * is;
   const float dvy = (d[2] - b.vy * d[0]) * is;
   vx = b.vx + dvx;
@@ -91,7 +102,7 @@ __device__ __forceinline__ void dllf32(const Bg32& bL, const Bg32& bR, const flo
   dflux32(bR, dR, fxR, fyR, vxR, vyR);
   const float* fL = DIR == 0 ? fxL : fyL;
   const float* fR = DIR == 0 ? fxR : fyR;
-  const float c = sqrtf(bL.c2);
+  const float c = sqrt_fast(bL.c2);
   const float al = fmaxf(fabsf(DIR == 0 ? vxL : vyL), fabsf(DIR == 0 ? vxR : vyR)) + c;
   const float alb = fmaxf(fabsf(DIR == 0 ? bL.vx : bL.vy), fabsf(DIR == 0 ? bR.vx : bR.vy)) + c;
   const float jb[3] = {bR.sig - bL.sig, bR.mx - bL.mx, bR.my - bL.my};
@@ -129,100 +140,175 @@ __device__ __noinline__ Bg32 bg32_poly(const float* bm, const float* fa, const f
   return r;
 }
 
-// FP64 torque terms of the m nodes (xi_q, eta_r) of one element near the
-// planet: node mass from the FP64 background modes plus the FP32 perturbation.
+// FP64 torque term of node (q, r) of one element near the planet: node mass
+// from the FP64 background modes plus the FP32 perturbation.
 template <int P>
-__device__ __noinline__ void torque_near64(const double* bg, const float* dsig, int q, double xcd,
+__device__ __noinline__ void torque_node64(const double* bg, float dsig, int q, int r, double xcd,
                                            double ycd, double xp, double yp, double hdx,
                                            double hdy, double area, double eps2, double& gx,
                                            double& gy) {
   constexpr int m = P + 1;
-  double t[m][m];  // t[a][r] = sum_b u_b,ab phi_b(eta_r)
+  double sb = 0.0;
+#pragma unroll
+  for (int aa = 0; aa < m; aa++) {
+    double t = 0.0;
+#pragma unroll
+    for (int b = 0; b < m; b++) t = fma(bg[(aa * m + b) * 32], c32_phi64[r][b], t);
+    sb = fma(c32_phi64[q][aa], t, sb);
+  }
+  const double mass = (sb + (double)dsig) * c32_wh64[q] * c32_wh64[r] * area;
+  const double ddx = xcd + hdx * c32_xi64[q] - xp;
+  const double ddy = ycd + hdy * c32_xi64[r] - yp;
+  const double d2 = fma(ddx, ddx, fma(ddy, ddy, eps2));
+  const double id = rsqrt(d2);
+  const double f = mass * id * id * id;
+  gx = fma(f, ddx, gx);
+  gy = fma(f, ddy, gy);
+}
+
+// Shared-memory plan (floats) of the precision-form stage kernel.
+template <int P>
+struct Smem32 {
+  static constexpr int m = P + 1, M = m * m;
+  static constexpr int U = 0;                      // nodal values          [3][M][32]
+  static constexpr int F = U + 3 * M * 32;         // fx[3], fy[3] 2/dy, src[2] at nodes [8][M][32]
+  static constexpr int XT = F + 8 * M * 32;        // x traces [2][3][m][33]: 0 right (slot e+1), 1 left (slot e)
+  static constexpr int YT = XT + 2 * 3 * m * 33;   // own y traces [2][3][m][32]: 0 top, 1 bottom
+  static constexpr int YN = YT + 2 * 3 * m * 32;   // neighbour traces [2][3][m][32]: 0 below's top, 1 above's bottom
+  static constexpr int FX = YN + 2 * 3 * m * 32;   // x-face flux differences [3][m][33]
+  static constexpr int FY = FX + 3 * m * 33;       // y-face flux differences [2][3][m][32]: 0 bottom, 1 top
+  static constexpr int B0 = FY + 2 * 3 * m * 32;   // element averages of the new state [3][32]
+  static constexpr int FLAGS = B0 + 3 * 32;        // 32 ints
+  static constexpr int TOTAL = FLAGS + 32;
+  static constexpr int ND = 16 + 2 * M;            // doubles: planet, offsets, torque partials
+  static constexpr size_t BYTES = (size_t)ND * sizeof(double) + (size_t)TOTAL * sizeof(float);
+};
+
+// exact int -> float for 0 <= x < 2^23 on the integer and FP32 pipes (this
+// part executes conversion instructions on its narrow FP64 unit)
+__device__ __forceinline__ float i2f(int x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
+
+// modal -> nodal values of one variable of one element (registers), written to
+// u_out[n * 32] for node n = q*m + r; with xr/xl the x-face traces at the m
+// y-nodes are taken from the same first pass
+template <int P, bool TRACES>
+__device__ __forceinline__ void nodal32(const float* c, float* u_out, float* xr, float* xl) {
+  constexpr int m = P + 1;
+  float T[m][m];
 #pragma unroll
   for (int aa = 0; aa < m; aa++)
 #pragma unroll
     for (int r = 0; r < m; r++) {
-      double acc = 0.0;
+      float acc = 0.0f;
 #pragma unroll
-      for (int b = 0; b < m; b++) acc = fma(bg[(aa * m + b) * 32], c32_phi64[r][b], acc);
-      t[aa][r] = acc;
+      for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32_phi[r][b], acc);
+      T[aa][r] = acc;
     }
-  const double ddx = xcd + hdx * c32_xi64[q] - xp;
 #pragma unroll
-  for (int r = 0; r < m; r++) {
-    double sb = 0.0;
+  for (int q = 0; q < m; q++)
 #pragma unroll
-    for (int aa = 0; aa < m; aa++) sb = fma(c32_phi64[q][aa], t[aa][r], sb);
-    const double mass = (sb + (double)dsig[r]) * c32_wh64[q] * c32_wh64[r] * area;
-    const double ddy = ycd + hdy * c32_xi64[r] - yp;
-    const double d2 = fma(ddx, ddx, fma(ddy, ddy, eps2));
-    const double id = rsqrt(d2);
-    const double f = mass * id * id * id;
-    gx = fma(f, ddx, gx);
-    gy = fma(f, ddy, gy);
+    for (int r = 0; r < m; r++) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], T[aa][r], acc);
+      u_out[(q * m + r) * 32] = acc;
+    }
+  if (TRACES) {
+#pragma unroll
+    for (int r = 0; r < m; r++) {
+      float sr = 0.0f, sl = 0.0f;
+#pragma unroll
+      for (int aa = 0; aa < m; aa++) {
+        sr = fmaf(c32_pp[aa], T[aa][r], sr);
+        sl = fmaf(c32_pm[aa], T[aa][r], sl);
+      }
+      xr[r] = sr;
+      xl[r] = sl;
+    }
   }
 }
 
+// y-face trace polynomial of one variable: R[a] = sum_b c_ab f[b], then its
+// values at the m x-nodes, written to out[q * 32]
 template <int P>
-struct Smem32 {
-  static constexpr int m = P + 1, M = m * m, NV = 3;
-  static constexpr int C = 0;                      // delta^(s) of the tile [NV][M][32]
-  static constexpr int T = C + NV * M * 32;        // T_a(r) / A_b(q)   [NV][m][m][32]
-  static constexpr int B = T + NV * m * m * 32;    // B_b(q)            [NV][m][m][32]
-  static constexpr int R = B + NV * m * m * 32;    // R+-, neighbours [4][NV][m][32]; x fluxes [NV][m][33]
-  static constexpr int XR = R + 4 * NV * m * 32;   // right x traces [NV][m][33]; then HL
-  static constexpr int XL = XR + NV * m * 33;      // left x traces  [NV][m][33]; then HR
-  static constexpr int FYB = XL + NV * m * 33;
-  static constexpr int FYT = FYB + NV * m * 32;
-  static constexpr int H = FYT + NV * m * 32;      // x-halo coefficients [2][NV*M]
-  static constexpr int FLAGS = H + 2 * NV * M;     // 32 ints
-  static constexpr int TOTAL = FLAGS + 32;         // floats
-  static constexpr int ND = 16 + 2 * m * 32;       // doubles: planet data, torque partials
-  static constexpr size_t BYTES = (size_t)TOTAL * sizeof(float) + ND * sizeof(double);
-};
+__device__ __forceinline__ void ytrace32(const float* c, const float* f, float* out) {
+  constexpr int m = P + 1;
+  float R[m];
+#pragma unroll
+  for (int aa = 0; aa < m; aa++) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], f[b], acc);
+    R[aa] = acc;
+  }
+#pragma unroll
+  for (int q = 0; q < m; q++) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], R[aa], acc);
+    out[q * 32] = acc;
+  }
+}
+
+// x-face trace of one variable at the m y-nodes: sum_a f[a] sum_b c_ab phi_b(eta_r)
+template <int P>
+__device__ __forceinline__ void xtrace32(const float* c, const float* f, float* out) {
+  constexpr int m = P + 1;
+#pragma unroll
+  for (int r = 0; r < m; r++) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int aa = 0; aa < m; aa++) {
+      float t = 0.0f;
+#pragma unroll
+      for (int b = 0; b < m; b++) t = fmaf(c[aa * m + b], c32_phi[r][b], t);
+      acc = fmaf(f[aa], t, acc);
+    }
+    out[r * 33] = acc;
+  }
+}
 
 // minimum resident CTAs per SM asked of the register allocator
 #ifndef DG_STAGE32_MIN_CTAS
-#define DG_STAGE32_MIN_CTAS 3
+#define DG_STAGE32_MIN_CTAS 4
 #endif
 
-template <int P>
-__global__ void __launch_bounds__(32 * (P + 1), DG_STAGE32_MIN_CTAS) k_stage32(const StageArgs32 a) {
-  constexpr int m = P + 1, M = m * m, NV = 3, NT = 32 * m;
+// LAST = false: modes 0 (operator only) and 1 (RK stage); LAST = true: mode 2
+// (last RK stage with damping, torque and CFL), compiled apart so that the
+// first two stages do not carry the epilogue's code
+template <int P, bool LAST>
+__global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const StageArgs32 a) {
+  constexpr int m = P + 1, M = m * m, NV = 3;
   constexpr int NVM = NV * M;
   using S = Smem32<P>;
   extern __shared__ double smd[];
-  double* sD = smd;                       // [0..3] planet (stage, end); [16..] torque partials
-  float* sF = reinterpret_cast<float*>(smd + 4);  // [0..3] tile offsets from the planets
+  double* sD = smd;                                 // [0,1] planet at t^{n+1}; [8..13] torque
+  float* sF = reinterpret_cast<float*>(smd + 2);    // tile offsets from the planets (hi, lo)
   float* sm = reinterpret_cast<float*>(smd + S::ND);
-  float* sC = sm + S::C;
-  float* sT = sm + S::T;
-  float* sB = sm + S::B;
-  float* sR = sm + S::R;
-  float* sFX = sm + S::R;
-  float* sXR = sm + S::XR;
-  float* sXL = sm + S::XL;
-  float* sHL = sm + S::XR;
-  float* sHR = sm + S::XL;
-  float* sFYB = sm + S::FYB;
-  float* sFYT = sm + S::FYT;
-  float* sH = sm + S::H;
+  float* sU = sm + S::U;
+  float* sFl = sm + S::F;
+  float* sXT = sm + S::XT;
+  float* sYT = sm + S::YT;
+  float* sYN = sm + S::YN;
+  float* sFX = sm + S::FX;
+  float* sFY = sm + S::FY;
+  float* sB0 = sm + S::B0;
   int* sFlag = reinterpret_cast<int*>(sm + S::FLAGS);
 
   const Mesh& ms = a.mesh;
   const Prec32& pc = a.pc;
   if (a.ts->status != 0) return;
 
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, v = tid >> 5;
   const int bx = blockIdx.x, j = blockIdx.y;
   const int i0 = bx * 32;
   const int nvalid = min(32, ms.nx - i0);
   const bool valid = lane < nvalid;
   const int lc = valid ? lane : nvalid - 1;
   const double dtd = (a.fixed_dt > 0.0) ? a.fixed_dt : a.ts->dt;
-  const float dt = (float)dtd;
 
   if (tid == 0) {
+    sF[8] = (float)dtd;
     // planet at the stage time and at t^{n+1}; centre of the tile's first
     // element relative to each, formed in FP64 and kept as a pair of floats
     // (hi, lo): a single rounding here would shift every element of the tile
@@ -249,576 +335,484 @@ __global__ void __launch_bounds__(32 * (P + 1), DG_STAGE32_MIN_CTAS) k_stage32(c
   }
   if (tid < 32) sFlag[tid] = 0;
 
-  // ---- loads -----------------------------------------------------------------
+  // element pointers of this thread's variable (stride 32 between modes);
+  // bc 0 periodic wrap, bc 1 ghosts carry the background (delta = 0),
+  // bc 2 transmissive (exterior trace = interior trace)
   const size_t tile = (size_t)j * ms.ntx + bx;
-  const float* Ut = a.D + tile * NVM * 32;
-  for (int idx = tid; idx < NVM * 32; idx += NT) {
-    const int l = idx & 31;
-    sC[idx] = Ut[(l < nvalid) ? idx : idx - l + nvalid - 1];
-  }
-  // x neighbours: periodic wrap; bc 1 ghosts carry the background (delta = 0);
-  // bc 2 transmissive mirrors the interior trace
+  const size_t voff = (size_t)v * M * 32;
+  const float* own = a.D + tile * NVM * 32 + voff + lc;
+  const float* pB = nullptr;
+  const float* pT = nullptr;
+  bool zB = false, zT = false;
+  if (j > 0) pB = a.D + ((size_t)(j - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
+  else if (ms.bc == 0) pB = a.D + ((size_t)(ms.ny - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
+  else if (ms.bc == 1) zB = true;
+  if (j + 1 < ms.ny) pT = a.D + ((size_t)(j + 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
+  else if (ms.bc == 0) pT = a.D + (size_t)bx * NVM * 32 + voff + lc;
+  else if (ms.bc == 1) zT = true;
+  const bool trB = !pB && !zB, trT = !pT && !zT;
   const int il = i0 - 1, ir = i0 + nvalid;
   const float* pL = nullptr;
   const float* pR = nullptr;
   bool zL = false, zR = false;
-  if (il >= 0) pL = a.D + ((size_t)j * ms.ntx + (il >> 5)) * NVM * 32 + (il & 31);
-  else if (ms.bc == 0) { const int iw = ms.nx - 1; pL = a.D + ((size_t)j * ms.ntx + (iw >> 5)) * NVM * 32 + (iw & 31); }
+  if (il >= 0) pL = a.D + ((size_t)j * ms.ntx + (il >> 5)) * NVM * 32 + voff + (il & 31);
+  else if (ms.bc == 0) { const int iw = ms.nx - 1; pL = a.D + ((size_t)j * ms.ntx + (iw >> 5)) * NVM * 32 + voff + (iw & 31); }
   else if (ms.bc == 1) zL = true;
-  if (ir < ms.nx) pR = a.D + ((size_t)j * ms.ntx + (ir >> 5)) * NVM * 32 + (ir & 31);
-  else if (ms.bc == 0) pR = a.D + (size_t)j * ms.ntx * NVM * 32;
+  if (ir < ms.nx) pR = a.D + ((size_t)j * ms.ntx + (ir >> 5)) * NVM * 32 + voff + (ir & 31);
+  else if (ms.bc == 0) pR = a.D + (size_t)j * ms.ntx * NVM * 32 + voff;
   else if (ms.bc == 1) zR = true;
-  const bool trL = (pL == nullptr) && !zL, trR = (pR == nullptr) && !zR;
-  for (int idx = tid; idx < 2 * NVM; idx += NT) {
-    const int side = idx >= NVM;
-    const int vk = idx - side * NVM;
-    const float* p = side ? pR : pL;
-    sH[idx] = p ? p[(size_t)vk * 32] : 0.0f;
-  }
-  const float* pB = nullptr;
-  const float* pT = nullptr;
-  bool zB = false, zT = false;
-  if (j > 0) pB = a.D + ((size_t)(j - 1) * ms.ntx + bx) * NVM * 32;
-  else if (ms.bc == 0) pB = a.D + ((size_t)(ms.ny - 1) * ms.ntx + bx) * NVM * 32;
-  else if (ms.bc == 1) zB = true;
-  if (j + 1 < ms.ny) pT = a.D + ((size_t)(j + 1) * ms.ntx + bx) * NVM * 32;
-  else if (ms.bc == 0) pT = a.D + (size_t)bx * NVM * 32;
-  else if (ms.bc == 1) zT = true;
-  const bool trB = (pB == nullptr) && !zB, trT = (pT == nullptr) && !zT;
+  const bool trL = !pL && !zL, trR = !pR && !zR;
   // tiles near the singular centre use the exact projected background (FP32
-  // modes of u_b, same tiled layout as delta); all others the analytic one
+  // modes of u_b, same tiled layout as delta, all three variables)
   const int exact = a.TileFlag[tile];
-  const float* bOwn = exact ? a.Bmodes + tile * NVM * 32 + lc : nullptr;
-  const float* pLm = (exact && pL) ? a.Bmodes + (pL - a.D) : nullptr;
-  const float* pRm = (exact && pR) ? a.Bmodes + (pR - a.D) : nullptr;
-  const float* pBm = (exact && pB) ? a.Bmodes + (pB - a.D) : nullptr;
-  const float* pTm = (exact && pT) ? a.Bmodes + (pT - a.D) : nullptr;
+  const float* bgOwn = exact ? a.Bmodes + tile * NVM * 32 + lc : nullptr;
+  const float* bgB = (exact && pB) ? a.Bmodes + (pB - a.D) - voff : nullptr;
+  const float* bgT = (exact && pT) ? a.Bmodes + (pT - a.D) - voff : nullptr;
+  const float* bgL = (exact && pL) ? a.Bmodes + (pL - a.D) - voff : nullptr;
+  const float* bgR = (exact && pR) ? a.Bmodes + (pR - a.D) - voff : nullptr;
   // FP32 geometry of this thread's element
-  const float xcf = pc.x0 + ((float)(i0 + lane) + 0.5f) * pc.dx;
-  const float ycf = pc.y0 + ((float)j + 0.5f) * pc.dy;
-  const float yBf = pc.y0 + (float)j * pc.dy, yTf = yBf + pc.dy;
-  const float xt0 = pc.x0 + (float)i0 * pc.dx;
-  __syncthreads();
+  const float lanef = i2f(lane);
+  const float xcf = pc.x0 + (i2f(i0 + lane) + 0.5f) * pc.dx;
+  const float ycf = pc.y0 + (i2f(j) + 0.5f) * pc.dy;
+  const float yBf = pc.y0 + i2f(j) * pc.dy, yTf = yBf + pc.dy;
+  const float xt0 = pc.x0 + i2f(i0) * pc.dx;
 
-  // ---- P1 ---------------------------------------------------------------------
+  // ---- P1: nodal values and face traces of this thread's variable ------------
   {
-    const int aa = w;
+    float c[M];
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      float c[m];
-#pragma unroll
-      for (int b = 0; b < m; b++) c[b] = sC[(v * M + aa * m + b) * 32 + lane];
-#pragma unroll
-      for (int r = 0; r < m; r++) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int b = 0; b < m; b++) acc = fmaf(c[b], c32_phi[r][b], acc);
-        sT[((v * m + aa) * m + r) * 32 + lane] = acc;
-      }
-      float rp = 0.0f, rm = 0.0f;
-#pragma unroll
-      for (int b = 0; b < m; b++) {
-        rp = fmaf(c[b], c32_pp[b], rp);
-        rm = fmaf(c[b], c32_pm[b], rm);
-      }
-      sR[((0 * NV + v) * m + aa) * 32 + lane] = rp;
-      sR[((1 * NV + v) * m + aa) * 32 + lane] = rm;
-      float acc = 0.0f;
-      if (pB) {
-#pragma unroll
-        for (int b = 0; b < m; b++) acc = fmaf(pB[(v * M + aa * m + b) * 32 + lc], c32_pp[b], acc);
-      }
-      sR[((2 * NV + v) * m + aa) * 32 + lane] = acc;
-      acc = 0.0f;
-      if (pT) {
-#pragma unroll
-        for (int b = 0; b < m; b++) acc = fmaf(pT[(v * M + aa * m + b) * 32 + lc], c32_pm[b], acc);
-      }
-      sR[((3 * NV + v) * m + aa) * 32 + lane] = acc;
-    }
-  }
-  if (lane < 2) {
-    const int r = w, side = lane;
-    if ((side == 0 && !trL) || (side == 1 && !trR)) {
-      const float* hc = sH + side * NVM;
-#pragma unroll
-      for (int v = 0; v < NV; v++) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int aa = 0; aa < m; aa++) {
-          float t = 0.0f;
-#pragma unroll
-          for (int b = 0; b < m; b++) t = fmaf(hc[v * M + aa * m + b], c32_phi[r][b], t);
-          acc = fmaf(side == 0 ? c32_pp[aa] : c32_pm[aa], t, acc);
-        }
-        if (side == 0) sXR[(v * m + r) * 33 + 0] = acc;
-        else sXL[(v * m + r) * 33 + nvalid] = acc;
-      }
-    }
-  }
-  __syncthreads();
-
-  // ---- P2 ---------------------------------------------------------------------
-  float A[NV][m], Bv[NV][m];
-  {
-    const int q = w;
-    float u[NV][m];
-#pragma unroll
-    for (int v = 0; v < NV; v++)
-#pragma unroll
-      for (int r = 0; r < m; r++) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], sT[((v * m + aa) * m + r) * 32 + lane], acc);
-        u[v][r] = acc;
-      }
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-      float xr = 0.0f, xl = 0.0f;
-#pragma unroll
-      for (int aa = 0; aa < m; aa++) {
-        const float t = sT[((v * m + aa) * m + w) * 32 + lane];
-        xr = fmaf(c32_pp[aa], t, xr);
-        xl = fmaf(c32_pm[aa], t, xl);
-      }
-      sXR[(v * m + w) * 33 + lane + 1] = xr;
-      if (valid) sXL[(v * m + w) * 33 + lane] = xl;
-      if (trL && lane == 0) sXR[(v * m + w) * 33 + 0] = xl;
-      if (trR && lane == nvalid - 1) sXL[(v * m + w) * 33 + nvalid] = xr;
-      if (zL && lane == 0) sXR[(v * m + w) * 33 + 0] = 0.0f;
-      if (zR && lane == nvalid - 1) sXL[(v * m + w) * 33 + nvalid] = 0.0f;
-    }
-    const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
-    {
-      float yt[NV], yb[NV], nb[NV], na[NV];
-#pragma unroll
-      for (int v = 0; v < NV; v++) {
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-#pragma unroll
-        for (int aa = 0; aa < m; aa++) {
-          const float f = c32_phi[q][aa];
-          s0 = fmaf(f, sR[((0 * NV + v) * m + aa) * 32 + lane], s0);
-          s1 = fmaf(f, sR[((1 * NV + v) * m + aa) * 32 + lane], s1);
-          s2 = fmaf(f, sR[((2 * NV + v) * m + aa) * 32 + lane], s2);
-          s3 = fmaf(f, sR[((3 * NV + v) * m + aa) * 32 + lane], s3);
-        }
-        yt[v] = s0;
-        yb[v] = s1;
-        nb[v] = trB ? s1 : s2;  // zB: s2 = 0 (background ghost)
-        na[v] = trT ? s0 : s3;
-      }
-      float hf[NV];
-      {
-        Bg32 bO = bg32_at(pc, xq, yBf), bN = bO;
-        if (exact) {
-          bO = bg32_poly<P>(bOwn, c32_phi[q], c32_pm, bO.c2);
-          if (pBm) bN = bg32_poly<P>(pBm + lc, c32_phi[q], c32_pp, bO.c2);
-          else if (trB) bN = bO;
-        }
-        dllf32<1>(bN, bO, nb, yb, hf);
-      }
-#pragma unroll
-      for (int v = 0; v < NV; v++) sFYB[(v * m + q) * 32 + lane] = hf[v];
-      {
-        Bg32 bO = bg32_at(pc, xq, yTf), bN = bO;
-        if (exact) {
-          bO = bg32_poly<P>(bOwn, c32_phi[q], c32_pp, bO.c2);
-          if (pTm) bN = bg32_poly<P>(pTm + lc, c32_phi[q], c32_pm, bO.c2);
-          else if (trT) bN = bO;
-        }
-        dllf32<1>(bO, bN, yt, na, hf);
-      }
-#pragma unroll
-      for (int v = 0; v < NV; v++) sFYT[(v * m + q) * 32 + lane] = hf[v];
-    }
-#pragma unroll
-    for (int v = 0; v < NV; v++)
-#pragma unroll
-      for (int b = 0; b < m; b++) {
-        A[v][b] = 0.0f;
-        Bv[v][b] = 0.0f;
-      }
-    // node offsets from the planet at the stage time
-    const float pdx = fmaf((float)lane, pc.dx, sF[0]) + fmaf(pc.hdx, c32_xi[q], sF[4]);
+    for (int k = 0; k < M; k++) c[k] = own[k * 32];
+    // x traces: right trace of element e at slot e+1, left trace at slot e
+    float* xr = sXT + (0 * 3 + v) * m * 33;
+    float* xl = sXT + (1 * 3 + v) * m * 33;
+    float tr_r[m], tr_l[m];
+    nodal32<P, true>(c, sU + voff + lane, tr_r, tr_l);
 #pragma unroll
     for (int r = 0; r < m; r++) {
-      const float y = fmaf(pc.hdy, c32_xi[r], ycf);
-      Bg32 bgn = bg32_at(pc, xq, y);
-      if (exact) bgn = bg32_poly<P>(bOwn, c32_phi[q], c32_phi[r], bgn.c2);
-      float d[NV], fx[NV], fy[NV], vx, vy;
+      xr[r * 33 + lane + 1] = tr_r[r];
+      if (valid) xl[r * 33 + lane] = tr_l[r];
+      if (lane == 0 && trL) xr[r * 33] = tr_l[r];  // mirror: exterior = interior
+      if (lane == nvalid - 1 && trR) xl[r * 33 + nvalid] = tr_r[r];
+    }
+    ytrace32<P>(c, c32_pp, sYT + ((0 * 3 + v) * m) * 32 + lane);
+    ytrace32<P>(c, c32_pm, sYT + ((1 * 3 + v) * m) * 32 + lane);
+    if (trB) ytrace32<P>(c, c32_pm, sYN + ((0 * 3 + v) * m) * 32 + lane);
+    if (trT) ytrace32<P>(c, c32_pp, sYN + ((1 * 3 + v) * m) * 32 + lane);
+  }
+  {
+    // neighbour rows: the face polynomial of the element below (top face) and above (bottom face)
+    float c[M];
+    if (pB) {
 #pragma unroll
-      for (int v = 0; v < NV; v++) d[v] = u[v][r];
-      dflux32(bgn, d, fx, fy, vx, vy);
-      // star: -dSigma grad Phi_*; planet: -Sigma grad Phi_p
-      float src1 = 0.0f, src2 = 0.0f;
-      if (pc.star) {
-        const float r2 = fmaf(xq, xq, y * y);
-        float inv;
-        if (r2 >= pc.rs * pc.rs) {
-          const float irr = rsqrtf(r2);
-          inv = irr * irr * irr;
-        } else {
-          inv = pc.irs3;
-        }
-        src1 = -d[0] * xq * inv;
-        src2 = -d[0] * y * inv;
+      for (int k = 0; k < M; k++) c[k] = pB[k * 32];
+      ytrace32<P>(c, c32_pp, sYN + ((0 * 3 + v) * m) * 32 + lane);
+    } else if (zB) {
+#pragma unroll
+      for (int q = 0; q < m; q++) sYN[((0 * 3 + v) * m + q) * 32 + lane] = 0.0f;
+    }
+    if (pT) {
+#pragma unroll
+      for (int k = 0; k < M; k++) c[k] = pT[k * 32];
+      ytrace32<P>(c, c32_pm, sYN + ((1 * 3 + v) * m) * 32 + lane);
+    } else if (zT) {
+#pragma unroll
+      for (int q = 0; q < m; q++) sYN[((1 * 3 + v) * m + q) * 32 + lane] = 0.0f;
+    }
+    // the two x-halo elements: right trace of the left halo, left trace of the right halo
+    if (lane == 0) {
+      if (pL) {
+#pragma unroll
+        for (int k = 0; k < M; k++) c[k] = pL[k * 32];
+        xtrace32<P>(c, c32_pp, sXT + (0 * 3 + v) * m * 33);
+      } else if (zL) {
+#pragma unroll
+        for (int r = 0; r < m; r++) sXT[((0 * 3 + v) * m + r) * 33] = 0.0f;
       }
-      if (pc.planet) {
-        const float pdy = sF[1] + fmaf(pc.hdy, c32_xi[r], sF[5]);
-        const float d2 = fmaf(pdx, pdx, fmaf(pdy, pdy, pc.eps2));
-        const float id = rsqrtf(d2);
-        const float f = pc.q * id * id * id * (bgn.sig + d[0]);
-        src1 = fmaf(-f, pdx, src1);
-        src2 = fmaf(-f, pdy, src2);
-      }
+    }
+    if (lane == nvalid - 1) {
+      if (pR) {
 #pragma unroll
-      for (int v = 0; v < NV; v++) {
-        const float fyy = fy[v] * pc.s2y;
+        for (int k = 0; k < M; k++) c[k] = pR[k * 32];
+        xtrace32<P>(c, c32_pm, sXT + (1 * 3 + v) * m * 33 + nvalid);
+      } else if (zR) {
 #pragma unroll
-        for (int b = 0; b < m; b++) {
-          A[v][b] = fmaf(c32_wphi[r][b], fx[v], A[v][b]);
-          Bv[v][b] = fmaf(c32_wdphi[r][b], fyy, Bv[v][b]);
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < m; b++) {
-        Bv[1][b] = fmaf(c32_wphi[r][b], src1, Bv[1][b]);
-        Bv[2][b] = fmaf(c32_wphi[r][b], src2, Bv[2][b]);
+        for (int r = 0; r < m; r++) sXT[((1 * 3 + v) * m + r) * 33 + nvalid] = 0.0f;
       }
     }
   }
   __syncthreads();
-
-  // ---- P2b: publish A, B; x-face fluxes ----------------------------------------
-#pragma unroll
-  for (int v = 0; v < NV; v++)
-#pragma unroll
-    for (int b = 0; b < m; b++) {
-      sT[((v * m + b) * m + w) * 32 + lane] = A[v][b];
-      sB[((v * m + b) * m + w) * 32 + lane] = Bv[v][b];
-    }
+  const float dt = sF[8];
+  // ---- P2: pointwise flux differences and sources at the nodes (dealt
+  // round-robin over the three threads of an element), then face fluxes ------
   {
-    const int r = w;
-    const float y = fmaf(pc.hdy, c32_xi[r], ycf);
-    for (int f = lane; f <= nvalid; f += 32) {
-      float uL[NV], uR[NV], hf[NV];
+    const float pdx0 = fmaf(lanef, pc.dx, sF[0]);
+#pragma unroll 1
+    for (int kk = 0; kk < (M + 2) / 3; kk++) {
+      const int n = v + 3 * kk;
+      if (n < M) {
+        const int q = n / m, r = n - q * m;
+        float d[3];
 #pragma unroll
-      for (int v = 0; v < NV; v++) {
-        uL[v] = sXR[(v * m + r) * 33 + f];
-        uR[v] = sXL[(v * m + r) * 33 + f];
+        for (int w3 = 0; w3 < 3; w3++) d[w3] = sU[(w3 * M + n) * 32 + lane];
+        const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
+        const float y = fmaf(pc.hdy, c32_xi[r], ycf);
+        Bg32 bgn = bg32_at(pc, xq, y);
+        if (exact) bgn = bg32_poly<P>(bgOwn, c32_phi[q], c32_phi[r], bgn.c2);
+        float fx[3], fy[3], vx, vy;
+        dflux32(bgn, d, fx, fy, vx, vy);
+        // star: -dSigma grad Phi_*; planet: -Sigma grad Phi_p
+        float src1 = 0.0f, src2 = 0.0f;
+        if (pc.star) {
+          const float r2 = fmaf(xq, xq, y * y);
+          float inv;
+          if (r2 >= pc.rs * pc.rs) {
+            const float irr = rsqrtf(r2);
+            inv = irr * irr * irr;
+          } else {
+            inv = pc.irs3;
+          }
+          src1 = -d[0] * xq * inv;
+          src2 = -d[0] * y * inv;
+        }
+        if (pc.planet) {
+          const float pdx = pdx0 + fmaf(pc.hdx, c32_xi[q], sF[4]);
+          const float pdy = sF[1] + fmaf(pc.hdy, c32_xi[r], sF[5]);
+          const float d2 = fmaf(pdx, pdx, fmaf(pdy, pdy, pc.eps2));
+          const float id = rsqrtf(d2);
+          const float f = pc.q * id * id * id * (bgn.sig + d[0]);
+          src1 = fmaf(-f, pdx, src1);
+          src2 = fmaf(-f, pdy, src2);
+        }
+        float* o = sFl + n * 32 + lane;
+        o[0 * M * 32] = fx[0];
+        o[1 * M * 32] = fx[1];
+        o[2 * M * 32] = fx[2];
+        o[3 * M * 32] = fy[0] * pc.s2y;
+        o[4 * M * 32] = fy[1] * pc.s2y;
+        o[5 * M * 32] = fy[2] * pc.s2y;
+        o[6 * M * 32] = src1;
+        o[7 * M * 32] = src2;
       }
-      Bg32 bL = bg32_at(pc, fmaf((float)f, pc.dx, xt0), y), bR = bL;
+    }
+    // y faces of the element: bottom (below | own) and top (own | above)
+    for (int kk = v; kk < 2 * m; kk += 3) {
+      const int side = kk >= m, q = kk - side * m;
+      const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
+      float dL[3], dR[3], hf[3];
+#pragma unroll
+      for (int w3 = 0; w3 < 3; w3++) {
+        const int o = ((w3)*m + q) * 32 + lane;
+        dL[w3] = side ? sYT[0 * 3 * m * 32 + o] : sYN[0 * 3 * m * 32 + o];
+        dR[w3] = side ? sYN[1 * 3 * m * 32 + o] : sYT[1 * 3 * m * 32 + o];
+      }
+      Bg32 bO = bg32_at(pc, xq, side ? yTf : yBf), bN = bO;
       if (exact) {
-        // left element: lane f-1 or the left halo; right: lane f or the right halo
-        const float* eL = (f > 0) ? bOwn - lc + (f - 1) : pLm;
-        const float* eR = (f < nvalid) ? bOwn - lc + f : pRm;
-        const float c2 = bL.c2;
-        if (eL) bL = bg32_poly<P>(eL, c32_pp, c32_phi[r], c2);
-        if (eR) bR = bg32_poly<P>(eR, c32_pm, c32_phi[r], c2);
-        if (!eL && trL && f == 0) bL = bR;
-        if (!eR && trR && f == nvalid) bR = bL;
+        const float c2 = bO.c2;
+        bO = bg32_poly<P>(bgOwn, c32_phi[q], side ? c32_pp : c32_pm, c2);
+        const float* nb = side ? bgT : bgB;
+        if (nb) bN = bg32_poly<P>(nb, c32_phi[q], side ? c32_pm : c32_pp, c2);
+        else if (side ? trT : trB) bN = bO;
       }
-      dllf32<0>(bL, bR, uL, uR, hf);
+      dllf32<1>(side ? bO : bN, side ? bN : bO, dL, dR, hf);
 #pragma unroll
-      for (int v = 0; v < NV; v++) sFX[(v * m + r) * 33 + f] = hf[v];
+      for (int w3 = 0; w3 < 3; w3++) sFY[((side * 3 + w3) * m + q) * 32 + lane] = hf[w3];
+    }
+    // x faces f = 0..nvalid of the tile row (face f between elements f-1 and f)
+    for (int idx = tid; idx < m * 33; idx += 96) {
+      const int r = idx / 33, f = idx - 33 * r;
+      if (f <= nvalid) {
+        float dL[3], dR[3], hf[3];
+#pragma unroll
+        for (int w3 = 0; w3 < 3; w3++) {
+          dL[w3] = sXT[((0 * 3 + w3) * m + r) * 33 + f];
+          dR[w3] = sXT[((1 * 3 + w3) * m + r) * 33 + f];
+        }
+        const float y = fmaf(pc.hdy, c32_xi[r], ycf);
+        Bg32 bL = bg32_at(pc, fmaf(i2f(f), pc.dx, xt0), y), bR = bL;
+        if (exact) {
+          const float* eL = (f > 0) ? bgOwn - lc + (f - 1) : bgL;
+          const float* eR = (f < nvalid) ? bgOwn - lc + f : bgR;
+          const float c2 = bL.c2;
+          if (eL) bL = bg32_poly<P>(eL, c32_pp, c32_phi[r], c2);
+          if (eR) bR = bg32_poly<P>(eR, c32_pm, c32_phi[r], c2);
+          if (!eL && trL && f == 0) bL = bR;
+          if (!eR && trR && f == nvalid) bR = bL;
+        }
+        dllf32<0>(bL, bR, dL, dR, hf);
+#pragma unroll
+        for (int w3 = 0; w3 < 3; w3++) sFX[(w3 * m + r) * 33 + f] = hf[w3];
+      }
     }
   }
   __syncthreads();
-
-  // ---- P3 ---------------------------------------------------------------------
-  const int aa = w;
-  float L[NV][m];
+  // ---- P3: volume integral and surface lift of this thread's variable -------
+  float L[M];
   {
-    const int b = w;
+    float Aq[m][m], Bq[m][m];  // first contraction over r, [b][q]
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      float hl = 0.0f, hr = 0.0f;
+    for (int b = 0; b < m; b++)
+#pragma unroll
+      for (int q = 0; q < m; q++) Aq[b][q] = Bq[b][q] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < m; q++)
 #pragma unroll
       for (int r = 0; r < m; r++) {
-        hl = fmaf(c32_wphi[r][b], sFX[(v * m + r) * 33 + lane], hl);
-        hr = fmaf(c32_wphi[r][b], sFX[(v * m + r) * 33 + lane + 1], hr);
-      }
-      sHL[(v * m + b) * 32 + lane] = hl;
-      sHR[(v * m + b) * 32 + lane] = hr;
-    }
+        const int n = q * m + r;
+        const float fxv = sFl[(v * M + n) * 32 + lane];
+        const float fyv = sFl[((3 + v) * M + n) * 32 + lane];
+        const float sv = (v > 0) ? sFl[((5 + v) * M + n) * 32 + lane] : 0.0f;
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      float ht = 0.0f, hb = 0.0f;
-#pragma unroll
-      for (int q = 0; q < m; q++) {
-        ht = fmaf(c32_wphi[q][aa], sFYT[(v * m + q) * 32 + lane], ht);
-        hb = fmaf(c32_wphi[q][aa], sFYB[(v * m + q) * 32 + lane], hb);
+        for (int b = 0; b < m; b++) {
+          Aq[b][q] = fmaf(c32_wphi[r][b], fxv, Aq[b][q]);
+          Bq[b][q] = fmaf(c32_wdphi[r][b], fyv, fmaf(c32_wphi[r][b], sv, Bq[b][q]));
+        }
       }
 #pragma unroll
-      for (int bb = 0; bb < m; bb++) {
+    for (int aa = 0; aa < m; aa++)
+#pragma unroll
+      for (int b = 0; b < m; b++) {
         float va = 0.0f, vb = 0.0f;
 #pragma unroll
         for (int q = 0; q < m; q++) {
-          va = fmaf(c32_wdphi[q][aa], sT[((v * m + bb) * m + q) * 32 + lane], va);
-          vb = fmaf(c32_wphi[q][aa], sB[((v * m + bb) * m + q) * 32 + lane], vb);
+          va = fmaf(c32_wdphi[q][aa], Aq[b][q], va);
+          vb = fmaf(c32_wphi[q][aa], Bq[b][q], vb);
         }
-        L[v][bb] = fmaf(pc.s2x, va, vb) + pc.idy * (c32_pm[bb] * hb - c32_pp[bb] * ht);
+        L[aa * m + b] = fmaf(pc.s2x, va, vb);
+      }
+  }
+  {
+    float HL[m], HR[m], HB[m], HT[m];
+#pragma unroll
+    for (int b = 0; b < m; b++) HL[b] = HR[b] = HB[b] = HT[b] = 0.0f;
+#pragma unroll
+    for (int r = 0; r < m; r++) {
+      const float fl = sFX[(v * m + r) * 33 + lane], fr = sFX[(v * m + r) * 33 + lane + 1];
+      const float fb = sFY[((0 * 3 + v) * m + r) * 32 + lane], ft = sFY[((1 * 3 + v) * m + r) * 32 + lane];
+#pragma unroll
+      for (int b = 0; b < m; b++) {
+        HL[b] = fmaf(c32_wphi[r][b], fl, HL[b]);
+        HR[b] = fmaf(c32_wphi[r][b], fr, HR[b]);
+        HB[b] = fmaf(c32_wphi[r][b], fb, HB[b]);
+        HT[b] = fmaf(c32_wphi[r][b], ft, HT[b]);
       }
     }
+#pragma unroll
+    for (int aa = 0; aa < m; aa++)
+#pragma unroll
+      for (int b = 0; b < m; b++) {
+        const float lx = fmaf(c32_pm[aa], HL[b], -c32_pp[aa] * HR[b]);
+        const float ly = fmaf(c32_pm[b], HB[aa], -c32_pp[b] * HT[aa]);
+        L[aa * m + b] = fmaf(pc.idx, lx, fmaf(pc.idy, ly, L[aa * m + b]));
+      }
   }
-  // the background residual and u^n of this thread's modes, issued before the sync
-  const size_t obase = tile * NVM * 32;
-  float rb[NV][m], dn[NV][m];
+  // background residual R_b, then the Shu-Osher combination
+  const size_t gbase = tile * NVM * 32 + voff;
 #pragma unroll
-  for (int v = 0; v < NV; v++)
-#pragma unroll
-    for (int bb = 0; bb < m; bb++) {
-      const size_t idx = obase + (v * M + aa * m + bb) * 32 + lc;
-      rb[v][bb] = a.Rb[idx];
-      dn[v][bb] = (a.mode != 0 && a.alpha != 0.0f) ? a.Dn[idx] : 0.0f;
-    }
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < NV; v++)
-#pragma unroll
-    for (int bb = 0; bb < m; bb++) {
-      L[v][bb] += pc.idx * (c32_pm[aa] * sHL[(v * m + bb) * 32 + lane] - c32_pp[aa] * sHR[(v * m + bb) * 32 + lane]);
-      L[v][bb] += rb[v][bb];
-    }
+  for (int k = 0; k < M; k++) L[k] += a.Rb[gbase + k * 32 + lc];
   if (a.mode == 0) {
     if (valid) {
 #pragma unroll
-      for (int v = 0; v < NV; v++)
-#pragma unroll
-        for (int bb = 0; bb < m; bb++) a.Out[obase + (v * M + aa * m + bb) * 32 + lane] = L[v][bb];
+      for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = L[k];
     }
     return;
   }
-  float un[NV][m];
+  float un[M];
 #pragma unroll
-  for (int v = 0; v < NV; v++)
-#pragma unroll
-    for (int bb = 0; bb < m; bb++) {
-      const int idx = (v * M + aa * m + bb) * 32 + lane;
-      un[v][bb] = fmaf(a.alpha, dn[v][bb], a.beta * fmaf(dt, L[v][bb], sC[idx]));
-    }
-  if (a.mode == 1) {
+  for (int k = 0; k < M; k++) {
+    const float dn = (a.alpha != 0.0f) ? a.Dn[gbase + k * 32 + lc] : 0.0f;
+    un[k] = fmaf(a.alpha, dn, a.beta * fmaf(dt, L[k], own[k * 32]));
+  }
+  if (!LAST) {
     if (valid) {
 #pragma unroll
-      for (int v = 0; v < NV; v++)
-#pragma unroll
-        for (int bb = 0; bb < m; bb++) a.Out[obase + (v * M + aa * m + bb) * 32 + lane] = un[v][bb];
+      for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = un[k];
     }
     return;
   }
-
-  // ---- P4 (last stage): damping in delta form, torque, CFL ---------------------
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < NV; v++)
-#pragma unroll
-    for (int bb = 0; bb < m; bb++) sC[(v * M + aa * m + bb) * 32 + lane] = un[v][bb];
-  __syncthreads();
-#pragma unroll
-  for (int v = 0; v < NV; v++) {
-    float c[m];
-#pragma unroll
-    for (int b = 0; b < m; b++) c[b] = sC[(v * M + aa * m + b) * 32 + lane];
-#pragma unroll
-    for (int r = 0; r < m; r++) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int b = 0; b < m; b++) acc = fmaf(c[b], c32_phi[r][b], acc);
-      sT[((v * m + aa) * m + r) * 32 + lane] = acc;
-    }
-  }
+  // ---- P4 (last stage): damping in delta form, torque, CFL --------------------
+  __syncthreads();  // every read of sU by P2 is done
+  nodal32<P, false>(un, sU + voff + lane, nullptr, nullptr);
   __syncthreads();
   int damped = 0;
+  double gxd = 0.0, gyd = 0.0;
   {
-    const int q = w;
-    float u[NV][m];
-#pragma unroll
-    for (int v = 0; v < NV; v++)
-#pragma unroll
-      for (int r = 0; r < m; r++) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int k = 0; k < m; k++) acc = fmaf(c32_phi[q][k], sT[((v * m + k) * m + r) * 32 + lane], acc);
-        u[v][r] = acc;
-      }
-    const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
     const bool zones = (pc.rd_in > 0.0f) || (pc.rd_out > 0.0f);
     const float* db = a.Db + tile * (size_t)(3 * M * 32);
-#pragma unroll
-    for (int r = 0; r < m; r++) {
+    const float* sbn = a.SigbN + tile * (size_t)(M * 32);
+    const float cdx = fmaf(lanef, pc.dx, sF[2]), cdy = sF[3];
+    const bool nearp = valid && fmaf(cdx, cdx, cdy * cdy) < pc.near2;
+#pragma unroll 1
+    for (int kk = 0; kk < (M + 2) / 3; kk++) {
+      const int n = v + 3 * kk;
+      if (n >= M) break;  // warp-uniform
+      const int q = n / m, r = n - q * m;
+      const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
       const float y = fmaf(pc.hdy, c32_xi[r], ycf);
+      float d0 = sU[(0 * M + n) * 32 + lane];
       if (zones) {
-        const float rr = sqrtf(fmaf(xq, xq, y * y));
+        const float rr = sqrt_fast(fmaf(xq, xq, y * y));
         float R = 0.0f, rd = 0.0f;
         if (pc.rd_in > 0.0f && rr < pc.rd_in) {
           rd = pc.rd_in;
-          const float x = (rr - rd) / (rd / pc.damp_ratio - rd);
+          const float x = __fdividef(rr - rd, __fdividef(rd, pc.damp_ratio) - rd);
           R = fminf(x * x, 1.0f);
         } else if (pc.rd_out > 0.0f && rr > pc.rd_out) {
           rd = pc.rd_out;
-          const float x = (rr - rd) / (rd * pc.damp_ratio - rd);
+          const float x = __fdividef(rr - rd, rd * pc.damp_ratio - rd);
           R = fminf(x * x, 1.0f);
         }
         if (R > 0.0f) {
           damped = 1;
           // Q_new = Q0 + kappa (Q - Q0), kappa = tau / (tau + dt), written for
           // delta Q = Q - Q_b: dQ_new = kappa dQ + (1 - kappa) (Q0 - Q_b)
-          const float tau = 6.2831853071795864769f * sqrtf(rd * rd * rd) / R;
-          const float kap = tau / (tau + dt), omk = dt / (tau + dt);
+          const float tau = __fdividef(6.2831853071795864769f * sqrt_fast(rd * rd * rd), R);
+          const float itd = __fdividef(1.0f, tau + dt);
+          const float kap = tau * itd, omk = dt * itd;
           Bg32 bgn = bg32_at(pc, xq, y);
-          if (exact) bgn = bg32_poly<P>(bOwn, c32_phi[q], c32_phi[r], bgn.c2);
-          const int nn = q * m + r;
-          const float sg = bgn.sig + u[0][r];
-          const float dvx = (u[1][r] - bgn.vx * u[0][r]) / sg;
-          const float dvy = (u[2][r] - bgn.vy * u[0][r]) / sg;
-          const float ds2 = fmaf(kap, u[0][r], omk * db[(0 * M + nn) * 32 + lc]);
-          const float dvx2 = fmaf(kap, dvx, omk * db[(1 * M + nn) * 32 + lc]);
-          const float dvy2 = fmaf(kap, dvy, omk * db[(2 * M + nn) * 32 + lc]);
+          if (exact) bgn = bg32_poly<P>(bgOwn, c32_phi[q], c32_phi[r], bgn.c2);
+          const float d1 = sU[(1 * M + n) * 32 + lane], d2 = sU[(2 * M + n) * 32 + lane];
+          const float sg = bgn.sig + d0;
+          const float isg = __fdividef(1.0f, sg);
+          const float dvx = (d1 - bgn.vx * d0) * isg;
+          const float dvy = (d2 - bgn.vy * d0) * isg;
+          const float ds2 = fmaf(kap, d0, omk * db[(0 * M + n) * 32 + lc]);
+          const float dvx2 = fmaf(kap, dvx, omk * db[(1 * M + n) * 32 + lc]);
+          const float dvy2 = fmaf(kap, dvy, omk * db[(2 * M + n) * 32 + lc]);
           const float sg2 = bgn.sig + ds2;
-          u[0][r] = ds2;
-          u[1][r] = fmaf(ds2, bgn.vx, sg2 * dvx2);
-          u[2][r] = fmaf(ds2, bgn.vy, sg2 * dvy2);
+          d0 = ds2;
+          sU[(0 * M + n) * 32 + lane] = ds2;
+          sU[(1 * M + n) * 32 + lane] = fmaf(ds2, bgn.vx, sg2 * dvx2);
+          sU[(2 * M + n) * 32 + lane] = fmaf(ds2, bgn.vy, sg2 * dvy2);
         }
       }
-    }
-    // torque on the planet at t^{n+1}.  Elements within sqrt(near2) of the
-    // planet: FP64 terms from the FP64 background modes.  Beyond: unweighted
-    // FP32 terms Sigma(node) (r_n - r_p) / (d^2 + eps^2)^(3/2) with a correctly
-    // rounded rsqrt, summed over the 32 lanes per node class (q, r); the
-    // quadrature weights w_q w_r |K| / 4 are applied to the class sums in FP64
-    // once per CTA, so no rounding is shared by every element.
-    double gxd = 0.0, gyd = 0.0;
-    float fx[m], fy[m];
-#pragma unroll
-    for (int r = 0; r < m; r++) fx[r] = fy[r] = 0.0f;
-    if (valid) {
-      const float cdx = fmaf((float)lane, pc.dx, sF[2]), cdy = sF[3];
-      if (fmaf(cdx, cdx, cdy * cdy) < pc.near2) {
+      // torque on the planet at t^{n+1}: FP64 terms near the planet; beyond,
+      // unweighted FP32 terms kept per node class (q, r) for the class sums
+      float tx = 0.0f, ty = 0.0f;
+      if (nearp) {
         const double xcd = ms.x0 + (i0 + lane + 0.5) * ms.dx, ycd = ms.y0 + (j + 0.5) * ms.dy;
-        torque_near64<P>(a.BG64 + tile * NVM * 32 + lane, u[0], q, xcd, ycd, sD[0], sD[1],
+        torque_node64<P>(a.BG64 + tile * NVM * 32 + lane, d0, q, r, xcd, ycd, sD[0], sD[1],
                          0.5 * ms.dx, 0.5 * ms.dy, ms.dx * ms.dy, pc.eps2_d, gxd, gyd);
-      } else {
-        const float* sbn = a.SigbN + tile * (size_t)(M * 32);
+      } else if (valid) {
+        const float sig = sbn[n * 32 + lane] + d0;
         const float pdx = cdx + fmaf(pc.hdx, c32_xi[q], sF[6]);
+        const float pdy = cdy + fmaf(pc.hdy, c32_xi[r], sF[7]);
+        const float dd = fmaf(pdx, pdx, fmaf(pdy, pdy, pc.eps2));
+        // rsqrt refined by one Newton step: ~1 ulp, no bias of the raw approximation
+        float id = rsqrtf(dd);
+        id = id * fmaf(-0.5f * dd * id, id, 1.5f);
+        const float f = sig * (id * id * id);
+        tx = f * pdx;
+        ty = f * pdy;
+      }
+      sFl[(0 * M + n) * 32 + lane] = tx;
+      sFl[(1 * M + n) * 32 + lane] = ty;
+    }
+  }
+  if (damped) sFlag[lane] = 1;
+  if (__syncthreads_or(damped)) {
+    if (sFlag[lane]) {
+      // back to modes by the m-point projection of the damped nodal values
+      float P1[m][m];  // [b][q] = sum_r w_r/2 phi_b(eta_r) u(q, r)
 #pragma unroll
-        for (int r = 0; r < m; r++) {
-          const float sig = sbn[(q * m + r) * 32 + lane] + u[0][r];
-          const float pdy = cdy + fmaf(pc.hdy, c32_xi[r], sF[7]);
-          const float d2 = fmaf(pdx, pdx, fmaf(pdy, pdy, pc.eps2));
-          const float id = __frsqrt_rn(d2);
-          const float f = sig * (id * id * id);
-          fx[r] = f * pdx;
-          fy[r] = f * pdy;
+      for (int b = 0; b < m; b++)
+#pragma unroll
+        for (int q = 0; q < m; q++) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int r = 0; r < m; r++) acc = fmaf(c32_wphi[r][b], sU[(v * M + q * m + r) * 32 + lane], acc);
+          P1[b][q] = acc;
         }
-      }
+#pragma unroll
+      for (int aa = 0; aa < m; aa++)
+#pragma unroll
+        for (int b = 0; b < m; b++) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int q = 0; q < m; q++) acc = fmaf(c32_wphi[q][aa], P1[b][q], acc);
+          un[aa * m + b] = acc;
+        }
     }
+  }
+  if (valid) {
 #pragma unroll
-    for (int r = 0; r < m; r++)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        fx[r] += __shfl_xor_sync(0xffffffffu, fx[r], o);
-        fy[r] += __shfl_xor_sync(0xffffffffu, fy[r], o);
-      }
-    if (lane == 0) {
-      // this warp's node classes (q, r), weighted in FP64
-      const double wq = c32_wh64[q] * ms.dx * ms.dy;
-#pragma unroll
-      for (int r = 0; r < m; r++) {
-        gxd += wq * c32_wh64[r] * (double)fx[r];
-        gyd += wq * c32_wh64[r] * (double)fy[r];
-      }
-    }
+    for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = un[k];
+  }
+  sB0[v * 32 + lane] = un[0];
+  if (tid < 2 * M) {
+    // class sums of the FP32 torque terms over the 32 elements (a lane-rotated
+    // fixed order, free of bank conflicts), weighted in FP64
+    const int comp = tid >= M, n = tid - comp * M;
+    const float* col = sFl + (comp * M + n) * 32;
+    float s = 0.0f;
+#pragma unroll 8
+    for (int l = 0; l < 32; l++) s += col[(l + tid) & 31];
+    const int q = n / m, r = n - q * m;
+    sD[16 + tid] = c32_wh64[q] * c32_wh64[r] * ms.dx * ms.dy * (double)s;
+  }
+  if (__any_sync(0xffffffffu, gxd != 0.0 || gyd != 0.0)) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       gxd += __shfl_xor_sync(0xffffffffu, gxd, o);
       gyd += __shfl_xor_sync(0xffffffffu, gyd, o);
     }
-    if (lane == 0) {
-      sD[16 + w] = gxd;
-      sD[16 + m + w] = gyd;
-    }
-    if (damped) sFlag[lane] = 1;
-    if (__syncthreads_or(damped)) {
-#pragma unroll
-      for (int v = 0; v < NV; v++)
-#pragma unroll
-        for (int b = 0; b < m; b++) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int r = 0; r < m; r++) acc = fmaf(c32_wphi[r][b], u[v][r], acc);
-          sB[((v * m + b) * m + q) * 32 + lane] = acc;
-        }
-      __syncthreads();
-      if (sFlag[lane]) {
-#pragma unroll
-        for (int v = 0; v < NV; v++)
-#pragma unroll
-          for (int bb = 0; bb < m; bb++) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int qq = 0; qq < m; qq++) acc = fmaf(c32_wphi[qq][aa], sB[((v * m + bb) * m + qq) * 32 + lane], acc);
-            un[v][bb] = acc;
-          }
-      }
-    }
   }
-  if (valid) {
-#pragma unroll
-    for (int v = 0; v < NV; v++)
-#pragma unroll
-      for (int bb = 0; bb < m; bb++) a.Out[obase + (v * M + aa * m + bb) * 32 + lane] = un[v][bb];
+  if (lane == 0) {
+    sD[8 + v] = gxd;
+    sD[11 + v] = gyd;
   }
-  if (w == 0) {
-    // CFL minimum of the new state (mode 0 of the full state), then the torque
-    // partial of the CTA in a fixed order
-    double dtk = __longlong_as_double(0x7ff0000000000000LL);
+  __syncthreads();
+  if (v == 0) {
+    // CFL minimum of the new state from the element averages of u_b + delta
+    float dtf = __int_as_float(0x7f800000);
     int bad = 0;
     if (valid) {
       const float* b0 = a.Bm0 + tile * (size_t)(3 * 32);
-      const float rho = b0[0 * 32 + lane] + un[0][0];
+      const float rho = b0[0 * 32 + lane] + sB0[0 * 32 + lane];
       const float irho = 1.0f / rho;
-      const float vx = (b0[1 * 32 + lane] + un[1][0]) * irho, vy = (b0[2 * 32 + lane] + un[2][0]) * irho;
+      const float vx = (b0[1 * 32 + lane] + sB0[1 * 32 + lane]) * irho;
+      const float vy = (b0[2 * 32 + lane] + sB0[2 * 32 + lane]) * irho;
       const float c = sqrtf(bg32_at(pc, xcf, ycf).c2);
-      const float dtf = pc.cfl_fac / ((fabsf(vx) + c) / pc.dx + (fabsf(vy) + c) / pc.dy);
-      dtk = (double)dtf;
+      dtf = pc.cfl_fac / ((fabsf(vx) + c) / pc.dx + (fabsf(vy) + c) / pc.dy);
       bad = !(rho > 0.0f) || !(dtf > 0.0f) || !isfinite(dtf);
-      if (bad) dtk = __longlong_as_double(0x7ff0000000000000LL);
+      if (bad) dtf = __int_as_float(0x7f800000);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      dtk = fmin(dtk, __shfl_xor_sync(0xffffffffu, dtk, o));
+      dtf = fminf(dtf, __shfl_xor_sync(0xffffffffu, dtf, o));
       bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if (lane == 0) {
       if (bad) atomicOr(&a.ts->pending, 1);
-      atomicMin(&a.ts->dt_bits, (unsigned long long)__double_as_longlong(dtk));
+      atomicMin(&a.ts->dt_bits, (unsigned long long)__double_as_longlong((double)dtf));
+      double gx = sD[8] + sD[9] + sD[10], gy = sD[11] + sD[12] + sD[13];
+      for (int k = 0; k < M; k++) {
+        gx += sD[16 + k];
+        gy += sD[16 + M + k];
+      }
+      a.part[2 * tile] = gx;
+      a.part[2 * tile + 1] = gy;
     }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double gx = 0.0, gy = 0.0;
-#pragma unroll
-    for (int k = 0; k < m; k++) {
-      gx += sD[16 + k];
-      gy += sD[16 + m + k];
-    }
-    a.part[2 * tile] = gx;
-    a.part[2 * tile + 1] = gy;
   }
 }
 
-template <int P>
-cudaError_t launch_stage32_impl(const StageArgs32& a, cudaStream_t s) {
+template <int P, bool LAST>
+cudaError_t launch_stage32_kind(const StageArgs32& a, cudaStream_t s) {
   static bool configured = false;
   const size_t bytes = Smem32<P>::BYTES;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_stage32<P, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid(a.mesh.ntx, a.mesh.ny);
-  k_stage32<P><<<grid, 32 * (P + 1), bytes, s>>>(a);
+  k_stage32<P, LAST><<<grid, 96, bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_stage32_impl(const StageArgs32& a, cudaStream_t s) {
+  return a.mode == 2 ? launch_stage32_kind<P, true>(a, s) : launch_stage32_kind<P, false>(a, s);
 }
 
 template <int P>
