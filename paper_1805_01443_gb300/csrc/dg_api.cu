@@ -318,7 +318,7 @@ int read_state(dg_handle* h, DevState* out) {
 // CFL step of a full FP64 tiled state into the device time state
 int launch_cfl_and_dt(dg_handle* h, const double* full) {
   CU(h, launch_cfl(full, h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
-  CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, h->ph.r_p, h->ph.omega_p,
+  CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, 0, h->ph.r_p, h->ph.omega_p,
                       h->ph.phi0, h->stream));
   return DG_OK;
 }
@@ -351,25 +351,25 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
   a.part = h->part;
   a.mesh = h->dm;
   a.pc = h->pc;
-  a.fixed_dt = fixed_dt;
+  if (n > 0) CU(h, launch_planet32(h->ts, fixed_dt, h->ph.r_p, h->ph.omega_p, h->ph.phi0, h->stream));
   for (int s = 0; s < n; s++) {
     float* un = h->D[h->cur];
     float* nx = h->D[1 - h->cur];
     a.Dn = un;
     if (h->disc.rk == 3) {
-      a.D = un; a.Out = nx; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
+      a.D = un; a.Out = nx; a.alpha = 0.0f; a.beta = 1.0f; a.pidx = 0; a.mode = 1;
       CU(h, launch_stage32_h(h, a));
-      a.D = nx; a.Out = h->DZ; a.alpha = 0.75; a.beta = 0.25; a.cstage = 1.0; a.mode = 1;
+      a.D = nx; a.Out = h->DZ; a.alpha = 0.75f; a.beta = 0.25f; a.pidx = 2; a.mode = 1;
       CU(h, launch_stage32_h(h, a));
-      a.D = h->DZ; a.Out = nx; a.alpha = 1.0 / 3.0; a.beta = 2.0 / 3.0; a.cstage = 0.5; a.mode = 2;
+      a.D = h->DZ; a.Out = nx; a.alpha = 1.0f / 3.0f; a.beta = 2.0f / 3.0f; a.pidx = 1; a.mode = 2;
       CU(h, launch_stage32_h(h, a));
     } else {
-      a.D = un; a.Out = h->DZ; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
+      a.D = un; a.Out = h->DZ; a.alpha = 0.0f; a.beta = 1.0f; a.pidx = 0; a.mode = 1;
       CU(h, launch_stage32_h(h, a));
-      a.D = h->DZ; a.Out = nx; a.alpha = 0.5; a.beta = 0.5; a.cstage = 1.0; a.mode = 2;
+      a.D = h->DZ; a.Out = nx; a.alpha = 0.5f; a.beta = 0.5f; a.pidx = 2; a.mode = 2;
       CU(h, launch_stage32_h(h, a));
     }
-    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, h->ph.r_p,
+    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, 1, h->ph.r_p,
                         h->ph.omega_p, h->ph.phi0, h->stream));
     h->cur = 1 - h->cur;
   }
@@ -407,7 +407,7 @@ int do_steps(dg_handle* h, int n, double fixed_dt) {
       a.U = h->Z; a.Out = nx; a.alpha = 0.5; a.beta = 0.5; a.cstage = 1.0; a.mode = 2;
       CU(h, launch_stage_h(h, a));
     }
-    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, h->ph.r_p,
+    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, 0, h->ph.r_p,
                         h->ph.omega_p, h->ph.phi0, h->stream));
     h->cur = 1 - h->cur;
   }
@@ -505,9 +505,14 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     pc.planet = planet->enabled;
     pc.q = (float)planet->q;
     pc.eps2 = (float)(planet->eps * planet->eps);
-    pc.r_p = planet->r_p;
-    pc.omega_p = planet->omega_p;
-    pc.phi0 = planet->phi0;
+    auto split = [](double x, float* pr) {
+      pr[0] = (float)x;
+      pr[1] = (float)(x - (double)pr[0]);
+    };
+    split(dm.x0, pc.x0p);
+    split(dm.y0, pc.y0p);
+    split(dm.dx, pc.dxp);
+    split(dm.dy, pc.dyp);
     pc.rd_in = (float)disc->rdamp_in;
     pc.rd_out = (float)disc->rdamp_out;
     pc.damp_ratio = (float)pow(1.15, 1.5);
@@ -698,7 +703,9 @@ int dg_rhs(dg_handle* h, double* out) {
     a.part = h->part;
     a.mesh = h->dm;
     a.pc = h->pc;
+    a.pidx = 0;
     a.mode = 0;
+    CU(h, launch_planet32(h->ts, 0.0, h->ph.r_p, h->ph.omega_p, h->ph.phi0, h->stream));
     CU(h, launch_stage32_h(h, a));
     CU(h, launch_f32_to_f64(h->DZ, h->Z, tiled_count(h), h->stream));
   } else {

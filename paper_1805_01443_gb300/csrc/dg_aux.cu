@@ -116,8 +116,34 @@ __global__ void k_cfl(const double* U, DevState* ts, const Mesh ms, const Phys p
 // End of a step: fixed-order sum of the per-CTA torque partials, torque on the
 // planet at t^{n+1} (Sec. 5.2), time advance, and the next CFL step.  With
 // advance = 0 only the CFL slot is turned into ts->dt.
+// planet positions of the precision form for the step starting at ts->t with
+// step dt (see DevState::plf)
+__device__ void store_planet32(DevState* ts, double dt, double r_p, double omega_p, double phi0) {
+  const double c[3] = {0.0, 0.5, 1.0};
+  for (int k = 0; k < 3; k++) {
+    double sn, cs;
+    sincos(omega_p * (ts->t + c[k] * dt) + phi0, &sn, &cs);
+    const double x = r_p * cs, y = r_p * sn;
+    const float xh = (float)x, yh = (float)y;
+    ts->plf[k][0] = xh;
+    ts->plf[k][1] = (float)(x - (double)xh);
+    ts->plf[k][2] = yh;
+    ts->plf[k][3] = (float)(y - (double)yh);
+    if (k == 2) {
+      ts->pl1[0] = x;
+      ts->pl1[1] = y;
+    }
+  }
+  ts->dtf = (float)dt;
+}
+
+__global__ void k_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0) {
+  store_planet32(ts, fixed_dt > 0.0 ? fixed_dt : ts->dt, r_p, omega_p, phi0);
+}
+
 __global__ void k_finish(DevState* ts, const double* part, int nparts, double* series,
-                         double fixed_dt, int advance, double r_p, double omega_p, double phi0) {
+                         double fixed_dt, int advance, int planet32, double r_p, double omega_p,
+                         double phi0) {
   __shared__ double sx[256], sy[256];
   const int tid = threadIdx.x;
   if (ts->status != 0) return;
@@ -140,7 +166,8 @@ __global__ void k_finish(DevState* ts, const double* part, int nparts, double* s
   }
   if (tid != 0) return;
   if (ts->pending) {
-    ts->status = DG_ERR_NUMERIC;
+    // bit 0: non-finite or non-positive state; bit 1: a bounded wait gave up
+    ts->status = (ts->pending & 2) ? DG_ERR_TIMEOUT : DG_ERR_NUMERIC;
     return;
   }
   if (advance) {
@@ -163,6 +190,7 @@ __global__ void k_finish(DevState* ts, const double* part, int nparts, double* s
     ts->dt = dtn;
   }
   ts->dt_bits = INF_BITS;
+  if (planet32 && ts->status == 0) store_planet32(ts, fixed_dt > 0.0 ? fixed_dt : ts->dt, r_p, omega_p, phi0);
 }
 
 __global__ void k_reset(DevState* ts, double t, long long step) {
@@ -254,9 +282,15 @@ cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Ph
 }
 
 cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
-                          double fixed_dt, int advance, double r_p, double omega_p, double phi0,
-                          cudaStream_t s) {
-  k_finish<<<1, 256, 0, s>>>(ts, part, nparts, series, fixed_dt, advance, r_p, omega_p, phi0);
+                          double fixed_dt, int advance, int planet32, double r_p, double omega_p,
+                          double phi0, cudaStream_t s) {
+  k_finish<<<1, 256, 0, s>>>(ts, part, nparts, series, fixed_dt, advance, planet32, r_p, omega_p, phi0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0,
+                            cudaStream_t s) {
+  k_planet32<<<1, 1, 0, s>>>(ts, fixed_dt, r_p, omega_p, phi0);
   return cudaGetLastError();
 }
 

@@ -26,9 +26,16 @@ struct DevState {
   double torque;               // Gamma_z of the last completed step
   long long step;              // completed steps
   int status;                  // 0 or a DG_ERR_* code; set => every kernel is a no-op
-  int pending;                 // error flagged by a stage kernel, promoted by finish
+  int pending;                 // error bits of a stage kernel (1 numeric, 2 timeout), promoted by finish
   unsigned long long dt_bits;  // atomicMin slot for the next CFL step (bits of a double > 0)
   long long series_count;      // torque values written to the ring so far
+  // precision form: planet position at t^n + c dt for c = 0, 1/2, 1, each
+  // coordinate as an unevaluated pair of floats (x hi, x lo, y hi, y lo),
+  // the planet at t^{n+1} in FP64, and the step in use rounded to FP32;
+  // written once per step so that no stage CTA evaluates FP64 sin/cos
+  float plf[3][4];
+  double pl1[2];
+  float dtf;
 };
 
 // Physical parameters shared by all kernels of a handle.
@@ -80,11 +87,11 @@ struct Prec32 {
   int slope_half;          // slope == -1/2: Sigma_b = r^-1/2 by rsqrt
   int star, planet;
   float q, eps2;
-  double r_p, omega_p, phi0;
+  float x0p[2], y0p[2], dxp[2], dyp[2];  // x0, y0, dx, dy as (hi, lo) float pairs
   float rd_in, rd_out, damp_ratio;
   float cfl_fac;           // C / (2p + 1)
   // mesh geometry in FP32 (coefficients only; offsets from the planet are
-  // formed per CTA in FP64 and then rounded)
+  // formed per CTA in float-float arithmetic from the pairs above)
   float x0, y0, dx, dy, hdx, hdy, s2x, s2y, idx, idy, area;
   float near2;             // torque terms within sqrt(near2) of the planet use FP64
   double eps2_d;           // planet smoothing^2 in FP64 (near-planet torque terms)
@@ -106,7 +113,7 @@ struct StageArgs32 {
   double* part;
   Mesh mesh;
   Prec32 pc;
-  double cstage, fixed_dt;
+  int pidx;            // stage time t^n + c dt: DevState::plf row (c = 0, 1/2, 1 -> 0, 1, 2)
   float alpha, beta;
   int mode;
 };
@@ -151,8 +158,8 @@ cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s);
 cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
                        int nv, cudaStream_t s);
 cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
-                          double fixed_dt, int advance, double r_p, double omega_p, double phi0,
-                          cudaStream_t s);
+                          double fixed_dt, int advance, int planet32, double r_p, double omega_p,
+                          double phi0, cudaStream_t s);
 cudaError_t launch_to_tiled(const double* canon, double* tiled, const Mesh& mesh, int nv, int M,
                             cudaStream_t s);
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
@@ -160,6 +167,10 @@ cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,
                              int M, cudaStream_t s);
 cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s);
+// planet positions and FP32 step of the precision form for the current t and
+// step (fixed_dt > 0 replaces the CFL step)
+cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0,
+                            cudaStream_t s);
 
 // precision-form setup and conversions (dg_prec.cu)
 cudaError_t launch_delta_from_full(const double* full, const double* bg, float* d, size_t n,

@@ -38,6 +38,7 @@ static __constant__ float c32_wphi[MAXM][MAXM];   // w_q/2 phi_a(xi_q)
 static __constant__ float c32_wdphi[MAXM][MAXM];  // w_q/2 phi'_a(xi_q)
 static __constant__ float c32_pp[MAXM], c32_pm[MAXM], c32_xi[MAXM], c32_wh[MAXM];
 static __constant__ double c32_phi64[MAXM][MAXM], c32_xi64[MAXM], c32_wh64[MAXM];
+static __constant__ double c32_w2_64[MAXM * MAXM];  // [q*m + r] (w_q/2)(w_r/2)
 
 // Analytic background of the disc and the isothermal sound speed at (x, y).
 struct Bg32 {
@@ -170,8 +171,11 @@ __device__ __noinline__ void torque_node64(const double* bg, float dsig, int q, 
 template <int P>
 struct Smem32 {
   static constexpr int m = P + 1, M = m * m;
-  static constexpr int U = 0;                      // nodal values          [3][M][32]
-  static constexpr int F = U + 3 * M * 32;         // fx[3], fy[3] 2/dy, src[2] at nodes [8][M][32]
+  // nodal values [3][M][32]; the pointwise terms fx[3], fy[3] 2/dy, src[2]
+  // [8][M][32] overwrite them in place (planes 0-2 alias U: each node's
+  // values are read and replaced by the one thread that owns the node)
+  static constexpr int U = 0;
+  static constexpr int F = 0;
   static constexpr int XT = F + 8 * M * 32;        // x traces [2][3][m][33]: 0 right (slot e+1), 1 left (slot e)
   static constexpr int YT = XT + 2 * 3 * m * 33;   // own y traces [2][3][m][32]: 0 top, 1 bottom
   static constexpr int YN = YT + 2 * 3 * m * 32;   // neighbour traces [2][3][m][32]: 0 below's top, 1 above's bottom
@@ -187,6 +191,71 @@ struct Smem32 {
 // exact int -> float for 0 <= x < 2^23 on the integer and FP32 pipes (this
 // part executes conversion instructions on its narrow FP64 unit)
 __device__ __forceinline__ float i2f(int x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
+
+// ---- 1D bulk copies global -> shared by the TMA unit, completion counted in
+// transaction bytes on an mbarrier (one phase per kernel) ---------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(void* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (TMA) writes to it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(void* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// bytes and both addresses multiples of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, void* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(void* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity: false after ~2^22 polls
+// (a fraction of a second), so that a copy that never lands cannot hang the GPU
+__device__ __forceinline__ bool mbar_wait(void* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 22); i++) {
+    if (mbar_test(bar, parity)) return true;
+    if (i >= 8) __nanosleep(64);
+  }
+  return false;
+}
+
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// x0 + k dx - p as a normalised (hi, lo) float pair, from the float pairs of
+// x0, dx and p (float-float arithmetic on the FP32 pipe, ~2^-46 relative)
+__device__ __forceinline__ void ff_offset(float k, const float* x0p, const float* dxp, float ph,
+                                          float pl, float& hi, float& lo) {
+  const float p = k * dxp[0];
+  const float pe = fmaf(k, dxp[1], fmaf(k, dxp[0], -p));  // k dx - p, exact part by FMA
+  float s1, e1, s2, e2;
+  two_sum(x0p[0], p, s1, e1);
+  two_sum(s1, -ph, s2, e2);
+  const float t = (e1 + e2) + ((x0p[1] - pl) + pe);
+  hi = s2 + t;
+  lo = t - (hi - s2);
+}
 
 // modal -> nodal values of one variable of one element (registers), written to
 // u_out[n * 32] for node n = q*m + r; with xr/xl the x-face traces at the m
@@ -270,7 +339,7 @@ __device__ __forceinline__ void xtrace32(const float* c, const float* f, float* 
 
 // minimum resident CTAs per SM asked of the register allocator
 #ifndef DG_STAGE32_MIN_CTAS
-#define DG_STAGE32_MIN_CTAS 4
+#define DG_STAGE32_MIN_CTAS 5
 #endif
 
 // LAST = false: modes 0 (operator only) and 1 (RK stage); LAST = true: mode 2
@@ -305,33 +374,26 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   const int nvalid = min(32, ms.nx - i0);
   const bool valid = lane < nvalid;
   const int lc = valid ? lane : nvalid - 1;
-  const double dtd = (a.fixed_dt > 0.0) ? a.fixed_dt : a.ts->dt;
 
   if (tid == 0) {
-    sF[8] = (float)dtd;
-    // planet at the stage time and at t^{n+1}; centre of the tile's first
-    // element relative to each, formed in FP64 and kept as a pair of floats
-    // (hi, lo): a single rounding here would shift every element of the tile
-    // row by the same amount, a correlated error the torque sum does not
-    // average out
-    const double tn = a.ts->t;
-    const double xc0 = ms.x0 + (i0 + 0.5) * ms.dx, yc0 = ms.y0 + (j + 0.5) * ms.dy;
-    double sn, cs;
-    sincos(pc.omega_p * (tn + a.cstage * dtd) + pc.phi0, &sn, &cs);
-    double ox = xc0 - pc.r_p * cs, oy = yc0 - pc.r_p * sn;
-    sF[0] = (float)ox;
-    sF[1] = (float)oy;
-    sF[4] = (float)(ox - (double)sF[0]);
-    sF[5] = (float)(oy - (double)sF[1]);
-    sincos(pc.omega_p * (tn + dtd) + pc.phi0, &sn, &cs);
-    sD[0] = pc.r_p * cs;
-    sD[1] = pc.r_p * sn;
-    ox = xc0 - sD[0];
-    oy = yc0 - sD[1];
-    sF[2] = (float)ox;
-    sF[3] = (float)oy;
-    sF[6] = (float)(ox - (double)sF[2]);
-    sF[7] = (float)(oy - (double)sF[3]);
+    // centre of the tile's first element relative to the planet at the stage
+    // time and (last stage) at t^{n+1}, kept as (hi, lo) float pairs: a single
+    // rounding here would shift every element of the tile row by the same
+    // amount, a correlated error the torque sum does not average out
+    const DevState* ts = a.ts;
+    sF[8] = ts->dtf;
+    const float kx = i2f(i0) + 0.5f, ky = i2f(j) + 0.5f;
+    const float* pl = ts->plf[a.pidx];
+    ff_offset(kx, pc.x0p, pc.dxp, pl[0], pl[1], sF[0], sF[4]);
+    ff_offset(ky, pc.y0p, pc.dyp, pl[2], pl[3], sF[1], sF[5]);
+    if (LAST) {
+      const float* p1 = ts->plf[2];
+      ff_offset(kx, pc.x0p, pc.dxp, p1[0], p1[1], sF[2], sF[6]);
+      ff_offset(ky, pc.y0p, pc.dyp, p1[2], p1[3], sF[3], sF[7]);
+      sD[0] = ts->pl1[0];
+      sD[1] = ts->pl1[1];
+      mbar_init(smd + 14, 1);
+    }
   }
   if (tid < 32) sFlag[tid] = 0;
 
@@ -630,15 +692,44 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     return;
   }
   // ---- P4 (last stage): damping in delta form, torque, CFL --------------------
-  __syncthreads();  // every read of sU by P2 is done
+  // does any node of the tile lie in a damping zone (a conservative test on
+  // the tile's box; the per-node test below decides)
+  bool zones;
+  {
+    const float xlo = xt0, xhi = fmaf(i2f(nvalid), pc.dx, xt0);
+    const float cx = fminf(fmaxf(0.0f, xlo), xhi), cy = fminf(fmaxf(0.0f, yBf), yTf);
+    const float rmin2 = fmaf(cx, cx, cy * cy);
+    const float rmax2 = fmaxf(xlo * xlo, xhi * xhi) + fmaxf(yBf * yBf, yTf * yTf);
+    zones = (pc.rd_in > 0.0f && rmin2 < 1.001f * pc.rd_in * pc.rd_in) ||
+            (pc.rd_out > 0.0f && rmax2 > 0.999f * pc.rd_out * pc.rd_out);
+  }
+  // Sigma_b at the nodes (torque) and, in a damping tile, Q0 - Q_b (damping)
+  // are copied by the TMA unit into the face buffers, dead from here on,
+  // while the nodal values of the new state are formed
+  float* sSb = sXT;
+  float* sDb = sXT + M * 32;
+  static_assert(4 * M * 32 <= S::B0 - S::XT, "prefetch buffers exceed the face buffers");
+  fence_proxy_async_smem();
+  __syncthreads();  // every read of the pointwise terms and face fluxes by P3 is done
+  if (tid == 0) {
+    const unsigned bs = M * 32 * sizeof(float);
+    mbar_expect_tx(smd + 14, zones ? 4 * bs : bs);
+    bulk_g2s(sSb, a.SigbN + tile * (size_t)(M * 32), bs, smd + 14);
+    if (zones) bulk_g2s(sDb, a.Db + tile * (size_t)(3 * M * 32), 3 * bs, smd + 14);
+  }
   nodal32<P, false>(un, sU + voff + lane, nullptr, nullptr);
-  __syncthreads();
+  if (__syncthreads_or(!mbar_wait(smd + 14, 0))) {
+    // the copy did not land in time: flag the step (it is discarded) and
+    // give the copy a last bounded chance to drain before the CTA exits
+    if (tid == 0) atomicOr(&a.ts->pending, 2);
+    mbar_wait(smd + 14, 0);
+    return;
+  }
   int damped = 0;
   double gxd = 0.0, gyd = 0.0;
   {
-    const bool zones = (pc.rd_in > 0.0f) || (pc.rd_out > 0.0f);
-    const float* db = a.Db + tile * (size_t)(3 * M * 32);
-    const float* sbn = a.SigbN + tile * (size_t)(M * 32);
+    const float* db = sDb;
+    const float* sbn = sSb;
     const float cdx = fmaf(lanef, pc.dx, sF[2]), cdy = sF[3];
     const bool nearp = valid && fmaf(cdx, cdx, cdy * cdy) < pc.near2;
 #pragma unroll 1
@@ -704,8 +795,8 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
         tx = f * pdx;
         ty = f * pdy;
       }
-      sFl[(0 * M + n) * 32 + lane] = tx;
-      sFl[(1 * M + n) * 32 + lane] = ty;
+      sFl[(3 * M + n) * 32 + lane] = tx;  // planes 3, 4: free of the nodal values
+      sFl[(4 * M + n) * 32 + lane] = ty;
     }
   }
   if (damped) sFlag[lane] = 1;
@@ -738,16 +829,21 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = un[k];
   }
   sB0[v * 32 + lane] = un[0];
-  if (tid < 2 * M) {
+  if (v < 2) {
     // class sums of the FP32 torque terms over the 32 elements (a lane-rotated
-    // fixed order, free of bank conflicts), weighted in FP64
-    const int comp = tid >= M, n = tid - comp * M;
-    const float* col = sFl + (comp * M + n) * 32;
-    float s = 0.0f;
+    // fixed order, free of bank conflicts), weighted in FP64 and summed over
+    // the classes by a shuffle tree; warp 0 the x component, warp 1 the y one
+    double w = 0.0;
+    if (lane < M) {
+      const float* col = sFl + ((3 + v) * M + lane) * 32;
+      float s = 0.0f;
 #pragma unroll 8
-    for (int l = 0; l < 32; l++) s += col[(l + tid) & 31];
-    const int q = n / m, r = n - q * m;
-    sD[16 + tid] = c32_wh64[q] * c32_wh64[r] * ms.dx * ms.dy * (double)s;
+      for (int l = 0; l < 32; l++) s += col[(l + lane) & 31];
+      w = c32_w2_64[lane] * (double)s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) sD[16 + v] = w * (ms.dx * ms.dy);
   }
   if (__any_sync(0xffffffffu, gxd != 0.0 || gyd != 0.0)) {
 #pragma unroll
@@ -784,13 +880,8 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     if (lane == 0) {
       if (bad) atomicOr(&a.ts->pending, 1);
       atomicMin(&a.ts->dt_bits, (unsigned long long)__double_as_longlong((double)dtf));
-      double gx = sD[8] + sD[9] + sD[10], gy = sD[11] + sD[12] + sD[13];
-      for (int k = 0; k < M; k++) {
-        gx += sD[16 + k];
-        gy += sD[16 + M + k];
-      }
-      a.part[2 * tile] = gx;
-      a.part[2 * tile + 1] = gy;
+      a.part[2 * tile] = (sD[8] + sD[9]) + (sD[10] + sD[16]);
+      a.part[2 * tile + 1] = (sD[11] + sD[12]) + (sD[13] + sD[17]);
     }
   }
 }
@@ -840,6 +931,10 @@ cudaError_t upload_tables32_impl(const Tables& t) {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_phi64, t.phi, sizeof(t.phi));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_xi64, t.xi, sizeof(t.xi));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_wh64, t.wh, sizeof(t.wh));
+  double w2[MAXM * MAXM] = {};
+  for (int q = 0; q <= P; q++)
+    for (int r = 0; r <= P; r++) w2[q * (P + 1) + r] = t.wh[q] * t.wh[r];
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_w2_64, w2, sizeof(w2));
   return e;
 }
 
