@@ -213,7 +213,7 @@ def error_vs_fp64(dg, cfg, cfg32, nsteps):
             "rel_l2_sigma_minus_bg": rel(up[0] - sig_bg, ua[0] - sig_bg),
             "rel_l2_momentum": max(rel(up[1], ua[1]), rel(up[2], ua[2])),
             "rel_l2_torque_series": rel(tp, ta),
-            "bounds": {"sigma": 1e-5, "torque": 1e-4}}
+            "bounds": {"sigma": 1e-5, "torque": 1e-6}}
 
 
 def main():

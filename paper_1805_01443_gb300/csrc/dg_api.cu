@@ -201,6 +201,17 @@ cudaError_t launch_stage32_raw(const StageArgs32& a, int p, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_torque32_h(dg_handle* h, const float* D) {
+  const float* sb = h->SigbN;
+  switch (h->p) {
+    case 1: return launch_torque32_p1(D, sb, h->ts, h->part, h->dm, h->pc, h->stream);
+    case 2: return launch_torque32_p2(D, sb, h->ts, h->part, h->dm, h->pc, h->stream);
+    case 3: return launch_torque32_p3(D, sb, h->ts, h->part, h->dm, h->pc, h->stream);
+    case 4: return launch_torque32_p4(D, sb, h->ts, h->part, h->dm, h->pc, h->stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t record_start(dg_handle* h) {
   if (!h->ev) h->ev = new std::vector<cudaEvent_t>();
   std::vector<cudaEvent_t>& ev = *h->ev;
@@ -295,7 +306,7 @@ Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec) {
   L.state32 = L.nodes32 = L.db32 = L.bm032 = L.disc32 = L.flags = 0;
   if (prec == 1) {
     L.state32 = align256((size_t)mesh->ny * ntx * nvm * TILE * sizeof(float));
-    L.nodes32 = align256((size_t)mesh->ny * ntx * M * TILE * sizeof(float));
+    L.nodes32 = align256((size_t)mesh->ny * ntx * 2 * M * TILE * sizeof(float));
     L.db32 = align256((size_t)mesh->ny * ntx * 3 * M * TILE * sizeof(float));
     L.bm032 = align256((size_t)mesh->ny * ntx * 3 * TILE * sizeof(float));
     L.disc32 = align256((size_t)mesh->ny * ntx * TILE * sizeof(float));
@@ -341,12 +352,10 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
   StageArgs32 a;
   memset(&a, 0, sizeof(a));
   a.Rb = h->Rb;
-  a.SigbN = h->SigbN;
   a.Db = h->Db;
   a.Bm0 = h->Bm0;
   a.Bmodes = h->Bmodes;
   a.TileFlag = h->TileFlag;
-  a.BG64 = h->BG;
   a.ts = h->ts;
   a.part = h->part;
   a.mesh = h->dm;
@@ -369,6 +378,7 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
       a.D = h->DZ; a.Out = nx; a.alpha = 0.5f; a.beta = 0.5f; a.pidx = 2; a.mode = 2;
       CU(h, launch_stage32_h(h, a));
     }
+    CU(h, launch_torque32_h(h, nx));
     CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, 1, h->ph.r_p,
                         h->ph.omega_p, h->ph.phi0, h->stream));
     h->cur = 1 - h->cur;
@@ -513,6 +523,8 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     split(dm.y0, pc.y0p);
     split(dm.dx, pc.dxp);
     split(dm.dy, pc.dyp);
+    split(planet->eps * planet->eps, pc.eps2p);
+    pc.near2 = 0.09f;  // 0.3^2: the planet's envelope, where delta Sigma ~ Sigma_b
     pc.rd_in = (float)disc->rdamp_in;
     pc.rd_out = (float)disc->rdamp_out;
     pc.damp_ratio = (float)pow(1.15, 1.5);
@@ -528,11 +540,6 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     pc.idx = (float)(1.0 / dm.dx);
     pc.idy = (float)(1.0 / dm.dy);
     pc.area = (float)(dm.dx * dm.dy);
-#ifndef DG_TORQUE_NEAR2
-#define DG_TORQUE_NEAR2 0.04f
-#endif
-    pc.near2 = DG_TORQUE_NEAR2;  // FP64 torque terms within 0.2 of the planet
-    pc.eps2_d = planet->eps * planet->eps;
   }
 
   char* base;
@@ -693,13 +700,11 @@ int dg_rhs(dg_handle* h, double* out) {
     a.D = a.Dn = h->D[h->cur];
     a.Out = h->DZ;
     a.Rb = h->Rb;
-    a.SigbN = h->SigbN;
     a.Db = h->Db;
     a.Bm0 = h->Bm0;
     a.Bmodes = h->Bmodes;
     a.TileFlag = h->TileFlag;
-    a.BG64 = h->BG;
-    a.ts = h->ts;
+      a.ts = h->ts;
     a.part = h->part;
     a.mesh = h->dm;
     a.pc = h->pc;

@@ -88,13 +88,13 @@ struct Prec32 {
   int star, planet;
   float q, eps2;
   float x0p[2], y0p[2], dxp[2], dyp[2];  // x0, y0, dx, dy as (hi, lo) float pairs
+  float eps2p[2];          // planet smoothing^2 as a float pair (torque)
+  float near2;             // torque: float-float delta contraction within sqrt(near2) of the planet
   float rd_in, rd_out, damp_ratio;
   float cfl_fac;           // C / (2p + 1)
   // mesh geometry in FP32 (coefficients only; offsets from the planet are
   // formed per CTA in float-float arithmetic from the pairs above)
   float x0, y0, dx, dy, hdx, hdy, s2x, s2y, idx, idy, area;
-  float near2;             // torque terms within sqrt(near2) of the planet use FP64
-  double eps2_d;           // planet smoothing^2 in FP64 (near-planet torque terms)
 };
 
 // Arguments of one precision-form stage launch (tiled FP32 arrays).
@@ -103,12 +103,10 @@ struct StageArgs32 {
   const float* Dn;     // delta^n
   float* Out;
   const float* Rb;     // R_b = L(u_b), evaluated in FP64, stored FP32 [tile][var][mode][32]
-  const float* SigbN;  // Sigma_b at the m x m nodes [tile][node][32] (torque)
   const float* Db;     // Q0 - Q_b at the nodes for (Sigma, vx, vy) [tile][3][node][32] (damping)
   const float* Bm0;    // element averages of u_b [tile][3][32] (CFL)
   const float* Bmodes; // u_b modes in FP32 [tile][var][mode][32] (exact-background tiles)
   const int* TileFlag; // 1: the tile uses the exact projected background
-  const double* BG64;  // u_b modes in FP64, tiled (torque near the planet)
   DevState* ts;
   double* part;
   Mesh mesh;
@@ -134,6 +132,8 @@ struct Tables {
   cudaError_t upload_tables_p##P(const Tables& t);                                 \
   size_t stage_smem_p##P(int kind);                                                \
   cudaError_t launch_stage32_p##P(const StageArgs32& a, cudaStream_t s);          \
+  cudaError_t launch_torque32_p##P(const float* D, const float* SigbN, const DevState* ts, double* part, \
+                                   const Mesh& ms, const Prec32& pc, cudaStream_t s);               \
   cudaError_t upload_tables32_p##P(const Tables& t);
 DG_DECLARE_ORDER(1)
 DG_DECLARE_ORDER(2)

@@ -33,7 +33,7 @@ __global__ void k_f32_to_f64(const float* __restrict__ x, double* __restrict__ y
 
 // One thread per element: FP64 nodal values of the projected background u_b
 // at the m x m Gauss-Legendre nodes (dense contraction), giving
-//   Sigma_b(node)                         -> sigbn (torque node masses)
+//   Sigma_b(node) as a (hi, lo) float pair -> sigbn [tile][2][node][32] (torque node masses)
 //   Q0 - Q_b for Q = (Sigma, vx, vy)      -> db    (damping target offsets)
 //   element averages (mode 0) of u_b      -> bm0   (CFL step)
 __global__ void k_bg_nodes(const double* __restrict__ bg, float* __restrict__ sigbn,
@@ -92,7 +92,9 @@ __global__ void k_bg_nodes(const double* __restrict__ bg, float* __restrict__ si
       const double x = xc + 0.5 * ms.dx * tab.xi[q], y = yc + 0.5 * ms.dy * tab.xi[r];
       double w0[4];
       ic_prim(ph, ms, x, y, w0);
-      sigbn[(tile * M + n) * TILE + lane] = (float)u[0];
+      const float shi = (float)u[0];
+      sigbn[((tile * 2 + 0) * M + n) * TILE + lane] = shi;
+      sigbn[((tile * 2 + 1) * M + n) * TILE + lane] = (float)(u[0] - (double)shi);
       db[((tile * 3 + 0) * M + n) * TILE + lane] = (float)(w0[0] - u[0]);
       db[((tile * 3 + 1) * M + n) * TILE + lane] = (float)(w0[1] - u[1] / u[0]);
       db[((tile * 3 + 2) * M + n) * TILE + lane] = (float)(w0[2] - u[2] / u[0]);

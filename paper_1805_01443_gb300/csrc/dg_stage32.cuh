@@ -21,9 +21,9 @@
 // no shared-memory operand); shared memory only exchanges the nodal values,
 // face traces, pointwise fluxes and face fluxes between the three variable
 // threads of an element.  Pointwise and face work is dealt round-robin over
-// the three threads.  The last stage adds damping in delta form, the torque
-// (FP64 terms within a radius of the planet, compensated FP32 terms beyond,
-// FP64 weights and reduction) and the CFL minimum.
+// the three threads.  The last stage adds damping in delta form (tiles that
+// touch a zone) and the CFL minimum; the torque of the new state is a
+// separate one-variable pass (k_torque32 below).
 #pragma once
 #include "dg_internal.cuh"
 
@@ -37,8 +37,9 @@ static __constant__ float c32_phi[MAXM][MAXM];    // [q][a] sqrt(2a+1) P_a(xi_q)
 static __constant__ float c32_wphi[MAXM][MAXM];   // w_q/2 phi_a(xi_q)
 static __constant__ float c32_wdphi[MAXM][MAXM];  // w_q/2 phi'_a(xi_q)
 static __constant__ float c32_pp[MAXM], c32_pm[MAXM], c32_xi[MAXM], c32_wh[MAXM];
-static __constant__ double c32_phi64[MAXM][MAXM], c32_xi64[MAXM], c32_wh64[MAXM];
-static __constant__ double c32_w2_64[MAXM * MAXM];  // [q*m + r] (w_q/2)(w_r/2)
+// low parts of the FP64 tables as float pairs (float-float torque)
+static __constant__ float c32_phil[MAXM][MAXM], c32_xil[MAXM];
+static __constant__ float c32_w2h[MAXM * MAXM], c32_w2l[MAXM * MAXM];  // [q*m + r] (w_q/2)(w_r/2)
 
 // Analytic background of the disc and the isothermal sound speed at (x, y).
 struct Bg32 {
@@ -141,32 +142,6 @@ __device__ __noinline__ Bg32 bg32_poly(const float* bm, const float* fa, const f
   return r;
 }
 
-// FP64 torque term of node (q, r) of one element near the planet: node mass
-// from the FP64 background modes plus the FP32 perturbation.
-template <int P>
-__device__ __noinline__ void torque_node64(const double* bg, float dsig, int q, int r, double xcd,
-                                           double ycd, double xp, double yp, double hdx,
-                                           double hdy, double area, double eps2, double& gx,
-                                           double& gy) {
-  constexpr int m = P + 1;
-  double sb = 0.0;
-#pragma unroll
-  for (int aa = 0; aa < m; aa++) {
-    double t = 0.0;
-#pragma unroll
-    for (int b = 0; b < m; b++) t = fma(bg[(aa * m + b) * 32], c32_phi64[r][b], t);
-    sb = fma(c32_phi64[q][aa], t, sb);
-  }
-  const double mass = (sb + (double)dsig) * c32_wh64[q] * c32_wh64[r] * area;
-  const double ddx = xcd + hdx * c32_xi64[q] - xp;
-  const double ddy = ycd + hdy * c32_xi64[r] - yp;
-  const double d2 = fma(ddx, ddx, fma(ddy, ddy, eps2));
-  const double id = rsqrt(d2);
-  const double f = mass * id * id * id;
-  gx = fma(f, ddx, gx);
-  gy = fma(f, ddy, gy);
-}
-
 // Shared-memory plan (floats) of the precision-form stage kernel.
 template <int P>
 struct Smem32 {
@@ -184,7 +159,7 @@ struct Smem32 {
   static constexpr int B0 = FY + 2 * 3 * m * 32;   // element averages of the new state [3][32]
   static constexpr int FLAGS = B0 + 3 * 32;        // 32 ints
   static constexpr int TOTAL = FLAGS + 32;
-  static constexpr int ND = 16 + 2 * M;            // doubles: planet, offsets, torque partials
+  static constexpr int ND = 8;                     // 8-byte words: offsets, dt, mbarrier
   static constexpr size_t BYTES = (size_t)ND * sizeof(double) + (size_t)TOTAL * sizeof(float);
 };
 
@@ -236,25 +211,69 @@ __device__ __forceinline__ bool mbar_wait(void* bar, unsigned parity) {
   return false;
 }
 
+// ---- float-float ("double-float") arithmetic on the FP32 pipe --------------
+// The _rn intrinsics are never contracted into FMAs, which the error-free
+// transformations below rely on.
+
 // s + e = a + b exactly (Knuth's two-sum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// an unevaluated pair h + l with |l| <= ulp(h)/2 (~2^-46 relative)
+struct F2 {
+  float h, l;
+};
+__device__ __forceinline__ F2 f2_norm(float s, float e) {  // |e| small against s
+  F2 r;
+  r.h = __fadd_rn(s, e);
+  r.l = __fsub_rn(e, __fsub_rn(r.h, s));
+  return r;
+}
+__device__ __forceinline__ F2 f2_make(float h, float l) { return f2_norm(h, l); }
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return f2_norm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 f2_addf(F2 a, float b) {
+  float s, e;
+  two_sum(a.h, b, s, e);
+  return f2_norm(s, __fadd_rn(e, a.l));
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {  // exact product of the heads by an FMA
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)));
+  return f2_norm(p, e);
+}
+__device__ __forceinline__ F2 f2_mulf(F2 a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+  return f2_norm(p, e);
+}
+// 1/sqrt(d), d > 0: one Newton step y (1 + r/2), r = 1 - d y^2 formed in
+// float-float, from the hardware estimate (error ~ (3/2) eps0^2 ~ 2^-44)
+__device__ __forceinline__ F2 f2_rsqrt(F2 d) {
+  const float y = rsqrtf(d.h);
+  F2 y2;
+  y2.h = __fmul_rn(y, y);
+  y2.l = fmaf(y, y, -y2.h);
+  const F2 t = f2_mul(d, y2);
+  const float r = __fsub_rn(__fsub_rn(1.0f, t.h), t.l);  // 1 - t.h exact: t.h within [1/2, 2]
+  return f2_norm(y, __fmul_rn(__fmul_rn(0.5f, y), r));
 }
 
 // x0 + k dx - p as a normalised (hi, lo) float pair, from the float pairs of
 // x0, dx and p (float-float arithmetic on the FP32 pipe, ~2^-46 relative)
 __device__ __forceinline__ void ff_offset(float k, const float* x0p, const float* dxp, float ph,
                                           float pl, float& hi, float& lo) {
-  const float p = k * dxp[0];
-  const float pe = fmaf(k, dxp[1], fmaf(k, dxp[0], -p));  // k dx - p, exact part by FMA
-  float s1, e1, s2, e2;
-  two_sum(x0p[0], p, s1, e1);
-  two_sum(s1, -ph, s2, e2);
-  const float t = (e1 + e2) + ((x0p[1] - pl) + pe);
-  hi = s2 + t;
-  lo = t - (hi - s2);
+  const F2 kd = f2_mulf(F2{dxp[0], dxp[1]}, k);
+  F2 r = f2_add(F2{x0p[0], x0p[1]}, kd);
+  r = f2_add(r, F2{-ph, -pl});
+  hi = r.h;
+  lo = r.l;
 }
 
 // modal -> nodal values of one variable of one element (registers), written to
@@ -351,8 +370,9 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   constexpr int NVM = NV * M;
   using S = Smem32<P>;
   extern __shared__ double smd[];
-  double* sD = smd;                                 // [0,1] planet at t^{n+1}; [8..13] torque
-  float* sF = reinterpret_cast<float*>(smd + 2);    // tile offsets from the planets (hi, lo)
+  // smd[0..4]: floats sF[0..8] (tile offsets from the planet (hi, lo), dt);
+  // smd[7]: the mbarrier of the last stage's TMA copy
+  float* sF = reinterpret_cast<float*>(smd);
   float* sm = reinterpret_cast<float*>(smd + S::ND);
   float* sU = sm + S::U;
   float* sFl = sm + S::F;
@@ -386,14 +406,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     const float* pl = ts->plf[a.pidx];
     ff_offset(kx, pc.x0p, pc.dxp, pl[0], pl[1], sF[0], sF[4]);
     ff_offset(ky, pc.y0p, pc.dyp, pl[2], pl[3], sF[1], sF[5]);
-    if (LAST) {
-      const float* p1 = ts->plf[2];
-      ff_offset(kx, pc.x0p, pc.dxp, p1[0], p1[1], sF[2], sF[6]);
-      ff_offset(ky, pc.y0p, pc.dyp, p1[2], p1[3], sF[3], sF[7]);
-      sD[0] = ts->pl1[0];
-      sD[1] = ts->pl1[1];
-      mbar_init(smd + 14, 1);
-    }
+    if (LAST) mbar_init(smd + 7, 1);
   }
   if (tid < 32) sFlag[tid] = 0;
 
@@ -691,7 +704,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     }
     return;
   }
-  // ---- P4 (last stage): damping in delta form, torque, CFL --------------------
+  // ---- P4 (last stage): damping in delta form, CFL ---------------------------
   // does any node of the tile lie in a damping zone (a conservative test on
   // the tile's box; the per-node test below decides)
   bool zones;
@@ -703,35 +716,28 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     zones = (pc.rd_in > 0.0f && rmin2 < 1.001f * pc.rd_in * pc.rd_in) ||
             (pc.rd_out > 0.0f && rmax2 > 0.999f * pc.rd_out * pc.rd_out);
   }
-  // Sigma_b at the nodes (torque) and, in a damping tile, Q0 - Q_b (damping)
-  // are copied by the TMA unit into the face buffers, dead from here on,
-  // while the nodal values of the new state are formed
-  float* sSb = sXT;
-  float* sDb = sXT + M * 32;
-  static_assert(4 * M * 32 <= S::B0 - S::XT, "prefetch buffers exceed the face buffers");
-  fence_proxy_async_smem();
-  __syncthreads();  // every read of the pointwise terms and face fluxes by P3 is done
-  if (tid == 0) {
-    const unsigned bs = M * 32 * sizeof(float);
-    mbar_expect_tx(smd + 14, zones ? 4 * bs : bs);
-    bulk_g2s(sSb, a.SigbN + tile * (size_t)(M * 32), bs, smd + 14);
-    if (zones) bulk_g2s(sDb, a.Db + tile * (size_t)(3 * M * 32), 3 * bs, smd + 14);
-  }
-  nodal32<P, false>(un, sU + voff + lane, nullptr, nullptr);
-  if (__syncthreads_or(!mbar_wait(smd + 14, 0))) {
-    // the copy did not land in time: flag the step (it is discarded) and
-    // give the copy a last bounded chance to drain before the CTA exits
-    if (tid == 0) atomicOr(&a.ts->pending, 2);
-    mbar_wait(smd + 14, 0);
-    return;
-  }
-  int damped = 0;
-  double gxd = 0.0, gyd = 0.0;
-  {
-    const float* db = sDb;
-    const float* sbn = sSb;
-    const float cdx = fmaf(lanef, pc.dx, sF[2]), cdy = sF[3];
-    const bool nearp = valid && fmaf(cdx, cdx, cdy * cdy) < pc.near2;
+  if (zones) {
+    // the damping targets Q0 - Q_b at the nodes are copied by the TMA unit
+    // into the face buffers, dead from here on, while the nodal values of the
+    // new state are formed
+    float* sDb = sXT;
+    static_assert(3 * M * 32 <= S::B0 - S::XT, "prefetch buffer exceeds the face buffers");
+    fence_proxy_async_smem();
+    __syncthreads();  // every read of the pointwise terms and face fluxes by P3 is done
+    if (tid == 0) {
+      const unsigned bytes = 3 * M * 32 * sizeof(float);
+      mbar_expect_tx(smd + 7, bytes);
+      bulk_g2s(sDb, a.Db + tile * (size_t)(3 * M * 32), bytes, smd + 7);
+    }
+    nodal32<P, false>(un, sU + voff + lane, nullptr, nullptr);
+    if (__syncthreads_or(!mbar_wait(smd + 7, 0))) {
+      // the copy did not land in time: flag the step (it is discarded) and
+      // give the copy a last bounded chance to drain before the CTA exits
+      if (tid == 0) atomicOr(&a.ts->pending, 2);
+      mbar_wait(smd + 7, 0);
+      return;
+    }
+    int damped = 0;
 #pragma unroll 1
     for (int kk = 0; kk < (M + 2) / 3; kk++) {
       const int n = v + 3 * kk;
@@ -739,89 +745,65 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
       const int q = n / m, r = n - q * m;
       const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
       const float y = fmaf(pc.hdy, c32_xi[r], ycf);
-      float d0 = sU[(0 * M + n) * 32 + lane];
-      if (zones) {
-        const float rr = sqrt_fast(fmaf(xq, xq, y * y));
-        float R = 0.0f, rd = 0.0f;
-        if (pc.rd_in > 0.0f && rr < pc.rd_in) {
-          rd = pc.rd_in;
-          const float x = __fdividef(rr - rd, __fdividef(rd, pc.damp_ratio) - rd);
-          R = fminf(x * x, 1.0f);
-        } else if (pc.rd_out > 0.0f && rr > pc.rd_out) {
-          rd = pc.rd_out;
-          const float x = __fdividef(rr - rd, rd * pc.damp_ratio - rd);
-          R = fminf(x * x, 1.0f);
-        }
-        if (R > 0.0f) {
-          damped = 1;
-          // Q_new = Q0 + kappa (Q - Q0), kappa = tau / (tau + dt), written for
-          // delta Q = Q - Q_b: dQ_new = kappa dQ + (1 - kappa) (Q0 - Q_b)
-          const float tau = __fdividef(6.2831853071795864769f * sqrt_fast(rd * rd * rd), R);
-          const float itd = __fdividef(1.0f, tau + dt);
-          const float kap = tau * itd, omk = dt * itd;
-          Bg32 bgn = bg32_at(pc, xq, y);
-          if (exact) bgn = bg32_poly<P>(bgOwn, c32_phi[q], c32_phi[r], bgn.c2);
-          const float d1 = sU[(1 * M + n) * 32 + lane], d2 = sU[(2 * M + n) * 32 + lane];
-          const float sg = bgn.sig + d0;
-          const float isg = __fdividef(1.0f, sg);
-          const float dvx = (d1 - bgn.vx * d0) * isg;
-          const float dvy = (d2 - bgn.vy * d0) * isg;
-          const float ds2 = fmaf(kap, d0, omk * db[(0 * M + n) * 32 + lc]);
-          const float dvx2 = fmaf(kap, dvx, omk * db[(1 * M + n) * 32 + lc]);
-          const float dvy2 = fmaf(kap, dvy, omk * db[(2 * M + n) * 32 + lc]);
-          const float sg2 = bgn.sig + ds2;
-          d0 = ds2;
-          sU[(0 * M + n) * 32 + lane] = ds2;
-          sU[(1 * M + n) * 32 + lane] = fmaf(ds2, bgn.vx, sg2 * dvx2);
-          sU[(2 * M + n) * 32 + lane] = fmaf(ds2, bgn.vy, sg2 * dvy2);
-        }
+      const float rr = sqrt_fast(fmaf(xq, xq, y * y));
+      float R = 0.0f, rd = 0.0f;
+      if (pc.rd_in > 0.0f && rr < pc.rd_in) {
+        rd = pc.rd_in;
+        const float x = __fdividef(rr - rd, __fdividef(rd, pc.damp_ratio) - rd);
+        R = fminf(x * x, 1.0f);
+      } else if (pc.rd_out > 0.0f && rr > pc.rd_out) {
+        rd = pc.rd_out;
+        const float x = __fdividef(rr - rd, rd * pc.damp_ratio - rd);
+        R = fminf(x * x, 1.0f);
       }
-      // torque on the planet at t^{n+1}: FP64 terms near the planet; beyond,
-      // unweighted FP32 terms kept per node class (q, r) for the class sums
-      float tx = 0.0f, ty = 0.0f;
-      if (nearp) {
-        const double xcd = ms.x0 + (i0 + lane + 0.5) * ms.dx, ycd = ms.y0 + (j + 0.5) * ms.dy;
-        torque_node64<P>(a.BG64 + tile * NVM * 32 + lane, d0, q, r, xcd, ycd, sD[0], sD[1],
-                         0.5 * ms.dx, 0.5 * ms.dy, ms.dx * ms.dy, pc.eps2_d, gxd, gyd);
-      } else if (valid) {
-        const float sig = sbn[n * 32 + lane] + d0;
-        const float pdx = cdx + fmaf(pc.hdx, c32_xi[q], sF[6]);
-        const float pdy = cdy + fmaf(pc.hdy, c32_xi[r], sF[7]);
-        const float dd = fmaf(pdx, pdx, fmaf(pdy, pdy, pc.eps2));
-        // rsqrt refined by one Newton step: ~1 ulp, no bias of the raw approximation
-        float id = rsqrtf(dd);
-        id = id * fmaf(-0.5f * dd * id, id, 1.5f);
-        const float f = sig * (id * id * id);
-        tx = f * pdx;
-        ty = f * pdy;
+      if (R > 0.0f) {
+        damped = 1;
+        // Q_new = Q0 + kappa (Q - Q0), kappa = tau / (tau + dt), written for
+        // delta Q = Q - Q_b: dQ_new = kappa dQ + (1 - kappa) (Q0 - Q_b)
+        const float tau = __fdividef(6.2831853071795864769f * sqrt_fast(rd * rd * rd), R);
+        const float itd = __fdividef(1.0f, tau + dt);
+        const float kap = tau * itd, omk = dt * itd;
+        Bg32 bgn = bg32_at(pc, xq, y);
+        if (exact) bgn = bg32_poly<P>(bgOwn, c32_phi[q], c32_phi[r], bgn.c2);
+        const float d0 = sU[(0 * M + n) * 32 + lane];
+        const float d1 = sU[(1 * M + n) * 32 + lane], d2 = sU[(2 * M + n) * 32 + lane];
+        const float sg = bgn.sig + d0;
+        const float isg = __fdividef(1.0f, sg);
+        const float dvx = (d1 - bgn.vx * d0) * isg;
+        const float dvy = (d2 - bgn.vy * d0) * isg;
+        const float ds2 = fmaf(kap, d0, omk * sDb[(0 * M + n) * 32 + lc]);
+        const float dvx2 = fmaf(kap, dvx, omk * sDb[(1 * M + n) * 32 + lc]);
+        const float dvy2 = fmaf(kap, dvy, omk * sDb[(2 * M + n) * 32 + lc]);
+        const float sg2 = bgn.sig + ds2;
+        sU[(0 * M + n) * 32 + lane] = ds2;
+        sU[(1 * M + n) * 32 + lane] = fmaf(ds2, bgn.vx, sg2 * dvx2);
+        sU[(2 * M + n) * 32 + lane] = fmaf(ds2, bgn.vy, sg2 * dvy2);
       }
-      sFl[(3 * M + n) * 32 + lane] = tx;  // planes 3, 4: free of the nodal values
-      sFl[(4 * M + n) * 32 + lane] = ty;
     }
-  }
-  if (damped) sFlag[lane] = 1;
-  if (__syncthreads_or(damped)) {
-    if (sFlag[lane]) {
-      // back to modes by the m-point projection of the damped nodal values
-      float P1[m][m];  // [b][q] = sum_r w_r/2 phi_b(eta_r) u(q, r)
+    if (damped) sFlag[lane] = 1;
+    if (__syncthreads_or(damped)) {
+      if (sFlag[lane]) {
+        // back to modes by the m-point projection of the damped nodal values
+        float P1[m][m];  // [b][q] = sum_r w_r/2 phi_b(eta_r) u(q, r)
 #pragma unroll
-      for (int b = 0; b < m; b++)
+        for (int b = 0; b < m; b++)
 #pragma unroll
-        for (int q = 0; q < m; q++) {
-          float acc = 0.0f;
+          for (int q = 0; q < m; q++) {
+            float acc = 0.0f;
 #pragma unroll
-          for (int r = 0; r < m; r++) acc = fmaf(c32_wphi[r][b], sU[(v * M + q * m + r) * 32 + lane], acc);
-          P1[b][q] = acc;
-        }
+            for (int r = 0; r < m; r++) acc = fmaf(c32_wphi[r][b], sU[(v * M + q * m + r) * 32 + lane], acc);
+            P1[b][q] = acc;
+          }
 #pragma unroll
-      for (int aa = 0; aa < m; aa++)
+        for (int aa = 0; aa < m; aa++)
 #pragma unroll
-        for (int b = 0; b < m; b++) {
-          float acc = 0.0f;
+          for (int b = 0; b < m; b++) {
+            float acc = 0.0f;
 #pragma unroll
-          for (int q = 0; q < m; q++) acc = fmaf(c32_wphi[q][aa], P1[b][q], acc);
-          un[aa * m + b] = acc;
-        }
+            for (int q = 0; q < m; q++) acc = fmaf(c32_wphi[q][aa], P1[b][q], acc);
+            un[aa * m + b] = acc;
+          }
+      }
     }
   }
   if (valid) {
@@ -829,33 +811,6 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = un[k];
   }
   sB0[v * 32 + lane] = un[0];
-  if (v < 2) {
-    // class sums of the FP32 torque terms over the 32 elements (a lane-rotated
-    // fixed order, free of bank conflicts), weighted in FP64 and summed over
-    // the classes by a shuffle tree; warp 0 the x component, warp 1 the y one
-    double w = 0.0;
-    if (lane < M) {
-      const float* col = sFl + ((3 + v) * M + lane) * 32;
-      float s = 0.0f;
-#pragma unroll 8
-      for (int l = 0; l < 32; l++) s += col[(l + lane) & 31];
-      w = c32_w2_64[lane] * (double)s;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (lane == 0) sD[16 + v] = w * (ms.dx * ms.dy);
-  }
-  if (__any_sync(0xffffffffu, gxd != 0.0 || gyd != 0.0)) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      gxd += __shfl_xor_sync(0xffffffffu, gxd, o);
-      gyd += __shfl_xor_sync(0xffffffffu, gyd, o);
-    }
-  }
-  if (lane == 0) {
-    sD[8 + v] = gxd;
-    sD[11 + v] = gyd;
-  }
   __syncthreads();
   if (v == 0) {
     // CFL minimum of the new state from the element averages of u_b + delta
@@ -880,9 +835,133 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     if (lane == 0) {
       if (bad) atomicOr(&a.ts->pending, 1);
       atomicMin(&a.ts->dt_bits, (unsigned long long)__double_as_longlong((double)dtf));
-      a.part[2 * tile] = (sD[8] + sD[9]) + (sD[10] + sD[16]);
-      a.part[2 * tile + 1] = (sD[11] + sD[12]) + (sD[13] + sD[17]);
     }
+  }
+}
+
+// Torque on the planet at t^{n+1} from the new state (Sec. 5.1 torque with the
+// quadrature-node masses).  One warp per tile, lane e owns element e.  The
+// terms w_n m_n (r_n - r_p) / (|r_n - r_p|^2 + eps^2)^{3/2} are large and
+// cancel to a few 1e-5 of their absolute sum, and their absolute sum is
+// spread evenly over the decades of distance from the planet, so every term
+// is evaluated and summed in float-float arithmetic (~2^-44 relative): node
+// mass Sigma_b (a float pair from the FP64 background) + delta Sigma, offsets
+// from the planet as float pairs from the FP64 position, the inverse cube by
+// a float-float Newton step.  delta Sigma at the nodes is contracted in FP32
+// (its rounding is ~1e-7 of delta, far below the mass where delta << Sigma_b)
+// and in float-float within sqrt(near2) of the planet, where delta ~ Sigma_b.
+// The per-tile pair is stored as a double; the finish kernel sums the tiles
+// in FP64.
+template <int P>
+__global__ void __launch_bounds__(128) k_torque32(const float* D, const float* SigbN, const DevState* ts,
+                                                   double* part, const Mesh ms, const Prec32 pc) {
+  constexpr int m = P + 1, M = m * m, NVM = 3 * M;
+  if (ts->status != 0) return;
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int ntiles = ms.ntx * ms.ny;
+  if (tile >= ntiles) return;  // warp-uniform
+  const int j = tile / ms.ntx, bx = tile - j * ms.ntx;
+  const int i = bx * 32 + lane;
+  const bool valid = i < ms.nx;
+  const int lc = valid ? lane : 0;
+  const float* dsig = D + (size_t)tile * NVM * 32 + lc;  // variable 0
+  const float* sbh = SigbN + (size_t)tile * 2 * M * 32 + lc;
+  const float* sbl = sbh + M * 32;
+  const float* p1 = ts->plf[2];
+  F2 ox, oy;
+  ff_offset(i2f(i) + 0.5f, pc.x0p, pc.dxp, p1[0], p1[1], ox.h, ox.l);
+  ff_offset(i2f(j) + 0.5f, pc.y0p, pc.dyp, p1[2], p1[3], oy.h, oy.l);
+  const bool near = valid && fmaf(ox.h, ox.h, oy.h * oy.h) < pc.near2;
+  // delta Sigma at the nodes, [q][r]
+  float dsn[m][m], dsl[m][m];
+  {
+    float c[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) c[k] = dsig[k * 32];
+    if (__any_sync(0xffffffffu, near)) {
+      F2 T[m][m];  // [a][r] = sum_b c_ab phi_b(eta_r), float-float
+#pragma unroll
+      for (int aa = 0; aa < m; aa++)
+#pragma unroll
+        for (int r = 0; r < m; r++) {
+          F2 acc{0.0f, 0.0f};
+#pragma unroll
+          for (int b = 0; b < m; b++) acc = f2_add(acc, f2_mulf(F2{c32_phi[r][b], c32_phil[r][b]}, c[aa * m + b]));
+          T[aa][r] = acc;
+        }
+#pragma unroll
+      for (int q = 0; q < m; q++)
+#pragma unroll
+        for (int r = 0; r < m; r++) {
+          F2 acc{0.0f, 0.0f};
+#pragma unroll
+          for (int aa = 0; aa < m; aa++) acc = f2_add(acc, f2_mul(F2{c32_phi[q][aa], c32_phil[q][aa]}, T[aa][r]));
+          dsn[q][r] = acc.h;
+          dsl[q][r] = acc.l;
+        }
+    } else {
+      float T[m][m];
+#pragma unroll
+      for (int aa = 0; aa < m; aa++)
+#pragma unroll
+        for (int r = 0; r < m; r++) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32_phi[r][b], acc);
+          T[aa][r] = acc;
+        }
+#pragma unroll
+      for (int q = 0; q < m; q++)
+#pragma unroll
+        for (int r = 0; r < m; r++) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], T[aa][r], acc);
+          dsn[q][r] = acc;
+          dsl[q][r] = 0.0f;
+        }
+    }
+  }
+  // offsets of the node rows and columns from the planet, and their squares
+  const F2 hdx{0.5f * pc.dxp[0], 0.5f * pc.dxp[1]}, hdy{0.5f * pc.dyp[0], 0.5f * pc.dyp[1]};
+  F2 px[m], py[m], px2[m], py2[m];
+#pragma unroll
+  for (int q = 0; q < m; q++) {
+    const F2 xi{c32_xi[q], c32_xil[q]};
+    px[q] = f2_add(ox, f2_mul(hdx, xi));
+    py[q] = f2_add(oy, f2_mul(hdy, xi));
+    px2[q] = f2_mul(px[q], px[q]);
+    py2[q] = f2_mul(py[q], py[q]);
+  }
+  const F2 eps2{pc.eps2p[0], pc.eps2p[1]};
+  F2 gx{0.0f, 0.0f}, gy{0.0f, 0.0f};
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < m; q++) {
+#pragma unroll
+      for (int r = 0; r < m; r++) {
+        const int n = q * m + r;
+        // w_n (Sigma_b + delta Sigma)
+        F2 mass = f2_add(F2{sbh[n * 32], sbl[n * 32]}, F2{dsn[q][r], dsl[q][r]});
+        mass = f2_mul(mass, F2{c32_w2h[n], c32_w2l[n]});
+        const F2 id = f2_rsqrt(f2_add(f2_add(px2[q], py2[r]), eps2));
+        const F2 f = f2_mul(mass, f2_mul(f2_mul(id, id), id));
+        gx = f2_add(gx, f2_mul(f, px[q]));
+        gy = f2_add(gy, f2_mul(f, py[r]));
+      }
+    }
+  }
+  // warp sum of the pairs
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gx = f2_add(gx, F2{__shfl_xor_sync(0xffffffffu, gx.h, o), __shfl_xor_sync(0xffffffffu, gx.l, o)});
+    gy = f2_add(gy, F2{__shfl_xor_sync(0xffffffffu, gy.h, o), __shfl_xor_sync(0xffffffffu, gy.l, o)});
+  }
+  if (lane == 0) {
+    const double area = ms.dx * ms.dy;
+    part[2 * tile] = ((double)gx.h + (double)gx.l) * area;
+    part[2 * tile + 1] = ((double)gy.h + (double)gy.l) * area;
   }
 }
 
@@ -907,6 +986,14 @@ cudaError_t launch_stage32_impl(const StageArgs32& a, cudaStream_t s) {
 }
 
 template <int P>
+cudaError_t launch_torque32_impl(const float* D, const float* SigbN, const DevState* ts, double* part,
+                                 const Mesh& ms, const Prec32& pc, cudaStream_t s) {
+  const int ntiles = ms.ntx * ms.ny;
+  k_torque32<P><<<(ntiles + 3) / 4, 128, 0, s>>>(D, SigbN, ts, part, ms, pc);
+  return cudaGetLastError();
+}
+
+template <int P>
 cudaError_t upload_tables32_impl(const Tables& t) {
   float phi[MAXM][MAXM] = {}, wphi[MAXM][MAXM] = {}, wdphi[MAXM][MAXM] = {};
   float pp[MAXM] = {}, pm[MAXM] = {}, xi[MAXM] = {}, wh[MAXM] = {};
@@ -928,13 +1015,20 @@ cudaError_t upload_tables32_impl(const Tables& t) {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_pm, pm, sizeof(pm));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_xi, xi, sizeof(xi));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_wh, wh, sizeof(wh));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_phi64, t.phi, sizeof(t.phi));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_xi64, t.xi, sizeof(t.xi));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_wh64, t.wh, sizeof(t.wh));
-  double w2[MAXM * MAXM] = {};
-  for (int q = 0; q <= P; q++)
-    for (int r = 0; r <= P; r++) w2[q * (P + 1) + r] = t.wh[q] * t.wh[r];
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_w2_64, w2, sizeof(w2));
+  float phil[MAXM][MAXM] = {}, xil[MAXM] = {}, w2h[MAXM * MAXM] = {}, w2l[MAXM * MAXM] = {};
+  for (int q = 0; q <= P; q++) {
+    xil[q] = (float)(t.xi[q] - (double)xi[q]);
+    for (int a = 0; a <= P; a++) phil[q][a] = (float)(t.phi[q][a] - (double)phi[q][a]);
+    for (int r = 0; r <= P; r++) {
+      const double w2 = t.wh[q] * t.wh[r];
+      w2h[q * (P + 1) + r] = (float)w2;
+      w2l[q * (P + 1) + r] = (float)(w2 - (double)w2h[q * (P + 1) + r]);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_phil, phil, sizeof(phil));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_xil, xil, sizeof(xil));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_w2h, w2h, sizeof(w2h));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_w2l, w2l, sizeof(w2l));
   return e;
 }
 

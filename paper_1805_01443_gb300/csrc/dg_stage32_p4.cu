@@ -4,5 +4,9 @@
 
 namespace dg {
 cudaError_t launch_stage32_p4(const StageArgs32& a, cudaStream_t s) { return launch_stage32_impl<4>(a, s); }
+cudaError_t launch_torque32_p4(const float* D, const float* SigbN, const DevState* ts, double* part,
+                                const Mesh& ms, const Prec32& pc, cudaStream_t s) {
+  return launch_torque32_impl<4>(D, SigbN, ts, part, ms, pc, s);
+}
 cudaError_t upload_tables32_p4(const Tables& t) { return upload_tables32_impl<4>(t); }
 }  // namespace dg
