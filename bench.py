@@ -34,12 +34,15 @@ WORKLOAD = "planet-disc P4 512x512 (q=3e-5, damping 0.4/2.1, SSP(3,3), torque ev
 # u^(s+1) written on average over the 3 SSP(3,3) stages)
 FLOP_PER_ELEM_STAGE = 10.0e3
 BYTES_PER_ELEM_STAGE_FP64 = 1600.0
-# precision form (FP32 delta, 75 floats = 300 B per element and array): reads
-# delta^(s), delta^n (stages 2, 3) and R_b, writes delta^(s+1); the last stage
-# also reads the nodal background density (100 B), the background averages
-# (12 B) and, in damped elements (47 % at 512^2), the damping offsets (300 B):
-# (900 + 1200 + 1200 + 100 + 12 + 141) / 3 = 1184 B per element per stage
-BYTES_PER_ELEM_STAGE_PREC = 1184.0
+# precision form (FP32 delta, 75 floats = 300 B per element and array): a stage
+# reads delta^(s), delta^n (stages 2, 3) and R_b and writes delta^(s+1); the
+# last stage also reads the background averages (12 B) and, in the tiles that
+# touch a damping zone (53.5 % of the 32-element tiles at 512^2), the damping
+# offsets (300 B): (900 + 1200 + 1200 + 12 + 160) / 3 = 1157 B per element and
+# stage launch.  The torque pass reads delta Sigma (100 B) and Sigma_b at the
+# nodes as a float pair (200 B) once per step.
+BYTES_PER_ELEM_STAGE_PREC = 1157.0
+BYTES_PER_ELEM_TORQUE_PREC = 300.0
 # FP64 peak of GB300 derived from unit counts and clock: 2 FP64 FMA / clk / SM
 # x 152 SMs x 2 flop x 2.07 GHz = 1.26 TFLOP/s
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12

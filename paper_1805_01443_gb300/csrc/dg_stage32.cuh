@@ -873,81 +873,74 @@ __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* S
   ff_offset(i2f(i) + 0.5f, pc.x0p, pc.dxp, p1[0], p1[1], ox.h, ox.l);
   ff_offset(i2f(j) + 0.5f, pc.y0p, pc.dyp, p1[2], p1[3], oy.h, oy.l);
   const bool near = valid && fmaf(ox.h, ox.h, oy.h * oy.h) < pc.near2;
-  // delta Sigma at the nodes, [q][r]
-  float dsn[m][m], dsl[m][m];
+  const bool ffw = __any_sync(0xffffffffu, near);  // float-float delta contraction in this warp
+  // T[a][r] = sum_b c_ab phi_b(eta_r) (head, and tail in a float-float warp)
+  float Th[m][m], Tl[m][m];
   {
     float c[M];
 #pragma unroll
     for (int k = 0; k < M; k++) c[k] = dsig[k * 32];
-    if (__any_sync(0xffffffffu, near)) {
-      F2 T[m][m];  // [a][r] = sum_b c_ab phi_b(eta_r), float-float
 #pragma unroll
-      for (int aa = 0; aa < m; aa++)
+    for (int aa = 0; aa < m; aa++)
 #pragma unroll
-        for (int r = 0; r < m; r++) {
+      for (int r = 0; r < m; r++) {
+        if (ffw) {
           F2 acc{0.0f, 0.0f};
 #pragma unroll
           for (int b = 0; b < m; b++) acc = f2_add(acc, f2_mulf(F2{c32_phi[r][b], c32_phil[r][b]}, c[aa * m + b]));
-          T[aa][r] = acc;
-        }
-#pragma unroll
-      for (int q = 0; q < m; q++)
-#pragma unroll
-        for (int r = 0; r < m; r++) {
-          F2 acc{0.0f, 0.0f};
-#pragma unroll
-          for (int aa = 0; aa < m; aa++) acc = f2_add(acc, f2_mul(F2{c32_phi[q][aa], c32_phil[q][aa]}, T[aa][r]));
-          dsn[q][r] = acc.h;
-          dsl[q][r] = acc.l;
-        }
-    } else {
-      float T[m][m];
-#pragma unroll
-      for (int aa = 0; aa < m; aa++)
-#pragma unroll
-        for (int r = 0; r < m; r++) {
+          Th[aa][r] = acc.h;
+          Tl[aa][r] = acc.l;
+        } else {
           float acc = 0.0f;
 #pragma unroll
           for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32_phi[r][b], acc);
-          T[aa][r] = acc;
+          Th[aa][r] = acc;
+          Tl[aa][r] = 0.0f;
         }
-#pragma unroll
-      for (int q = 0; q < m; q++)
-#pragma unroll
-        for (int r = 0; r < m; r++) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], T[aa][r], acc);
-          dsn[q][r] = acc;
-          dsl[q][r] = 0.0f;
-        }
-    }
+      }
   }
-  // offsets of the node rows and columns from the planet, and their squares
   const F2 hdx{0.5f * pc.dxp[0], 0.5f * pc.dxp[1]}, hdy{0.5f * pc.dyp[0], 0.5f * pc.dyp[1]};
-  F2 px[m], py[m], px2[m], py2[m];
-#pragma unroll
-  for (int q = 0; q < m; q++) {
-    const F2 xi{c32_xi[q], c32_xil[q]};
-    px[q] = f2_add(ox, f2_mul(hdx, xi));
-    py[q] = f2_add(oy, f2_mul(hdy, xi));
-    px2[q] = f2_mul(px[q], px[q]);
-    py2[q] = f2_mul(py[q], py[q]);
-  }
   const F2 eps2{pc.eps2p[0], pc.eps2p[1]};
+  // offsets of the node columns from the planet and their squares plus eps^2
+  F2 py[m], pye[m];
+#pragma unroll
+  for (int r = 0; r < m; r++) {
+    py[r] = f2_add(oy, f2_mul(hdy, F2{c32_xi[r], c32_xil[r]}));
+    pye[r] = f2_add(f2_mul(py[r], py[r]), eps2);
+  }
   F2 gx{0.0f, 0.0f}, gy{0.0f, 0.0f};
   if (valid) {
-#pragma unroll
+    // one node row q per iteration (rolled: the float-float body is long)
+#pragma unroll 1
     for (int q = 0; q < m; q++) {
+      float sh[m], sl[m];
 #pragma unroll
       for (int r = 0; r < m; r++) {
+        sh[r] = sbh[(q * m + r) * 32];
+        sl[r] = sbl[(q * m + r) * 32];
+      }
+      const F2 px = f2_add(ox, f2_mul(hdx, F2{c32_xi[q], c32_xil[q]}));
+      const F2 px2 = f2_mul(px, px);
+#pragma unroll
+      for (int r = 0; r < m; r++) {
+        // delta Sigma at node (q, r)
+        F2 ds{0.0f, 0.0f};
+        if (ffw) {
+#pragma unroll
+          for (int aa = 0; aa < m; aa++)
+            ds = f2_add(ds, f2_mul(F2{c32_phi[q][aa], c32_phil[q][aa]}, F2{Th[aa][r], Tl[aa][r]}));
+        } else {
+          float acc = 0.0f;
+#pragma unroll
+          for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], Th[aa][r], acc);
+          ds.h = acc;
+        }
+        // w_n (Sigma_b + delta Sigma) / (d^2 + eps^2)^{3/2}
         const int n = q * m + r;
-        // w_n (Sigma_b + delta Sigma)
-        F2 mass = f2_add(F2{sbh[n * 32], sbl[n * 32]}, F2{dsn[q][r], dsl[q][r]});
-        mass = f2_mul(mass, F2{c32_w2h[n], c32_w2l[n]});
-        const F2 id = f2_rsqrt(f2_add(f2_add(px2[q], py2[r]), eps2));
+        const F2 mass = f2_mul(f2_add(F2{sh[r], sl[r]}, ds), F2{c32_w2h[n], c32_w2l[n]});
+        const F2 id = f2_rsqrt(f2_add(px2, pye[r]));
         const F2 f = f2_mul(mass, f2_mul(f2_mul(id, id), id));
-        gx = f2_add(gx, f2_mul(f, px[q]));
+        gx = f2_add(gx, f2_mul(f, px));
         gy = f2_add(gy, f2_mul(f, py[r]));
       }
     }
