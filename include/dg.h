@@ -222,8 +222,67 @@ int dg_conserved_static(const double *coeffs, int nv, int nmodes, int nx, int ny
 /* Release the handle and the device memory it allocated. */
 int dg_destroy(dg_handle *h);
 
-/* Static description of the last error of h (or of the last failed dg_init for NULL). */
+/* Static description of the last error of h (or of the last failed dg_init
+   or dg_batch_* call of this thread for NULL). */
 const char *dg_last_error(dg_handle *h);
+
+/* ---- Batched precision form ------------------------------------------------
+   Many independent discs (the Sec. 5.1 problem with its own mesh size, degree,
+   planet mass and seed each) advanced together on one GPU.  The paper runs one
+   disc over many GPUs (Sec. 3.1); it has no batched form.  Each RK stage of
+   every instance is one launch over the 32-element tiles of all instances
+   (mixed degrees), with persistent CTAs that take (instance, tile) work items
+   from a device counter in a tuned order; the torque of every instance and
+   its end-of-step work (torque sum, time advance, CFL step) are one launch
+   each.  One step is captured as a CUDA graph and replayed.  Every instance
+   keeps its own CFL step, time, torque series and error status, and gives the
+   same results as dg_step on its own handle (same kernels, same arithmetic);
+   after batched steps the handles are used as usual (dg_fetch, dg_torque...).
+
+   Requirements: 1 <= n <= DG_BATCH_MAX handles, each created with
+   disc.prec = 1 and disc.rk = 3 (locally isothermal), all on the same stream
+   and device, each in at most one batch.  The batch keeps pointers to the
+   handles, which must outlive it; it owns a CUDA stream, two events, its
+   work table and three counters.  Batched work is ordered after everything
+   queued on the handles' stream before the call and before everything queued
+   there after it.  Errors: DG_ERR_ARG (bad argument), DG_ERR_UNSUPPORTED
+   (a handle not in the precision form or not SSP(3,3)), DG_ERR_CUDA,
+   DG_ERR_NOMEM; device-side errors of an instance surface on that handle
+   (and in dg_batch_sync) as for dg_step. */
+#define DG_BATCH_MAX 64
+typedef struct dg_batch dg_batch;
+
+int dg_batch_create(dg_batch **b, dg_handle *const *handles, int n);
+
+/* Schedule of the batched stage launches:
+     policy       work order: 0 instances as given, 1 costliest tiles first
+                  (highest degree, then largest instance), 2 one tile row of
+                  each instance in turn
+     dynamic      1: persistent CTAs (ctas_per_sm per SM) take items from a
+                  counter; 0: one CTA per tile in work order
+     ctas_per_sm  resident CTAs per SM of the persistent grid (0 or above the
+                  occupancy limit: the limit)
+   Default: policy 1, dynamic 1, the occupancy limit. */
+int dg_batch_config(dg_batch *b, int policy, int dynamic, int ctas_per_sm);
+int dg_batch_get_config(const dg_batch *b, int *policy, int *dynamic, int *ctas_per_sm);
+
+/* Autotuner: times `steps` batched steps under each schedule (3 work orders x
+   {persistent at the occupancy limit, one CTA below it, one CTA per tile}),
+   keeps the fastest and returns it (any output pointer may be NULL; best_ms
+   is the time of one batched step).  The instances are restored afterwards
+   (state, time, step count), so tuning does not advance them.  Synchronous. */
+int dg_batch_tune(dg_batch *b, int steps, int *policy, int *dynamic, int *ctas_per_sm,
+                  double *best_ms);
+
+/* nsteps SSP(3,3) steps of every instance, each with its own CFL step.
+   Asynchronous. */
+int dg_batch_step(dg_batch *b, int nsteps);
+
+/* Wait for the batch; DG_OK or the first instance's error code. */
+int dg_batch_sync(dg_batch *b);
+
+/* Release the batch (not the handles). */
+int dg_batch_destroy(dg_batch *b);
 
 #ifdef __cplusplus
 }

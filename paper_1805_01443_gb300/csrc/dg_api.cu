@@ -878,4 +878,359 @@ int dg_destroy(dg_handle* h) {
   return DG_OK;
 }
 
+// ---- batched precision form --------------------------------------------------
+
+struct dg_batch {
+  int n;
+  dg_handle* h[BATCH_MAX];
+  cudaStream_t hstream;  // the handles' stream
+  cudaStream_t stream;   // the batch's own stream (capturable), joined to hstream by events
+  cudaEvent_t ev_in, ev_out;
+  BatchLaunch32* L;   // host copy of the launch arguments (captured by value)
+  int* d_counter;     // work counters of the three stages
+  int* d_items;       // work order
+  int policy, dynamic, ctas_per_sm, sms;
+  cudaGraphExec_t exec;
+  bool graph_ok;
+};
+
+namespace {
+
+double tile_cost(const dg_handle* h) { return (double)(h->p + 1) * (h->p + 1); }
+
+// work order: 0 instances as given; 1 the costliest tiles (highest degree,
+// then largest instance) first; 2 one tile row from each instance in turn
+int batch_items(dg_batch* b) {
+  BatchLaunch32& L = *b->L;
+  std::vector<int> order(b->n), items;
+  for (int k = 0; k < b->n; k++) order[k] = k;
+  if (b->policy == 1) {
+    std::vector<int> o2;
+    std::vector<bool> used(b->n, false);
+    for (int r = 0; r < b->n; r++) {
+      int best = -1;
+      for (int k = 0; k < b->n; k++) {
+        if (used[k]) continue;
+        const double ck = tile_cost(b->h[k]), cb = best < 0 ? -1.0 : tile_cost(b->h[best]);
+        const int nk = L.tile0[k + 1] - L.tile0[k], nb = best < 0 ? -1 : L.tile0[best + 1] - L.tile0[best];
+        if (best < 0 || ck > cb || (ck == cb && nk > nb)) best = k;
+      }
+      used[best] = true;
+      o2.push_back(best);
+    }
+    order = o2;
+  }
+  items.reserve(L.nitems);
+  if (b->policy == 2) {
+    std::vector<int> row(b->n, 0);
+    bool more = true;
+    while (more) {
+      more = false;
+      for (int k = 0; k < b->n; k++) {
+        const Mesh& ms = b->h[k]->dm;
+        if (row[k] >= ms.ny) continue;
+        for (int bx = 0; bx < ms.ntx; bx++) items.push_back((k << 25) | (row[k] * ms.ntx + bx));
+        row[k]++;
+        more = true;
+      }
+    }
+  } else {
+    for (int k : order)
+      for (int t = 0; t < L.tile0[k + 1] - L.tile0[k]; t++) items.push_back((k << 25) | t);
+  }
+  if ((int)items.size() != L.nitems) return fail(nullptr, DG_ERR_ARG, "batch: work table size");
+  cudaError_t e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(nullptr, DG_ERR_CUDA, "batch: %s", cudaGetErrorString(e));
+  return DG_OK;
+}
+
+// per-instance ping-pong bookkeeping as the handles see it now
+bool batch_refresh(dg_batch* b) {
+  bool changed = false;
+  for (int k = 0; k < b->n; k++) {
+    BatchInst32& I = b->L->inst[k];
+    if (I.cur0 != b->h[k]->cur0 || I.step0 != b->h[k]->step0) changed = true;
+    I.cur0 = b->h[k]->cur0;
+    I.step0 = b->h[k]->step0;
+  }
+  return changed;
+}
+
+int batch_grid(const dg_batch* b) {
+  if (!b->dynamic) return b->L->nitems;
+  const int g = b->sms * b->ctas_per_sm;
+  return g < b->L->nitems ? g : b->L->nitems;
+}
+
+// one SSP(3,3) step of every instance, as stream work
+cudaError_t batch_enqueue_step(dg_batch* b) {
+  BatchLaunch32& L = *b->L;
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(int), b->stream);
+  for (int st = 0; st < 3 && e == cudaSuccess; st++) {
+    L.stage = st;
+    L.counter = b->d_counter + st;
+    e = launch_batch_stage32(L, batch_grid(b), b->stream);
+  }
+  if (e == cudaSuccess) e = launch_batch_torque32(L, b->stream);
+  if (e == cudaSuccess) e = launch_batch_finish(L, b->stream);
+  return e;
+}
+
+int batch_capture(dg_batch* b) {
+  if (b->graph_ok) {
+    cudaGraphExecDestroy(b->exec);
+    b->graph_ok = false;
+  }
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = batch_enqueue_step(b);
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+  }
+  if (e != cudaSuccess) return fail(nullptr, DG_ERR_CUDA, "batch graph: %s", cudaGetErrorString(e));
+  b->graph_ok = true;
+  return DG_OK;
+}
+
+int batch_run(dg_batch* b, int nsteps) {
+  if (batch_refresh(b) || !b->graph_ok) {
+    int rc = batch_capture(b);
+    if (rc) return rc;
+  }
+  // after everything queued on the handles' stream; the handles' stream in
+  // turn waits for the batch
+  cudaError_t e = cudaEventRecord(b->ev_in, b->hstream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+  if (e == cudaSuccess) e = launch_batch_planet32(*b->L, b->stream);
+  for (int s = 0; s < nsteps && e == cudaSuccess; s++) e = cudaGraphLaunch(b->exec, b->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hstream, b->ev_out, 0);
+  if (e != cudaSuccess) return fail(nullptr, DG_ERR_CUDA, "batch step: %s", cudaGetErrorString(e));
+  for (int k = 0; k < b->n; k++) b->h[k]->cur ^= (nsteps & 1);
+  return DG_OK;
+}
+
+}  // namespace
+
+int dg_batch_destroy(dg_batch* b);
+
+int dg_batch_create(dg_batch** out, dg_handle* const* hs, int n) {
+  if (!out || !hs || n < 1 || n > BATCH_MAX) return fail(nullptr, DG_ERR_ARG, "batch: 1 <= n <= %d handles", BATCH_MAX);
+  *out = nullptr;
+  const Tables* tabs[MAXP + 1] = {};
+  long long tiles = 0;
+  for (int k = 0; k < n; k++) {
+    const dg_handle* h = hs[k];
+    if (!h) return fail(nullptr, DG_ERR_ARG, "batch: null handle %d", k);
+    if (h->prec != 1 || h->disc.rk != 3)
+      return fail(nullptr, DG_ERR_UNSUPPORTED, "batch: handle %d is not the precision form with SSP(3,3)", k);
+    if (h->stream != hs[0]->stream) return fail(nullptr, DG_ERR_ARG, "batch: handles on different streams");
+    if (h->dm.ntx * h->dm.ny >= (1 << 25)) return fail(nullptr, DG_ERR_ARG, "batch: instance %d too large", k);
+    tabs[h->p] = &h->tab;
+    tiles += (long long)h->dm.ntx * h->dm.ny;
+  }
+  if (tiles >= (1LL << 31)) return fail(nullptr, DG_ERR_ARG, "batch: too many tiles");
+  dg_batch* b = new (std::nothrow) dg_batch();
+  if (!b) return fail(nullptr, DG_ERR_NOMEM, "batch: host allocation");
+  b->L = new (std::nothrow) BatchLaunch32();
+  if (!b->L) {
+    delete b;
+    return fail(nullptr, DG_ERR_NOMEM, "batch: host allocation");
+  }
+  b->n = n;
+  b->hstream = hs[0]->stream;
+  b->policy = 1;
+  b->dynamic = 1;
+  BatchLaunch32& L = *b->L;
+  memset(&L, 0, sizeof(L));
+  L.n = n;
+  L.dynamic = 1;
+  L.tile0[0] = 0;
+  for (int k = 0; k < n; k++) {
+    dg_handle* h = hs[k];
+    b->h[k] = h;
+    BatchInst32& I = L.inst[k];
+    I.a.Rb = h->Rb;
+    I.a.Db = h->Db;
+    I.a.Bm0 = h->Bm0;
+    I.a.Bmodes = h->Bmodes;
+    I.a.TileFlag = h->TileFlag;
+    I.a.ts = h->ts;
+    I.a.part = h->part;
+    I.a.mesh = h->dm;
+    I.a.pc = h->pc;
+    I.buf[0] = h->D[0];
+    I.buf[1] = h->D[1];
+    I.DZ = h->DZ;
+    I.SigbN = h->SigbN;
+    I.series = h->series;
+    I.r_p = h->ph.r_p;
+    I.omega_p = h->ph.omega_p;
+    I.phi0 = h->ph.phi0;
+    I.p = h->p;
+    I.nparts = h->nparts;
+    I.cur0 = h->cur0;
+    I.step0 = h->step0;
+    L.tile0[k + 1] = L.tile0[k] + h->dm.ntx * h->dm.ny;
+  }
+  L.nitems = L.tile0[n];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = batch_upload_tables32(tabs);
+  b->ctas_per_sm = batch_stage32_ctas_per_sm();
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, 3 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, (size_t)L.nitems * sizeof(int));
+  int rc = e == cudaSuccess ? DG_OK : fail(nullptr, DG_ERR_CUDA, "batch: %s", cudaGetErrorString(e));
+  if (!rc && b->ctas_per_sm < 1) rc = fail(nullptr, DG_ERR_CUDA, "batch: stage kernel does not fit an SM");
+  if (!rc) {
+    L.items = b->d_items;
+    rc = batch_items(b);
+  }
+  if (rc) {
+    dg_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return DG_OK;
+}
+
+int dg_batch_config(dg_batch* b, int policy, int dynamic, int ctas_per_sm) {
+  if (!b || policy < 0 || policy > 2 || ctas_per_sm < 0) return fail(nullptr, DG_ERR_ARG, "batch: bad config");
+  const int maxc = batch_stage32_ctas_per_sm();
+  b->policy = policy;
+  b->dynamic = dynamic ? 1 : 0;
+  b->L->dynamic = b->dynamic;
+  b->ctas_per_sm = (ctas_per_sm == 0 || ctas_per_sm > maxc) ? maxc : ctas_per_sm;
+  if (b->graph_ok) {
+    cudaGraphExecDestroy(b->exec);
+    b->graph_ok = false;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail(nullptr, DG_ERR_CUDA, "batch: %s", cudaGetErrorString(e));
+  return batch_items(b);
+}
+
+int dg_batch_get_config(const dg_batch* b, int* policy, int* dynamic, int* ctas_per_sm) {
+  if (!b) return fail(nullptr, DG_ERR_ARG, "batch: null");
+  if (policy) *policy = b->policy;
+  if (dynamic) *dynamic = b->dynamic;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  return DG_OK;
+}
+
+int dg_batch_step(dg_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return fail(nullptr, DG_ERR_ARG, "batch: bad argument");
+  if (nsteps == 0) return DG_OK;
+  return batch_run(b, nsteps);
+}
+
+int dg_batch_sync(dg_batch* b) {
+  if (!b) return fail(nullptr, DG_ERR_ARG, "batch: null");
+  for (int k = 0; k < b->n; k++) {
+    DevState st;
+    int rc = read_state(b->h[k], &st);
+    if (rc) return fail(nullptr, rc, "batch instance %d: %s", k, b->h[k]->err);
+  }
+  return DG_OK;
+}
+
+int dg_batch_tune(dg_batch* b, int steps, int* policy, int* dynamic, int* ctas_per_sm, double* best_ms) {
+  if (!b || steps < 1) return fail(nullptr, DG_ERR_ARG, "batch: bad argument");
+  int rc = dg_batch_sync(b);
+  if (rc) return rc;
+  // snapshot of every instance (state buffer and device time state), put back
+  // after the trials so that tuning does not advance the discs
+  std::vector<float*> save(b->n, nullptr);
+  std::vector<DevState> st(b->n);
+  std::vector<int> cur(b->n);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < b->n && e == cudaSuccess; k++) {
+    dg_handle* h = b->h[k];
+    const size_t bytes = tiled_count(h) * sizeof(float);
+    cur[k] = h->cur;
+    e = cudaMalloc((void**)&save[k], bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save[k], h->D[h->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st[k], h->ts, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  // the trials: every work order, with persistent CTAs (resident CTAs per SM
+  // at the occupancy limit and one below) and with one CTA per tile
+  const int maxc = batch_stage32_ctas_per_sm();
+  struct Trial {
+    int policy, dynamic, ctas;
+  };
+  std::vector<Trial> trials;
+  for (int pol = 0; pol < 3; pol++) {
+    trials.push_back({pol, 1, maxc});
+    if (maxc > 1) trials.push_back({pol, 1, maxc - 1});
+    trials.push_back({pol, 0, maxc});
+  }
+  Trial bestc = {b->policy, b->dynamic, b->ctas_per_sm};
+  double best = 1e30;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (const Trial& t : trials) {
+    if (rc || e != cudaSuccess) break;
+    rc = dg_batch_config(b, t.policy, t.dynamic, t.ctas);
+    if (!rc) rc = batch_run(b, 1);  // builds the graph, warms up
+    if (!rc) e = cudaEventRecord(e0, b->stream);
+    if (!rc && e == cudaSuccess) rc = batch_run(b, steps);
+    if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (!rc && e == cudaSuccess && ms / steps < best) {
+      best = ms / steps;
+      bestc = t;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // restore every instance
+  for (int k = 0; k < b->n; k++) {
+    dg_handle* h = b->h[k];
+    const size_t bytes = tiled_count(h) * sizeof(float);
+    if (save[k] && e == cudaSuccess) {
+      h->cur = cur[k];
+      e = cudaMemcpyAsync(h->D[h->cur], save[k], bytes, cudaMemcpyDeviceToDevice, b->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->ts, &st[k], sizeof(DevState), cudaMemcpyHostToDevice, b->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  for (int k = 0; k < b->n; k++) cudaFree(save[k]);
+  if (e != cudaSuccess) return fail(nullptr, DG_ERR_CUDA, "batch tune: %s", cudaGetErrorString(e));
+  if (rc) return rc;
+  rc = dg_batch_config(b, bestc.policy, bestc.dynamic, bestc.ctas);
+  if (rc) return rc;
+  if (policy) *policy = bestc.policy;
+  if (dynamic) *dynamic = bestc.dynamic;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (best_ms) *best_ms = best;
+  return DG_OK;
+}
+
+int dg_batch_destroy(dg_batch* b) {
+  if (!b) return DG_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph_ok) cudaGraphExecDestroy(b->exec);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_items);
+  delete b->L;
+  delete b;
+  return DG_OK;
+}
+
 }  // extern "C"

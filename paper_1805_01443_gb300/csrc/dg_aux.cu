@@ -2,6 +2,7 @@
 // layout transforms and conserved sums.
 #include <math.h>
 
+#include "dg_finish.cuh"
 #include "dg_internal.cuh"
 #include "dg_physics.cuh"
 
@@ -9,7 +10,7 @@ namespace dg {
 
 namespace {
 
-constexpr unsigned long long INF_BITS = 0x7ff0000000000000ULL;
+constexpr unsigned long long INF_BITS = DT_INF_BITS;
 
 // SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator:
 // value(c) = mix(seed + (c + 1) * 0x9E3779B97F4A7C15), top 53 bits -> [0, 1).
@@ -113,30 +114,6 @@ __global__ void k_cfl(const double* U, DevState* ts, const Mesh ms, const Phys p
   }
 }
 
-// End of a step: fixed-order sum of the per-CTA torque partials, torque on the
-// planet at t^{n+1} (Sec. 5.2), time advance, and the next CFL step.  With
-// advance = 0 only the CFL slot is turned into ts->dt.
-// planet positions of the precision form for the step starting at ts->t with
-// step dt (see DevState::plf)
-__device__ void store_planet32(DevState* ts, double dt, double r_p, double omega_p, double phi0) {
-  const double c[3] = {0.0, 0.5, 1.0};
-  for (int k = 0; k < 3; k++) {
-    double sn, cs;
-    sincos(omega_p * (ts->t + c[k] * dt) + phi0, &sn, &cs);
-    const double x = r_p * cs, y = r_p * sn;
-    const float xh = (float)x, yh = (float)y;
-    ts->plf[k][0] = xh;
-    ts->plf[k][1] = (float)(x - (double)xh);
-    ts->plf[k][2] = yh;
-    ts->plf[k][3] = (float)(y - (double)yh);
-    if (k == 2) {
-      ts->pl1[0] = x;
-      ts->pl1[1] = y;
-    }
-  }
-  ts->dtf = (float)dt;
-}
-
 __global__ void k_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0) {
   store_planet32(ts, fixed_dt > 0.0 ? fixed_dt : ts->dt, r_p, omega_p, phi0);
 }
@@ -144,53 +121,7 @@ __global__ void k_planet32(DevState* ts, double fixed_dt, double r_p, double ome
 __global__ void k_finish(DevState* ts, const double* part, int nparts, double* series,
                          double fixed_dt, int advance, int planet32, double r_p, double omega_p,
                          double phi0) {
-  __shared__ double sx[256], sy[256];
-  const int tid = threadIdx.x;
-  if (ts->status != 0) return;
-  if (advance) {
-    double gx = 0.0, gy = 0.0;
-    for (int k = tid; k < nparts; k += 256) {
-      gx += part[2 * k];
-      gy += part[2 * k + 1];
-    }
-    sx[tid] = gx;
-    sy[tid] = gy;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s) {
-        sx[tid] += sx[tid + s];
-        sy[tid] += sy[tid + s];
-      }
-      __syncthreads();
-    }
-  }
-  if (tid != 0) return;
-  if (ts->pending) {
-    // bit 0: non-finite or non-positive state; bit 1: a bounded wait gave up
-    ts->status = (ts->pending & 2) ? DG_ERR_TIMEOUT : DG_ERR_NUMERIC;
-    return;
-  }
-  if (advance) {
-    const double dt = fixed_dt > 0.0 ? fixed_dt : ts->dt;
-    const double tn1 = ts->t + dt;
-    double sn, cs;
-    sincos(omega_p * tn1 + phi0, &sn, &cs);
-    const double xp = r_p * cs, yp = r_p * sn;
-    const double gz = xp * sy[0] - yp * sx[0];
-    series[ts->series_count % SERIES_CAP] = gz;
-    ts->series_count += 1;
-    ts->torque = gz;
-    ts->t = tn1;
-    ts->step += 1;
-  }
-  const double dtn = __longlong_as_double((long long)ts->dt_bits);
-  if (!(dtn > 0.0) || !isfinite(dtn)) {
-    if (fixed_dt <= 0.0) ts->status = DG_ERR_NUMERIC;
-  } else {
-    ts->dt = dtn;
-  }
-  ts->dt_bits = INF_BITS;
-  if (planet32 && ts->status == 0) store_planet32(ts, fixed_dt > 0.0 ? fixed_dt : ts->dt, r_p, omega_p, phi0);
+  finish_step(ts, part, nparts, series, fixed_dt, advance, planet32, r_p, omega_p, phi0);
 }
 
 __global__ void k_reset(DevState* ts, double t, long long step) {

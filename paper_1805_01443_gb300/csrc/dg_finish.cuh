@@ -1,0 +1,90 @@
+// dg_finish.cuh -- end-of-step work shared by the single-handle and the
+// batched drivers: fixed-order torque sum, time advance, next CFL step and
+// the planet positions of the precision form.
+#pragma once
+#include "dg_internal.cuh"
+
+namespace dg {
+
+constexpr unsigned long long DT_INF_BITS = 0x7ff0000000000000ULL;  // +inf, the empty CFL slot
+
+// planet positions of the precision form for the step starting at ts->t with
+// step dt (see DevState::plf)
+__device__ __forceinline__ void store_planet32(DevState* ts, double dt, double r_p, double omega_p,
+                                               double phi0) {
+  const double c[3] = {0.0, 0.5, 1.0};
+  for (int k = 0; k < 3; k++) {
+    double sn, cs;
+    sincos(omega_p * (ts->t + c[k] * dt) + phi0, &sn, &cs);
+    const double x = r_p * cs, y = r_p * sn;
+    const float xh = (float)x, yh = (float)y;
+    ts->plf[k][0] = xh;
+    ts->plf[k][1] = (float)(x - (double)xh);
+    ts->plf[k][2] = yh;
+    ts->plf[k][3] = (float)(y - (double)yh);
+    if (k == 2) {
+      ts->pl1[0] = x;
+      ts->pl1[1] = y;
+    }
+  }
+  ts->dtf = (float)dt;
+}
+
+// End of a step, by one CTA of 256 threads: fixed-order sum of the per-tile
+// torque partials, torque on the planet at t^{n+1} (Sec. 5.2), time advance,
+// the next CFL step and (planet32) the next step's planet positions.  With
+// advance = 0 only the CFL slot is turned into ts->dt.
+__device__ __forceinline__ void finish_step(DevState* ts, const double* part, int nparts, double* series,
+                                            double fixed_dt, int advance, int planet32, double r_p,
+                                            double omega_p, double phi0) {
+  __shared__ double sx[256], sy[256];
+  const int tid = threadIdx.x;
+  if (ts->status != 0) return;
+  if (advance) {
+    double gx = 0.0, gy = 0.0;
+    for (int k = tid; k < nparts; k += 256) {
+      gx += part[2 * k];
+      gy += part[2 * k + 1];
+    }
+    sx[tid] = gx;
+    sy[tid] = gy;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (tid < s) {
+        sx[tid] += sx[tid + s];
+        sy[tid] += sy[tid + s];
+      }
+      __syncthreads();
+    }
+  }
+  if (tid != 0) return;
+  if (ts->pending) {
+    // bit 0: non-finite or non-positive state; bit 1: a bounded wait gave up
+    ts->status = (ts->pending & 2) ? DG_ERR_TIMEOUT : DG_ERR_NUMERIC;
+    return;
+  }
+  if (advance) {
+    const double dt = fixed_dt > 0.0 ? fixed_dt : ts->dt;
+    const double tn1 = ts->t + dt;
+    double sn, cs;
+    sincos(omega_p * tn1 + phi0, &sn, &cs);
+    const double xp = r_p * cs, yp = r_p * sn;
+    const double gz = xp * sy[0] - yp * sx[0];
+    series[ts->series_count % SERIES_CAP] = gz;
+    ts->series_count += 1;
+    ts->torque = gz;
+    ts->t = tn1;
+    ts->step += 1;
+  }
+  const double dtn = __longlong_as_double((long long)ts->dt_bits);
+  if (!(dtn > 0.0) || !isfinite(dtn)) {
+    if (fixed_dt <= 0.0) ts->status = DG_ERR_NUMERIC;
+  } else {
+    ts->dt = dtn;
+  }
+  ts->dt_bits = DT_INF_BITS;
+  if (planet32 && ts->status == 0)
+    store_planet32(ts, fixed_dt > 0.0 ? fixed_dt : ts->dt, r_p, omega_p, phi0);
+}
+
+}  // namespace dg

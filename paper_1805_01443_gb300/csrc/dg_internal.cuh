@@ -185,4 +185,42 @@ cudaError_t launch_bg_nodes(const double* bg, float* sigbn, float* db, float* bm
 cudaError_t launch_tile_flags(const float* disc, int* flags, const Mesh& mesh, float threshold,
                               cudaStream_t s);
 
+// ---- batched precision form (dg_batch.cu) ----------------------------------
+// Many independent discs advanced together: every launch covers the tiles of
+// all instances (mixed degrees), and the ping-pong state of each instance is
+// chosen on the device from the parity of its step counter, so the launch
+// arguments do not change from step to step and one captured step replays.
+constexpr int BATCH_MAX = 64;
+
+struct BatchInst32 {
+  StageArgs32 a;        // per-instance arguments (D, Dn, Out, alpha, beta, pidx, mode unused)
+  float* buf[2];        // delta^n / delta^{n+1} by step parity
+  float* DZ;            // stage scratch
+  const float* SigbN;   // Sigma_b node pairs (torque)
+  double* series;       // torque ring of the instance
+  double r_p, omega_p, phi0;
+  long long step0;      // step count at which buf[cur0] held the state
+  int cur0, p, nparts;
+};
+
+struct BatchLaunch32 {
+  int n;                // instances
+  int nitems;           // tiles over all instances
+  int stage;            // SSP(3,3) stage 0, 1, 2
+  int dynamic;          // 1: persistent CTAs take items from *counter; 0: one item per CTA
+  int* counter;         // work counter of this stage (reset every step)
+  const int* items;     // work order: (instance << 25) | tile
+  int tile0[BATCH_MAX + 1];  // prefix sums of the instances' tile counts
+  BatchInst32 inst[BATCH_MAX];
+};
+
+// tables of every degree used by the batch (tabs[p], p = 1..4, or null)
+cudaError_t batch_upload_tables32(const Tables* const* tabs);
+size_t batch_stage32_smem();
+int batch_stage32_ctas_per_sm();
+cudaError_t launch_batch_stage32(const BatchLaunch32& L, int grid, cudaStream_t s);
+cudaError_t launch_batch_torque32(const BatchLaunch32& L, cudaStream_t s);
+cudaError_t launch_batch_finish(const BatchLaunch32& L, cudaStream_t s);
+cudaError_t launch_batch_planet32(const BatchLaunch32& L, cudaStream_t s);
+
 }  // namespace dg

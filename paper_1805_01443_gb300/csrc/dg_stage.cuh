@@ -689,12 +689,12 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
 }
 
 template <int P>
-size_t stage_smem_impl(int kind) {
+static size_t stage_smem_impl(int kind) {
   return kind == 1 ? Smem<P, 1>::BYTES : Smem<P, 0>::BYTES;
 }
 
 template <int P, int KIND>
-cudaError_t launch_kind(const StageArgs& a, cudaStream_t s) {
+static cudaError_t launch_kind(const StageArgs& a, cudaStream_t s) {
   static bool configured = false;
   const size_t bytes = Smem<P, KIND>::BYTES;
   if (!configured) {
@@ -709,7 +709,7 @@ cudaError_t launch_kind(const StageArgs& a, cudaStream_t s) {
 }
 
 template <int P>
-cudaError_t launch_stage_impl(const StageArgs& a, cudaStream_t s) {
+static cudaError_t launch_stage_impl(const StageArgs& a, cudaStream_t s) {
   switch (a.phys.kind) {
     case 0: return launch_kind<P, 0>(a, s);
     case 1: return launch_kind<P, 1>(a, s);
@@ -719,7 +719,7 @@ cudaError_t launch_stage_impl(const StageArgs& a, cudaStream_t s) {
 }
 
 template <int P>
-cudaError_t upload_tables_impl(const Tables& t) {
+static cudaError_t upload_tables_impl(const Tables& t) {
   double wphi[MAXM][MAXM] = {}, wdphi[MAXM][MAXM] = {};
   for (int q = 0; q <= P; q++)
     for (int a = 0; a <= P; a++) {

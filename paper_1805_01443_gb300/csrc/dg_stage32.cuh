@@ -27,19 +27,22 @@
 #pragma once
 #include "dg_internal.cuh"
 
-#ifndef DG_P
-#error "define DG_P before including dg_stage32.cuh"
-#endif
 
 namespace dg {
 
-static __constant__ float c32_phi[MAXM][MAXM];    // [q][a] sqrt(2a+1) P_a(xi_q)
-static __constant__ float c32_wphi[MAXM][MAXM];   // w_q/2 phi_a(xi_q)
-static __constant__ float c32_wdphi[MAXM][MAXM];  // w_q/2 phi'_a(xi_q)
-static __constant__ float c32_pp[MAXM], c32_pm[MAXM], c32_xi[MAXM], c32_wh[MAXM];
-// low parts of the FP64 tables as float pairs (float-float torque)
-static __constant__ float c32_phil[MAXM][MAXM], c32_xil[MAXM];
-static __constant__ float c32_w2h[MAXM * MAXM], c32_w2l[MAXM * MAXM];  // [q*m + r] (w_q/2)(w_r/2)
+// FP32 quadrature and basis tables of degree P (the m-point Gauss-Legendre
+// rule), one slice per degree so that one translation unit can hold kernels
+// of several degrees
+struct Tab32 {
+  float phi[MAXM][MAXM];    // [q][a] sqrt(2a+1) P_a(xi_q)
+  float wphi[MAXM][MAXM];   // w_q/2 phi_a(xi_q)
+  float wdphi[MAXM][MAXM];  // w_q/2 phi'_a(xi_q)
+  float pp[MAXM], pm[MAXM], xi[MAXM], wh[MAXM];
+  // low parts of the FP64 tables as float pairs (float-float torque)
+  float phil[MAXM][MAXM], xil[MAXM];
+  float w2h[MAXM * MAXM], w2l[MAXM * MAXM];  // [q*m + r] (w_q/2)(w_r/2)
+};
+static __constant__ Tab32 c32t[MAXP + 1];
 
 // Analytic background of the disc and the isothermal sound speed at (x, y).
 struct Bg32 {
@@ -289,7 +292,7 @@ __device__ __forceinline__ void nodal32(const float* c, float* u_out, float* xr,
     for (int r = 0; r < m; r++) {
       float acc = 0.0f;
 #pragma unroll
-      for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32_phi[r][b], acc);
+      for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32t[P].phi[r][b], acc);
       T[aa][r] = acc;
     }
 #pragma unroll
@@ -298,7 +301,7 @@ __device__ __forceinline__ void nodal32(const float* c, float* u_out, float* xr,
     for (int r = 0; r < m; r++) {
       float acc = 0.0f;
 #pragma unroll
-      for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], T[aa][r], acc);
+      for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], T[aa][r], acc);
       u_out[(q * m + r) * 32] = acc;
     }
   if (TRACES) {
@@ -307,8 +310,8 @@ __device__ __forceinline__ void nodal32(const float* c, float* u_out, float* xr,
       float sr = 0.0f, sl = 0.0f;
 #pragma unroll
       for (int aa = 0; aa < m; aa++) {
-        sr = fmaf(c32_pp[aa], T[aa][r], sr);
-        sl = fmaf(c32_pm[aa], T[aa][r], sl);
+        sr = fmaf(c32t[P].pp[aa], T[aa][r], sr);
+        sl = fmaf(c32t[P].pm[aa], T[aa][r], sl);
       }
       xr[r] = sr;
       xl[r] = sl;
@@ -333,7 +336,7 @@ __device__ __forceinline__ void ytrace32(const float* c, const float* f, float* 
   for (int q = 0; q < m; q++) {
     float acc = 0.0f;
 #pragma unroll
-    for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], R[aa], acc);
+    for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], R[aa], acc);
     out[q * 32] = acc;
   }
 }
@@ -349,7 +352,7 @@ __device__ __forceinline__ void xtrace32(const float* c, const float* f, float* 
     for (int aa = 0; aa < m; aa++) {
       float t = 0.0f;
 #pragma unroll
-      for (int b = 0; b < m; b++) t = fmaf(c[aa * m + b], c32_phi[r][b], t);
+      for (int b = 0; b < m; b++) t = fmaf(c[aa * m + b], c32t[P].phi[r][b], t);
       acc = fmaf(f[aa], t, acc);
     }
     out[r * 33] = acc;
@@ -365,11 +368,12 @@ __device__ __forceinline__ void xtrace32(const float* c, const float* f, float* 
 // (last RK stage with damping, torque and CFL), compiled apart so that the
 // first two stages do not carry the epilogue's code
 template <int P, bool LAST>
-__global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const StageArgs32 a) {
+__device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* Dcur, const float* Dn0,
+                                             float* Outp, float alpha, float beta, int pidx, int mode,
+                                             int bx, int j, double* smd) {
   constexpr int m = P + 1, M = m * m, NV = 3;
   constexpr int NVM = NV * M;
   using S = Smem32<P>;
-  extern __shared__ double smd[];
   // smd[0..4]: floats sF[0..8] (tile offsets from the planet (hi, lo), dt);
   // smd[7]: the mbarrier of the last stage's TMA copy
   float* sF = reinterpret_cast<float*>(smd);
@@ -389,7 +393,6 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   if (a.ts->status != 0) return;
 
   const int tid = threadIdx.x, lane = tid & 31, v = tid >> 5;
-  const int bx = blockIdx.x, j = blockIdx.y;
   const int i0 = bx * 32;
   const int nvalid = min(32, ms.nx - i0);
   const bool valid = lane < nvalid;
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     const DevState* ts = a.ts;
     sF[8] = ts->dtf;
     const float kx = i2f(i0) + 0.5f, ky = i2f(j) + 0.5f;
-    const float* pl = ts->plf[a.pidx];
+    const float* pl = ts->plf[pidx];
     ff_offset(kx, pc.x0p, pc.dxp, pl[0], pl[1], sF[0], sF[4]);
     ff_offset(ky, pc.y0p, pc.dyp, pl[2], pl[3], sF[1], sF[5]);
     if (LAST) mbar_init(smd + 7, 1);
@@ -415,36 +418,36 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   // bc 2 transmissive (exterior trace = interior trace)
   const size_t tile = (size_t)j * ms.ntx + bx;
   const size_t voff = (size_t)v * M * 32;
-  const float* own = a.D + tile * NVM * 32 + voff + lc;
+  const float* own = Dcur + tile * NVM * 32 + voff + lc;
   const float* pB = nullptr;
   const float* pT = nullptr;
   bool zB = false, zT = false;
-  if (j > 0) pB = a.D + ((size_t)(j - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
-  else if (ms.bc == 0) pB = a.D + ((size_t)(ms.ny - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
+  if (j > 0) pB = Dcur + ((size_t)(j - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
+  else if (ms.bc == 0) pB = Dcur + ((size_t)(ms.ny - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
   else if (ms.bc == 1) zB = true;
-  if (j + 1 < ms.ny) pT = a.D + ((size_t)(j + 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
-  else if (ms.bc == 0) pT = a.D + (size_t)bx * NVM * 32 + voff + lc;
+  if (j + 1 < ms.ny) pT = Dcur + ((size_t)(j + 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
+  else if (ms.bc == 0) pT = Dcur + (size_t)bx * NVM * 32 + voff + lc;
   else if (ms.bc == 1) zT = true;
   const bool trB = !pB && !zB, trT = !pT && !zT;
   const int il = i0 - 1, ir = i0 + nvalid;
   const float* pL = nullptr;
   const float* pR = nullptr;
   bool zL = false, zR = false;
-  if (il >= 0) pL = a.D + ((size_t)j * ms.ntx + (il >> 5)) * NVM * 32 + voff + (il & 31);
-  else if (ms.bc == 0) { const int iw = ms.nx - 1; pL = a.D + ((size_t)j * ms.ntx + (iw >> 5)) * NVM * 32 + voff + (iw & 31); }
+  if (il >= 0) pL = Dcur + ((size_t)j * ms.ntx + (il >> 5)) * NVM * 32 + voff + (il & 31);
+  else if (ms.bc == 0) { const int iw = ms.nx - 1; pL = Dcur + ((size_t)j * ms.ntx + (iw >> 5)) * NVM * 32 + voff + (iw & 31); }
   else if (ms.bc == 1) zL = true;
-  if (ir < ms.nx) pR = a.D + ((size_t)j * ms.ntx + (ir >> 5)) * NVM * 32 + voff + (ir & 31);
-  else if (ms.bc == 0) pR = a.D + (size_t)j * ms.ntx * NVM * 32 + voff;
+  if (ir < ms.nx) pR = Dcur + ((size_t)j * ms.ntx + (ir >> 5)) * NVM * 32 + voff + (ir & 31);
+  else if (ms.bc == 0) pR = Dcur + (size_t)j * ms.ntx * NVM * 32 + voff;
   else if (ms.bc == 1) zR = true;
   const bool trL = !pL && !zL, trR = !pR && !zR;
   // tiles near the singular centre use the exact projected background (FP32
   // modes of u_b, same tiled layout as delta, all three variables)
   const int exact = a.TileFlag[tile];
   const float* bgOwn = exact ? a.Bmodes + tile * NVM * 32 + lc : nullptr;
-  const float* bgB = (exact && pB) ? a.Bmodes + (pB - a.D) - voff : nullptr;
-  const float* bgT = (exact && pT) ? a.Bmodes + (pT - a.D) - voff : nullptr;
-  const float* bgL = (exact && pL) ? a.Bmodes + (pL - a.D) - voff : nullptr;
-  const float* bgR = (exact && pR) ? a.Bmodes + (pR - a.D) - voff : nullptr;
+  const float* bgB = (exact && pB) ? a.Bmodes + (pB - Dcur) - voff : nullptr;
+  const float* bgT = (exact && pT) ? a.Bmodes + (pT - Dcur) - voff : nullptr;
+  const float* bgL = (exact && pL) ? a.Bmodes + (pL - Dcur) - voff : nullptr;
+  const float* bgR = (exact && pR) ? a.Bmodes + (pR - Dcur) - voff : nullptr;
   // FP32 geometry of this thread's element
   const float lanef = i2f(lane);
   const float xcf = pc.x0 + (i2f(i0 + lane) + 0.5f) * pc.dx;
@@ -469,10 +472,10 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
       if (lane == 0 && trL) xr[r * 33] = tr_l[r];  // mirror: exterior = interior
       if (lane == nvalid - 1 && trR) xl[r * 33 + nvalid] = tr_r[r];
     }
-    ytrace32<P>(c, c32_pp, sYT + ((0 * 3 + v) * m) * 32 + lane);
-    ytrace32<P>(c, c32_pm, sYT + ((1 * 3 + v) * m) * 32 + lane);
-    if (trB) ytrace32<P>(c, c32_pm, sYN + ((0 * 3 + v) * m) * 32 + lane);
-    if (trT) ytrace32<P>(c, c32_pp, sYN + ((1 * 3 + v) * m) * 32 + lane);
+    ytrace32<P>(c, c32t[P].pp, sYT + ((0 * 3 + v) * m) * 32 + lane);
+    ytrace32<P>(c, c32t[P].pm, sYT + ((1 * 3 + v) * m) * 32 + lane);
+    if (trB) ytrace32<P>(c, c32t[P].pm, sYN + ((0 * 3 + v) * m) * 32 + lane);
+    if (trT) ytrace32<P>(c, c32t[P].pp, sYN + ((1 * 3 + v) * m) * 32 + lane);
   }
   {
     // neighbour rows: the face polynomial of the element below (top face) and above (bottom face)
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     if (pB) {
 #pragma unroll
       for (int k = 0; k < M; k++) c[k] = pB[k * 32];
-      ytrace32<P>(c, c32_pp, sYN + ((0 * 3 + v) * m) * 32 + lane);
+      ytrace32<P>(c, c32t[P].pp, sYN + ((0 * 3 + v) * m) * 32 + lane);
     } else if (zB) {
 #pragma unroll
       for (int q = 0; q < m; q++) sYN[((0 * 3 + v) * m + q) * 32 + lane] = 0.0f;
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     if (pT) {
 #pragma unroll
       for (int k = 0; k < M; k++) c[k] = pT[k * 32];
-      ytrace32<P>(c, c32_pm, sYN + ((1 * 3 + v) * m) * 32 + lane);
+      ytrace32<P>(c, c32t[P].pm, sYN + ((1 * 3 + v) * m) * 32 + lane);
     } else if (zT) {
 #pragma unroll
       for (int q = 0; q < m; q++) sYN[((1 * 3 + v) * m + q) * 32 + lane] = 0.0f;
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
       if (pL) {
 #pragma unroll
         for (int k = 0; k < M; k++) c[k] = pL[k * 32];
-        xtrace32<P>(c, c32_pp, sXT + (0 * 3 + v) * m * 33);
+        xtrace32<P>(c, c32t[P].pp, sXT + (0 * 3 + v) * m * 33);
       } else if (zL) {
 #pragma unroll
         for (int r = 0; r < m; r++) sXT[((0 * 3 + v) * m + r) * 33] = 0.0f;
@@ -508,7 +511,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
       if (pR) {
 #pragma unroll
         for (int k = 0; k < M; k++) c[k] = pR[k * 32];
-        xtrace32<P>(c, c32_pm, sXT + (1 * 3 + v) * m * 33 + nvalid);
+        xtrace32<P>(c, c32t[P].pm, sXT + (1 * 3 + v) * m * 33 + nvalid);
       } else if (zR) {
 #pragma unroll
         for (int r = 0; r < m; r++) sXT[((1 * 3 + v) * m + r) * 33 + nvalid] = 0.0f;
@@ -529,10 +532,10 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
         float d[3];
 #pragma unroll
         for (int w3 = 0; w3 < 3; w3++) d[w3] = sU[(w3 * M + n) * 32 + lane];
-        const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
-        const float y = fmaf(pc.hdy, c32_xi[r], ycf);
+        const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
+        const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
         Bg32 bgn = bg32_at(pc, xq, y);
-        if (exact) bgn = bg32_poly<P>(bgOwn, c32_phi[q], c32_phi[r], bgn.c2);
+        if (exact) bgn = bg32_poly<P>(bgOwn, c32t[P].phi[q], c32t[P].phi[r], bgn.c2);
         float fx[3], fy[3], vx, vy;
         dflux32(bgn, d, fx, fy, vx, vy);
         // star: -dSigma grad Phi_*; planet: -Sigma grad Phi_p
@@ -550,8 +553,8 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
           src2 = -d[0] * y * inv;
         }
         if (pc.planet) {
-          const float pdx = pdx0 + fmaf(pc.hdx, c32_xi[q], sF[4]);
-          const float pdy = sF[1] + fmaf(pc.hdy, c32_xi[r], sF[5]);
+          const float pdx = pdx0 + fmaf(pc.hdx, c32t[P].xi[q], sF[4]);
+          const float pdy = sF[1] + fmaf(pc.hdy, c32t[P].xi[r], sF[5]);
           const float d2 = fmaf(pdx, pdx, fmaf(pdy, pdy, pc.eps2));
           const float id = rsqrtf(d2);
           const float f = pc.q * id * id * id * (bgn.sig + d[0]);
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
     // y faces of the element: bottom (below | own) and top (own | above)
     for (int kk = v; kk < 2 * m; kk += 3) {
       const int side = kk >= m, q = kk - side * m;
-      const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
+      const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
       float dL[3], dR[3], hf[3];
 #pragma unroll
       for (int w3 = 0; w3 < 3; w3++) {
@@ -583,9 +586,9 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
       Bg32 bO = bg32_at(pc, xq, side ? yTf : yBf), bN = bO;
       if (exact) {
         const float c2 = bO.c2;
-        bO = bg32_poly<P>(bgOwn, c32_phi[q], side ? c32_pp : c32_pm, c2);
+        bO = bg32_poly<P>(bgOwn, c32t[P].phi[q], side ? c32t[P].pp : c32t[P].pm, c2);
         const float* nb = side ? bgT : bgB;
-        if (nb) bN = bg32_poly<P>(nb, c32_phi[q], side ? c32_pm : c32_pp, c2);
+        if (nb) bN = bg32_poly<P>(nb, c32t[P].phi[q], side ? c32t[P].pm : c32t[P].pp, c2);
         else if (side ? trT : trB) bN = bO;
       }
       dllf32<1>(side ? bO : bN, side ? bN : bO, dL, dR, hf);
@@ -602,14 +605,14 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
           dL[w3] = sXT[((0 * 3 + w3) * m + r) * 33 + f];
           dR[w3] = sXT[((1 * 3 + w3) * m + r) * 33 + f];
         }
-        const float y = fmaf(pc.hdy, c32_xi[r], ycf);
+        const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
         Bg32 bL = bg32_at(pc, fmaf(i2f(f), pc.dx, xt0), y), bR = bL;
         if (exact) {
           const float* eL = (f > 0) ? bgOwn - lc + (f - 1) : bgL;
           const float* eR = (f < nvalid) ? bgOwn - lc + f : bgR;
           const float c2 = bL.c2;
-          if (eL) bL = bg32_poly<P>(eL, c32_pp, c32_phi[r], c2);
-          if (eR) bR = bg32_poly<P>(eR, c32_pm, c32_phi[r], c2);
+          if (eL) bL = bg32_poly<P>(eL, c32t[P].pp, c32t[P].phi[r], c2);
+          if (eR) bR = bg32_poly<P>(eR, c32t[P].pm, c32t[P].phi[r], c2);
           if (!eL && trL && f == 0) bL = bR;
           if (!eR && trR && f == nvalid) bR = bL;
         }
@@ -638,8 +641,8 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
         const float sv = (v > 0) ? sFl[((5 + v) * M + n) * 32 + lane] : 0.0f;
 #pragma unroll
         for (int b = 0; b < m; b++) {
-          Aq[b][q] = fmaf(c32_wphi[r][b], fxv, Aq[b][q]);
-          Bq[b][q] = fmaf(c32_wdphi[r][b], fyv, fmaf(c32_wphi[r][b], sv, Bq[b][q]));
+          Aq[b][q] = fmaf(c32t[P].wphi[r][b], fxv, Aq[b][q]);
+          Bq[b][q] = fmaf(c32t[P].wdphi[r][b], fyv, fmaf(c32t[P].wphi[r][b], sv, Bq[b][q]));
         }
       }
 #pragma unroll
@@ -649,8 +652,8 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
         float va = 0.0f, vb = 0.0f;
 #pragma unroll
         for (int q = 0; q < m; q++) {
-          va = fmaf(c32_wdphi[q][aa], Aq[b][q], va);
-          vb = fmaf(c32_wphi[q][aa], Bq[b][q], vb);
+          va = fmaf(c32t[P].wdphi[q][aa], Aq[b][q], va);
+          vb = fmaf(c32t[P].wphi[q][aa], Bq[b][q], vb);
         }
         L[aa * m + b] = fmaf(pc.s2x, va, vb);
       }
@@ -665,18 +668,18 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
       const float fb = sFY[((0 * 3 + v) * m + r) * 32 + lane], ft = sFY[((1 * 3 + v) * m + r) * 32 + lane];
 #pragma unroll
       for (int b = 0; b < m; b++) {
-        HL[b] = fmaf(c32_wphi[r][b], fl, HL[b]);
-        HR[b] = fmaf(c32_wphi[r][b], fr, HR[b]);
-        HB[b] = fmaf(c32_wphi[r][b], fb, HB[b]);
-        HT[b] = fmaf(c32_wphi[r][b], ft, HT[b]);
+        HL[b] = fmaf(c32t[P].wphi[r][b], fl, HL[b]);
+        HR[b] = fmaf(c32t[P].wphi[r][b], fr, HR[b]);
+        HB[b] = fmaf(c32t[P].wphi[r][b], fb, HB[b]);
+        HT[b] = fmaf(c32t[P].wphi[r][b], ft, HT[b]);
       }
     }
 #pragma unroll
     for (int aa = 0; aa < m; aa++)
 #pragma unroll
       for (int b = 0; b < m; b++) {
-        const float lx = fmaf(c32_pm[aa], HL[b], -c32_pp[aa] * HR[b]);
-        const float ly = fmaf(c32_pm[b], HB[aa], -c32_pp[b] * HT[aa]);
+        const float lx = fmaf(c32t[P].pm[aa], HL[b], -c32t[P].pp[aa] * HR[b]);
+        const float ly = fmaf(c32t[P].pm[b], HB[aa], -c32t[P].pp[b] * HT[aa]);
         L[aa * m + b] = fmaf(pc.idx, lx, fmaf(pc.idy, ly, L[aa * m + b]));
       }
   }
@@ -684,23 +687,23 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   const size_t gbase = tile * NVM * 32 + voff;
 #pragma unroll
   for (int k = 0; k < M; k++) L[k] += a.Rb[gbase + k * 32 + lc];
-  if (a.mode == 0) {
+  if (mode == 0) {
     if (valid) {
 #pragma unroll
-      for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = L[k];
+      for (int k = 0; k < M; k++) Outp[gbase + k * 32 + lane] = L[k];
     }
     return;
   }
   float un[M];
 #pragma unroll
   for (int k = 0; k < M; k++) {
-    const float dn = (a.alpha != 0.0f) ? a.Dn[gbase + k * 32 + lc] : 0.0f;
-    un[k] = fmaf(a.alpha, dn, a.beta * fmaf(dt, L[k], own[k * 32]));
+    const float dn = (alpha != 0.0f) ? Dn0[gbase + k * 32 + lc] : 0.0f;
+    un[k] = fmaf(alpha, dn, beta * fmaf(dt, L[k], own[k * 32]));
   }
   if (!LAST) {
     if (valid) {
 #pragma unroll
-      for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = un[k];
+      for (int k = 0; k < M; k++) Outp[gbase + k * 32 + lane] = un[k];
     }
     return;
   }
@@ -743,8 +746,8 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
       const int n = v + 3 * kk;
       if (n >= M) break;  // warp-uniform
       const int q = n / m, r = n - q * m;
-      const float xq = fmaf(pc.hdx, c32_xi[q], xcf);
-      const float y = fmaf(pc.hdy, c32_xi[r], ycf);
+      const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
+      const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
       const float rr = sqrt_fast(fmaf(xq, xq, y * y));
       float R = 0.0f, rd = 0.0f;
       if (pc.rd_in > 0.0f && rr < pc.rd_in) {
@@ -764,7 +767,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
         const float itd = __fdividef(1.0f, tau + dt);
         const float kap = tau * itd, omk = dt * itd;
         Bg32 bgn = bg32_at(pc, xq, y);
-        if (exact) bgn = bg32_poly<P>(bgOwn, c32_phi[q], c32_phi[r], bgn.c2);
+        if (exact) bgn = bg32_poly<P>(bgOwn, c32t[P].phi[q], c32t[P].phi[r], bgn.c2);
         const float d0 = sU[(0 * M + n) * 32 + lane];
         const float d1 = sU[(1 * M + n) * 32 + lane], d2 = sU[(2 * M + n) * 32 + lane];
         const float sg = bgn.sig + d0;
@@ -791,7 +794,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
           for (int q = 0; q < m; q++) {
             float acc = 0.0f;
 #pragma unroll
-            for (int r = 0; r < m; r++) acc = fmaf(c32_wphi[r][b], sU[(v * M + q * m + r) * 32 + lane], acc);
+            for (int r = 0; r < m; r++) acc = fmaf(c32t[P].wphi[r][b], sU[(v * M + q * m + r) * 32 + lane], acc);
             P1[b][q] = acc;
           }
 #pragma unroll
@@ -800,7 +803,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
           for (int b = 0; b < m; b++) {
             float acc = 0.0f;
 #pragma unroll
-            for (int q = 0; q < m; q++) acc = fmaf(c32_wphi[q][aa], P1[b][q], acc);
+            for (int q = 0; q < m; q++) acc = fmaf(c32t[P].wphi[q][aa], P1[b][q], acc);
             un[aa * m + b] = acc;
           }
       }
@@ -808,7 +811,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   }
   if (valid) {
 #pragma unroll
-    for (int k = 0; k < M; k++) a.Out[gbase + k * 32 + lane] = un[k];
+    for (int k = 0; k < M; k++) Outp[gbase + k * 32 + lane] = un[k];
   }
   sB0[v * 32 + lane] = un[0];
   __syncthreads();
@@ -839,6 +842,13 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   }
 }
 
+// one tile per CTA: grid (tiles per row, rows)
+template <int P, bool LAST>
+__global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const StageArgs32 a) {
+  extern __shared__ double smd[];
+  stage32_tile<P, LAST>(a, a.D, a.Dn, a.Out, a.alpha, a.beta, a.pidx, a.mode, blockIdx.x, blockIdx.y, smd);
+}
+
 // Torque on the planet at t^{n+1} from the new state (Sec. 5.1 torque with the
 // quadrature-node masses).  One warp per tile, lane e owns element e.  The
 // terms w_n m_n (r_n - r_p) / (|r_n - r_p|^2 + eps^2)^{3/2} are large and
@@ -853,14 +863,11 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
 // The per-tile pair is stored as a double; the finish kernel sums the tiles
 // in FP64.
 template <int P>
-__global__ void __launch_bounds__(128) k_torque32(const float* D, const float* SigbN, const DevState* ts,
-                                                   double* part, const Mesh ms, const Prec32 pc) {
+__device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN, const DevState* ts,
+                                              double* part, const Mesh& ms, const Prec32& pc, int tile) {
   constexpr int m = P + 1, M = m * m, NVM = 3 * M;
   if (ts->status != 0) return;
   const int lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int ntiles = ms.ntx * ms.ny;
-  if (tile >= ntiles) return;  // warp-uniform
   const int j = tile / ms.ntx, bx = tile - j * ms.ntx;
   const int i = bx * 32 + lane;
   const bool valid = i < ms.nx;
@@ -887,13 +894,13 @@ __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* S
         if (ffw) {
           F2 acc{0.0f, 0.0f};
 #pragma unroll
-          for (int b = 0; b < m; b++) acc = f2_add(acc, f2_mulf(F2{c32_phi[r][b], c32_phil[r][b]}, c[aa * m + b]));
+          for (int b = 0; b < m; b++) acc = f2_add(acc, f2_mulf(F2{c32t[P].phi[r][b], c32t[P].phil[r][b]}, c[aa * m + b]));
           Th[aa][r] = acc.h;
           Tl[aa][r] = acc.l;
         } else {
           float acc = 0.0f;
 #pragma unroll
-          for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32_phi[r][b], acc);
+          for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32t[P].phi[r][b], acc);
           Th[aa][r] = acc;
           Tl[aa][r] = 0.0f;
         }
@@ -905,7 +912,7 @@ __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* S
   F2 py[m], pye[m];
 #pragma unroll
   for (int r = 0; r < m; r++) {
-    py[r] = f2_add(oy, f2_mul(hdy, F2{c32_xi[r], c32_xil[r]}));
+    py[r] = f2_add(oy, f2_mul(hdy, F2{c32t[P].xi[r], c32t[P].xil[r]}));
     pye[r] = f2_add(f2_mul(py[r], py[r]), eps2);
   }
   F2 gx{0.0f, 0.0f}, gy{0.0f, 0.0f};
@@ -919,7 +926,7 @@ __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* S
         sh[r] = sbh[(q * m + r) * 32];
         sl[r] = sbl[(q * m + r) * 32];
       }
-      const F2 px = f2_add(ox, f2_mul(hdx, F2{c32_xi[q], c32_xil[q]}));
+      const F2 px = f2_add(ox, f2_mul(hdx, F2{c32t[P].xi[q], c32t[P].xil[q]}));
       const F2 px2 = f2_mul(px, px);
 #pragma unroll
       for (int r = 0; r < m; r++) {
@@ -928,16 +935,16 @@ __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* S
         if (ffw) {
 #pragma unroll
           for (int aa = 0; aa < m; aa++)
-            ds = f2_add(ds, f2_mul(F2{c32_phi[q][aa], c32_phil[q][aa]}, F2{Th[aa][r], Tl[aa][r]}));
+            ds = f2_add(ds, f2_mul(F2{c32t[P].phi[q][aa], c32t[P].phil[q][aa]}, F2{Th[aa][r], Tl[aa][r]}));
         } else {
           float acc = 0.0f;
 #pragma unroll
-          for (int aa = 0; aa < m; aa++) acc = fmaf(c32_phi[q][aa], Th[aa][r], acc);
+          for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], Th[aa][r], acc);
           ds.h = acc;
         }
         // w_n (Sigma_b + delta Sigma) / (d^2 + eps^2)^{3/2}
         const int n = q * m + r;
-        const F2 mass = f2_mul(f2_add(F2{sh[r], sl[r]}, ds), F2{c32_w2h[n], c32_w2l[n]});
+        const F2 mass = f2_mul(f2_add(F2{sh[r], sl[r]}, ds), F2{c32t[P].w2h[n], c32t[P].w2l[n]});
         const F2 id = f2_rsqrt(f2_add(px2, pye[r]));
         const F2 f = f2_mul(mass, f2_mul(f2_mul(id, id), id));
         gx = f2_add(gx, f2_mul(f, px));
@@ -958,8 +965,16 @@ __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* S
   }
 }
 
+// four tiles (warps) per CTA
+template <int P>
+__global__ void __launch_bounds__(128) k_torque32(const float* D, const float* SigbN, const DevState* ts,
+                                                   double* part, const Mesh ms, const Prec32 pc) {
+  const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (tile < ms.ntx * ms.ny) torque32_tile<P>(D, SigbN, ts, part, ms, pc, tile);  // warp-uniform
+}
+
 template <int P, bool LAST>
-cudaError_t launch_stage32_kind(const StageArgs32& a, cudaStream_t s) {
+static cudaError_t launch_stage32_kind(const StageArgs32& a, cudaStream_t s) {
   static bool configured = false;
   const size_t bytes = Smem32<P>::BYTES;
   if (!configured) {
@@ -974,12 +989,12 @@ cudaError_t launch_stage32_kind(const StageArgs32& a, cudaStream_t s) {
 }
 
 template <int P>
-cudaError_t launch_stage32_impl(const StageArgs32& a, cudaStream_t s) {
+static cudaError_t launch_stage32_impl(const StageArgs32& a, cudaStream_t s) {
   return a.mode == 2 ? launch_stage32_kind<P, true>(a, s) : launch_stage32_kind<P, false>(a, s);
 }
 
 template <int P>
-cudaError_t launch_torque32_impl(const float* D, const float* SigbN, const DevState* ts, double* part,
+static cudaError_t launch_torque32_impl(const float* D, const float* SigbN, const DevState* ts, double* part,
                                  const Mesh& ms, const Prec32& pc, cudaStream_t s) {
   const int ntiles = ms.ntx * ms.ny;
   k_torque32<P><<<(ntiles + 3) / 4, 128, 0, s>>>(D, SigbN, ts, part, ms, pc);
@@ -987,42 +1002,36 @@ cudaError_t launch_torque32_impl(const float* D, const float* SigbN, const DevSt
 }
 
 template <int P>
-cudaError_t upload_tables32_impl(const Tables& t) {
-  float phi[MAXM][MAXM] = {}, wphi[MAXM][MAXM] = {}, wdphi[MAXM][MAXM] = {};
-  float pp[MAXM] = {}, pm[MAXM] = {}, xi[MAXM] = {}, wh[MAXM] = {};
+static Tab32 make_tab32(const Tables& t) {
+  Tab32 c{};
   for (int q = 0; q <= P; q++) {
-    xi[q] = (float)t.xi[q];
-    wh[q] = (float)t.wh[q];
-    pp[q] = (float)t.pp[q];
-    pm[q] = (float)t.pm[q];
+    c.xi[q] = (float)t.xi[q];
+    c.xil[q] = (float)(t.xi[q] - (double)c.xi[q]);
+    c.wh[q] = (float)t.wh[q];
+    c.pp[q] = (float)t.pp[q];
+    c.pm[q] = (float)t.pm[q];
     for (int a = 0; a <= P; a++) {
-      phi[q][a] = (float)t.phi[q][a];
-      wphi[q][a] = (float)(t.wh[q] * t.phi[q][a]);
-      wdphi[q][a] = (float)(t.wh[q] * t.dphi[q][a]);
+      c.phi[q][a] = (float)t.phi[q][a];
+      c.phil[q][a] = (float)(t.phi[q][a] - (double)c.phi[q][a]);
+      c.wphi[q][a] = (float)(t.wh[q] * t.phi[q][a]);
+      c.wdphi[q][a] = (float)(t.wh[q] * t.dphi[q][a]);
     }
-  }
-  cudaError_t e = cudaMemcpyToSymbol(c32_phi, phi, sizeof(phi));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_wphi, wphi, sizeof(wphi));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_wdphi, wdphi, sizeof(wdphi));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_pp, pp, sizeof(pp));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_pm, pm, sizeof(pm));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_xi, xi, sizeof(xi));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_wh, wh, sizeof(wh));
-  float phil[MAXM][MAXM] = {}, xil[MAXM] = {}, w2h[MAXM * MAXM] = {}, w2l[MAXM * MAXM] = {};
-  for (int q = 0; q <= P; q++) {
-    xil[q] = (float)(t.xi[q] - (double)xi[q]);
-    for (int a = 0; a <= P; a++) phil[q][a] = (float)(t.phi[q][a] - (double)phi[q][a]);
     for (int r = 0; r <= P; r++) {
       const double w2 = t.wh[q] * t.wh[r];
-      w2h[q * (P + 1) + r] = (float)w2;
-      w2l[q * (P + 1) + r] = (float)(w2 - (double)w2h[q * (P + 1) + r]);
+      c.w2h[q * (P + 1) + r] = (float)w2;
+      c.w2l[q * (P + 1) + r] = (float)(w2 - (double)c.w2h[q * (P + 1) + r]);
     }
   }
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_phil, phil, sizeof(phil));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_xil, xil, sizeof(xil));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_w2h, w2h, sizeof(w2h));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c32_w2l, w2l, sizeof(w2l));
-  return e;
+  return c;
+}
+
+// this translation unit's slice P of the tables (internal linkage: every
+// translation unit that includes this header has its own copy of the tables,
+// and a merged instantiation would fill another unit's copy)
+template <int P>
+static cudaError_t upload_tables32_impl(const Tables& t) {
+  const Tab32 c = make_tab32<P>(t);
+  return cudaMemcpyToSymbol(c32t, &c, sizeof(Tab32), P * sizeof(Tab32));
 }
 
 }  // namespace dg

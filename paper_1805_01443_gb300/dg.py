@@ -26,7 +26,9 @@ DG_ERR_NOMEM = -6
 EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_dt", "dg_sync",
             "dg_rhs", "dg_torque", "dg_torque_series", "dg_fetch", "dg_set_state", "dg_get_time",
             "dg_conserved", "dg_set_stream", "dg_shape", "dg_destroy", "dg_last_error",
-            "dg_set_timing", "dg_timing", "dg_conserved_static"]
+            "dg_set_timing", "dg_timing", "dg_conserved_static", "dg_batch_create",
+            "dg_batch_config", "dg_batch_get_config", "dg_batch_tune", "dg_batch_step",
+            "dg_batch_sync", "dg_batch_destroy"]
 
 
 class DgMesh(ctypes.Structure):
@@ -97,6 +99,14 @@ def lib(build_if_missing=True):
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, _VP, _VP]
         L.dg_last_error.argtypes = [_VP]
         L.dg_last_error.restype = ctypes.c_char_p
+        L.dg_batch_create.argtypes = [P(_VP), P(_VP), ctypes.c_int]
+        L.dg_batch_config.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.dg_batch_get_config.argtypes = [_VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
+        L.dg_batch_tune.argtypes = [_VP, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
+                                    P(ctypes.c_int), _DP]
+        L.dg_batch_step.argtypes = [_VP, ctypes.c_int]
+        L.dg_batch_sync.argtypes = [_VP]
+        L.dg_batch_destroy.argtypes = [_VP]
         _lib = L
     return _lib
 
@@ -326,3 +336,56 @@ def dg_conserved_static(coeffs, dx, dy, out, stream=None):
 
 def dg_destroy(d):
     d.close()
+
+
+class Batch:
+    """Several precision-form discs advanced together (a dg_batch).  The discs
+    must outlive the batch; after batched steps each Disc is used as usual."""
+
+    POLICIES = ("given", "costliest-first", "row-interleaved")
+
+    def __init__(self, discs):
+        L = lib()
+        self.discs = list(discs)
+        arr = (_VP * len(self.discs))(*[d.h for d in self.discs])
+        b = _VP()
+        _check(L.dg_batch_create(ctypes.byref(b), arr, len(self.discs)))
+        self.b = b
+
+    def config(self, policy=1, dynamic=1, ctas_per_sm=0):
+        _check(lib().dg_batch_config(self.b, policy, dynamic, ctas_per_sm))
+
+    def get_config(self):
+        p, d, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().dg_batch_get_config(self.b, ctypes.byref(p), ctypes.byref(d), ctypes.byref(c)))
+        return {"policy": p.value, "dynamic": d.value, "ctas_per_sm": c.value}
+
+    def tune(self, steps=3):
+        p, d, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(lib().dg_batch_tune(self.b, steps, ctypes.byref(p), ctypes.byref(d), ctypes.byref(c),
+                                   ctypes.byref(ms)))
+        return {"policy": p.value, "dynamic": d.value, "ctas_per_sm": c.value, "ms_per_step": ms.value}
+
+    def step(self, n=1):
+        _check(lib().dg_batch_step(self.b, n))
+
+    def sync(self):
+        _check(lib().dg_batch_sync(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().dg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

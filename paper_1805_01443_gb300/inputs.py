@@ -75,6 +75,36 @@ def uniform_state(n=8, order=2, kind=1, vx0=0.0, vy0=0.0, bc=0, h=0.0):
     return cfg
 
 
+def batch_discs(n=48, seed0=100, prec=1):
+    """Batched workload: n independent planet discs (damping zones as above),
+    instance k with seed seed0 + k, mesh {128, 256, 384, 512}^2 cycling with k,
+    degree {2, 3, 4} cycling with k, and planet mass q = 10^U(-6, -4) drawn
+    from the instance's seed."""
+    sizes, orders = (128, 256, 384, 512), (2, 3, 4)
+    out = []
+    for k in range(n):
+        seed = seed0 + k
+        q = 10.0 ** np.random.Generator(np.random.PCG64(seed)).uniform(-6.0, -4.0)
+        cfg = _disc_base(sizes[k % 4], orders[k % 3], seed, planet_q=float(q), damping=True)
+        cfg["disc"]["prec"] = prec
+        out.append(cfg)
+    return out
+
+
+def batch_small(prec=1):
+    """Small mixed batch for parity tests: degrees 1-4, square and rectangular
+    meshes, tile rows with a ragged last tile."""
+    shapes = [(40, 24, 1, 1e-5), (48, 48, 2, 3e-5), (64, 32, 3, 1e-4), (72, 40, 4, 3e-5),
+              (32, 32, 4, 1e-6), (96, 64, 2, 1e-4)]
+    out = []
+    for k, (nx, ny, p, q) in enumerate(shapes):
+        cfg = _disc_base(nx, p, 200 + k, planet_q=q, damping=True)
+        cfg["mesh"]["ny"] = ny
+        cfg["disc"]["prec"] = prec
+        out.append(cfg)
+    return out
+
+
 WORKLOADS = {
     "disc_p2_64": disc_small,
     "disc_p4_256": disc_planet,
