@@ -35,7 +35,9 @@ class RefDisc(ctypes.Structure):
                 ("noise_amp", ctypes.c_double), ("seed", ctypes.c_ulonglong),
                 ("rdamp_in", ctypes.c_double), ("rdamp_out", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("rk", ctypes.c_int), ("prec", ctypes.c_int),
-                ("amp", ctypes.c_double), ("vx0", ctypes.c_double), ("vy0", ctypes.c_double)]
+                ("amp", ctypes.c_double), ("vx0", ctypes.c_double), ("vy0", ctypes.c_double),
+                ("limiter", ctypes.c_int), ("tvb_m", ctypes.c_double), ("positivity", ctypes.c_int),
+                ("ring_r", ctypes.c_double), ("ring_p", ctypes.c_double)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -58,6 +60,10 @@ def lib():
         L.ref_damp.argtypes = [vp, ctypes.c_double]
         L.ref_torque.argtypes = [vp, _DP, _DP]
         L.ref_torque_now.argtypes = [vp, ctypes.c_double, _DP, _DP]
+        L.ref_indicator.argtypes = [vp, ctypes.c_double, ctypes.c_void_p]
+        L.ref_limit.argtypes = [vp]
+        L.ref_limit_flags.argtypes = [vp, ctypes.c_void_p]
+        L.ref_step_so.argtypes = [vp, ctypes.c_int]
         L.ref_fetch.argtypes = [vp, _DP]
         L.ref_set_state.argtypes = [vp, _DP, ctypes.c_double, ctypes.c_long]
         L.ref_get_time.argtypes = [vp, _DP, _DP, ctypes.POINTER(ctypes.c_long)]
@@ -173,6 +179,22 @@ class Oracle:
 
     def damp(self, dt):
         _check(lib().ref_damp(self.h, dt), "damp")
+
+    def indicator(self, M):
+        """TVB-minmod troubled-cell flags of the current state, uint8 [ny, nx]."""
+        out = np.zeros((self.mesh.ny, self.mesh.nx), dtype=np.uint8)
+        _check(lib().ref_indicator(self.h, M, out.ctypes.data_as(ctypes.c_void_p)), "indicator")
+        return out
+
+    def limit(self):
+        _check(lib().ref_limit(self.h), "limit")
+
+    def limit_flags(self, flags):
+        f = np.ascontiguousarray(flags, dtype=np.uint8).reshape(self.mesh.ny, self.mesh.nx)
+        _check(lib().ref_limit_flags(self.h, f.ctypes.data_as(ctypes.c_void_p)), "limit_flags")
+
+    def step_so(self, n=1):
+        _check(lib().ref_step_so(self.h, n), "step_so")
 
     def torque(self):
         g = ctypes.c_double()

@@ -338,7 +338,7 @@ static void grad_phi(const ref_state *s, double x, double y, double xp, double y
 /* background primitive state (rho, vx, vy, p) of the chosen initial condition,
    without noise: the damping target Q0 and the fixed ghost state */
 static void background_prim(const ref_state *s, double x, double y, double *w) {
-  if (s->d.ic == 0) {
+  if (s->d.ic == 0 || s->d.ic == 3) {
     /* READING (configs): Sigma = max(r^slope, floor); rotational equilibrium
        v_phi^2 = r dPhi_s/dr + (r/Sigma) d(c_s^2 Sigma)/dr (Sec. 5.1) with c_s = h v_K,
        which for Sigma ~ r^s gives (1 + (s-1) h^2)/r outside r_s and
@@ -358,6 +358,9 @@ static void background_prim(const ref_state *s, double x, double y, double *w) {
     w[1] = -vphi * y / r;
     w[2] = vphi * x / r;
     w[3] = h * h * vk2_at(s, r) * sig; /* p = c_s,iso^2 Sigma (adiabatic disc) */
+    /* READING (config 5): the imposed shock ring is a pressure step, p x ring_p
+       inside r < ring_r, on the same disc (sharp at the nodes, then projected) */
+    if (s->d.ic == 3 && r < s->d.ring_r) w[3] *= s->d.ring_p;
   } else if (s->d.ic == 1) {
     double lx = s->mesh.x1 - s->mesh.x0, ly = s->mesh.y1 - s->mesh.y0;
     double ph = TWO_PI * ((x - s->mesh.x0) / lx + (y - s->mesh.y0) / ly);
@@ -397,7 +400,7 @@ static void project_element(const ref_state *s, int i, int j, int noise, double 
       double x = xc + 0.5 * s->dx * xq[q], y = yc + 0.5 * s->dy * xq[r];
       double w[4], u[4];
       background_prim(s, x, y, w);
-      if (noise && s->d.ic == 0 && s->d.noise_amp > 0.0) {
+      if (noise && (s->d.ic == 0 || s->d.ic == 3) && s->d.noise_amp > 0.0) {
         /* READING (configs): additive U(-amp, amp) on Sigma at each projection node,
            keyed by (seed, element, node). */
         double U;
@@ -581,6 +584,22 @@ static void rhs_eval(void *vctx, double t, const double *u, double *out) {
 /* Sec. 2.3: dt_K = C/(2p+1) * (sum_i (|v_i| + c_s)/dx_i)^-1 from the element
    averages (mode 0), global minimum.  READING: for the isothermal EOS c_s is
    taken at the element centre. */
+/* the factor of C in the CFL step (Sec. 2.3): 1/(2p+1), and with the
+   positivity limiter min(1/(2p+1), w_1/2) where w_1 is the first weight of the
+   N-point Gauss-Lobatto rule normalised to sum 1.  READING: N is the smallest
+   count with 2N - 3 >= p (the rule Zhang & Shu use for degree p), and the
+   endpoint weight of that rule is 2/(N(N-1)) on [-1,1], i.e. 1/(N(N-1)). */
+static double cfl_factor(const ref_state *s) {
+  double f = 1.0 / (2.0 * s->p + 1.0);
+  if (s->d.positivity) {
+    int N = 2;
+    while (2 * N - 3 < s->p) N++;
+    double w1 = 1.0 / (N * (N - 1.0));
+    if (0.5 * w1 < f) f = 0.5 * w1;
+  }
+  return f;
+}
+
 static double cfl_dt(const ref_state *s, const double *u) {
   const int nx = s->mesh.nx, ny = s->mesh.ny;
   double best = INFINITY;
@@ -596,7 +615,7 @@ static double cfl_dt(const ref_state *s, const double *u) {
         double xc = s->mesh.x0 + (i + 0.5) * s->dx, yc = s->mesh.y0 + (j + 0.5) * s->dy;
         c = sqrt(cs2_at(s, xc, yc));
       }
-      double dtk = s->d.cfl / (2.0 * s->p + 1.0) / ((fabs(vx) + c) / s->dx + (fabs(vy) + c) / s->dy);
+      double dtk = s->d.cfl * cfl_factor(s) / ((fabs(vx) + c) / s->dx + (fabs(vy) + c) / s->dy);
       if (!(dtk >= best)) best = dtk; /* NaN propagates */
     }
   return best;
@@ -712,6 +731,248 @@ static void torque_eval(const ref_state *s, const double *u, double t, double *g
 /* ------------------------------------------------------------------------ */
 /* Public entry points                                                       */
 
+/* ------------------------------------------------------------------------ */
+/* Troubled-cell indicator and limiters                                       */
+
+static int all_finite(const ref_state *s);
+
+#define SQRT3 1.7320508075688772935274463415059 /* phi_1(+1) / phi_0: the linear mode's face increment */
+
+/* minmod of three numbers */
+static double minmod3(double a, double b, double c) {
+  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+  return 0.0;
+}
+
+/* Cockburn & Shu's TVB-modified minmod: a1 itself when |a1| <= M h^2 */
+static double tvb_minmod(double a1, double a2, double a3, double mh2) {
+  if (fabs(a1) <= mh2) return a1;
+  return minmod3(a1, a2, a3);
+}
+
+/* element mean (mode 0) of each variable of element (i, j) of u, outside
+   elements by the boundary rule (transmissive: the element's own mean) */
+static void mean_at(const ref_state *s, const double *u, int i, int j, int ii, int jj, double *out) {
+  double c[MAXV][MAXN];
+  if (!gather(s, u, ii, jj, c)) gather(s, u, i, j, c);
+  for (int v = 0; v < s->nv; v++) out[v] = c[v][0];
+}
+
+/* TVB test of element (i, j): per variable and direction, the face increment
+   of the linear mode, sqrt(3) u_(1,0) in x and sqrt(3) u_(0,1) in y, against
+   the forward and backward differences of the element means.  Returns 1 when
+   any of them would be changed (the element is troubled) and gives the
+   limited increments. */
+static int tvb_element(const ref_state *s, const double *u, int i, int j, double M, double *sx,
+                       double *sy) {
+  const int m = s->m, nv = s->nv;
+  double mL[MAXV], mR[MAXV], mB[MAXV], mT[MAXV];
+  mean_at(s, u, i, j, i - 1, j, mL);
+  mean_at(s, u, i, j, i + 1, j, mR);
+  mean_at(s, u, i, j, i, j - 1, mB);
+  mean_at(s, u, i, j, i, j + 1, mT);
+  const double mhx = M * s->dx * s->dx, mhy = M * s->dy * s->dy;
+  int troubled = 0;
+  for (int v = 0; v < nv; v++) {
+    const double mean = u[cidx(s, v, 0, i, j)];
+    const double ax = SQRT3 * u[cidx(s, v, m, i, j)];   /* mode (a, b) = (1, 0) */
+    const double ay = SQRT3 * u[cidx(s, v, 1, i, j)];   /* mode (0, 1) */
+    sx[v] = tvb_minmod(ax, mR[v] - mean, mean - mL[v], mhx);
+    sy[v] = tvb_minmod(ay, mT[v] - mean, mean - mB[v], mhy);
+    if (sx[v] != ax || sy[v] != ay) troubled = 1;
+  }
+  return troubled;
+}
+
+static void tvb_flags(const ref_state *s, const double *u, double M, unsigned char *flags) {
+  const int nx = s->mesh.nx, ny = s->mesh.ny;
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < (long)nx * ny; e++) {
+    double sx[MAXV], sy[MAXV];
+    flags[e] = (unsigned char)tvb_element(s, u, (int)(e % nx), (int)(e / nx), M, sx, sy);
+  }
+}
+
+/* A troubled element becomes its mean plus the limited linear modes in x and
+   y, every other mode zero (all variables).  Means are kept, so limiting in
+   place does not change what the neighbours see. */
+static void limit_p1(const ref_state *s, double *u, const unsigned char *flags) {
+  const int nx = s->mesh.nx, ny = s->mesh.ny, m = s->m, M = s->M, nv = s->nv;
+  double *lim = s->tmp; /* limited increments, [e][2 * nv] */
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < (long)nx * ny; e++) {
+    if (!flags[e]) continue;
+    double sx[MAXV], sy[MAXV];
+    tvb_element(s, u, (int)(e % nx), (int)(e / nx), s->d.tvb_m, sx, sy);
+    for (int v = 0; v < nv; v++) {
+      lim[e * 2 * MAXV + v] = sx[v];
+      lim[e * 2 * MAXV + MAXV + v] = sy[v];
+    }
+  }
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < (long)nx * ny; e++) {
+    if (!flags[e]) continue;
+    const int i = (int)(e % nx), j = (int)(e / nx);
+    for (int v = 0; v < nv; v++) {
+      for (int k = 1; k < M; k++) u[cidx(s, v, k, i, j)] = 0.0;
+      u[cidx(s, v, m, i, j)] = lim[e * 2 * MAXV + v] / SQRT3;
+      u[cidx(s, v, 1, i, j)] = lim[e * 2 * MAXV + MAXV + v] / SQRT3;
+    }
+  }
+}
+
+static double pressure_of(const ref_state *s, const double *U) {
+  return (s->eos.gamma - 1.0) * (U[3] - 0.5 * (U[1] * U[1] + U[2] * U[2]) / U[0]);
+}
+
+/* point values of element coefficients c at check point n: the m x m volume
+   nodes (n < M), then the m points of the faces x = +1, x = -1, y = +1, y = -1 */
+static void eval_point(const ref_state *s, double c[MAXV][MAXN], int n, double *U) {
+  const int M = s->M, m = s->m;
+  for (int v = 0; v < s->nv; v++) {
+    double acc = 0.0;
+    for (int k = 0; k < M; k++) {
+      double phi;
+      if (n < M) phi = s->Phi[k][n];
+      else {
+        int f = (n - M) / m, r = (n - M) % m;
+        phi = f == 0 ? s->FxP[k][r] : f == 1 ? s->FxM[k][r] : f == 2 ? s->FyP[k][r] : s->FyM[k][r];
+      }
+      acc += c[v][k] * phi;
+    }
+    U[v] = acc;
+  }
+}
+
+/* Zhang & Shu's positivity limiter (Sec. 2.3) on one element.  READING: the
+   check points are the points where the operator evaluates the solution (the
+   m x m volume nodes and the 4m face points), eps = 1e-13; density first
+   (theta = (mean - eps)/(mean - min)), then pressure with
+   theta = min over points with p < eps of (p(mean) - eps)/(p(mean) - p(point)),
+   which keeps p >= eps because p is concave in the conserved variables. */
+static void positivity_element(const ref_state *s, double c[MAXV][MAXN]) {
+  const double eps = 1e-13;
+  const int M = s->M, np = s->M + 4 * s->m, nv = s->nv;
+  double U[MAXV];
+  double rmin = INFINITY;
+  for (int n = 0; n < np; n++) {
+    eval_point(s, c, n, U);
+    if (U[0] < rmin) rmin = U[0];
+  }
+  const double rbar = c[0][0];
+  if (rmin < eps && rbar > eps) {
+    double th = (rbar - eps) / (rbar - rmin);
+    if (th < 0.0) th = 0.0;
+    for (int k = 1; k < M; k++) c[0][k] *= th;
+  }
+  if (nv < 4) return;
+  double Ub[MAXV];
+  for (int v = 0; v < nv; v++) Ub[v] = c[v][0];
+  const double pbar = pressure_of(s, Ub);
+  if (!(pbar > eps)) return;
+  double th = 1.0;
+  for (int n = 0; n < np; n++) {
+    eval_point(s, c, n, U);
+    const double p = pressure_of(s, U);
+    if (p < eps) {
+      const double t = (pbar - eps) / (pbar - p);
+      if (t < th) th = t;
+    }
+  }
+  if (th < 1.0) {
+    if (th < 0.0) th = 0.0;
+    for (int v = 0; v < nv; v++)
+      for (int k = 1; k < M; k++) c[v][k] *= th;
+  }
+}
+
+static void positivity_all(const ref_state *s, double *u) {
+  const int nx = s->mesh.nx, ny = s->mesh.ny;
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < (long)nx * ny; e++) {
+    const int i = (int)(e % nx), j = (int)(e / nx);
+    double c[MAXV][MAXN];
+    gather(s, u, i, j, c);
+    positivity_element(s, c);
+    for (int v = 0; v < s->nv; v++)
+      for (int k = 0; k < s->M; k++) u[cidx(s, v, k, i, j)] = c[v][k];
+  }
+}
+
+/* the limiter of a stage value: troubled cells by the TVB test (limiter 1) or
+   by the given flags, then positivity */
+static void limit_apply(ref_state *s, double *u, const unsigned char *given) {
+  const size_t ne = (size_t)s->mesh.nx * s->mesh.ny;
+  if (given || s->d.limiter == 1) {
+    unsigned char *fl = (unsigned char *)malloc(ne);
+    if (given) memcpy(fl, given, ne);
+    else tvb_flags(s, u, s->d.tvb_m, fl);
+    limit_p1(s, u, fl);
+    free(fl);
+  }
+  if (s->d.positivity) positivity_all(s, u);
+}
+
+/* One SSP(3,3) step in Shu-Osher form (Sec. 3.1, Table A5 with c = (0, 1, 1/2)),
+   each stage value limited.  READING: after the last stage the damping, the
+   torque and the CFL data are taken first (limiting keeps the element means
+   the CFL step uses) and the limiter closes the step. */
+static int do_step_so(ref_state *s, int fixed, double dtf) {
+  double dt = fixed ? dtf : cfl_dt(s, s->u);
+  if (!(dt > 0.0) || !isfinite(dt)) return -4;
+  const long N = (long)s->ncoef;
+  double *k = s->kbuf[0], *u1 = s->kbuf[1], *u2 = s->kbuf[2], *u = s->u;
+  op_ctx ctx = {s};
+  const double t = s->t;
+  rhs_eval(&ctx, t, u, k);
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < N; e++) u1[e] = u[e] + dt * k[e];
+  limit_apply(s, u1, NULL);
+  rhs_eval(&ctx, t + dt, u1, k);
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < N; e++) u2[e] = 0.75 * u[e] + 0.25 * (u1[e] + dt * k[e]);
+  limit_apply(s, u2, NULL);
+  rhs_eval(&ctx, t + 0.5 * dt, u2, k);
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < N; e++) u[e] = u[e] / 3.0 + 2.0 / 3.0 * (u2[e] + dt * k[e]);
+  damp_apply(s, u, dt);
+  torque_eval(s, u, t + dt, &s->torque, &s->torque_abs);
+  limit_apply(s, u, NULL);
+  s->t += dt;
+  s->dt = dt;
+  s->step += 1;
+  if (!all_finite(s)) return -4;
+  return 0;
+}
+
+int ref_indicator(ref_state *s, double M, unsigned char *flags) {
+  if (!s || !flags || !(M >= 0.0)) return -1;
+  tvb_flags(s, s->u, M, flags);
+  return 0;
+}
+
+int ref_limit(ref_state *s) {
+  if (!s) return -1;
+  limit_apply(s, s->u, NULL);
+  return 0;
+}
+
+int ref_limit_flags(ref_state *s, const unsigned char *flags) {
+  if (!s || !flags) return -1;
+  limit_apply(s, s->u, flags);
+  return 0;
+}
+
+int ref_step_so(ref_state *s, int n) {
+  if (!s || n < 0 || s->d.rk != 3) return -1;
+  for (int i = 0; i < n; i++) {
+    int rc = do_step_so(s, 0, 0.0);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
 int ref_nthreads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
@@ -729,8 +990,12 @@ int ref_init(ref_state **out, const ref_mesh *mesh, int order, const ref_eos *eo
   if (mesh->bc < 0 || mesh->bc > 2) return -1;
   if (eos->kind < 0 || eos->kind > 2) return -2;
   if (eos->kind == 1 && !(eos->gamma > 1.0)) return -1;
-  if ((eos->kind == 0 || disc->star || disc->ic == 0) && !(disc->r_soft > 0.0)) return -1;
-  if (disc->ic < 0 || disc->ic > 2) return -2;
+  if ((eos->kind == 0 || disc->star || disc->ic == 0 || disc->ic == 3) && !(disc->r_soft > 0.0)) return -1;
+  if (disc->ic < 0 || disc->ic > 3) return -2;
+  if (disc->ic == 3 && (eos->kind != 1 || !(disc->ring_p > 0.0))) return -1;
+  if (disc->limiter < 0 || disc->limiter > 1 || disc->positivity < 0 || disc->positivity > 1) return -1;
+  if ((disc->limiter || disc->positivity) && disc->rk != 3) return -2;
+  if (disc->limiter && !(disc->tvb_m >= 0.0)) return -1;
   tableau T;
   if (get_tableau(disc->rk, &T)) return -2;
   ref_state *s = (ref_state *)calloc(1, sizeof(ref_state));
@@ -788,6 +1053,10 @@ int ref_init(ref_state **out, const ref_mesh *mesh, int order, const ref_eos *eo
     return -1;
   }
   init_ic(s);
+  /* READING: with the limiters on they also act on the projected initial
+     data (the adiabatic disc's pressure vanishes at the centre, so its
+     projection dips below zero at some nodes) */
+  if (s->d.limiter || s->d.positivity) limit_apply(s, s->u, NULL);
   s->t = 0.0;
   s->dt = 0.0;
   s->step = 0;
@@ -832,8 +1101,9 @@ static int do_step(ref_state *s, int fixed, double dtf) {
 
 int ref_step(ref_state *s, int n) {
   if (!s || n < 0) return -1;
+  const int lim = s->d.limiter || s->d.positivity;
   for (int i = 0; i < n; i++) {
-    int rc = do_step(s, 0, 0.0);
+    int rc = lim ? do_step_so(s, 0, 0.0) : do_step(s, 0, 0.0);
     if (rc) return rc;
   }
   return 0;
@@ -841,8 +1111,9 @@ int ref_step(ref_state *s, int n) {
 
 int ref_step_dt(ref_state *s, int n, double dt) {
   if (!s || n < 0 || !(dt > 0.0)) return -1;
+  const int lim = s->d.limiter || s->d.positivity;
   for (int i = 0; i < n; i++) {
-    int rc = do_step(s, 1, dt);
+    int rc = lim ? do_step_so(s, 1, dt) : do_step(s, 1, dt);
     if (rc) return rc;
   }
   return 0;

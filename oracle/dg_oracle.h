@@ -58,7 +58,7 @@ typedef struct {
 } ref_planet;
 
 typedef struct {
-  int ic;                     /* 0 Keplerian disc, 1 density wave, 2 uniform state */
+  int ic;                     /* 0 Keplerian disc, 1 density wave, 2 uniform state, 3 disc with a pressure ring */
   int star;                   /* 1: softened point-mass star potential in the source */
   double r_soft;              /* star softening radius r_s */
   double sigma_slope;         /* Sigma ~ r^slope */
@@ -70,6 +70,10 @@ typedef struct {
   int rk;                     /* 2 SSP(2,2), 3 SSP(3,3), 4 SSP-RK(4,5), 5 Cash-Karp */
   int prec;                   /* ignored by the oracle (always FP64) */
   double amp, vx0, vy0;       /* wave amplitude and uniform velocity (ic 1, 2) */
+  int limiter;                /* 0 none; 1 TVB-minmod troubled cells reduced to limited P1 after each stage */
+  double tvb_m;               /* TVB constant M of the modified minmod (0: plain minmod) */
+  int positivity;             /* 1: Zhang-Shu positivity limiter after each stage (Sec. 2.3) */
+  double ring_r, ring_p;      /* ic 3: the disc of ic 0 with pressure x ring_p inside r < ring_r */
 } ref_disc;
 
 typedef struct ref_state ref_state;
@@ -91,6 +95,17 @@ int  ref_nodal(ref_state *s, double *out);               /* [var][q*m+r][j][i] a
 int  ref_l1_wave(ref_state *s, double t, int var, double *err); /* Sec. 4.1 L1 norm vs exact wave */
 int  ref_ghosts(ref_state *s, double *out);              /* bc 1 ghost coefficients: [side][var][k][n] */
 int  ref_nthreads(void);
+/* troubled-cell flags (1 byte per element, [j][i]) of the current state by the
+   TVB-modified minmod test with constant M */
+int  ref_indicator(ref_state *s, double M, unsigned char *flags);
+/* the limiter of the step (TVB limiting of troubled cells if limiter = 1, then
+   positivity if set) applied once to the current state */
+int  ref_limit(ref_state *s);
+/* limited-P1 reconstruction of the elements flagged in `flags` (then
+   positivity if set), for flags from another indicator */
+int  ref_limit_flags(ref_state *s, const unsigned char *flags);
+/* n SSP(3,3) steps in Shu-Osher form (limiters applied if configured) */
+int  ref_step_so(ref_state *s, int n);
 
 /* tables and building blocks exposed for pinning */
 int  ref_gauss_legendre(int m, double *x, double *w);

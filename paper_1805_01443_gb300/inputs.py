@@ -23,7 +23,8 @@ def _disc_base(n, order, seed, planet_q=None, damping=False, bc=1):
                    "phi0": 0.0, "enabled": 0},
         "disc": {"ic": 0, "star": 1, "r_soft": 0.2, "sigma_slope": -0.5, "sigma_floor": 1e-4,
                  "noise_amp": 1e-4, "seed": seed, "rdamp_in": 0.0, "rdamp_out": 0.0,
-                 "cfl": 0.1, "rk": 3, "prec": 0, "amp": 0.0, "vx0": 0.0, "vy0": 0.0},
+                 "cfl": 0.1, "rk": 3, "prec": 0, "amp": 0.0, "vx0": 0.0, "vy0": 0.0,
+                 "limiter": 0, "tvb_m": 50.0, "positivity": 0, "ring_r": 0.0, "ring_p": 1.0},
     }
     if planet_q is not None:
         cfg["planet"]["q"] = planet_q
@@ -59,7 +60,8 @@ def density_wave(n=32, order=2, amp=0.2):
         "planet": {"q": 0.0, "r_p": 1.0, "eps": 0.03, "omega_p": 1.0, "phi0": 0.0, "enabled": 0},
         "disc": {"ic": 1, "star": 0, "r_soft": 0.2, "sigma_slope": -0.5, "sigma_floor": 1e-4,
                  "noise_amp": 0.0, "seed": 0, "rdamp_in": 0.0, "rdamp_out": 0.0, "cfl": 0.1,
-                 "rk": 3, "prec": 0, "amp": amp, "vx0": 1.0, "vy0": 1.0},
+                 "rk": 3, "prec": 0, "amp": amp, "vx0": 1.0, "vy0": 1.0, "limiter": 0,
+                 "tvb_m": 50.0, "positivity": 0, "ring_r": 0.0, "ring_p": 1.0},
     }
 
 
@@ -72,6 +74,19 @@ def uniform_state(n=8, order=2, kind=1, vx0=0.0, vy0=0.0, bc=0, h=0.0):
     cfg["eos"]["kind"] = kind
     cfg["eos"]["h"] = h
     cfg["mesh"]["bc"] = bc
+    return cfg
+
+
+def shock_ring(n=1024, order=3, seed=5, q=1e-3, limiter=1, positivity=1):
+    """Adiabatic (gamma = 1.4) planet disc with an imposed shock ring: the disc
+    of Sec. 5.1 with pressure x10 inside r < 1.5, gap-opening planet q = 1e-3,
+    damping zones, seeded noise; TVB-limited troubled cells and the
+    positivity limiter."""
+    cfg = _disc_base(n, order, seed, planet_q=q, damping=True)
+    cfg["eos"]["kind"] = 1
+    cfg["eos"]["gamma"] = 1.4
+    cfg["disc"].update({"ic": 3, "ring_r": 1.5, "ring_p": 10.0, "limiter": limiter,
+                        "positivity": positivity})
     return cfg
 
 
