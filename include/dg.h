@@ -93,7 +93,9 @@ typedef struct {
   int ic;             /* 0 rotational-equilibrium disc Sigma = max(r^slope, floor)
                          (Sec. 5.1 equilibrium with c_s = h v_K); 1 density wave
                          rho = 1 + amp sin(2 pi (x~ + y~)), v = (vx0, vy0), p = 1;
-                         2 uniform rho = 1, v = (vx0, vy0), p = 1 */
+                         2 uniform rho = 1, v = (vx0, vy0), p = 1; 3 the disc of
+                         ic 0 (adiabatic only) with pressure x ring_p inside
+                         r < ring_r (an imposed shock ring) */
   int star;           /* 1: softened point-mass star at the origin in the source;
                          Phi_* = -1/r for r >= r_soft, solid-body core inside */
   double r_soft;      /* star softening radius (> 0 for kind 0, star or ic 0) */
@@ -112,6 +114,20 @@ typedef struct {
                          in FP64 once, FP64 torque reduction and sums; the
                          state is exchanged as FP64 u = u_b + delta */
   double amp, vx0, vy0;
+  int limiter;        /* troubled-cell limiting after every RK stage (FP64 form,
+                         SSP(3,3)): 0 none; 1 the TVB-modified minmod test
+                         (Cockburn-Shu) per variable and direction on the linear
+                         modes against the differences of the neighbours' means,
+                         troubled elements reduced to their mean plus the limited
+                         linear modes; 2 the same reduction on the flags of the
+                         learned indicator (dg_set_indicator), the TVB test while
+                         no network is set */
+  double tvb_m;       /* TVB constant M (|slope| <= M h^2 is never limited); 0: minmod */
+  int positivity;     /* 1: Zhang-Shu positivity limiter after every stage
+                         (Sec. 2.3; density, and pressure for the adiabatic
+                         EOS, >= 1e-13 at the volume and face quadrature points),
+                         with the time-step factor min(1/(2p+1), w_1/2) */
+  double ring_r, ring_p; /* ic 3 ring radius and pressure factor */
 } dg_disc;
 
 /* Create a handle: validates the arguments, allocates device memory with
@@ -218,6 +234,28 @@ int dg_timing(dg_handle *h, double *stage_ms, long long *nstage);
    if the address lookup or a launch fails. */
 int dg_conserved_static(const double *coeffs, int nv, int nmodes, int nx, int ny, double dx,
                         double dy, double *out, void *stream);
+
+/* ---- Troubled cells and limiters (FP64 form; DG_ERR_UNSUPPORTED otherwise) --
+   The TVB-modified minmod test of Cockburn & Shu, the limited-P1 reduction of
+   troubled elements and the positivity limiter of Sec. 2.3 (Zhang & Shu), as
+   dg_disc.limiter / tvb_m / positivity describe them.  Flags are one byte per
+   element, 1 = troubled, layout [j][i] (nx*ny bytes, caller-owned host
+   buffers).  All four synchronise. */
+
+/* Flags of the TVB test with constant M on the current state (state unchanged). */
+int dg_indicator(dg_handle *h, double M, unsigned char *flags);
+
+/* The step's limiter (TVB limiting if dg_disc.limiter > 0, then positivity if
+   set) applied once to the current state. */
+int dg_limit(dg_handle *h);
+
+/* Limited-P1 reduction of the elements flagged in `flags` (from any
+   indicator), then positivity if set, on the current state. */
+int dg_limit_flags(dg_handle *h, const unsigned char *flags);
+
+/* TVB flags computed by the last limiter pass, i.e. of the last stage value
+   before it was limited (the labels of the learned indicator). */
+int dg_last_flags(dg_handle *h, unsigned char *flags);
 
 /* Release the handle and the device memory it allocated. */
 int dg_destroy(dg_handle *h);

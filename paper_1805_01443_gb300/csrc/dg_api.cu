@@ -60,6 +60,8 @@ struct dg_handle {
   float* Disc;         // per-element projected-vs-analytic background discrepancy
   int* TileFlag;
   Tables tab;
+  unsigned char* tflags;  // TVB flags of the last limiter pass (pre-limit) [j][i]
+  unsigned char* gflags;  // flags given to the limiter (learned indicator, dg_limit_flags) [j][i]
   int timing;                                   // bracket stage launches with events
   std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
   size_t ev_used;
@@ -259,7 +261,7 @@ cudaError_t launch_stage_h(dg_handle* h, const StageArgs& a) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t state, canon, gcol, grow, tsb, part, series, cpart, csum;
+  size_t state, canon, gcol, grow, tsb, part, series, cpart, csum, flags8;
   size_t state32, nodes32, db32, bm032, disc32, flags;  // precision form only (0 otherwise)
   size_t total;
 };
@@ -277,9 +279,16 @@ int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* d
   if (order < 1 || order > MAXP) return fail(nullptr, DG_ERR_UNSUPPORTED, "order %d not in 1..4", order);
   if (eos->kind < 0 || eos->kind > 2) return fail(nullptr, DG_ERR_UNSUPPORTED, "eos kind %d", eos->kind);
   if (eos->kind == 1 && !(eos->gamma > 1.0)) return fail(nullptr, DG_ERR_ARG, "gamma must be > 1");
-  if ((eos->kind == 0 || disc->star || disc->ic == 0) && !(disc->r_soft > 0.0))
+  if ((eos->kind == 0 || disc->star || disc->ic == 0 || disc->ic == 3) && !(disc->r_soft > 0.0))
     return fail(nullptr, DG_ERR_ARG, "r_soft must be > 0");
-  if (disc->ic < 0 || disc->ic > 2) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
+  if (disc->ic < 0 || disc->ic > 3) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
+  if (disc->ic == 3 && (eos->kind != 1 || !(disc->ring_p > 0.0)))
+    return fail(nullptr, DG_ERR_ARG, "ic 3 needs the adiabatic EOS and ring_p > 0");
+  if (disc->limiter < 0 || disc->limiter > 2 || disc->positivity < 0 || disc->positivity > 1)
+    return fail(nullptr, DG_ERR_ARG, "limiter %d / positivity %d", disc->limiter, disc->positivity);
+  if ((disc->limiter || disc->positivity) && (disc->rk != 3 || disc->prec != 0))
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "limiters need the FP64 form with SSP(3,3)");
+  if (disc->limiter && !(disc->tvb_m >= 0.0)) return fail(nullptr, DG_ERR_ARG, "tvb_m must be >= 0");
   if (disc->rk != 2 && disc->rk != 3) return fail(nullptr, DG_ERR_UNSUPPORTED, "rk %d", disc->rk);
   if (disc->prec != 0 && disc->prec != 1)
     return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form %d", disc->prec);
@@ -287,6 +296,20 @@ int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* d
     return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form 1 needs the locally isothermal disc (eos 0, ic 0)");
   if (!(disc->cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "cfl must be > 0");
   return DG_OK;
+}
+
+// factor of C in the CFL step (Sec. 2.3): 1/(2p+1); with the positivity
+// limiter min(1/(2p+1), w_1/2), w_1 = 1/(N(N-1)) the first weight (sum 1) of
+// the N-point Gauss-Lobatto rule with the smallest N such that 2N - 3 >= p
+double cfl_factor(int p, int positivity) {
+  double f = 1.0 / (2.0 * p + 1.0);
+  if (positivity) {
+    int N = 2;
+    while (2 * N - 3 < p) N++;
+    const double w1 = 1.0 / (N * (N - 1.0));
+    if (0.5 * w1 < f) f = 0.5 * w1;
+  }
+  return f;
 }
 
 Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec) {
@@ -312,7 +335,9 @@ Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec) {
     L.disc32 = align256((size_t)mesh->ny * ntx * TILE * sizeof(float));
     L.flags = align256((size_t)mesh->ny * ntx * sizeof(int));
   }
-  L.total = 3 * L.state + L.canon + 2 * L.gcol + 2 * L.grow + L.tsb + L.part + L.series + L.cpart + L.csum;
+  L.flags8 = align256((size_t)mesh->nx * mesh->ny);
+  L.total = 3 * L.state + L.canon + 2 * L.gcol + 2 * L.grow + L.tsb + L.part + L.series + L.cpart + L.csum +
+            2 * L.flags8;
   if (prec == 1) L.total += L.state + 5 * L.state32 + L.nodes32 + L.db32 + L.bm032 + L.disc32 + L.flags;
   return L;
 }
@@ -386,9 +411,16 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
   return DG_OK;
 }
 
+// the limiter of a stage value (TVB test or given flags, then positivity), in place
+cudaError_t limit_state(dg_handle* h, double* U, const unsigned char* given) {
+  return launch_limit(U, h->GL, h->GR, h->GB, h->GT, given, h->tflags, h->ts, h->dm, h->ph, h->tab, h->p,
+                      h->nv, h->ph.limiter != 0 || given != nullptr, 1, h->ph.positivity, h->stream);
+}
+
 int do_steps(dg_handle* h, int n, double fixed_dt) {
   if (!h || n < 0) return fail(h, DG_ERR_ARG, "bad argument");
   if (h->prec == 1) return do_steps32(h, n, fixed_dt);
+  const bool lim = h->ph.limiter || h->ph.positivity;  // SSP(3,3) only (validated)
   StageArgs a;
   memset(&a, 0, sizeof(a));
   a.GL = h->GL;
@@ -405,12 +437,18 @@ int do_steps(dg_handle* h, int n, double fixed_dt) {
     double* nx = h->B[1 - h->cur];
     a.Un = un;
     if (h->disc.rk == 3) {
+      // each stage value is limited; after the last stage the damping, the
+      // torque partials and the CFL minimum (of the means, which limiting
+      // keeps) come first and the limiter closes the step
       a.U = un; a.Out = nx; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
       CU(h, launch_stage_h(h, a));
+      if (lim) CU(h, limit_state(h, nx, nullptr));
       a.U = nx; a.Out = h->Z; a.alpha = 0.75; a.beta = 0.25; a.cstage = 1.0; a.mode = 1;
       CU(h, launch_stage_h(h, a));
+      if (lim) CU(h, limit_state(h, h->Z, nullptr));
       a.U = h->Z; a.Out = nx; a.alpha = 1.0 / 3.0; a.beta = 2.0 / 3.0; a.cstage = 0.5; a.mode = 2;
       CU(h, launch_stage_h(h, a));
+      if (lim) CU(h, limit_state(h, nx, nullptr));
     } else {
       a.U = un; a.Out = h->Z; a.alpha = 0.0; a.beta = 1.0; a.cstage = 0.0; a.mode = 1;
       CU(h, launch_stage_h(h, a));
@@ -497,6 +535,12 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   ph.vx0 = disc->vx0;
   ph.vy0 = disc->vy0;
   ph.cfl = disc->cfl;
+  ph.cfl_fac = cfl_factor(order, disc->positivity);
+  ph.limiter = disc->limiter;
+  ph.tvb_m = disc->tvb_m;
+  ph.positivity = disc->positivity;
+  ph.ring_r = disc->ring_r;
+  ph.ring_p = disc->ring_p;
   h->nparts = dm.ntx * dm.ny;
   h->prec = disc->prec;
   make_tables(order, &h->tab);
@@ -574,6 +618,8 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   h->series = (double*)take(L.series);
   h->cpart = (double*)take(L.cpart);
   h->csum = (double*)take(L.csum);
+  h->tflags = (unsigned char*)take(L.flags8);
+  h->gflags = (unsigned char*)take(L.flags8);
   if (h->prec == 1) {
     h->BG = (double*)take(L.state);
     h->D[0] = (float*)take(L.state32);
@@ -622,6 +668,8 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     if (e == cudaSuccess) { ia.out = h->GB; ia.target = 3; e = launch_init(ia, mesh->nx, h->stream); }
     if (e == cudaSuccess) { ia.out = h->GT; ia.target = 4; e = launch_init(ia, mesh->nx, h->stream); }
   }
+  // with the limiters on they also act on the projected initial data
+  if (e == cudaSuccess && (ph.limiter || ph.positivity)) e = limit_state(h, h->B[0], nullptr);
   if (e != cudaSuccess) {
     fail(h, DG_ERR_CUDA, "init kernels: %s", cudaGetErrorString(e));
     return bail(DG_ERR_CUDA);
@@ -875,6 +923,49 @@ int dg_destroy(dg_handle* h) {
   }
   if (h->owns) cudaFree(h->ws);
   delete h;
+  return DG_OK;
+}
+
+int dg_indicator(dg_handle* h, double M, unsigned char* flags) {
+  if (!h || !flags || !(M >= 0.0)) return fail(h, DG_ERR_ARG, "bad argument");
+  if (h->prec != 0) return fail(h, DG_ERR_UNSUPPORTED, "the indicator works on the FP64 form");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc) return rc;
+  Phys ph = h->ph;
+  ph.tvb_m = M;
+  CU(h, launch_limit(h->B[h->cur], h->GL, h->GR, h->GB, h->GT, nullptr, h->tflags, h->ts, h->dm, ph, h->tab,
+                     h->p, h->nv, 1, 0, 0, h->stream));
+  CU(h, cudaMemcpyAsync(flags, h->tflags, (size_t)h->mesh.nx * h->mesh.ny, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+int dg_limit(dg_handle* h) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  if (h->prec != 0) return fail(h, DG_ERR_UNSUPPORTED, "the limiters work on the FP64 form");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc) return rc;
+  CU(h, limit_state(h, h->B[h->cur], nullptr));
+  return read_state(h, &st);
+}
+
+int dg_limit_flags(dg_handle* h, const unsigned char* flags) {
+  if (!h || !flags) return fail(h, DG_ERR_ARG, "null argument");
+  if (h->prec != 0) return fail(h, DG_ERR_UNSUPPORTED, "the limiters work on the FP64 form");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc) return rc;
+  CU(h, cudaMemcpyAsync(h->gflags, flags, (size_t)h->mesh.nx * h->mesh.ny, cudaMemcpyHostToDevice, h->stream));
+  CU(h, limit_state(h, h->B[h->cur], h->gflags));
+  return read_state(h, &st);
+}
+
+int dg_last_flags(dg_handle* h, unsigned char* flags) {
+  if (!h || !flags) return fail(h, DG_ERR_ARG, "null argument");
+  CU(h, cudaMemcpyAsync(flags, h->tflags, (size_t)h->mesh.nx * h->mesh.ny, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
   return DG_OK;
 }
 

@@ -46,7 +46,7 @@ __global__ void k_init(const InitArgs a, int count) {
       const double x = xc + 0.5 * ms.dx * a.xq[q], y = yc + 0.5 * ms.dy * a.xq[r];
       double w[4], u[4];
       ic_prim(a.phys, ms, x, y, w);
-      if (a.target == 0 && a.phys.ic == 0 && a.noise_amp > 0.0) {
+      if (a.target == 0 && (a.phys.ic == 0 || a.phys.ic == 3) && a.noise_amp > 0.0) {
         const unsigned long long ctr =
             ((unsigned long long)j * ms.nx + i) * (unsigned long long)(mq * mq) + q * mq + r;
         w[0] += a.noise_amp * (2.0 * splitmix_uniform(a.seed, ctr) - 1.0);
@@ -100,7 +100,7 @@ __global__ void k_cfl(const double* U, DevState* ts, const Mesh ms, const Phys p
       const double xc = ms.x0 + (i + 0.5) * ms.dx, yc = ms.y0 + (j + 0.5) * ms.dy;
       c = ph.h * sqrt(vk2_of(ph, sqrt(xc * xc + yc * yc)));
     }
-    dtk = ph.cfl / (2.0 * p + 1.0) / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
+    dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
     bad = !(rho > 0.0) || !(dtk > 0.0) || !isfinite(dtk);
     if (bad) dtk = __longlong_as_double((long long)INF_BITS);
   }

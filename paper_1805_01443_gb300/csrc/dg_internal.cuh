@@ -53,6 +53,11 @@ struct Phys {
   int ic;
   double slope, sig_floor, amp, vx0, vy0;
   double cfl;
+  double cfl_fac;    // factor of C in the CFL step (1/(2p+1), or the positivity bound)
+  int limiter;       // 0 none, 1 TVB test, 2 given flags (learned indicator)
+  double tvb_m;
+  int positivity;
+  double ring_r, ring_p;  // ic 3
 };
 
 struct Mesh {
@@ -171,6 +176,14 @@ cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStrea
 // step (fixed_dt > 0 replaces the CFL step)
 cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0,
                             cudaStream_t s);
+
+// troubled-cell indicator and limiters of the FP64 form, in place (dg_limit.cu):
+// tvb runs the TVB test (flags to tvb_out if given), `given` replaces its flags
+// for the limiting, apply = 0 only writes the flags
+cudaError_t launch_limit(double* U, const double* GL, const double* GR, const double* GB, const double* GT,
+                         const unsigned char* given, unsigned char* tvb_out, const DevState* ts,
+                         const Mesh& ms, const Phys& ph, const Tables& tab, int p, int nv, int tvb,
+                         int apply, int positivity, cudaStream_t s);
 
 // precision-form setup and conversions (dg_prec.cu)
 cudaError_t launch_delta_from_full(const double* full, const double* bg, float* d, size_t n,

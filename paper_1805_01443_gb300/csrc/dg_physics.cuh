@@ -15,10 +15,11 @@ __device__ __forceinline__ double vk2_of(const Phys& ph, double r) {
 // Primitive state (rho, vx, vy, p) of the initial condition without noise:
 // ic 0 the rotational-equilibrium disc Sigma = max(r^s, floor),
 // v_phi^2 = (1 + (s-1) h^2)/r outside r_s and (1 + (s+2) h^2) r^2/r_s^3
-// inside, p = h^2 v_K^2 Sigma; ic 1 the density wave; ic 2 a uniform state.
+// inside, p = h^2 v_K^2 Sigma; ic 3 the same with p x ring_p inside r < ring_r;
+// ic 1 the density wave; ic 2 a uniform state.
 __device__ __forceinline__ void ic_prim(const Phys& ph, const Mesh& ms, double x, double y,
                                         double* w) {
-  if (ph.ic == 0) {
+  if (ph.ic == 0 || ph.ic == 3) {
     double r = fmax(sqrt(x * x + y * y), 1e-12);
     double h2 = ph.h * ph.h, rs3 = ph.rs * ph.rs * ph.rs;
     double sig = fmax(pow(r, ph.slope), ph.sig_floor);
@@ -29,6 +30,7 @@ __device__ __forceinline__ void ic_prim(const Phys& ph, const Mesh& ms, double x
     w[1] = -vphi * y / r;
     w[2] = vphi * x / r;
     w[3] = h2 * vk2_of(ph, r) * sig;
+    if (ph.ic == 3 && r < ph.ring_r) w[3] *= ph.ring_p;  // the imposed shock ring
   } else if (ph.ic == 1) {
     double lx = ms.x1 - ms.x0, ly = ms.y1 - ms.y0;
     w[0] = 1.0 + ph.amp * sin(6.283185307179586476925286766559 * ((x - ms.x0) / lx + (y - ms.y0) / ly));

@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
         const double xc = ms.x0 + (i0 + lane + 0.5) * ms.dx, yc = ms.y0 + (j + 0.5) * ms.dy;
         c = sqrt(cs2_at<KIND>(ph, xc, yc));
       }
-      dtk = ph.cfl / (2.0 * P + 1.0) / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
+      dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
       bad = !(rho > 0.0) || !(dtk > 0.0) || !isfinite(dtk);
       if (bad) dtk = __longlong_as_double(0x7ff0000000000000LL);
     }

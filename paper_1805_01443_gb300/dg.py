@@ -28,7 +28,8 @@ EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_d
             "dg_conserved", "dg_set_stream", "dg_shape", "dg_destroy", "dg_last_error",
             "dg_set_timing", "dg_timing", "dg_conserved_static", "dg_batch_create",
             "dg_batch_config", "dg_batch_get_config", "dg_batch_tune", "dg_batch_step",
-            "dg_batch_sync", "dg_batch_destroy"]
+            "dg_batch_sync", "dg_batch_destroy", "dg_indicator", "dg_limit", "dg_limit_flags",
+            "dg_last_flags"]
 
 
 class DgMesh(ctypes.Structure):
@@ -52,7 +53,9 @@ class DgDisc(ctypes.Structure):
                 ("noise_amp", ctypes.c_double), ("seed", ctypes.c_ulonglong),
                 ("rdamp_in", ctypes.c_double), ("rdamp_out", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("rk", ctypes.c_int), ("prec", ctypes.c_int),
-                ("amp", ctypes.c_double), ("vx0", ctypes.c_double), ("vy0", ctypes.c_double)]
+                ("amp", ctypes.c_double), ("vx0", ctypes.c_double), ("vy0", ctypes.c_double),
+                ("limiter", ctypes.c_int), ("tvb_m", ctypes.c_double), ("positivity", ctypes.c_int),
+                ("ring_r", ctypes.c_double), ("ring_p", ctypes.c_double)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -99,6 +102,10 @@ def lib(build_if_missing=True):
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, _VP, _VP]
         L.dg_last_error.argtypes = [_VP]
         L.dg_last_error.restype = ctypes.c_char_p
+        L.dg_indicator.argtypes = [_VP, ctypes.c_double, _VP]
+        L.dg_limit.argtypes = [_VP]
+        L.dg_limit_flags.argtypes = [_VP, _VP]
+        L.dg_last_flags.argtypes = [_VP, _VP]
         L.dg_batch_create.argtypes = [P(_VP), P(_VP), ctypes.c_int]
         L.dg_batch_config.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.dg_batch_get_config.argtypes = [_VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
@@ -231,6 +238,24 @@ class Disc:
         if out is None:
             out = np.empty(self.shape)
         _check(lib().dg_fetch(self.h, _ptr(out)), self.h)
+        return out
+
+    def indicator(self, M):
+        """TVB troubled-cell flags of the current state, uint8 [ny, nx]."""
+        out = np.zeros((self.ny, self.nx), dtype=np.uint8)
+        _check(lib().dg_indicator(self.h, M, out.ctypes.data_as(_VP)), self.h)
+        return out
+
+    def limit(self):
+        _check(lib().dg_limit(self.h), self.h)
+
+    def limit_flags(self, flags):
+        f = np.ascontiguousarray(flags, dtype=np.uint8).reshape(self.ny, self.nx)
+        _check(lib().dg_limit_flags(self.h, f.ctypes.data_as(_VP)), self.h)
+
+    def last_flags(self):
+        out = np.zeros((self.ny, self.nx), dtype=np.uint8)
+        _check(lib().dg_last_flags(self.h, out.ctypes.data_as(_VP)), self.h)
         return out
 
     def set_state(self, coeffs, t=0.0, step=0):
