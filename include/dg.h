@@ -257,6 +257,50 @@ int dg_limit_flags(dg_handle *h, const unsigned char *flags);
    before it was limited (the labels of the learned indicator). */
 int dg_last_flags(dg_handle *h, unsigned char *flags);
 
+/* ---- Learned troubled-cell indicator ----------------------------------------
+   No counterpart in the paper (its only limiter is the positivity limiter of
+   Sec. 2.3): a multilayer perceptron nin -> 64 (GELU) -> 64 (GELU) -> 1 logit
+   that stands in for the TVB test as the limiter's flagging step
+   (dg_disc.limiter = 2), trained on the TVB test's own flags (dg_last_flags).
+   BF16 weights (round to nearest even of an FP32 master copy), FP32
+   accumulation.  Parameters, flat FP32: W1 [64][nin], b1 [64], W2 [64][64],
+   b2 [64], w3 [64], b3.  Loss: mean over the batch of
+   w_y (softplus(z) - y z), w_1 = pos_weight, w_0 = 1; Adam (0.9, 0.999, 1e-8).
+   Features of an element (nin = 5 nv m^2 FP32): for the stencil element, left,
+   right, below and above neighbours (boundary rule for outside elements) and
+   each variable v, the modes divided by S_v, the largest |mode| of v over the
+   stencil (1 if all vanish), formed in FP64 and rounded once; index
+   (s nv + v) m^2 + k.
+   x, y, z and grad pointers marked _dev are device pointers; host pointers are
+   caller-owned; `stream` is a cudaStream_t (NULL: legacy default).  The
+   network calls synchronise their stream before returning. */
+typedef struct dg_mlp dg_mlp;
+
+/* Weights uniform in +-1/sqrt(fan_in) (counter-based SplitMix64 of seed), biases 0. */
+int dg_mlp_create(dg_mlp **net, int nin, unsigned long long seed);
+int dg_mlp_destroy(dg_mlp *net);
+int dg_mlp_nparams(const dg_mlp *net, int *n);
+int dg_mlp_get_params(const dg_mlp *net, float *host);
+/* Replace the master parameters (and reset Adam). */
+int dg_mlp_set_params(dg_mlp *net, const float *host);
+/* Logits z_dev[B] of features x_dev[B][nin]. */
+int dg_mlp_forward(dg_mlp *net, const float *x_dev, int B, float *z_dev, void *stream);
+/* Gradient of the loss w.r.t. the parameters (to grad_host, may be NULL) and the loss. */
+int dg_mlp_grad(dg_mlp *net, const float *x_dev, const float *y_dev, int B, float pos_weight,
+                float *grad_host, double *loss, void *stream);
+/* One Adam step on a batch (labels y_dev[B] in {0, 1}); loss before the step. */
+int dg_mlp_train_step(dg_mlp *net, const float *x_dev, const float *y_dev, int B, float pos_weight,
+                      float lr, double *loss, void *stream);
+/* Features out_dev[n][5 nv m^2] of the elements elems_dev[n] (index j*nx + i)
+   of the current state (FP64 form).  Synchronises. */
+int dg_features(dg_handle *h, const int *elems_dev, int n, float *out_dev);
+/* Hand a copy of the network (BF16) to the handle for limiter 2; flags where
+   the logit exceeds threshold.  net = NULL removes it (the TVB test again). */
+int dg_set_indicator(dg_handle *h, const dg_mlp *net, float threshold);
+/* Logits and/or flags ([j][i], host buffers) of the learned indicator on the
+   current state.  Synchronises. */
+int dg_indicator_logits(dg_handle *h, float *logits, unsigned char *flags);
+
 /* Release the handle and the device memory it allocated. */
 int dg_destroy(dg_handle *h);
 

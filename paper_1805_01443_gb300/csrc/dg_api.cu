@@ -62,6 +62,9 @@ struct dg_handle {
   Tables tab;
   unsigned char* tflags;  // TVB flags of the last limiter pass (pre-limit) [j][i]
   unsigned char* gflags;  // flags given to the limiter (learned indicator, dg_limit_flags) [j][i]
+  __nv_bfloat16* ind_w;   // learned indicator (limiter 2): W1 transposed [input][unit], then
+                          // b1, W2, b2, w3, b3, in BF16 (own allocation, null until set)
+  float ind_thr;          // flag when the logit exceeds this
   int timing;                                   // bracket stage launches with events
   std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
   size_t ev_used;
@@ -413,6 +416,16 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
 
 // the limiter of a stage value (TVB test or given flags, then positivity), in place
 cudaError_t limit_state(dg_handle* h, double* U, const unsigned char* given) {
+  if (!given && h->ph.limiter == 2 && h->ind_w) {
+    // the learned indicator flags the stage value; the TVB test still runs
+    // beside it (its flags are the judge, dg_last_flags)
+    const int nin = 5 * h->nv * h->M;
+    cudaError_t e = launch_mlp_flags(U, h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w,
+                                     h->ind_w + (size_t)nin * MLP_HIDDEN, h->ind_thr, h->ts, h->gflags, nullptr,
+                                     h->stream);
+    if (e != cudaSuccess) return e;
+    given = h->gflags;
+  }
   return launch_limit(U, h->GL, h->GR, h->GB, h->GT, given, h->tflags, h->ts, h->dm, h->ph, h->tab, h->p,
                       h->nv, h->ph.limiter != 0 || given != nullptr, 1, h->ph.positivity, h->stream);
 }
@@ -490,7 +503,7 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     return fail(nullptr, DG_ERR_ARG, "workspace must be 256-byte aligned");
   if (workspace && workspace_bytes < L.total)
     return fail(nullptr, DG_ERR_NOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, L.total);
-  dg_handle* h = new (std::nothrow) dg_handle;
+  dg_handle* h = new (std::nothrow) dg_handle();  // value-initialised: every pointer starts null
   if (!h) return fail(nullptr, DG_ERR_NOMEM, "host allocation failed");
   memset(h, 0, sizeof(*h));
   h->mesh = *mesh;
@@ -917,6 +930,7 @@ int dg_timing(dg_handle* h, double* stage_ms, long long* nstage) {
 int dg_destroy(dg_handle* h) {
   if (!h) return DG_OK;
   cudaStreamSynchronize(h->stream);
+  if (h->ind_w) cudaFree(h->ind_w);
   if (h->ev) {
     for (cudaEvent_t e : *h->ev) cudaEventDestroy(e);
     delete h->ev;
@@ -966,6 +980,247 @@ int dg_last_flags(dg_handle* h, unsigned char* flags) {
   if (!h || !flags) return fail(h, DG_ERR_ARG, "null argument");
   CU(h, cudaMemcpyAsync(flags, h->tflags, (size_t)h->mesh.nx * h->mesh.ny, cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+// ---- learned troubled-cell indicator -------------------------------------------
+
+struct dg_mlp {
+  MlpBufs b;
+  int np;
+  int t;        // Adam steps taken
+  double* dloss;
+};
+
+namespace {
+
+unsigned short bf16_rne(float f) {  // round to nearest even, as __float2bfloat16_rn
+  unsigned int u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x7fffffu)) return (unsigned short)((u >> 16) | 0x40);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (unsigned short)(u >> 16);
+}
+
+unsigned long long splitmix(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+void mlp_free_scratch(MlpBufs& b) {
+  float* f[] = {b.a1, b.h1, b.a2, b.h2, b.z, b.dz, b.d2, b.d1};
+  for (float* x : f) cudaFree(x);
+  cudaFree(b.lossb);
+  b.a1 = b.h1 = b.a2 = b.h2 = b.z = b.dz = b.d2 = b.d1 = nullptr;
+  b.lossb = nullptr;
+  b.cap = 0;
+}
+
+int mlp_reserve(dg_mlp* net, int B) {
+  MlpBufs& b = net->b;
+  if (B <= b.cap) return DG_OK;
+  mlp_free_scratch(b);
+  const size_t hb = (size_t)B * MLP_HIDDEN * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  float** big[] = {&b.a1, &b.h1, &b.a2, &b.h2, &b.d2, &b.d1};
+  for (float** x : big)
+    if (e == cudaSuccess) e = cudaMalloc((void**)x, hb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b.z, (size_t)B * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b.dz, (size_t)B * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b.lossb, (size_t)B * sizeof(double));
+  if (e != cudaSuccess) {
+    mlp_free_scratch(b);
+    return fail(nullptr, DG_ERR_NOMEM, "mlp scratch for batch %d: %s", B, cudaGetErrorString(e));
+  }
+  b.cap = B;
+  return DG_OK;
+}
+
+}  // namespace
+
+int dg_mlp_destroy(dg_mlp* net);
+
+int dg_mlp_create(dg_mlp** out, int nin, unsigned long long seed) {
+  if (!out || nin < 1 || nin > 4096) return fail(nullptr, DG_ERR_ARG, "mlp: 1 <= nin <= 4096");
+  *out = nullptr;
+  dg_mlp* net = new (std::nothrow) dg_mlp();
+  if (!net) return fail(nullptr, DG_ERR_NOMEM, "mlp: host allocation");
+  net->b.nin = nin;
+  net->np = mlp_nparams(nin);
+  const size_t nb = (size_t)net->np * sizeof(float);
+  cudaError_t e = cudaMalloc((void**)&net->b.p, nb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&net->b.m, nb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&net->b.v, nb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&net->b.g, nb);
+  if (e == cudaSuccess) e = cudaMalloc(&net->b.pb, (size_t)net->np * 2);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&net->dloss, sizeof(double));
+  if (e != cudaSuccess) {
+    dg_mlp_destroy(net);
+    return fail(nullptr, DG_ERR_NOMEM, "mlp: %s", cudaGetErrorString(e));
+  }
+  // weights uniform in +-1/sqrt(fan_in) from a counter-based SplitMix64 of the
+  // seed, biases zero
+  std::vector<float> p(net->np, 0.0f);
+  const int H = MLP_HIDDEN;
+  auto fill = [&](int off, int n, int fan_in) {
+    const double a = 1.0 / sqrt((double)fan_in);
+    for (int k = 0; k < n; k++) {
+      const double u = (splitmix(seed * 0x100000001B3ULL + (unsigned long long)(off + k)) >> 11) * 0x1.0p-53;
+      p[off + k] = (float)((2.0 * u - 1.0) * a);
+    }
+  };
+  fill(0, H * nin, nin);                         // W1
+  fill(H * nin + H, H * H, H);                   // W2
+  fill(H * nin + H + H * H + H, H, H);           // w3
+  if (e == cudaSuccess) e = cudaMemcpy(net->b.p, p.data(), nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(net->b.m, 0, nb);
+  if (e == cudaSuccess) e = cudaMemset(net->b.v, 0, nb);
+  if (e != cudaSuccess) {
+    dg_mlp_destroy(net);
+    return fail(nullptr, DG_ERR_CUDA, "mlp: %s", cudaGetErrorString(e));
+  }
+  *out = net;
+  return DG_OK;
+}
+
+int dg_mlp_destroy(dg_mlp* net) {
+  if (!net) return DG_OK;
+  cudaDeviceSynchronize();
+  mlp_free_scratch(net->b);
+  cudaFree(net->b.p);
+  cudaFree(net->b.m);
+  cudaFree(net->b.v);
+  cudaFree(net->b.g);
+  cudaFree(net->b.pb);
+  cudaFree(net->dloss);
+  delete net;
+  return DG_OK;
+}
+
+int dg_mlp_nparams(const dg_mlp* net, int* n) {
+  if (!net || !n) return fail(nullptr, DG_ERR_ARG, "null argument");
+  *n = net->np;
+  return DG_OK;
+}
+
+int dg_mlp_get_params(const dg_mlp* net, float* host) {
+  if (!net || !host) return fail(nullptr, DG_ERR_ARG, "null argument");
+  cudaError_t e = cudaMemcpy(host, net->b.p, (size_t)net->np * sizeof(float), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? DG_OK : fail(nullptr, DG_ERR_CUDA, "mlp: %s", cudaGetErrorString(e));
+}
+
+int dg_mlp_set_params(dg_mlp* net, const float* host) {
+  if (!net || !host) return fail(nullptr, DG_ERR_ARG, "null argument");
+  const size_t nb = (size_t)net->np * sizeof(float);
+  cudaError_t e = cudaMemcpy(net->b.p, host, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(net->b.m, 0, nb);
+  if (e == cudaSuccess) e = cudaMemset(net->b.v, 0, nb);
+  net->t = 0;
+  return e == cudaSuccess ? DG_OK : fail(nullptr, DG_ERR_CUDA, "mlp: %s", cudaGetErrorString(e));
+}
+
+int dg_mlp_forward(dg_mlp* net, const float* x, int B, float* z, void* stream) {
+  if (!net || !x || !z || B < 1) return fail(nullptr, DG_ERR_ARG, "bad argument");
+  int rc = mlp_reserve(net, B);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = mlp_sync_bf16(net->b, s);
+  if (e == cudaSuccess) e = mlp_forward(net->b, x, B, z, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? DG_OK : fail(nullptr, DG_ERR_CUDA, "mlp forward: %s", cudaGetErrorString(e));
+}
+
+int dg_mlp_grad(dg_mlp* net, const float* x, const float* y, int B, float pos_weight, float* grad_host,
+                double* loss, void* stream) {
+  if (!net || !x || !y || B < 1 || !(pos_weight > 0.0f)) return fail(nullptr, DG_ERR_ARG, "bad argument");
+  int rc = mlp_reserve(net, B);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  double lsum = 0.0;
+  cudaError_t e = mlp_sync_bf16(net->b, s);
+  if (e == cudaSuccess) e = mlp_backward(net->b, x, y, B, pos_weight, net->dloss, s);
+  if (e == cudaSuccess && grad_host)
+    e = cudaMemcpyAsync(grad_host, net->b.g, (size_t)net->np * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&lsum, net->dloss, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (loss) *loss = lsum / B;
+  return e == cudaSuccess ? DG_OK : fail(nullptr, DG_ERR_CUDA, "mlp grad: %s", cudaGetErrorString(e));
+}
+
+int dg_mlp_train_step(dg_mlp* net, const float* x, const float* y, int B, float pos_weight, float lr,
+                      double* loss, void* stream) {
+  if (!net || !x || !y || B < 1 || !(pos_weight > 0.0f) || !(lr > 0.0f))
+    return fail(nullptr, DG_ERR_ARG, "bad argument");
+  int rc = mlp_reserve(net, B);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = mlp_sync_bf16(net->b, s);
+  if (e == cudaSuccess) e = mlp_backward(net->b, x, y, B, pos_weight, net->dloss, s);
+  if (e == cudaSuccess) e = mlp_adam(net->b, ++net->t, lr, s);
+  if (e == cudaSuccess && loss) {
+    double lsum = 0.0;
+    e = cudaMemcpyAsync(&lsum, net->dloss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *loss = lsum / B;
+  }
+  return e == cudaSuccess ? DG_OK : fail(nullptr, DG_ERR_CUDA, "mlp train: %s", cudaGetErrorString(e));
+}
+
+int dg_features(dg_handle* h, const int* elems, int n, float* out) {
+  if (!h || !elems || !out || n < 0) return fail(h, DG_ERR_ARG, "bad argument");
+  if (h->prec != 0) return fail(h, DG_ERR_UNSUPPORTED, "features of the FP64 form only");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc) return rc;
+  if (n == 0) return DG_OK;
+  CU(h, launch_features(h->B[h->cur], h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, elems, n, out, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return DG_OK;
+}
+
+int dg_set_indicator(dg_handle* h, const dg_mlp* net, float threshold) {
+  if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
+  if (h->prec != 0) return fail(h, DG_ERR_UNSUPPORTED, "the learned indicator works on the FP64 form");
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (!net) {
+    if (h->ind_w) cudaFree(h->ind_w);
+    h->ind_w = nullptr;
+    return DG_OK;
+  }
+  const int nin = 5 * h->nv * h->M, H = MLP_HIDDEN;
+  if (net->b.nin != nin) return fail(h, DG_ERR_ARG, "network has %d inputs, this form needs %d", net->b.nin, nin);
+  std::vector<float> p(net->np);
+  CU(h, cudaMemcpy(p.data(), net->b.p, p.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  std::vector<unsigned short> w((size_t)nin * H + (net->np - (size_t)nin * H));
+  for (int u = 0; u < H; u++)
+    for (int i = 0; i < nin; i++) w[(size_t)i * H + u] = bf16_rne(p[(size_t)u * nin + i]);
+  for (size_t k = (size_t)nin * H; k < (size_t)net->np; k++) w[k] = bf16_rne(p[k]);
+  if (!h->ind_w) CU(h, cudaMalloc((void**)&h->ind_w, w.size() * 2));
+  CU(h, cudaMemcpy(h->ind_w, w.data(), w.size() * 2, cudaMemcpyHostToDevice));
+  h->ind_thr = threshold;
+  return DG_OK;
+}
+
+int dg_indicator_logits(dg_handle* h, float* logits, unsigned char* flags) {
+  if (!h || (!logits && !flags)) return fail(h, DG_ERR_ARG, "null argument");
+  if (!h->ind_w) return fail(h, DG_ERR_ARG, "no learned indicator set (dg_set_indicator)");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc) return rc;
+  const size_t ne = (size_t)h->mesh.nx * h->mesh.ny;
+  float* dl = nullptr;
+  CU(h, cudaMalloc((void**)&dl, ne * sizeof(float)));
+  const int nin = 5 * h->nv * h->M;
+  cudaError_t e = launch_mlp_flags(h->B[h->cur], h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w,
+                                   h->ind_w + (size_t)nin * MLP_HIDDEN, h->ind_thr, h->ts, h->gflags, dl,
+                                   h->stream);
+  if (e == cudaSuccess && logits) e = cudaMemcpyAsync(logits, dl, ne * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, h->gflags, ne, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(dl);
+  if (e != cudaSuccess) return fail(h, DG_ERR_CUDA, "indicator: %s", cudaGetErrorString(e));
   return DG_OK;
 }
 

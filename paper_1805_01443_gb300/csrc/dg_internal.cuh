@@ -7,6 +7,7 @@
 // elements as one coalesced 256-byte (FP64) transaction.  A state buffer is
 // [j][it][var][mode][32] doubles; lanes past nx in the last tile are padding.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -184,6 +185,38 @@ cudaError_t launch_limit(double* U, const double* GL, const double* GR, const do
                          const unsigned char* given, unsigned char* tvb_out, const DevState* ts,
                          const Mesh& ms, const Phys& ph, const Tables& tab, int p, int nv, int tvb,
                          int apply, int positivity, cudaStream_t s);
+
+// ---- learned troubled-cell indicator (dg_mlp.cu) ----------------------------
+constexpr int MLP_HIDDEN = 64;
+
+// device buffers of one network and its training scratch (batch <= cap)
+struct MlpBufs {
+  int nin;
+  float* p;   // FP32 master parameters (flat)
+  float* m;   // Adam moments
+  float* v;
+  void* pb;   // BF16 copy of p
+  float* g;   // gradient
+  int cap;
+  float *a1, *h1, *a2, *h2, *z, *dz, *d2, *d1;  // [cap][64] (z, dz: [cap])
+  double* lossb;  // [cap]
+};
+int mlp_nparams(int nin);
+cudaError_t mlp_sync_bf16(MlpBufs& b, cudaStream_t s);
+cudaError_t mlp_forward(MlpBufs& b, const float* x, int B, float* zout, cudaStream_t s);
+cudaError_t mlp_backward(MlpBufs& b, const float* x, const float* y, int B, float pos_weight, double* loss_sum,
+                         cudaStream_t s);
+cudaError_t mlp_adam(MlpBufs& b, int t, float lr, cudaStream_t s);
+// features (FP32 [n][5 nv M]) of the listed elements j*nx+i of a tiled FP64 state
+cudaError_t launch_features(const double* U, const double* GL, const double* GR, const double* GB,
+                            const double* GT, const Mesh& ms, int p, int nv, const int* elems, int n, float* out,
+                            cudaStream_t s);
+// flags (logit > threshold) and optionally logits of every element; Wt1 is the
+// first layer transposed [input][unit] in BF16, rest = b1, W2, b2, w3, b3 in BF16
+cudaError_t launch_mlp_flags(const double* U, const double* GL, const double* GR, const double* GB,
+                             const double* GT, const Mesh& ms, int p, int nv, const __nv_bfloat16* Wt1,
+                             const __nv_bfloat16* rest, float threshold, const DevState* ts,
+                             unsigned char* flags, float* logits, cudaStream_t s);
 
 // precision-form setup and conversions (dg_prec.cu)
 cudaError_t launch_delta_from_full(const double* full, const double* bg, float* d, size_t n,

@@ -29,7 +29,9 @@ EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_d
             "dg_set_timing", "dg_timing", "dg_conserved_static", "dg_batch_create",
             "dg_batch_config", "dg_batch_get_config", "dg_batch_tune", "dg_batch_step",
             "dg_batch_sync", "dg_batch_destroy", "dg_indicator", "dg_limit", "dg_limit_flags",
-            "dg_last_flags"]
+            "dg_last_flags", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_nparams", "dg_mlp_get_params",
+            "dg_mlp_set_params", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step", "dg_features",
+            "dg_set_indicator", "dg_indicator_logits"]
 
 
 class DgMesh(ctypes.Structure):
@@ -106,6 +108,17 @@ def lib(build_if_missing=True):
         L.dg_limit.argtypes = [_VP]
         L.dg_limit_flags.argtypes = [_VP, _VP]
         L.dg_last_flags.argtypes = [_VP, _VP]
+        L.dg_mlp_create.argtypes = [P(_VP), ctypes.c_int, ctypes.c_ulonglong]
+        L.dg_mlp_destroy.argtypes = [_VP]
+        L.dg_mlp_nparams.argtypes = [_VP, P(ctypes.c_int)]
+        L.dg_mlp_get_params.argtypes = [_VP, _VP]
+        L.dg_mlp_set_params.argtypes = [_VP, _VP]
+        L.dg_mlp_forward.argtypes = [_VP, _VP, ctypes.c_int, _VP, _VP]
+        L.dg_mlp_grad.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP, _DP, _VP]
+        L.dg_mlp_train_step.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, ctypes.c_float, _DP, _VP]
+        L.dg_features.argtypes = [_VP, _VP, ctypes.c_int, _VP]
+        L.dg_set_indicator.argtypes = [_VP, _VP, ctypes.c_float]
+        L.dg_indicator_logits.argtypes = [_VP, _VP, _VP]
         L.dg_batch_create.argtypes = [P(_VP), P(_VP), ctypes.c_int]
         L.dg_batch_config.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.dg_batch_get_config.argtypes = [_VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
@@ -257,6 +270,24 @@ class Disc:
         out = np.zeros((self.ny, self.nx), dtype=np.uint8)
         _check(lib().dg_last_flags(self.h, out.ctypes.data_as(_VP)), self.h)
         return out
+
+    def features(self, elems):
+        """FP32 features [n, 5 nv M] (a torch CUDA tensor) of the elements
+        `elems` (a torch int32 CUDA tensor of indices j*nx + i)."""
+        import torch
+        nin = 5 * self.nv * self.M
+        out = torch.empty((elems.numel(), nin), dtype=torch.float32, device=elems.device)
+        _check(lib().dg_features(self.h, _VP(elems.data_ptr()), elems.numel(), _VP(out.data_ptr())), self.h)
+        return out
+
+    def set_indicator(self, net, threshold=0.0):
+        _check(lib().dg_set_indicator(self.h, net.net if net is not None else None, threshold), self.h)
+
+    def indicator_logits(self):
+        z = np.zeros((self.ny, self.nx), dtype=np.float32)
+        f = np.zeros((self.ny, self.nx), dtype=np.uint8)
+        _check(lib().dg_indicator_logits(self.h, z.ctypes.data_as(_VP), f.ctypes.data_as(_VP)), self.h)
+        return z, f
 
     def set_state(self, coeffs, t=0.0, step=0):
         c = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(self.shape)
@@ -414,3 +445,62 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Mlp:
+    """The learned troubled-cell indicator's network (a dg_mlp): training and
+    inference run in libdg's kernels; batches are torch CUDA tensors."""
+
+    def __init__(self, nin, seed=0):
+        net = _VP()
+        _check(lib().dg_mlp_create(ctypes.byref(net), nin, seed))
+        self.net = net
+        self.nin = nin
+        n = ctypes.c_int()
+        _check(lib().dg_mlp_nparams(net, ctypes.byref(n)))
+        self.nparams = n.value
+
+    @staticmethod
+    def _stream():
+        import torch
+        return _VP(torch.cuda.current_stream().cuda_stream)
+
+    def get_params(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().dg_mlp_get_params(self.net, p.ctypes.data_as(_VP)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        _check(lib().dg_mlp_set_params(self.net, p.ctypes.data_as(_VP)))
+
+    def forward(self, x):
+        import torch
+        z = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _check(lib().dg_mlp_forward(self.net, _VP(x.data_ptr()), x.shape[0], _VP(z.data_ptr()), self._stream()))
+        return z
+
+    def grad(self, x, y, pos_weight=1.0):
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().dg_mlp_grad(self.net, _VP(x.data_ptr()), _VP(y.data_ptr()), x.shape[0], pos_weight,
+                                 g.ctypes.data_as(_VP), ctypes.byref(loss), self._stream()))
+        return g, loss.value
+
+    def train_step(self, x, y, pos_weight=1.0, lr=1e-3):
+        loss = ctypes.c_double()
+        _check(lib().dg_mlp_train_step(self.net, _VP(x.data_ptr()), _VP(y.data_ptr()), x.shape[0], pos_weight,
+                                       lr, ctypes.byref(loss), self._stream()))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "net", None):
+            lib().dg_mlp_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
