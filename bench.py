@@ -260,6 +260,21 @@ def batched_run(dg, torch, steps=10, tune_steps=3):
                        "instances": len(cfgs), "dof_per_stage": dof}}
 
 
+def indicator_run():
+    """The learned troubled-cell indicator on the shock-ring disc (adiabatic,
+    pressure ring x10 at r = 1.5, q = 1e-3, P3 1024^2): labels from the TVB
+    test on the method's own run (seed 5), training with libdg's kernels,
+    miss / false-flag rates on a held-out run (seed 6) and the induced density
+    error of a network-limited run against the TVB-limited one, next to the
+    run without troubled-cell limiting (seed 7)."""
+    from paper_1805_01443_gb300 import indicator, inputs
+    rec = indicator.evaluate(inputs.shock_ring(1024, 3, seed=5), inputs.shock_ring(1024, 3, seed=6),
+                             inputs.shock_ring(1024, 3, seed=7))
+    rec["config"] = {"workload": "shock-ring disc P3 1024x1024, gamma 1.4, q 1e-3, TVB M = 50, "
+                                 "positivity limiter; MLP 320-64-64-1 GELU, BF16 weights, FP32 accumulate"}
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,6 +289,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--n", type=int, default=512, help="mesh size (profiling cases only)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-disc batched workload")
+    ap.add_argument("--no-indicator", action="store_true", help="skip the learned-indicator workload")
     args = ap.parse_args()
 
     import copy
@@ -382,6 +398,8 @@ def main():
         line["error_vs_fp64"] = err
     if args.form == "prec" and world == 1 and not args.no_batched:
         line["batched"] = batched_run(dg, torch)
+    if args.form == "prec" and world == 1 and not args.no_indicator:
+        line["indicator"] = indicator_run()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(cfg)
     if rank == 0:

@@ -268,9 +268,9 @@ int dg_last_flags(dg_handle *h, unsigned char *flags);
    w_y (softplus(z) - y z), w_1 = pos_weight, w_0 = 1; Adam (0.9, 0.999, 1e-8).
    Features of an element (nin = 5 nv m^2 FP32): for the stencil element, left,
    right, below and above neighbours (boundary rule for outside elements) and
-   each variable v, the modes divided by S_v, the largest |mode| of v over the
-   stencil (1 if all vanish), formed in FP64 and rounded once; index
-   (s nv + v) m^2 + k.
+   each variable v, the modes times 1/S_v, S_v the largest |mode| of v over the
+   stencil (1 if all vanish), reciprocal and product in FP64, the product
+   rounded once; index (s nv + v) m^2 + k.
    x, y, z and grad pointers marked _dev are device pointers; host pointers are
    caller-owned; `stream` is a cudaStream_t (NULL: legacy default).  The
    network calls synchronise their stream before returning. */

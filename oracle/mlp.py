@@ -15,7 +15,8 @@ Features of element (i, j): stencil s = 0 the element, 1 left, 2 right,
 3 below, 4 above (outside elements: periodic wrap, the fixed ghost element,
 or the element itself for the transmissive boundary); for each variable v
 the modes divided by S_v = max |mode| of v over the stencil (1 if all
-vanish), computed in FP64 and rounded once to FP32.
+vanish): x = c * (1 / S_v), the reciprocal and the product in FP64, the product
+rounded once to FP32.
 """
 import numpy as np
 from scipy.special import erf
@@ -118,5 +119,5 @@ def features(o, elems=None):
                        elem(i, j - 1, i, j), elem(i, j + 1, i, j)])  # [5][nv][M]
         S = np.abs(st).max(axis=(0, 2))
         S = np.where(S > 0.0, S, 1.0)
-        out[t] = (st / S[None, :, None]).astype(np.float32).ravel()
+        out[t] = (st * (1.0 / S)[None, :, None]).astype(np.float32).ravel()
     return out

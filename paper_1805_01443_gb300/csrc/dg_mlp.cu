@@ -4,9 +4,9 @@
 //
 // Features of element e (FP32): for the stencil s = 0 the element, 1 left,
 // 2 right, 3 below, 4 above (outside elements by the boundary rule), variable
-// v and mode k, x[(s * nv + v) * M + k] = c_s[v][k] / S_v with S_v the largest
-// |c_s[v][k]| over the stencil and the modes (1 when all vanish), formed in
-// FP64 and rounded once.
+// v and mode k, x[(s * nv + v) * M + k] = c_s[v][k] * (1 / S_v) with S_v the
+// largest |c_s[v][k]| over the stencil and the modes (1 when all vanish): the
+// reciprocal and the product in FP64, the product rounded once to FP32.
 //
 // Parameters (FP32 master copy, flat): W1 [64][nin], b1 [64], W2 [64][64],
 // b2 [64], w3 [64], b3.  The products use the weights rounded to BF16
@@ -169,18 +169,26 @@ __device__ __forceinline__ double coef(const FeatArgs& a, int i, int j, int ci, 
   return a.U[((tile * NV + v) * M + k) * 32 + (i & 31)];
 }
 
+// R[v] = 1 / S_v.  The largest |c| is found on the bit patterns (sign bit
+// cleared, compared as integers: the order of non-negative doubles), which
+// keeps the scan off the narrow FP64 unit; one FP64 reciprocal per variable.
 template <int NV, int M>
-__device__ __forceinline__ void stencil_scales(const FeatArgs& a, int i, int j, double* S) {
+__device__ __forceinline__ void stencil_scales(const FeatArgs& a, int i, int j, double* R) {
   const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
+  unsigned long long mx[NV];
 #pragma unroll
-  for (int v = 0; v < NV; v++) S[v] = 0.0;
+  for (int v = 0; v < NV; v++) mx[v] = 0ull;
   for (int s = 0; s < 5; s++)
 #pragma unroll
     for (int v = 0; v < NV; v++)
-      for (int k = 0; k < M; k++) S[v] = fmax(S[v], fabs(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k)));
+      for (int k = 0; k < M; k++) {
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k)) &
+            0x7fffffffffffffffull;
+        mx[v] = b > mx[v] ? b : mx[v];
+      }
 #pragma unroll
-  for (int v = 0; v < NV; v++)
-    if (!(S[v] > 0.0)) S[v] = 1.0;
+  for (int v = 0; v < NV; v++) R[v] = mx[v] ? 1.0 / __longlong_as_double((long long)mx[v]) : 1.0;
 }
 
 template <int NV, int M>
@@ -198,7 +206,7 @@ __global__ void k_features(const FeatArgs a, const int* __restrict__ elems, int 
 #pragma unroll
     for (int v = 0; v < NV; v++)
       for (int k = 0; k < M; k++)
-        o[(s * NV + v) * M + k] = (float)(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k) / S[v]);
+        o[(s * NV + v) * M + k] = (float)(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k) * S[v]);
 }
 
 // one thread per element: features on the fly, the first layer against the
@@ -206,15 +214,18 @@ __global__ void k_features(const FeatArgs a, const int* __restrict__ elems, int 
 // same row, a broadcast), the second layer and the logit; writes the flag
 // (logit > threshold) and, when asked, the logit
 template <int NV, int M>
-__global__ void __launch_bounds__(128) k_mlp_flags(const FeatArgs a, const __nv_bfloat16* __restrict__ Wt1,
+__global__ void __launch_bounds__(256) k_mlp_flags(const FeatArgs a, const __nv_bfloat16* __restrict__ Wt1,
                                                    const __nv_bfloat16* __restrict__ rest, float threshold,
                                                    const DevState* ts, unsigned char* __restrict__ flags,
                                                    float* __restrict__ logits) {
   constexpr int NIN = 5 * NV * M;
-  extern __shared__ __nv_bfloat16 sw[];  // [NIN][H] then b1, W2 [H][H], b2, w3, b3
+  // BF16 weights widened to FP32 once (exact), [NIN][H] then b1, W2 [H][H],
+  // b2, w3, b3: the inner loop reads rows of four weights per load
+  extern __shared__ float4 sw4[];
+  float* sw = reinterpret_cast<float*>(sw4);
   const int nrest = H + H * H + H + H + 1;
-  for (int k = threadIdx.x; k < NIN * H; k += blockDim.x) sw[k] = Wt1[k];
-  for (int k = threadIdx.x; k < nrest; k += blockDim.x) sw[NIN * H + k] = rest[k];
+  for (int k = threadIdx.x; k < NIN * H; k += blockDim.x) sw[k] = __bfloat162float(Wt1[k]);
+  for (int k = threadIdx.x; k < nrest; k += blockDim.x) sw[NIN * H + k] = __bfloat162float(rest[k]);
   __syncthreads();
   if (ts->status != 0) return;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,30 +237,36 @@ __global__ void __launch_bounds__(128) k_mlp_flags(const FeatArgs a, const __nv_
   const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
   double S[NV];
   stencil_scales<NV, M>(a, i, j, S);
-  const __nv_bfloat16* b1 = sw + NIN * H;
-  const __nv_bfloat16* W2 = b1 + H;
-  const __nv_bfloat16* b2 = W2 + H * H;
-  const __nv_bfloat16* w3 = b2 + H;
-  const __nv_bfloat16* b3 = w3 + H;
+  const float* b1 = sw + NIN * H;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* w3 = b2 + H;
+  const float* b3 = w3 + H;
   float h[H];
 #pragma unroll
-  for (int u = 0; u < H; u++) h[u] = __bfloat162float(b1[u]);
+  for (int u = 0; u < H; u++) h[u] = b1[u];
   for (int s = 0; s < 5; s++)
     for (int v = 0; v < NV; v++)
       for (int k = 0; k < M; k++) {
-        const float x = (float)(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k) / S[v]);
-        const __nv_bfloat16* row = sw + (size_t)((s * NV + v) * M + k) * H;
+        const float x = (float)(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k) * S[v]);
+        const float4* row = reinterpret_cast<const float4*>(sw + (size_t)((s * NV + v) * M + k) * H);
 #pragma unroll
-        for (int u = 0; u < H; u++) h[u] = fmaf(x, __bfloat162float(row[u]), h[u]);
+        for (int u4 = 0; u4 < H / 4; u4++) {
+          const float4 w = row[u4];
+          h[4 * u4 + 0] = fmaf(x, w.x, h[4 * u4 + 0]);
+          h[4 * u4 + 1] = fmaf(x, w.y, h[4 * u4 + 1]);
+          h[4 * u4 + 2] = fmaf(x, w.z, h[4 * u4 + 2]);
+          h[4 * u4 + 3] = fmaf(x, w.w, h[4 * u4 + 3]);
+        }
       }
 #pragma unroll
   for (int u = 0; u < H; u++) h[u] = gelu(h[u]);
-  float z = __bfloat162float(b3[0]);
+  float z = b3[0];
   for (int u = 0; u < H; u++) {
-    float acc = __bfloat162float(b2[u]);
+    float acc = b2[u];
 #pragma unroll
-    for (int q = 0; q < H; q++) acc = fmaf(h[q], __bfloat162float(W2[u * H + q]), acc);
-    z = fmaf(gelu(acc), __bfloat162float(w3[u]), z);
+    for (int q = 0; q < H; q++) acc = fmaf(h[q], W2[u * H + q], acc);
+    z = fmaf(gelu(acc), w3[u], z);
   }
   const size_t e = (size_t)j * a.ms.nx + i;
   flags[e] = (unsigned char)(z > threshold);
@@ -261,7 +278,7 @@ cudaError_t launch_flags_t(const FeatArgs& fa, const __nv_bfloat16* Wt1, const _
                            float threshold, const DevState* ts, unsigned char* flags, float* logits,
                            cudaStream_t s) {
   constexpr int NIN = 5 * NV * M;
-  const size_t smem = (size_t)(NIN * H + H + H * H + H + H + 1) * sizeof(__nv_bfloat16);
+  const size_t smem = (size_t)(NIN * H + H + H * H + H + H + 1) * sizeof(float);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_mlp_flags<NV, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -269,7 +286,7 @@ cudaError_t launch_flags_t(const FeatArgs& fa, const __nv_bfloat16* Wt1, const _
     configured = true;
   }
   const long long threads = (long long)fa.ms.ntx * fa.ms.ny * 32;
-  k_mlp_flags<NV, M><<<blocks(threads, 128), 128, smem, s>>>(fa, Wt1, rest, threshold, ts, flags, logits);
+  k_mlp_flags<NV, M><<<blocks(threads, 256), 256, smem, s>>>(fa, Wt1, rest, threshold, ts, flags, logits);
   return cudaGetLastError();
 }
 
