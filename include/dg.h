@@ -65,7 +65,9 @@ typedef struct {
   double x0, x1, y0, y1;
   int bc; /* 0 periodic; 1 ghost elements holding the projected background
              state of the initial condition (fixed); 2 transmissive (exterior
-             trace = interior trace) */
+             trace = interior trace); 3 zero-gradient ghost elements, each a
+             copy of the adjacent boundary element (the "gradient free"
+             boundary of Sec. 4.2) */
 } dg_mesh;
 
 /* Equation of state (Sec. 2.1). */
@@ -95,7 +97,10 @@ typedef struct {
                          rho = 1 + amp sin(2 pi (x~ + y~)), v = (vx0, vy0), p = 1;
                          2 uniform rho = 1, v = (vx0, vy0), p = 1; 3 the disc of
                          ic 0 (adiabatic only) with pressure x ring_p inside
-                         r < ring_r (an imposed shock ring) */
+                         r < ring_r (an imposed shock ring); 4 the isentropic
+                         vortex of Sec. 4.1 (strength amp, free stream rho = p = 1,
+                         v = (vx0, vy0), centred in the box); 5 the Gresho vortex
+                         of Sec. 4.2 (centred in the box); 4 and 5 adiabatic */
   int star;           /* 1: softened point-mass star at the origin in the source;
                          Phi_* = -1/r for r >= r_soft, solid-body core inside */
   double r_soft;      /* star softening radius (> 0 for kind 0, star or ic 0) */

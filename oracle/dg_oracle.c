@@ -19,6 +19,9 @@
 #include "dg_oracle.h"
 
 #include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846264338327950288
+#endif
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -361,6 +364,38 @@ static void background_prim(const ref_state *s, double x, double y, double *w) {
     /* READING (config 5): the imposed shock ring is a pressure step, p x ring_p
        inside r < ring_r, on the same disc (sharp at the nodes, then projected) */
     if (s->d.ic == 3 && r < s->d.ring_r) w[3] *= s->d.ring_p;
+  } else if (s->d.ic == 4) {
+    /* Sec. 4.1 isentropic vortex (Yee et al.) about (x0 + x1, y0 + y1)/2 in
+       the free stream rho = p = 1, v = (vx0, vy0); READING: the vortex
+       strength beta is not printed, beta = amp (5 in the workloads) */
+    const double g = s->eos.gamma, beta = s->d.amp;
+    const double xc = 0.5 * (s->mesh.x0 + s->mesh.x1), yc = 0.5 * (s->mesh.y0 + s->mesh.y1);
+    const double dx = x - xc, dy = y - yc, r2 = dx * dx + dy * dy;
+    const double T = 1.0 - (g - 1.0) * beta * beta / (8.0 * g * M_PI * M_PI) * exp(1.0 - r2);
+    const double du = beta / (2.0 * M_PI) * exp(0.5 * (1.0 - r2));
+    w[0] = pow(T, 1.0 / (g - 1.0));
+    w[1] = s->d.vx0 - du * dy;
+    w[2] = s->d.vy0 + du * dx;
+    w[3] = pow(w[0], g);
+  } else if (s->d.ic == 5) {
+    /* Sec. 4.2 Gresho vortex about the box centre: rho = 1, v_phi and p(r) piecewise */
+    const double xc = 0.5 * (s->mesh.x0 + s->mesh.x1), yc = 0.5 * (s->mesh.y0 + s->mesh.y1);
+    const double dx = x - xc, dy = y - yc, r = sqrt(dx * dx + dy * dy);
+    double vphi, p;
+    if (r < 0.2) {
+      vphi = 5.0 * r;
+      p = 5.0 + 12.5 * r * r;
+    } else if (r < 0.4) {
+      vphi = 2.0 - 5.0 * r;
+      p = 9.0 - 4.0 * log(0.2) + 12.5 * r * r - 20.0 * r + 4.0 * log(r);
+    } else {
+      vphi = 0.0;
+      p = 3.0 + 4.0 * log(2.0);
+    }
+    w[0] = 1.0;
+    w[1] = r > 0.0 ? -vphi * dy / r : 0.0;
+    w[2] = r > 0.0 ? vphi * dx / r : 0.0;
+    w[3] = p;
   } else if (s->d.ic == 1) {
     double lx = s->mesh.x1 - s->mesh.x0, ly = s->mesh.y1 - s->mesh.y0;
     double ph = TWO_PI * ((x - s->mesh.x0) / lx + (y - s->mesh.y0) / ly);
@@ -449,7 +484,9 @@ static void init_ic(ref_state *s) {
 /* Spatial operator L(u, t): right-hand side of Eq. 2 divided by |K|          */
 
 /* coefficients of element (i,j), which may lie outside the mesh; returns 0
-   for a transmissive boundary (the caller then mirrors its own trace) */
+   for a transmissive boundary (the caller then mirrors its own trace).
+   READING (Sec. 4.2 "gradient free" boundaries): bc 3 is a zero-gradient
+   ghost layer, the ghost element a copy of the adjacent interior element */
 static int gather(const ref_state *s, const double *u, int i, int j, double c[MAXV][MAXN]) {
   int nx = s->mesh.nx, ny = s->mesh.ny;
   int inside = (i >= 0 && i < nx && j >= 0 && j < ny);
@@ -457,6 +494,10 @@ static int gather(const ref_state *s, const double *u, int i, int j, double c[MA
     if (s->mesh.bc == 0) {
       i = (i + nx) % nx;
       j = (j + ny) % ny;
+      inside = 1;
+    } else if (s->mesh.bc == 3) {
+      i = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+      j = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
       inside = 1;
     } else if (s->mesh.bc == 1) {
       int side = (i < 0) ? 0 : (i >= nx) ? 1 : (j < 0) ? 2 : 3;
@@ -987,11 +1028,12 @@ int ref_init(ref_state **out, const ref_mesh *mesh, int order, const ref_eos *eo
   *out = NULL;
   if (order < 1 || order > 4) return -2;
   if (mesh->nx < 1 || mesh->ny < 1 || !(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0)) return -1;
-  if (mesh->bc < 0 || mesh->bc > 2) return -1;
+  if (mesh->bc < 0 || mesh->bc > 3) return -1;
   if (eos->kind < 0 || eos->kind > 2) return -2;
   if (eos->kind == 1 && !(eos->gamma > 1.0)) return -1;
   if ((eos->kind == 0 || disc->star || disc->ic == 0 || disc->ic == 3) && !(disc->r_soft > 0.0)) return -1;
-  if (disc->ic < 0 || disc->ic > 3) return -2;
+  if (disc->ic < 0 || disc->ic > 5) return -2;
+  if ((disc->ic == 4 || disc->ic == 5) && eos->kind != 1) return -1;
   if (disc->ic == 3 && (eos->kind != 1 || !(disc->ring_p > 0.0))) return -1;
   if (disc->limiter < 0 || disc->limiter > 1 || disc->positivity < 0 || disc->positivity > 1) return -1;
   if ((disc->limiter || disc->positivity) && disc->rk != 3) return -2;

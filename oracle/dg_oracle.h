@@ -39,7 +39,8 @@ extern "C" {
 typedef struct {
   int nx, ny;                 /* elements per direction */
   double x0, x1, y0, y1;      /* box */
-  int bc;                     /* 0 periodic, 1 fixed background ghosts, 2 transmissive */
+  int bc;                     /* 0 periodic, 1 fixed background ghosts, 2 transmissive,
+                                 3 zero-gradient ghosts (copies of the adjacent element) */
 } ref_mesh;
 
 typedef struct {
@@ -58,7 +59,8 @@ typedef struct {
 } ref_planet;
 
 typedef struct {
-  int ic;                     /* 0 Keplerian disc, 1 density wave, 2 uniform state, 3 disc with a pressure ring */
+  int ic;                     /* 0 Keplerian disc, 1 density wave, 2 uniform state, 3 disc with a pressure ring,
+                                 4 isentropic vortex (strength amp), 5 Gresho vortex (adiabatic) */
   int star;                   /* 1: softened point-mass star potential in the source */
   double r_soft;              /* star softening radius r_s */
   double sigma_slope;         /* Sigma ~ r^slope */

@@ -278,13 +278,15 @@ int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* d
   if (!(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0) || !isfinite(mesh->x1 - mesh->x0) ||
       !isfinite(mesh->y1 - mesh->y0))
     return fail(nullptr, DG_ERR_ARG, "empty or non-finite box");
-  if (mesh->bc < 0 || mesh->bc > 2) return fail(nullptr, DG_ERR_ARG, "bc %d not in 0..2", mesh->bc);
+  if (mesh->bc < 0 || mesh->bc > 3) return fail(nullptr, DG_ERR_ARG, "bc %d not in 0..3", mesh->bc);
   if (order < 1 || order > MAXP) return fail(nullptr, DG_ERR_UNSUPPORTED, "order %d not in 1..4", order);
   if (eos->kind < 0 || eos->kind > 2) return fail(nullptr, DG_ERR_UNSUPPORTED, "eos kind %d", eos->kind);
   if (eos->kind == 1 && !(eos->gamma > 1.0)) return fail(nullptr, DG_ERR_ARG, "gamma must be > 1");
   if ((eos->kind == 0 || disc->star || disc->ic == 0 || disc->ic == 3) && !(disc->r_soft > 0.0))
     return fail(nullptr, DG_ERR_ARG, "r_soft must be > 0");
-  if (disc->ic < 0 || disc->ic > 3) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
+  if (disc->ic < 0 || disc->ic > 5) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
+  if ((disc->ic == 4 || disc->ic == 5) && eos->kind != 1)
+    return fail(nullptr, DG_ERR_ARG, "ic %d needs the adiabatic EOS", disc->ic);
   if (disc->ic == 3 && (eos->kind != 1 || !(disc->ring_p > 0.0)))
     return fail(nullptr, DG_ERR_ARG, "ic 3 needs the adiabatic EOS and ring_p > 0");
   if (disc->limiter < 0 || disc->limiter > 2 || disc->positivity < 0 || disc->positivity > 1)

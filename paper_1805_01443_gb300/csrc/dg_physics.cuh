@@ -31,6 +31,36 @@ __device__ __forceinline__ void ic_prim(const Phys& ph, const Mesh& ms, double x
     w[2] = vphi * x / r;
     w[3] = h2 * vk2_of(ph, r) * sig;
     if (ph.ic == 3 && r < ph.ring_r) w[3] *= ph.ring_p;  // the imposed shock ring
+  } else if (ph.ic == 4) {
+    // isentropic vortex (Sec. 4.1) of strength amp in the free stream (vx0, vy0)
+    const double g = ph.gamma, beta = ph.amp, pi = 3.141592653589793238462643383279503;
+    const double xc = 0.5 * (ms.x0 + ms.x1), yc = 0.5 * (ms.y0 + ms.y1);
+    const double dx = x - xc, dy = y - yc, r2 = dx * dx + dy * dy;
+    const double T = 1.0 - (g - 1.0) * beta * beta / (8.0 * g * pi * pi) * exp(1.0 - r2);
+    const double du = beta / (2.0 * pi) * exp(0.5 * (1.0 - r2));
+    w[0] = pow(T, 1.0 / (g - 1.0));
+    w[1] = ph.vx0 - du * dy;
+    w[2] = ph.vy0 + du * dx;
+    w[3] = pow(w[0], g);
+  } else if (ph.ic == 5) {
+    // Gresho vortex (Sec. 4.2) about the box centre
+    const double xc = 0.5 * (ms.x0 + ms.x1), yc = 0.5 * (ms.y0 + ms.y1);
+    const double dx = x - xc, dy = y - yc, r = sqrt(dx * dx + dy * dy);
+    double vphi, p;
+    if (r < 0.2) {
+      vphi = 5.0 * r;
+      p = 5.0 + 12.5 * r * r;
+    } else if (r < 0.4) {
+      vphi = 2.0 - 5.0 * r;
+      p = 9.0 - 4.0 * log(0.2) + 12.5 * r * r - 20.0 * r + 4.0 * log(r);
+    } else {
+      vphi = 0.0;
+      p = 3.0 + 4.0 * log(2.0);
+    }
+    w[0] = 1.0;
+    w[1] = r > 0.0 ? -vphi * dy / r : 0.0;
+    w[2] = r > 0.0 ? vphi * dx / r : 0.0;
+    w[3] = p;
   } else if (ph.ic == 1) {
     double lx = ms.x1 - ms.x0, ly = ms.y1 - ms.y0;
     w[0] = 1.0 + ph.amp * sin(6.283185307179586476925286766559 * ((x - ms.x0) / lx + (y - ms.y0) / ly));

@@ -210,7 +210,8 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
     const int l = idx & 31;
     sC[idx] = Ut[(l < nvalid) ? idx : idx - l + nvalid - 1];
   }
-  // x neighbours of the tile (periodic wrap, ghost column or transmissive)
+  // x neighbours of the tile (periodic wrap, ghost column, transmissive, or
+  // the zero-gradient copy of the boundary element)
   const int il = i0 - 1, ir = i0 + nvalid;
   const double* pL = nullptr;
   const double* pR = nullptr;
@@ -223,6 +224,8 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
   } else if (ms.bc == 1) {
     pL = a.GL + (size_t)j * NVM;
     stL = 1;
+  } else if (ms.bc == 3) {  // zero-gradient ghost: a copy of the boundary element
+    pL = a.U + (size_t)j * ms.ntx * NVM * 32;
   }
   if (ir < ms.nx) {
     pR = a.U + ((size_t)j * ms.ntx + (ir >> 5)) * NVM * 32 + (ir & 31);
@@ -231,6 +234,9 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
   } else if (ms.bc == 1) {
     pR = a.GR + (size_t)j * NVM;
     stR = 1;
+  } else if (ms.bc == 3) {
+    const int ie = ms.nx - 1;
+    pR = a.U + ((size_t)j * ms.ntx + (ie >> 5)) * NVM * 32 + (ie & 31);
   }
   const bool trL = (pL == nullptr), trR = (pR == nullptr);
   for (int idx = tid; idx < 2 * NVM; idx += NT) {
@@ -248,12 +254,16 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
     pB = a.U + ((size_t)(ms.ny - 1) * ms.ntx + bx) * NVM * 32;
   else if (ms.bc == 1)
     pB = a.GB + (size_t)bx * NVM * 32;
+  else if (ms.bc == 3)
+    pB = Ut;
   if (j + 1 < ms.ny)
     pT = a.U + ((size_t)(j + 1) * ms.ntx + bx) * NVM * 32;
   else if (ms.bc == 0)
     pT = a.U + (size_t)bx * NVM * 32;
   else if (ms.bc == 1)
     pT = a.GT + (size_t)bx * NVM * 32;
+  else if (ms.bc == 3)
+    pT = Ut;
   const bool trB = (pB == nullptr), trT = (pT == nullptr);
   __syncthreads();
 

@@ -425,9 +425,11 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   if (j > 0) pB = Dcur + ((size_t)(j - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
   else if (ms.bc == 0) pB = Dcur + ((size_t)(ms.ny - 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
   else if (ms.bc == 1) zB = true;
+  else if (ms.bc == 3) pB = own;  // zero-gradient ghost: a copy of this row
   if (j + 1 < ms.ny) pT = Dcur + ((size_t)(j + 1) * ms.ntx + bx) * NVM * 32 + voff + lc;
   else if (ms.bc == 0) pT = Dcur + (size_t)bx * NVM * 32 + voff + lc;
   else if (ms.bc == 1) zT = true;
+  else if (ms.bc == 3) pT = own;
   const bool trB = !pB && !zB, trT = !pT && !zT;
   const int il = i0 - 1, ir = i0 + nvalid;
   const float* pL = nullptr;
@@ -436,9 +438,11 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   if (il >= 0) pL = Dcur + ((size_t)j * ms.ntx + (il >> 5)) * NVM * 32 + voff + (il & 31);
   else if (ms.bc == 0) { const int iw = ms.nx - 1; pL = Dcur + ((size_t)j * ms.ntx + (iw >> 5)) * NVM * 32 + voff + (iw & 31); }
   else if (ms.bc == 1) zL = true;
+  else if (ms.bc == 3) pL = Dcur + (size_t)j * ms.ntx * NVM * 32 + voff;
   if (ir < ms.nx) pR = Dcur + ((size_t)j * ms.ntx + (ir >> 5)) * NVM * 32 + voff + (ir & 31);
   else if (ms.bc == 0) pR = Dcur + (size_t)j * ms.ntx * NVM * 32 + voff;
   else if (ms.bc == 1) zR = true;
+  else if (ms.bc == 3) { const int ie = ms.nx - 1; pR = Dcur + ((size_t)j * ms.ntx + (ie >> 5)) * NVM * 32 + voff + (ie & 31); }
   const bool trL = !pL && !zL, trR = !pR && !zR;
   // tiles near the singular centre use the exact projected background (FP32
   // modes of u_b, same tiled layout as delta, all three variables)

@@ -90,6 +90,24 @@ def shock_ring(n=1024, order=3, seed=5, q=1e-3, limiter=1, positivity=1):
     return cfg
 
 
+def isentropic_vortex(n=32, order=3, beta=5.0, cfl=0.1):
+    """Sec. 4.1: the isentropic vortex on the periodic box [0, 10]^2, gamma 1.4,
+    free stream rho = p = 1, v = (1, 1); it returns to its start at T = 10."""
+    cfg = density_wave(n, order)
+    cfg["mesh"].update({"x1": 10.0, "y1": 10.0})
+    cfg["disc"].update({"ic": 4, "amp": beta, "vx0": 1.0, "vy0": 1.0, "cfl": cfl})
+    return cfg
+
+
+def gresho_vortex(n=40, order=3, cfl=0.1):
+    """Sec. 4.2: the Gresho vortex on [0, 1]^2 with gradient-free boundaries
+    (zero-gradient ghost elements), gamma 1.4; a steady solution."""
+    cfg = density_wave(n, order)
+    cfg["mesh"]["bc"] = 3
+    cfg["disc"].update({"ic": 5, "amp": 0.0, "vx0": 0.0, "vy0": 0.0, "cfl": cfl})
+    return cfg
+
+
 def batch_discs(n=48, seed0=100, prec=1):
     """Batched workload: n independent planet discs (damping zones as above),
     instance k with seed seed0 + k, mesh {128, 256, 384, 512}^2 cycling with k,

@@ -423,3 +423,34 @@ def test_torque_point_mass_far_field():
     g = M / d2**1.5
     expect = xp * g * dyp - yp * g * dxp
     assert abs(gz - expect) < 1e-4 * abs(expect)
+
+
+def test_gresho_vortex_is_steady_under_refinement():
+    """Sec. 4.2: an exact steady solution; the mean residual |L(u0)| of its
+    projection falls at first order under refinement (the velocity profile
+    has kinks at r = 0.2 and 0.4, so first order is what the projection can
+    give), in every variable."""
+    res = []
+    for n in (10, 20, 40):
+        o = oracle.Oracle(inputs.gresho_vortex(n, 2))
+        res.append(np.abs(o.rhs()).mean(axis=(1, 2, 3)))
+    for k in range(2):
+        assert np.all(res[k] / res[k + 1] >= 1.8)
+
+
+def test_isentropic_vortex_translates_exactly():
+    """Sec. 4.1: the vortex is an exact solution translating with (1, 1); the
+    L1 error of the density after a quarter crossing falls at about second
+    order for P1 under refinement."""
+    import measures
+    errs = []
+    for n in (10, 20):
+        cfg = inputs.isentropic_vortex(n, 1, cfl=0.2)
+        o = oracle.Oracle(cfg)
+        T = 2.5
+        while o.get_time()[0] < T - 1e-12:
+            t = o.get_time()[0]
+            dt = o.cfl_dt()
+            o.step_dt(1, min(dt, T - t))
+        errs.append(measures.vortex_l1_density(o.fetch(), cfg, T))
+    assert np.log2(errs[0] / errs[1]) >= 1.5
