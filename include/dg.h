@@ -112,7 +112,9 @@ typedef struct {
   double rdamp_in;    /* inner damping radius r_d (Sec. 5.1), <= 0 disables */
   double rdamp_out;   /* outer damping radius r_d, <= 0 disables */
   double cfl;         /* Courant number C of Sec. 2.3 */
-  int rk;             /* 3: SSP(3,3) (Appendix A); 2: SSP(2,2) */
+  int rk;             /* Appendix A: 3 SSP(3,3); 2 SSP(2,2); 4 SSP-RK(4,5) (weights
+                         divided by their sum); 5 6-stage Cash-Karp; 4 and 5 in the
+                         FP64 form only */
   int prec;           /* 0: FP64 operator.  1: precision form (locally isothermal
                          disc only): FP32 operator on delta = u - u_b about the
                          projected equilibrium u_b, with R_b = L(u_b) evaluated

@@ -60,6 +60,8 @@ struct dg_handle {
   float* Disc;         // per-element projected-vs-analytic background discrepancy
   int* TileFlag;
   Tables tab;
+  double* K[5];           // stage slopes of the 5- and 6-stage Butcher tableaux
+  double* W;              // partial sum of their update
   unsigned char* tflags;  // TVB flags of the last limiter pass (pre-limit) [j][i]
   unsigned char* gflags;  // flags given to the limiter (learned indicator, dg_limit_flags) [j][i]
   __nv_bfloat16* ind_w;   // learned indicator (limiter 2): W1 transposed [input][unit], then
@@ -264,7 +266,7 @@ cudaError_t launch_stage_h(dg_handle* h, const StageArgs& a) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t state, canon, gcol, grow, tsb, part, series, cpart, csum, flags8;
+  size_t state, canon, gcol, grow, tsb, part, series, cpart, csum, flags8, rkx;
   size_t state32, nodes32, db32, bm032, disc32, flags;  // precision form only (0 otherwise)
   size_t total;
 };
@@ -294,13 +296,64 @@ int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* d
   if ((disc->limiter || disc->positivity) && (disc->rk != 3 || disc->prec != 0))
     return fail(nullptr, DG_ERR_UNSUPPORTED, "limiters need the FP64 form with SSP(3,3)");
   if (disc->limiter && !(disc->tvb_m >= 0.0)) return fail(nullptr, DG_ERR_ARG, "tvb_m must be >= 0");
-  if (disc->rk != 2 && disc->rk != 3) return fail(nullptr, DG_ERR_UNSUPPORTED, "rk %d", disc->rk);
+  if (disc->rk < 2 || disc->rk > 5) return fail(nullptr, DG_ERR_UNSUPPORTED, "rk %d", disc->rk);
+  if (disc->rk >= 4 && disc->prec != 0)
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "rk %d runs in the FP64 form only", disc->rk);
   if (disc->prec != 0 && disc->prec != 1)
     return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form %d", disc->prec);
   if (disc->prec == 1 && (eos->kind != 0 || disc->ic != 0))
     return fail(nullptr, DG_ERR_UNSUPPORTED, "precision form 1 needs the locally isothermal disc (eos 0, ic 0)");
   if (!(disc->cfl > 0.0)) return fail(nullptr, DG_ERR_ARG, "cfl must be > 0");
   return DG_OK;
+}
+
+// Butcher tableaux of Appendix A with more than three stages, as printed:
+// SSP-RK(4,5) (Table A1, its weights divided by their sum, 1 - 8.8e-11) and
+// the 6-stage Cash-Karp method (Table A2)
+struct Tableau {
+  int s;
+  double a[6][6], b[6], c[6];
+};
+
+const Tableau* rk_tableau(int rk) {
+  static Tableau t45, tck;
+  static bool made = false;
+  if (!made) {
+    Tableau& A = t45;
+    A.s = 5;
+    const double c45[5] = {0.0, 0.39175222700392, 0.58607968896779, 0.47454236302687, 0.93501063100924};
+    const double a45[5][4] = {{0, 0, 0, 0},
+                              {0.39175222700392, 0, 0, 0},
+                              {0.21766909633821, 0.36841059262959, 0, 0},
+                              {0.08269208670950, 0.13995850206999, 0.25189177424738, 0},
+                              {0.06796628370320, 0.11503469844438, 0.20703489864929, 0.54497475021237}};
+    const double b45[5] = {0.14681187618661, 0.24848290924556, 0.10425883036650, 0.27443890091960,
+                           0.22600748319395};
+    double sum = 0.0;
+    for (int i = 0; i < 5; i++) sum += b45[i];
+    for (int i = 0; i < 5; i++) {
+      A.c[i] = c45[i];
+      A.b[i] = b45[i] / sum;
+      for (int j = 0; j < 4; j++) A.a[i][j] = a45[i][j];
+    }
+    Tableau& C = tck;
+    C.s = 6;
+    const double cck[6] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0};
+    const double ack[6][5] = {{0, 0, 0, 0, 0},
+                              {1.0 / 5.0, 0, 0, 0, 0},
+                              {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
+                              {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0},
+                              {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0},
+                              {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
+    const double bck[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+    for (int i = 0; i < 6; i++) {
+      C.c[i] = cck[i];
+      C.b[i] = bck[i];
+      for (int j = 0; j < 5; j++) C.a[i][j] = ack[i][j];
+    }
+    made = true;
+  }
+  return rk == 4 ? &t45 : rk == 5 ? &tck : nullptr;
 }
 
 // factor of C in the CFL step (Sec. 2.3): 1/(2p+1); with the positivity
@@ -317,7 +370,7 @@ double cfl_factor(int p, int positivity) {
   return f;
 }
 
-Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec) {
+Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec, int rk) {
   Layout L;
   const int m = order + 1, M = m * m, nv = eos->kind == 1 ? 4 : 3;
   const size_t ntx = (mesh->nx + TILE - 1) / TILE;
@@ -343,6 +396,10 @@ Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec) {
   L.flags8 = align256((size_t)mesh->nx * mesh->ny);
   L.total = 3 * L.state + L.canon + 2 * L.gcol + 2 * L.grow + L.tsb + L.part + L.series + L.cpart + L.csum +
             2 * L.flags8;
+  // Butcher tableaux with more stages: one state per stage slope but the last,
+  // and the partial sum of the update
+  L.rkx = rk >= 4 ? (size_t)rk_tableau(rk)->s * L.state : 0;
+  L.total += L.rkx;
   if (prec == 1) L.total += L.state + 5 * L.state32 + L.nodes32 + L.db32 + L.bm032 + L.disc32 + L.flags;
   return L;
 }
@@ -416,6 +473,63 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
   return DG_OK;
 }
 
+// n steps of a tableau with more than three stages (FP64 form): stage slopes
+// k_i = L(X_i) with X_i = u^n + dt sum_{j<i} a_ij k_j; the last stage is the
+// fused kernel (damping, torque partials, CFL) with U = X_{s-1},
+// Un = W = u^n + dt sum_{i<s-1} b_i k_i - b_{s-1} X_{s-1}, alpha = 1 and
+// beta = b_{s-1}, which gives u^{n+1} = u^n + dt sum_i b_i k_i
+int do_steps_butcher(dg_handle* h, int n, double fixed_dt) {
+  const Tableau& T = *rk_tableau(h->disc.rk);
+  const size_t cnt = tiled_count(h);
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  a.GL = h->GL;
+  a.GR = h->GR;
+  a.GB = h->GB;
+  a.GT = h->GT;
+  a.ts = h->ts;
+  a.part = h->part;
+  a.mesh = h->dm;
+  a.phys = h->ph;
+  a.fixed_dt = fixed_dt;
+  for (int st = 0; st < n; st++) {
+    double* un = h->B[h->cur];
+    double* nx = h->B[1 - h->cur];
+    for (int i = 0; i < T.s; i++) {
+      const double* X = un;
+      if (i > 0) {
+        CU(h, launch_combine(h->Z, un, (const double* const*)h->K, T.a[i], i, nullptr, 0.0, cnt, h->ts, fixed_dt,
+                             h->stream));
+        X = h->Z;
+      }
+      if (i < T.s - 1) {
+        a.U = a.Un = X;
+        a.Out = h->K[i];
+        a.cstage = T.c[i];
+        a.alpha = 0.0;
+        a.beta = 1.0;
+        a.mode = 0;
+        CU(h, launch_stage_h(h, a));
+      } else {
+        CU(h, launch_combine(h->W, un, (const double* const*)h->K, T.b, T.s - 1, X, -T.b[T.s - 1], cnt, h->ts,
+                             fixed_dt, h->stream));
+        a.U = X;
+        a.Un = h->W;
+        a.Out = nx;
+        a.cstage = T.c[i];
+        a.alpha = 1.0;
+        a.beta = T.b[T.s - 1];
+        a.mode = 2;
+        CU(h, launch_stage_h(h, a));
+      }
+    }
+    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, 0, h->ph.r_p, h->ph.omega_p,
+                        h->ph.phi0, h->stream));
+    h->cur = 1 - h->cur;
+  }
+  return DG_OK;
+}
+
 // the limiter of a stage value (TVB test or given flags, then positivity), in place
 cudaError_t limit_state(dg_handle* h, double* U, const unsigned char* given) {
   if (!given && h->ph.limiter == 2 && h->ind_w) {
@@ -447,6 +561,7 @@ int do_steps(dg_handle* h, int n, double fixed_dt) {
   a.mesh = h->dm;
   a.phys = h->ph;
   a.fixed_dt = fixed_dt;
+  if (h->disc.rk >= 4) return do_steps_butcher(h, n, fixed_dt);
   for (int s = 0; s < n; s++) {
     double* un = h->B[h->cur];
     double* nx = h->B[1 - h->cur];
@@ -488,7 +603,7 @@ int dg_workspace_bytes(const dg_mesh* mesh, int order, const dg_eos* eos, const 
   int rc = validate(mesh, order, eos, disc);
   if (rc) return rc;
   if (!bytes) return fail(nullptr, DG_ERR_ARG, "null bytes");
-  *bytes = layout_of(mesh, order, eos, disc->prec).total;
+  *bytes = layout_of(mesh, order, eos, disc->prec, disc->rk).total;
   return DG_OK;
 }
 
@@ -500,7 +615,7 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   int rc = validate(mesh, order, eos, disc);
   if (rc) return rc;
   if (planet->enabled && !(planet->eps > 0.0)) return fail(nullptr, DG_ERR_ARG, "planet eps must be > 0");
-  const Layout L = layout_of(mesh, order, eos, disc->prec);
+  const Layout L = layout_of(mesh, order, eos, disc->prec, disc->rk);
   if (workspace && ((uintptr_t)workspace & 255))
     return fail(nullptr, DG_ERR_ARG, "workspace must be 256-byte aligned");
   if (workspace && workspace_bytes < L.total)
@@ -633,6 +748,11 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   h->series = (double*)take(L.series);
   h->cpart = (double*)take(L.cpart);
   h->csum = (double*)take(L.csum);
+  if (disc->rk >= 4) {
+    const int s = rk_tableau(disc->rk)->s;
+    for (int i = 0; i < s - 1; i++) h->K[i] = (double*)take(L.state);
+    h->W = (double*)take(L.state);
+  }
   h->tflags = (unsigned char*)take(L.flags8);
   h->gflags = (unsigned char*)take(L.flags8);
   if (h->prec == 1) {

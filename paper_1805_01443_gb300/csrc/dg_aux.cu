@@ -219,6 +219,40 @@ cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* 
   return cudaGetLastError();
 }
 
+// out = u0 + dt sum_{j<nk} c_j k_j + cx X (dt the step in use)
+__global__ void k_combine(double* __restrict__ out, const double* __restrict__ u0, const double* k0,
+                          const double* k1, const double* k2, const double* k3, const double* k4, double c0,
+                          double c1, double c2, double c3, double c4, int nk, const double* X, double cx,
+                          size_t n, const DevState* ts, double fixed_dt) {
+  if (ts->status != 0) return;
+  const double dt = fixed_dt > 0.0 ? fixed_dt : ts->dt;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    if (nk > 0) acc += c0 * k0[e];
+    if (nk > 1) acc += c1 * k1[e];
+    if (nk > 2) acc += c2 * k2[e];
+    if (nk > 3) acc += c3 * k3[e];
+    if (nk > 4) acc += c4 * k4[e];
+    double r = u0[e] + dt * acc;
+    if (X) r += cx * X[e];
+    out[e] = r;
+  }
+}
+
+cudaError_t launch_combine(double* out, const double* u0, const double* const* k, const double* c, int nk,
+                           const double* X, double cx, size_t n, const DevState* ts, double fixed_dt,
+                           cudaStream_t s) {
+  const double* kk[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double cc[5] = {0, 0, 0, 0, 0};
+  for (int j = 0; j < nk && j < 5; j++) {
+    kk[j] = k[j];
+    cc[j] = c[j];
+  }
+  k_combine<<<1216, 256, 0, s>>>(out, u0, kk[0], kk[1], kk[2], kk[3], kk[4], cc[0], cc[1], cc[2], cc[3], cc[4], nk,
+                                  X, cx, n, ts, fixed_dt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0,
                             cudaStream_t s) {
   k_planet32<<<1, 1, 0, s>>>(ts, fixed_dt, r_p, omega_p, phi0);

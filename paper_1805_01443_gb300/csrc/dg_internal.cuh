@@ -173,6 +173,10 @@ cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,
                              int M, cudaStream_t s);
 cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s);
+// out = u0 + dt sum_{j<nk} c_j k_j + cx X over n doubles (nk <= 5, X may be null)
+cudaError_t launch_combine(double* out, const double* u0, const double* const* k, const double* c, int nk,
+                           const double* X, double cx, size_t n, const DevState* ts, double fixed_dt,
+                           cudaStream_t s);
 // planet positions and FP32 step of the precision form for the current t and
 // step (fixed_dt > 0 replaces the CFL step)
 cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0,
