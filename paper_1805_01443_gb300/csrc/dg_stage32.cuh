@@ -157,9 +157,11 @@ struct Smem32 {
   static constexpr int XT = F + 8 * M * 32;        // x traces [2][3][m][33]: 0 right (slot e+1), 1 left (slot e)
   static constexpr int YT = XT + 2 * 3 * m * 33;   // own y traces [2][3][m][32]: 0 top, 1 bottom
   static constexpr int YN = YT + 2 * 3 * m * 32;   // neighbour traces [2][3][m][32]: 0 below's top, 1 above's bottom
-  static constexpr int FX = YN + 2 * 3 * m * 32;   // x-face flux differences [3][m][33]
-  static constexpr int FY = FX + 3 * m * 33;       // y-face flux differences [2][3][m][32]: 0 bottom, 1 top
-  static constexpr int B0 = FY + 2 * 3 * m * 32;   // element averages of the new state [3][32]
+  // face fluxes overwrite the traces they are formed from (each face point's
+  // traces are read and replaced by the one thread that owns the point):
+  static constexpr int FX = XT;                    // x-face flux differences [3][m][33] on plane 0 of XT
+  static constexpr int FY = YN;                    // y-face flux differences [2][3][m][32] on YN
+  static constexpr int B0 = YN + 2 * 3 * m * 32;   // element averages of the new state [3][32]
   static constexpr int FLAGS = B0 + 3 * 32;        // 32 ints
   static constexpr int TOTAL = FLAGS + 32;
   static constexpr int ND = 8;                     // 8-byte words: offsets, dt, mbarrier
@@ -361,7 +363,7 @@ __device__ __forceinline__ void xtrace32(const float* c, const float* f, float* 
 
 // minimum resident CTAs per SM asked of the register allocator
 #ifndef DG_STAGE32_MIN_CTAS
-#define DG_STAGE32_MIN_CTAS 5
+#define DG_STAGE32_MIN_CTAS 6
 #endif
 
 // LAST = false: modes 0 (operator only) and 1 (RK stage); LAST = true: mode 2
