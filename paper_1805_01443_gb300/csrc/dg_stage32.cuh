@@ -41,6 +41,9 @@ struct Tab32 {
   // low parts of the FP64 tables as float pairs (float-float torque)
   float phil[MAXM][MAXM], xil[MAXM];
   float w2h[MAXM * MAXM], w2l[MAXM * MAXM];  // [q*m + r] (w_q/2)(w_r/2)
+  // operand pairs of the packed (two-lane) FMAs of the volume and lift sums
+  float2 wphi2[MAXM][MAXM];  // [r][b] (wphi, wphi)
+  float2 wdw2[MAXM][MAXM];   // [q][a] (wdphi, wphi)
 };
 static __constant__ Tab32 c32t[MAXP + 1];
 
@@ -343,24 +346,6 @@ __device__ __forceinline__ void ytrace32(const float* c, const float* f, float* 
   }
 }
 
-// x-face trace of one variable at the m y-nodes: sum_a f[a] sum_b c_ab phi_b(eta_r)
-template <int P>
-__device__ __forceinline__ void xtrace32(const float* c, const float* f, float* out) {
-  constexpr int m = P + 1;
-#pragma unroll
-  for (int r = 0; r < m; r++) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int aa = 0; aa < m; aa++) {
-      float t = 0.0f;
-#pragma unroll
-      for (int b = 0; b < m; b++) t = fmaf(c[aa * m + b], c32t[P].phi[r][b], t);
-      acc = fmaf(f[aa], t, acc);
-    }
-    out[r * 33] = acc;
-  }
-}
-
 // minimum resident CTAs per SM asked of the register allocator
 #ifndef DG_STAGE32_MIN_CTAS
 #define DG_STAGE32_MIN_CTAS 6
@@ -502,25 +487,26 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
 #pragma unroll
       for (int q = 0; q < m; q++) sYN[((1 * 3 + v) * m + q) * 32 + lane] = 0.0f;
     }
-    // the two x-halo elements: right trace of the left halo, left trace of the right halo
-    if (lane == 0) {
-      if (pL) {
+    // the two x-halo elements: right trace of the left halo, left trace of the
+    // right halo, one y-node per lane (lanes 0..m-1 left, 16..16+m-1 right),
+    // each summed in the order of the owner tile's own trace
+    {
+      const bool right = lane >= 16;
+      const int r = lane & 15;
+      const float* ph = right ? pR : pL;
+      if (r < m && (ph || (right ? zR : zL))) {
+        float acc = 0.0f;
+        if (ph) {
 #pragma unroll
-        for (int k = 0; k < M; k++) c[k] = pL[k * 32];
-        xtrace32<P>(c, c32t[P].pp, sXT + (0 * 3 + v) * m * 33);
-      } else if (zL) {
+          for (int aa = 0; aa < m; aa++) {
+            float t = 0.0f;
 #pragma unroll
-        for (int r = 0; r < m; r++) sXT[((0 * 3 + v) * m + r) * 33] = 0.0f;
-      }
-    }
-    if (lane == nvalid - 1) {
-      if (pR) {
-#pragma unroll
-        for (int k = 0; k < M; k++) c[k] = pR[k * 32];
-        xtrace32<P>(c, c32t[P].pm, sXT + (1 * 3 + v) * m * 33 + nvalid);
-      } else if (zR) {
-#pragma unroll
-        for (int r = 0; r < m; r++) sXT[((1 * 3 + v) * m + r) * 33 + nvalid] = 0.0f;
+            for (int b = 0; b < m; b++) t = fmaf(ph[(aa * m + b) * 32], c32t[P].phi[r][b], t);
+            acc = fmaf(right ? c32t[P].pm[aa] : c32t[P].pp[aa], t, acc);
+          }
+        }
+        if (right) sXT[((1 * 3 + v) * m + r) * 33 + nvalid] = acc;
+        else sXT[((0 * 3 + v) * m + r) * 33] = acc;
       }
     }
   }
@@ -630,62 +616,61 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   }
   __syncthreads();
   // ---- P3: volume integral and surface lift of this thread's variable -------
+  // Sums that share a weight run as the two lanes of one packed FMA, each lane
+  // in the order of its scalar sum: (x-volume, y-volume) partial sums, the
+  // (x-volume, y-volume) second contractions, the (left, right) and (bottom,
+  // top) lifts.
   float L[M];
   {
-    float Aq[m][m], Bq[m][m];  // first contraction over r, [b][q]
+    float2 AB[m][m];  // first contraction over r, [b][q]: (x-volume, source part of the y-volume)
 #pragma unroll
     for (int b = 0; b < m; b++)
 #pragma unroll
-      for (int q = 0; q < m; q++) Aq[b][q] = Bq[b][q] = 0.0f;
+      for (int q = 0; q < m; q++) AB[b][q] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < m; q++)
 #pragma unroll
       for (int r = 0; r < m; r++) {
         const int n = q * m + r;
-        const float fxv = sFl[(v * M + n) * 32 + lane];
+        const float2 xs = make_float2(sFl[(v * M + n) * 32 + lane],
+                                      (v > 0) ? sFl[((5 + v) * M + n) * 32 + lane] : 0.0f);
         const float fyv = sFl[((3 + v) * M + n) * 32 + lane];
-        const float sv = (v > 0) ? sFl[((5 + v) * M + n) * 32 + lane] : 0.0f;
 #pragma unroll
         for (int b = 0; b < m; b++) {
-          Aq[b][q] = fmaf(c32t[P].wphi[r][b], fxv, Aq[b][q]);
-          Bq[b][q] = fmaf(c32t[P].wdphi[r][b], fyv, fmaf(c32t[P].wphi[r][b], sv, Bq[b][q]));
+          AB[b][q] = __ffma2_rn(c32t[P].wphi2[r][b], xs, AB[b][q]);
+          AB[b][q].y = fmaf(c32t[P].wdphi[r][b], fyv, AB[b][q].y);
         }
       }
 #pragma unroll
     for (int aa = 0; aa < m; aa++)
 #pragma unroll
       for (int b = 0; b < m; b++) {
-        float va = 0.0f, vb = 0.0f;
+        float2 vab = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int q = 0; q < m; q++) {
-          va = fmaf(c32t[P].wdphi[q][aa], Aq[b][q], va);
-          vb = fmaf(c32t[P].wphi[q][aa], Bq[b][q], vb);
-        }
-        L[aa * m + b] = fmaf(pc.s2x, va, vb);
+        for (int q = 0; q < m; q++) vab = __ffma2_rn(c32t[P].wdw2[q][aa], AB[b][q], vab);
+        L[aa * m + b] = fmaf(pc.s2x, vab.x, vab.y);
       }
   }
   {
-    float HL[m], HR[m], HB[m], HT[m];
+    float2 HLR[m], HBT[m];
 #pragma unroll
-    for (int b = 0; b < m; b++) HL[b] = HR[b] = HB[b] = HT[b] = 0.0f;
+    for (int b = 0; b < m; b++) HLR[b] = HBT[b] = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int r = 0; r < m; r++) {
-      const float fl = sFX[(v * m + r) * 33 + lane], fr = sFX[(v * m + r) * 33 + lane + 1];
-      const float fb = sFY[((0 * 3 + v) * m + r) * 32 + lane], ft = sFY[((1 * 3 + v) * m + r) * 32 + lane];
+      const float2 flr = make_float2(sFX[(v * m + r) * 33 + lane], sFX[(v * m + r) * 33 + lane + 1]);
+      const float2 fbt = make_float2(sFY[((0 * 3 + v) * m + r) * 32 + lane], sFY[((1 * 3 + v) * m + r) * 32 + lane]);
 #pragma unroll
       for (int b = 0; b < m; b++) {
-        HL[b] = fmaf(c32t[P].wphi[r][b], fl, HL[b]);
-        HR[b] = fmaf(c32t[P].wphi[r][b], fr, HR[b]);
-        HB[b] = fmaf(c32t[P].wphi[r][b], fb, HB[b]);
-        HT[b] = fmaf(c32t[P].wphi[r][b], ft, HT[b]);
+        HLR[b] = __ffma2_rn(c32t[P].wphi2[r][b], flr, HLR[b]);
+        HBT[b] = __ffma2_rn(c32t[P].wphi2[r][b], fbt, HBT[b]);
       }
     }
 #pragma unroll
     for (int aa = 0; aa < m; aa++)
 #pragma unroll
       for (int b = 0; b < m; b++) {
-        const float lx = fmaf(c32t[P].pm[aa], HL[b], -c32t[P].pp[aa] * HR[b]);
-        const float ly = fmaf(c32t[P].pm[b], HB[aa], -c32t[P].pp[b] * HT[aa]);
+        const float lx = fmaf(c32t[P].pm[aa], HLR[b].x, -c32t[P].pp[aa] * HLR[b].y);
+        const float ly = fmaf(c32t[P].pm[b], HBT[aa].x, -c32t[P].pp[b] * HBT[aa].y);
         L[aa * m + b] = fmaf(pc.idx, lx, fmaf(pc.idy, ly, L[aa * m + b]));
       }
   }
@@ -1021,6 +1006,8 @@ static Tab32 make_tab32(const Tables& t) {
       c.phil[q][a] = (float)(t.phi[q][a] - (double)c.phi[q][a]);
       c.wphi[q][a] = (float)(t.wh[q] * t.phi[q][a]);
       c.wdphi[q][a] = (float)(t.wh[q] * t.dphi[q][a]);
+      c.wphi2[q][a] = make_float2(c.wphi[q][a], c.wphi[q][a]);
+      c.wdw2[q][a] = make_float2(c.wdphi[q][a], c.wphi[q][a]);
     }
     for (int r = 0; r <= P; r++) {
       const double w2 = t.wh[q] * t.wh[r];
