@@ -64,8 +64,8 @@ struct dg_handle {
   double* W;              // partial sum of their update
   unsigned char* tflags;  // TVB flags of the last limiter pass (pre-limit) [j][i]
   unsigned char* gflags;  // flags given to the limiter (learned indicator, dg_limit_flags) [j][i]
-  __nv_bfloat16* ind_w;   // learned indicator (limiter 2): W1 transposed [input][unit], then
-                          // b1, W2, b2, w3, b3, in BF16 (own allocation, null until set)
+  unsigned char* ind_w;   // learned indicator (limiter 2): weights as tensor-core operands
+                          // (mlp_pack; own allocation, null until set)
   float ind_thr;          // flag when the logit exceeds this
   int timing;                                   // bracket stage launches with events
   std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
@@ -535,10 +535,8 @@ cudaError_t limit_state(dg_handle* h, double* U, const unsigned char* given) {
   if (!given && h->ph.limiter == 2 && h->ind_w) {
     // the learned indicator flags the stage value; the TVB test still runs
     // beside it (its flags are the judge, dg_last_flags)
-    const int nin = 5 * h->nv * h->M;
-    cudaError_t e = launch_mlp_flags(U, h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w,
-                                     h->ind_w + (size_t)nin * MLP_HIDDEN, h->ind_thr, h->ts, h->gflags, nullptr,
-                                     h->stream);
+    cudaError_t e = launch_mlp_flags(U, h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w, h->ind_thr,
+                                     h->ts, h->gflags, nullptr, h->stream);
     if (e != cudaSuccess) return e;
     given = h->gflags;
   }
@@ -1311,16 +1309,14 @@ int dg_set_indicator(dg_handle* h, const dg_mlp* net, float threshold) {
     h->ind_w = nullptr;
     return DG_OK;
   }
-  const int nin = 5 * h->nv * h->M, H = MLP_HIDDEN;
+  const int nin = 5 * h->nv * h->M;
   if (net->b.nin != nin) return fail(h, DG_ERR_ARG, "network has %d inputs, this form needs %d", net->b.nin, nin);
   std::vector<float> p(net->np);
   CU(h, cudaMemcpy(p.data(), net->b.p, p.size() * sizeof(float), cudaMemcpyDeviceToHost));
-  std::vector<unsigned short> w((size_t)nin * H + (net->np - (size_t)nin * H));
-  for (int u = 0; u < H; u++)
-    for (int i = 0; i < nin; i++) w[(size_t)i * H + u] = bf16_rne(p[(size_t)u * nin + i]);
-  for (size_t k = (size_t)nin * H; k < (size_t)net->np; k++) w[k] = bf16_rne(p[k]);
-  if (!h->ind_w) CU(h, cudaMalloc((void**)&h->ind_w, w.size() * 2));
-  CU(h, cudaMemcpy(h->ind_w, w.data(), w.size() * 2, cudaMemcpyHostToDevice));
+  std::vector<unsigned char> w(mlp_pack_bytes(nin));
+  mlp_pack(p.data(), nin, w.data());
+  if (!h->ind_w) CU(h, cudaMalloc((void**)&h->ind_w, w.size()));
+  CU(h, cudaMemcpy(h->ind_w, w.data(), w.size(), cudaMemcpyHostToDevice));
   h->ind_thr = threshold;
   return DG_OK;
 }
@@ -1334,10 +1330,8 @@ int dg_indicator_logits(dg_handle* h, float* logits, unsigned char* flags) {
   const size_t ne = (size_t)h->mesh.nx * h->mesh.ny;
   float* dl = nullptr;
   CU(h, cudaMalloc((void**)&dl, ne * sizeof(float)));
-  const int nin = 5 * h->nv * h->M;
   cudaError_t e = launch_mlp_flags(h->B[h->cur], h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w,
-                                   h->ind_w + (size_t)nin * MLP_HIDDEN, h->ind_thr, h->ts, h->gflags, dl,
-                                   h->stream);
+                                   h->ind_thr, h->ts, h->gflags, dl, h->stream);
   if (e == cudaSuccess && logits) e = cudaMemcpyAsync(logits, dl, ne * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, h->gflags, ne, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -16,10 +16,13 @@
 // (beta 0.9, 0.999, eps 1e-8) on the master copy.
 #include <cuda_bf16.h>
 
+#include <string.h>
+
 #include <new>
 #include <vector>
 
 #include "dg_internal.cuh"
+#include "dg_tc.cuh"
 
 namespace dg {
 
@@ -209,84 +212,257 @@ __global__ void k_features(const FeatArgs a, const int* __restrict__ elems, int 
         o[(s * NV + v) * M + k] = (float)(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k) * S[v]);
 }
 
-// one thread per element: features on the fly, the first layer against the
-// BF16 weights staged in shared memory ([input][unit]: every thread reads the
-// same row, a broadcast), the second layer and the logit; writes the flag
-// (logit > threshold) and, when asked, the logit
-template <int NV, int M>
-__global__ void __launch_bounds__(256) k_mlp_flags(const FeatArgs a, const __nv_bfloat16* __restrict__ Wt1,
-                                                   const __nv_bfloat16* __restrict__ rest, float threshold,
-                                                   const DevState* ts, unsigned char* __restrict__ flags,
-                                                   float* __restrict__ logits) {
-  constexpr int NIN = 5 * NV * M;
-  // BF16 weights widened to FP32 once (exact), [NIN][H] then b1, W2 [H][H],
-  // b2, w3, b3: the inner loop reads rows of four weights per load
-  extern __shared__ float4 sw4[];
-  float* sw = reinterpret_cast<float*>(sw4);
-  const int nrest = H + H * H + H + H + 1;
-  for (int k = threadIdx.x; k < NIN * H; k += blockDim.x) sw[k] = __bfloat162float(Wt1[k]);
-  for (int k = threadIdx.x; k < nrest; k += blockDim.x) sw[NIN * H + k] = __bfloat162float(rest[k]);
-  __syncthreads();
-  if (ts->status != 0) return;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = (int)(gid & 31);
-  const long long tile = gid >> 5;
-  if (tile >= (long long)a.ms.ntx * a.ms.ny) return;
-  const int j = (int)(tile / a.ms.ntx), i = (int)(tile - (long long)j * a.ms.ntx) * 32 + lane;
-  if (i >= a.ms.nx) return;
-  const int di[5] = {0, -1, 1, 0, 0}, dj[5] = {0, 0, 0, -1, 1};
-  double S[NV];
-  stencil_scales<NV, M>(a, i, j, S);
-  const float* b1 = sw + NIN * H;
-  const float* W2 = b1 + H;
-  const float* b2 = W2 + H * H;
-  const float* w3 = b2 + H;
-  const float* b3 = w3 + H;
-  float h[H];
+// ---- fused inference on the tensor cores ----------------------------------
+// One CTA of 256 threads per 128 elements (4 mesh tiles); element row r is
+// the MMA row r.  Layer 1 runs over the inputs in chunks of 64: the 256
+// threads form the chunk's features (two threads per row, 32 inputs each),
+// split each into BF16 hi + lo (x = hi + lo to 2^-16 relative; the weights are
+// BF16 already, so the two MMAs reproduce the FP32 products), and one thread
+// issues the chunk's MMAs (M 128, N 64, K 16) into tensor memory while the
+// next chunk's features are formed (two-stage ring; the W1 chunk of each
+// stage arrives by a bulk copy).  The epilogue reads the accumulators back
+// (warp w: lanes 32 (w mod 4).., columns 32 (w / 4)..), adds the bias,
+// applies GELU and splits the hidden units into BF16 hi + lo, the A operand
+// of layer 2 (64 -> 64, same scheme); the last epilogue forms the logit.
+constexpr int TC_ROWS = 128, TC_KC = 64, TC_THREADS = 256;
+constexpr int TC_A = 0;                          // [2 stages][hi, lo][128 x 64] BF16, 16 KB each
+constexpr int TC_B = TC_A + 4 * 16384;           // W1 chunks [2 stages][64 x 64] BF16
+constexpr int TC_W2 = TC_B + 2 * 8192;           // W2 [64 x 64] BF16
+constexpr int TC_PAR = TC_W2 + 8192;             // b1, b2, w3 [64] and b3, FP32 (1 KB)
+constexpr int TC_MX = TC_PAR + 1024;             // stencil maxima [2][128][4] (8 KB); then partial logits
+constexpr int TC_BAR = TC_MX + 8192;             // mbarriers: MMA done [2], W1 chunk [2], W2, layer 2
+constexpr int TC_TM = TC_BAR + 64;               // tensor-memory base address
+constexpr int TC_SMEM = TC_TM + 16;
+
+// byte offset of (row, k) in a K-major no-swizzle operand of `rows` rows
+__host__ __device__ inline int tc_off(int rows, int row, int k) {
+  return (k >> 3) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a in the low half
+  return *reinterpret_cast<const unsigned*>(&h);
+}
+
+// x = hi + lo exactly in FP32 terms: lo is the BF16 rounding of x - hi
+__device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
+  unsigned h[4], l[4];
 #pragma unroll
-  for (int u = 0; u < H; u++) h[u] = b1[u];
-  for (int s = 0; s < 5; s++)
-    for (int v = 0; v < NV; v++)
-      for (int k = 0; k < M; k++) {
-        const float x = (float)(coef<NV, M>(a, i + di[s], j + dj[s], i, j, v, k) * S[v]);
-        const float4* row = reinterpret_cast<const float4*>(sw + (size_t)((s * NV + v) * M + k) * H);
-#pragma unroll
-        for (int u4 = 0; u4 < H / 4; u4++) {
-          const float4 w = row[u4];
-          h[4 * u4 + 0] = fmaf(x, w.x, h[4 * u4 + 0]);
-          h[4 * u4 + 1] = fmaf(x, w.y, h[4 * u4 + 1]);
-          h[4 * u4 + 2] = fmaf(x, w.z, h[4 * u4 + 2]);
-          h[4 * u4 + 3] = fmaf(x, w.w, h[4 * u4 + 3]);
-        }
-      }
-#pragma unroll
-  for (int u = 0; u < H; u++) h[u] = gelu(h[u]);
-  float z = b3[0];
-  for (int u = 0; u < H; u++) {
-    float acc = b2[u];
-#pragma unroll
-    for (int q = 0; q < H; q++) acc = fmaf(h[q], W2[u * H + q], acc);
-    z = fmaf(gelu(acc), w3[u], z);
+  for (int e = 0; e < 4; e++) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+    h[e] = *reinterpret_cast<const unsigned*>(&hh);
+    l[e] = pack_bf16(x[2 * e] - __low2float(hh), x[2 * e + 1] - __high2float(hh));
   }
-  const size_t e = (size_t)j * a.ms.nx + i;
-  flags[e] = (unsigned char)(z > threshold);
-  if (logits) logits[e] = z;
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+#ifdef DG_TC_SWAP_LBO
+#define TC_DESC(addr, lbo, sbo) tc_sdesc(addr, sbo, lbo)
+#else
+#define TC_DESC(addr, lbo, sbo) tc_sdesc(addr, lbo, sbo)
+#endif
+
+template <int NV, int M>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_mlp_tc(const FeatArgs a, const unsigned char* __restrict__ wp, float threshold, DevState* ts,
+             unsigned char* __restrict__ flags, float* __restrict__ logits, long long ntiles) {
+  constexpr int NIN = 5 * NV * M, NC = (NIN + TC_KC - 1) / TC_KC, H2 = MLP_HIDDEN;
+  static_assert(MLP_HIDDEN == 64 && NV <= 4, "tile plan");
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TC_BAR);
+  unsigned* s_taddr = reinterpret_cast<unsigned*>(sm + TC_TM);
+  if (ts->status != 0) return;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (TC_ROWS - 1), half = tid >> 7;
+  const unsigned idesc = tc_idesc_bf16(TC_ROWS, H2);
+
+  if (warp == 0) tmem_alloc(s_taddr, 128);  // D1: columns 0..63, D2: 64..127
+  if (tid == 0) {
+#pragma unroll
+    for (int b = 0; b < 6; b++) mbar_init(&bar[b], 1);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[4], 8192 + 1024);
+    bulk_g2s(sm + TC_W2, wp + (size_t)NC * 8192, 8192, &bar[4]);
+    bulk_g2s(sm + TC_PAR, wp + (size_t)NC * 8192 + 8192, 1024, &bar[4]);
+#pragma unroll
+    for (int c = 0; c < (NC < 2 ? NC : 2); c++) {
+      mbar_expect_tx(&bar[2 + c], 8192);
+      bulk_g2s(sm + TC_B + c * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + c]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = *s_taddr;
+  bool ok = true;
+
+  // this row's element and its stencil (s = 0 own, 1 left, 2 right, 3 below, 4 above)
+  const long long tile = (long long)blockIdx.x * 4 + (row >> 5);
+  int i = 0, j = 0;
+  bool valid = false;
+  if (tile < ntiles) {
+    j = (int)(tile / a.ms.ntx);
+    i = (int)(tile - (long long)j * a.ms.ntx) * 32 + (row & 31);
+    valid = i < a.ms.nx;
+  }
+  // 1 / S_v over the stencil: each half scans every other mode, the maxima meet in shared memory
+  double R[NV];
+  {
+    unsigned long long* smx = reinterpret_cast<unsigned long long*>(sm + TC_MX);
+    unsigned long long mx[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) mx[v] = 0ull;
+    if (valid) {
+      for (int s = 0; s < 5; s++) {
+        const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+          for (int k = half; k < M; k += 2) {
+            const unsigned long long b =
+                (unsigned long long)__double_as_longlong(coef<NV, M>(a, ii, jj, i, j, v, k)) & 0x7fffffffffffffffull;
+            mx[v] = b > mx[v] ? b : mx[v];
+          }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) smx[(half * TC_ROWS + row) * 4 + v] = mx[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const unsigned long long m0 = smx[row * 4 + v], m1 = smx[(TC_ROWS + row) * 4 + v];
+      const unsigned long long mm = m0 > m1 ? m0 : m1;
+      R[v] = mm ? 1.0 / __longlong_as_double((long long)mm) : 1.0;
+    }
+  }
+
+  // ---- layer 1 over the input chunks ----
+  for (int c = 0; c < NC; c++) {
+    const int st = c & 1;
+    unsigned char* Ahi = sm + TC_A + st * 32768;
+    unsigned char* Alo = Ahi + 16384;
+    if (c >= 2) {
+      // the MMAs of chunk c - 2 have read this stage's buffers
+      ok &= mbar_wait(&bar[st], ((c - 2) >> 1) & 1);
+      if (tid == 0) {
+        mbar_expect_tx(&bar[2 + st], 8192);
+        bulk_g2s(sm + TC_B + st * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + st]);
+      }
+    }
+#pragma unroll 1
+    for (int g = 0; g < 4; g++) {
+      const int kl = half * 32 + g * 8;  // first input of this 16-byte row within the chunk
+      float x[8];
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        const int k = c * TC_KC + kl + e;
+        float xv = 0.0f;
+        if (valid && k < NIN) {
+          const int s = k / (NV * M), rem = k - s * (NV * M), v = rem / M, kk = rem - v * M;
+          const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
+          double rv = R[0];
+#pragma unroll
+          for (int w = 1; w < NV; w++) rv = (v == w) ? R[w] : rv;
+          xv = (float)(coef<NV, M>(a, ii, jj, i, j, v, kk) * rv);
+        }
+        x[e] = xv;
+      }
+      uint4 hi, lo;
+      split8(x, hi, lo);
+      const int off = tc_off(TC_ROWS, row, kl);
+      *reinterpret_cast<uint4*>(Ahi + off) = hi;
+      *reinterpret_cast<uint4*>(Alo + off) = lo;
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      ok &= mbar_wait(&bar[2 + st], (c >> 1) & 1);
+      tc_fence_after();
+      const unsigned aH = smem_addr(Ahi), aL = smem_addr(Alo), bB = smem_addr(sm + TC_B + st * 8192);
+#pragma unroll
+      for (int ks = 0; ks < TC_KC / 16; ks++) {
+        const uint64_t db = TC_DESC(bB + ks * 2048, 1024, 128);
+        tc_mma(taddr, TC_DESC(aH + ks * 4096, 2048, 128), db, idesc, (c > 0 || ks > 0) ? 1 : 0);
+        tc_mma(taddr, TC_DESC(aL + ks * 4096, 2048, 128), db, idesc, 1);
+      }
+      tc_commit(&bar[st]);
+    }
+  }
+  // the last commit covers every earlier MMA
+  ok &= mbar_wait(&bar[(NC - 1) & 1], ((NC - 1) >> 1) & 1);
+  ok &= mbar_wait(&bar[4], 0);
+  tc_fence_after();
+  const float* par = reinterpret_cast<const float*>(sm + TC_PAR);  // b1, b2, w3, b3
+  const int quarter = warp & 3, ch = warp >> 2;
+  const unsigned tl = taddr + ((unsigned)(quarter * 32) << 16);
+  float acc[32];
+  // ---- epilogue 1: h1 = GELU(D1 + b1) as the layer-2 A operand (stage 0's buffers) ----
+  tmem_ld32(tl + ch * 32, acc);
+  {
+    unsigned char* Hhi = sm + TC_A;
+    unsigned char* Hlo = Hhi + 16384;
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      float x[8];
+#pragma unroll
+      for (int e = 0; e < 8; e++) x[e] = gelu(acc[g * 8 + e] + par[ch * 32 + g * 8 + e]);
+      uint4 hi, lo;
+      split8(x, hi, lo);
+      const int off = tc_off(TC_ROWS, row, ch * 32 + g * 8);
+      *reinterpret_cast<uint4*>(Hhi + off) = hi;
+      *reinterpret_cast<uint4*>(Hlo + off) = lo;
+    }
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc_fence_after();
+    const unsigned aH = smem_addr(sm + TC_A), aL = aH + 16384, bW = smem_addr(sm + TC_W2);
+#pragma unroll
+    for (int ks = 0; ks < H2 / 16; ks++) {
+      const uint64_t db = TC_DESC(bW + ks * 2048, 1024, 128);
+      tc_mma(taddr + H2, TC_DESC(aH + ks * 4096, 2048, 128), db, idesc, ks > 0 ? 1 : 0);
+      tc_mma(taddr + H2, TC_DESC(aL + ks * 4096, 2048, 128), db, idesc, 1);
+    }
+    tc_commit(&bar[5]);
+  }
+  ok &= mbar_wait(&bar[5], 0);
+  tc_fence_after();
+  // ---- epilogue 2: z = w3 . GELU(D2 + b2) + b3 ----
+  tmem_ld32(tl + H2 + ch * 32, acc);
+  float zp = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 32; e++) zp = fmaf(gelu(acc[e] + par[H2 + ch * 32 + e]), par[2 * H2 + ch * 32 + e], zp);
+  float* szp = reinterpret_cast<float*>(sm + TC_MX);
+  if (ch == 1) szp[row] = zp;
+  tc_fence_before();
+  __syncthreads();
+  if (ch == 0 && valid) {
+    const float z = zp + szp[row] + par[3 * H2];
+    const size_t e = (size_t)j * a.ms.nx + i;
+    flags[e] = (unsigned char)(z > threshold);
+    if (logits) logits[e] = z;
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 128);
+  }
+  if (!ok) atomicOr(&ts->pending, 2);
 }
 
 template <int NV, int M>
-cudaError_t launch_flags_t(const FeatArgs& fa, const __nv_bfloat16* Wt1, const __nv_bfloat16* rest,
-                           float threshold, const DevState* ts, unsigned char* flags, float* logits,
-                           cudaStream_t s) {
-  constexpr int NIN = 5 * NV * M;
-  const size_t smem = (size_t)(NIN * H + H + H * H + H + H + 1) * sizeof(float);
+cudaError_t launch_flags_t(const FeatArgs& fa, const void* wpack, float threshold, DevState* ts,
+                           unsigned char* flags, float* logits, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_flags<NV, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<NV, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const long long threads = (long long)fa.ms.ntx * fa.ms.ny * 32;
-  k_mlp_flags<NV, M><<<blocks(threads, 256), 256, smem, s>>>(fa, Wt1, rest, threshold, ts, flags, logits);
+  const long long ntiles = (long long)fa.ms.ntx * fa.ms.ny;
+  const long long nblk = (ntiles + 3) / 4;
+  k_mlp_tc<NV, M><<<(unsigned)nblk, TC_THREADS, TC_SMEM, s>>>(
+      fa, static_cast<const unsigned char*>(wpack), threshold, ts, flags, logits, ntiles);
   return cudaGetLastError();
 }
 
@@ -340,13 +516,55 @@ cudaError_t launch_features(const double* U, const double* GL, const double* GR,
 }
 
 cudaError_t launch_mlp_flags(const double* U, const double* GL, const double* GR, const double* GB,
-                             const double* GT, const Mesh& ms, int p, int nv, const __nv_bfloat16* Wt1,
-                             const __nv_bfloat16* rest, float threshold, const DevState* ts,
-                             unsigned char* flags, float* logits, cudaStream_t s) {
+                             const double* GT, const Mesh& ms, int p, int nv, const void* wpack, float threshold,
+                             DevState* ts, unsigned char* flags, float* logits, cudaStream_t s) {
   const FeatArgs fa = feat_args(U, GL, GR, GB, GT, ms);
-#define CALL(a, b) launch_flags_t<a, b>(fa, Wt1, rest, threshold, ts, flags, logits, s)
+#define CALL(a, b) launch_flags_t<a, b>(fa, wpack, threshold, ts, flags, logits, s)
   DG_MLP_DISPATCH(nv, p, CALL);
 #undef CALL
+}
+
+size_t mlp_pack_bytes(int nin) { return (size_t)((nin + TC_KC - 1) / TC_KC) * 8192 + 8192 + 1024; }
+
+namespace {
+unsigned short bf16_bits(float f) {  // round to nearest even, as __float2bfloat16_rn
+  unsigned u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x7fffffu)) return (unsigned short)((u >> 16) | 0x40);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (unsigned short)(u >> 16);
+}
+float bf16_value(float f) {
+  const unsigned u = (unsigned)bf16_bits(f) << 16;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+void put_bf16(unsigned char* base, int off, float f) {
+  const unsigned short b = bf16_bits(f);
+  memcpy(base + off, &b, 2);
+}
+}  // namespace
+
+void mlp_pack(const float* prm, int nin, unsigned char* out) {
+  const Offs o = offs(nin);
+  const int nc = (nin + TC_KC - 1) / TC_KC;
+  memset(out, 0, mlp_pack_bytes(nin));
+  for (int c = 0; c < nc; c++)
+    for (int n = 0; n < H; n++)
+      for (int k = 0; k < TC_KC; k++)
+        if (c * TC_KC + k < nin) put_bf16(out + (size_t)c * 8192, tc_off(H, n, k), prm[o.W1 + (size_t)n * nin + c * TC_KC + k]);
+  unsigned char* w2 = out + (size_t)nc * 8192;
+  for (int u = 0; u < H; u++)
+    for (int q = 0; q < H; q++) put_bf16(w2, tc_off(H, u, q), prm[o.W2 + u * H + q]);
+  float pf[3 * H + 1];
+  for (int u = 0; u < H; u++) {
+    pf[u] = bf16_value(prm[o.b1 + u]);
+    pf[H + u] = bf16_value(prm[o.b2 + u]);
+    pf[2 * H + u] = bf16_value(prm[o.w3 + u]);
+  }
+  pf[3 * H] = bf16_value(prm[o.b3]);
+  memcpy(w2 + 8192, pf, sizeof(pf));
 }
 
 // ---- training ------------------------------------------------------------

@@ -25,6 +25,7 @@
 // touch a zone) and the CFL minimum; the torque of the new state is a
 // separate one-variable pass (k_torque32 below).
 #pragma once
+#include "dg_async.cuh"
 #include "dg_internal.cuh"
 
 
@@ -174,50 +175,6 @@ struct Smem32 {
 // exact int -> float for 0 <= x < 2^23 on the integer and FP32 pipes (this
 // part executes conversion instructions on its narrow FP64 unit)
 __device__ __forceinline__ float i2f(int x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
-
-// ---- 1D bulk copies global -> shared by the TMA unit, completion counted in
-// transaction bytes on an mbarrier (one phase per kernel) ---------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(void* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// orders this thread's earlier generic-proxy accesses of shared memory before
-// later async-proxy (TMA) writes to it
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(void* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-// bytes and both addresses multiples of 16
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, void* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(void* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the phase of the given parity: false after ~2^22 polls
-// (a fraction of a second), so that a copy that never lands cannot hang the GPU
-__device__ __forceinline__ bool mbar_wait(void* bar, unsigned parity) {
-  for (int i = 0; i < (1 << 22); i++) {
-    if (mbar_test(bar, parity)) return true;
-    if (i >= 8) __nanosleep(64);
-  }
-  return false;
-}
 
 // ---- float-float ("double-float") arithmetic on the FP32 pipe --------------
 // The _rn intrinsics are never contracted into FMAs, which the error-free
