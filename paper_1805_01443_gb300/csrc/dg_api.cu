@@ -65,7 +65,8 @@ struct dg_handle {
   unsigned char* tflags;  // TVB flags of the last limiter pass (pre-limit) [j][i]
   unsigned char* gflags;  // flags given to the limiter (learned indicator, dg_limit_flags) [j][i]
   unsigned char* ind_w;   // learned indicator (limiter 2): weights as tensor-core operands
-                          // (mlp_pack; own allocation, null until set)
+                          // (mlp_pack), then its scratch at ind_work (own allocation, null until set)
+  size_t ind_work;
   float ind_thr;          // flag when the logit exceeds this
   int timing;                                   // bracket stage launches with events
   std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
@@ -535,8 +536,8 @@ cudaError_t limit_state(dg_handle* h, double* U, const unsigned char* given) {
   if (!given && h->ph.limiter == 2 && h->ind_w) {
     // the learned indicator flags the stage value; the TVB test still runs
     // beside it (its flags are the judge, dg_last_flags)
-    cudaError_t e = launch_mlp_flags(U, h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w, h->ind_thr,
-                                     h->ts, h->gflags, nullptr, h->stream);
+    cudaError_t e = launch_mlp_flags(U, h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w,
+                                     h->ind_w + h->ind_work, h->ind_thr, h->ts, h->gflags, nullptr, h->stream);
     if (e != cudaSuccess) return e;
     given = h->gflags;
   }
@@ -1313,9 +1314,10 @@ int dg_set_indicator(dg_handle* h, const dg_mlp* net, float threshold) {
   if (net->b.nin != nin) return fail(h, DG_ERR_ARG, "network has %d inputs, this form needs %d", net->b.nin, nin);
   std::vector<float> p(net->np);
   CU(h, cudaMemcpy(p.data(), net->b.p, p.size() * sizeof(float), cudaMemcpyDeviceToHost));
-  std::vector<unsigned char> w(mlp_pack_bytes(nin));
-  mlp_pack(p.data(), nin, w.data());
-  if (!h->ind_w) CU(h, cudaMalloc((void**)&h->ind_w, w.size()));
+  std::vector<unsigned char> w(mlp_pack_bytes(h->nv, h->M));
+  mlp_pack(p.data(), h->nv, h->M, w.data());
+  h->ind_work = (w.size() + 255) / 256 * 256;
+  if (!h->ind_w) CU(h, cudaMalloc((void**)&h->ind_w, h->ind_work + mlp_work_bytes(h->dm, h->nv)));
   CU(h, cudaMemcpy(h->ind_w, w.data(), w.size(), cudaMemcpyHostToDevice));
   h->ind_thr = threshold;
   return DG_OK;
@@ -1331,7 +1333,7 @@ int dg_indicator_logits(dg_handle* h, float* logits, unsigned char* flags) {
   float* dl = nullptr;
   CU(h, cudaMalloc((void**)&dl, ne * sizeof(float)));
   cudaError_t e = launch_mlp_flags(h->B[h->cur], h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w,
-                                   h->ind_thr, h->ts, h->gflags, dl, h->stream);
+                                   h->ind_w + h->ind_work, h->ind_thr, h->ts, h->gflags, dl, h->stream);
   if (e == cudaSuccess && logits) e = cudaMemcpyAsync(logits, dl, ne * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, h->gflags, ne, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -216,15 +216,17 @@ cudaError_t launch_features(const double* U, const double* GL, const double* GR,
                             const double* GT, const Mesh& ms, int p, int nv, const int* elems, int n, float* out,
                             cudaStream_t s);
 // flags (logit > threshold) and optionally logits of every element, on the
-// tensor cores; wpack holds the weights in the layout mlp_pack writes
+// tensor cores; wpack holds the weights in the layout mlp_pack writes, work
+// is scratch of mlp_work_bytes (per-element maxima of |c|)
 cudaError_t launch_mlp_flags(const double* U, const double* GL, const double* GR, const double* GB,
-                             const double* GT, const Mesh& ms, int p, int nv, const void* wpack, float threshold,
-                             DevState* ts, unsigned char* flags, float* logits, cudaStream_t s);
+                             const double* GT, const Mesh& ms, int p, int nv, const void* wpack, void* work,
+                             float threshold, DevState* ts, unsigned char* flags, float* logits, cudaStream_t s);
+size_t mlp_work_bytes(const Mesh& ms, int nv);
 // host: the flat FP32 parameters as the inference kernel's operands (W1 in
 // 64-input chunks and W2 as BF16 tensor-core tiles, then b1, b2, w3, b3 as the
 // FP32 values of their BF16 roundings)
-size_t mlp_pack_bytes(int nin);
-void mlp_pack(const float* prm, int nin, unsigned char* out);
+size_t mlp_pack_bytes(int nv, int M);
+void mlp_pack(const float* prm, int nv, int M, unsigned char* out);
 
 // precision-form setup and conversions (dg_prec.cu)
 cudaError_t launch_delta_from_full(const double* full, const double* bg, float* d, size_t n,

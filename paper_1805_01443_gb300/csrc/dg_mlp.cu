@@ -218,21 +218,24 @@ __global__ void k_features(const FeatArgs a, const int* __restrict__ elems, int 
 // threads form the chunk's features (two threads per row, 32 inputs each),
 // split each into BF16 hi + lo (x = hi + lo to 2^-16 relative; the weights are
 // BF16 already, so the two MMAs reproduce the FP32 products), and one thread
-// issues the chunk's MMAs (M 128, N 64, K 16) into tensor memory while the
-// next chunk's features are formed (two-stage ring; the W1 chunk of each
-// stage arrives by a bulk copy).  The epilogue reads the accumulators back
-// (warp w: lanes 32 (w mod 4).., columns 32 (w / 4)..), adds the bias,
-// applies GELU and splits the hidden units into BF16 hi + lo, the A operand
-// of layer 2 (64 -> 64, same scheme); the last epilogue forms the logit.
+// issues the chunk's MMAs (M 128, N 64, K 16) into tensor memory.  The next
+// chunk's coefficients are loaded and scaled while those MMAs run; its
+// features are stored once they are done (one A buffer: the MMAs take a
+// small fraction of the feature time, and the smaller footprint lets three
+// CTAs share an SM).  The W1 chunks arrive by bulk copies into a two-stage
+// ring.  The epilogue reads the accumulators back (warp w: lanes 32 (w mod 4)..,
+// columns 32 (w / 4)..), adds the bias, applies GELU and splits the hidden
+// units into BF16 hi + lo, the A operand of layer 2 (64 -> 64, same scheme);
+// the last epilogue forms the logit.
 constexpr int TC_ROWS = 128, TC_KC = 64, TC_THREADS = 256;
-constexpr int TC_A = 0;                          // [2 stages][hi, lo][128 x 64] BF16, 16 KB each
-constexpr int TC_B = TC_A + 4 * 16384;           // W1 chunks [2 stages][64 x 64] BF16
+constexpr int TC_A = 0;                          // [hi, lo][128 x 64] BF16, 16 KB each
+constexpr int TC_B = TC_A + 2 * 16384;           // W1 chunks [2 stages][64 x 64] BF16
 constexpr int TC_W2 = TC_B + 2 * 8192;           // W2 [64 x 64] BF16
-constexpr int TC_PAR = TC_W2 + 8192;             // b1, b2, w3 [64] and b3, FP32 (1 KB)
-constexpr int TC_MX = TC_PAR + 1024;             // stencil maxima [2][128][4] (8 KB); then partial logits
-constexpr int TC_BAR = TC_MX + 8192;             // mbarriers: MMA done [2], W1 chunk [2], W2, layer 2
+constexpr int TC_PAR = TC_W2 + 8192;             // b1, b2, w3 [64] and b3, FP32 (1 KB); then partial logits
+constexpr int TC_BAR = TC_PAR + 1024;            // mbarriers: MMA done, (unused), W1 chunk [2], W2, layer 2
 constexpr int TC_TM = TC_BAR + 64;               // tensor-memory base address
 constexpr int TC_SMEM = TC_TM + 16;
+constexpr int TC_PZ = TC_A + 8192;               // partial logits [128] (A is dead by then)
 
 // byte offset of (row, k) in a K-major no-swizzle operand of `rows` rows
 __host__ __device__ inline int tc_off(int rows, int row, int k) {
@@ -257,6 +260,63 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// double -> float, round to nearest even, on the integer pipe (this part
+// runs the conversion instruction on its narrow FP64 unit); finite |x| < 2^128
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  unsigned f;
+  if (e >= 897) {  // normal result: keep 23 fraction bits, round on the 29 dropped
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    f = ((unsigned)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  } else if (e >= 872) {  // subnormal result: the significand shifted right by 926 - e
+    const unsigned long long sig = (1ull << 52) | (b & 0xFFFFFFFFFFFFFull);
+    const int sh = 926 - e;
+    const unsigned long long q = sig >> sh, r = sig & ((1ull << sh) - 1), h = 1ull << (sh - 1);
+    f = (unsigned)q + ((r > h || (r == h && (q & 1ull))) ? 1u : 0u);
+  } else {
+    f = 0u;
+  }
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// the mesh element standing for stencil element (ii, jj) of element (ci, cj):
+// false for a fixed ghost element (bc 1)
+__device__ __forceinline__ bool mesh_elem(const Mesh& ms, int ii, int jj, int ci, int cj, long long& tile,
+                                          int& lane) {
+  if (ii < 0 || ii >= ms.nx || jj < 0 || jj >= ms.ny) {
+    if (ms.bc == 0) {
+      ii = (ii + ms.nx) % ms.nx;
+      jj = (jj + ms.ny) % ms.ny;
+    } else if (ms.bc == 1) {
+      return false;
+    } else {
+      ii = ci;
+      jj = cj;
+    }
+  }
+  tile = (long long)jj * ms.ntx + (ii >> 5);
+  lane = ii & 31;
+  return true;
+}
+
+// bits of max |c| over the modes of variable v of every element, [tile][v][32]
+template <int NV, int M>
+__global__ void k_elem_max(const double* __restrict__ U, unsigned long long* __restrict__ mx, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double* p = U + (t >> 5) * (M * 32) + (t & 31);
+  unsigned long long m = 0ull;
+#pragma unroll
+  for (int k = 0; k < M; k++) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p[k * 32]) & 0x7fffffffffffffffull;
+    m = b > m ? b : m;
+  }
+  mx[t] = m;
+}
+
 #ifdef DG_TC_SWAP_LBO
 #define TC_DESC(addr, lbo, sbo) tc_sdesc(addr, sbo, lbo)
 #else
@@ -264,10 +324,14 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
 #endif
 
 template <int NV, int M>
-__global__ void __launch_bounds__(TC_THREADS, 2)
-    k_mlp_tc(const FeatArgs a, const unsigned char* __restrict__ wp, float threshold, DevState* ts,
-             unsigned char* __restrict__ flags, float* __restrict__ logits, long long ntiles) {
-  constexpr int NIN = 5 * NV * M, NC = (NIN + TC_KC - 1) / TC_KC, H2 = MLP_HIDDEN;
+__global__ void __launch_bounds__(TC_THREADS, 3)
+    k_mlp_tc(const FeatArgs a, const unsigned char* __restrict__ wp, const unsigned long long* __restrict__ emax,
+             float threshold, DevState* ts, unsigned char* __restrict__ flags, float* __restrict__ logits,
+             long long ntiles) {
+  // inputs in groups of 8 modes of one (stencil element, variable), the modes
+  // of a variable padded to a multiple of 8 (zero weights): a group has one
+  // base address, one stride and one scale
+  constexpr int GPB = (M + 7) / 8, NG = 5 * NV * GPB, NC = (NG + 7) / 8, H2 = MLP_HIDDEN;
   static_assert(MLP_HIDDEN == 64 && NV <= 4, "tile plan");
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TC_BAR);
@@ -305,72 +369,106 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     i = (int)(tile - (long long)j * a.ms.ntx) * 32 + (row & 31);
     valid = i < a.ms.nx;
   }
-  // 1 / S_v over the stencil: each half scans every other mode, the maxima meet in shared memory
+  // 1 / S_v over the stencil, from the per-element maxima (fixed ghost elements scanned here)
   double R[NV];
   {
-    unsigned long long* smx = reinterpret_cast<unsigned long long*>(sm + TC_MX);
     unsigned long long mx[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) mx[v] = 0ull;
     if (valid) {
+#pragma unroll
       for (int s = 0; s < 5; s++) {
         const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
+        long long te;
+        int le;
+        if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
 #pragma unroll
-        for (int v = 0; v < NV; v++)
-          for (int k = half; k < M; k += 2) {
-            const unsigned long long b =
-                (unsigned long long)__double_as_longlong(coef<NV, M>(a, ii, jj, i, j, v, k)) & 0x7fffffffffffffffull;
+          for (int v = 0; v < NV; v++) {
+            const unsigned long long b = emax[((size_t)te * NV + v) * 32 + le];
             mx[v] = b > mx[v] ? b : mx[v];
           }
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; v++)
+            for (int k = 0; k < M; k++) {
+              const unsigned long long b =
+                  (unsigned long long)__double_as_longlong(coef<NV, M>(a, ii, jj, i, j, v, k)) & 0x7fffffffffffffffull;
+              mx[v] = b > mx[v] ? b : mx[v];
+            }
+        }
       }
     }
 #pragma unroll
-    for (int v = 0; v < NV; v++) smx[(half * TC_ROWS + row) * 4 + v] = mx[v];
-    __syncthreads();
+    for (int v = 0; v < NV; v++) R[v] = mx[v] ? 1.0 / __longlong_as_double((long long)mx[v]) : 1.0;
+  }
+
+  // base address and stride (elements) of each stencil element's coefficients
+  const double* sp[5];
+  int sst[5];
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      const unsigned long long m0 = smx[row * 4 + v], m1 = smx[(TC_ROWS + row) * 4 + v];
-      const unsigned long long mm = m0 > m1 ? m0 : m1;
-      R[v] = mm ? 1.0 / __longlong_as_double((long long)mm) : 1.0;
+  for (int s = 0; s < 5; s++) {
+    const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
+    long long te;
+    int le;
+    sp[s] = a.U;
+    sst[s] = 0;
+    if (!valid) continue;
+    if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
+      sp[s] = a.U + (size_t)te * NV * M * 32 + le;
+      sst[s] = 32;
+    } else if (ii < 0 || ii >= a.ms.nx) {  // fixed ghost elements [j][v][k]
+      sp[s] = (ii < 0 ? a.GL : a.GR) + (size_t)j * NV * M;
+      sst[s] = 1;
+    } else {  // [tile][v][k][32]
+      sp[s] = (jj < 0 ? a.GB : a.GT) + (size_t)(i >> 5) * NV * M * 32 + (i & 31);
+      sst[s] = 32;
     }
   }
 
   // ---- layer 1 over the input chunks ----
+  unsigned char* Ahi = sm + TC_A;
+  unsigned char* Alo = Ahi + 16384;
   for (int c = 0; c < NC; c++) {
     const int st = c & 1;
-    unsigned char* Ahi = sm + TC_A + st * 32768;
-    unsigned char* Alo = Ahi + 16384;
-    if (c >= 2) {
-      // the MMAs of chunk c - 2 have read this stage's buffers
-      ok &= mbar_wait(&bar[st], ((c - 2) >> 1) & 1);
-      if (tid == 0) {
-        mbar_expect_tx(&bar[2 + st], 8192);
-        bulk_g2s(sm + TC_B + st * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + st]);
-      }
+    if (c >= 2 && tid == 0) {
+      // the MMAs of chunk c - 2, the last readers of this W1 stage, are done:
+      // every thread saw their commit before it wrote chunk c - 1
+      mbar_expect_tx(&bar[2 + st], 8192);
+      bulk_g2s(sm + TC_B + st * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + st]);
     }
 #pragma unroll 1
-    for (int g = 0; g < 4; g++) {
-      const int kl = half * 32 + g * 8;  // first input of this 16-byte row within the chunk
-      float x[8];
+    for (int g = 0; g < 4; g += 2) {
+      float x[16];
 #pragma unroll
-      for (int e = 0; e < 8; e++) {
-        const int k = c * TC_KC + kl + e;
-        float xv = 0.0f;
-        if (valid && k < NIN) {
-          const int s = k / (NV * M), rem = k - s * (NV * M), v = rem / M, kk = rem - v * M;
-          const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
-          double rv = R[0];
+      for (int h8 = 0; h8 < 2; h8++) {
+        const int G = c * 8 + half * 4 + g + h8;
+        const int sv = G / GPB, kk0 = (G - sv * GPB) * 8, s = sv / NV, v = sv - s * NV;
+        const double* q = sp[0];
+        int qs = sst[0];
 #pragma unroll
-          for (int w = 1; w < NV; w++) rv = (v == w) ? R[w] : rv;
-          xv = (float)(coef<NV, M>(a, ii, jj, i, j, v, kk) * rv);
-        }
-        x[e] = xv;
+        for (int w = 1; w < 5; w++)
+          if (s == w) {
+            q = sp[w];
+            qs = sst[w];
+          }
+        double rv = R[0];
+#pragma unroll
+        for (int w = 1; w < NV; w++) rv = (v == w) ? R[w] : rv;
+        const bool on = valid && G < NG;
+        q += (size_t)(v * M + kk0) * qs;
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[h8 * 8 + e] = (on && kk0 + e < M) ? d2f_rn(q[e * qs] * rv) : 0.0f;
       }
-      uint4 hi, lo;
-      split8(x, hi, lo);
-      const int off = tc_off(TC_ROWS, row, kl);
-      *reinterpret_cast<uint4*>(Ahi + off) = hi;
-      *reinterpret_cast<uint4*>(Alo + off) = lo;
+      // the previous chunk's MMAs have read the A buffer
+      if (c > 0 && g == 0) ok &= mbar_wait(&bar[0], (c - 1) & 1);
+#pragma unroll
+      for (int h8 = 0; h8 < 2; h8++) {
+        uint4 hi, lo;
+        split8(x + 8 * h8, hi, lo);
+        const int off = tc_off(TC_ROWS, row, half * 32 + (g + h8) * 8);
+        *reinterpret_cast<uint4*>(Ahi + off) = hi;
+        *reinterpret_cast<uint4*>(Alo + off) = lo;
+      }
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -384,18 +482,18 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         tc_mma(taddr, TC_DESC(aH + ks * 4096, 2048, 128), db, idesc, (c > 0 || ks > 0) ? 1 : 0);
         tc_mma(taddr, TC_DESC(aL + ks * 4096, 2048, 128), db, idesc, 1);
       }
-      tc_commit(&bar[st]);
+      tc_commit(&bar[0]);
     }
   }
   // the last commit covers every earlier MMA
-  ok &= mbar_wait(&bar[(NC - 1) & 1], ((NC - 1) >> 1) & 1);
+  ok &= mbar_wait(&bar[0], (NC - 1) & 1);
   ok &= mbar_wait(&bar[4], 0);
   tc_fence_after();
   const float* par = reinterpret_cast<const float*>(sm + TC_PAR);  // b1, b2, w3, b3
   const int quarter = warp & 3, ch = warp >> 2;
   const unsigned tl = taddr + ((unsigned)(quarter * 32) << 16);
   float acc[32];
-  // ---- epilogue 1: h1 = GELU(D1 + b1) as the layer-2 A operand (stage 0's buffers) ----
+  // ---- epilogue 1: h1 = GELU(D1 + b1) as the layer-2 A operand (the A buffer) ----
   tmem_ld32(tl + ch * 32, acc);
   {
     unsigned char* Hhi = sm + TC_A;
@@ -433,7 +531,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   float zp = 0.0f;
 #pragma unroll
   for (int e = 0; e < 32; e++) zp = fmaf(gelu(acc[e] + par[H2 + ch * 32 + e]), par[2 * H2 + ch * 32 + e], zp);
-  float* szp = reinterpret_cast<float*>(sm + TC_MX);
+  float* szp = reinterpret_cast<float*>(sm + TC_PZ);
   if (ch == 1) szp[row] = zp;
   tc_fence_before();
   __syncthreads();
@@ -451,8 +549,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 }
 
 template <int NV, int M>
-cudaError_t launch_flags_t(const FeatArgs& fa, const void* wpack, float threshold, DevState* ts,
-                           unsigned char* flags, float* logits, cudaStream_t s) {
+cudaError_t launch_flags_t(const FeatArgs& fa, const void* wpack, unsigned long long* emax, float threshold,
+                           DevState* ts, unsigned char* flags, float* logits, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<NV, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -460,9 +558,11 @@ cudaError_t launch_flags_t(const FeatArgs& fa, const void* wpack, float threshol
     configured = true;
   }
   const long long ntiles = (long long)fa.ms.ntx * fa.ms.ny;
+  const long long nmax = ntiles * NV * 32;
+  k_elem_max<NV, M><<<blocks(nmax, 256), 256, 0, s>>>(fa.U, emax, nmax);
   const long long nblk = (ntiles + 3) / 4;
   k_mlp_tc<NV, M><<<(unsigned)nblk, TC_THREADS, TC_SMEM, s>>>(
-      fa, static_cast<const unsigned char*>(wpack), threshold, ts, flags, logits, ntiles);
+      fa, static_cast<const unsigned char*>(wpack), emax, threshold, ts, flags, logits, ntiles);
   return cudaGetLastError();
 }
 
@@ -516,15 +616,20 @@ cudaError_t launch_features(const double* U, const double* GL, const double* GR,
 }
 
 cudaError_t launch_mlp_flags(const double* U, const double* GL, const double* GR, const double* GB,
-                             const double* GT, const Mesh& ms, int p, int nv, const void* wpack, float threshold,
-                             DevState* ts, unsigned char* flags, float* logits, cudaStream_t s) {
+                             const double* GT, const Mesh& ms, int p, int nv, const void* wpack, void* work,
+                             float threshold, DevState* ts, unsigned char* flags, float* logits, cudaStream_t s) {
   const FeatArgs fa = feat_args(U, GL, GR, GB, GT, ms);
-#define CALL(a, b) launch_flags_t<a, b>(fa, wpack, threshold, ts, flags, logits, s)
+  unsigned long long* emax = static_cast<unsigned long long*>(work);
+#define CALL(a, b) launch_flags_t<a, b>(fa, wpack, emax, threshold, ts, flags, logits, s)
   DG_MLP_DISPATCH(nv, p, CALL);
 #undef CALL
 }
 
-size_t mlp_pack_bytes(int nin) { return (size_t)((nin + TC_KC - 1) / TC_KC) * 8192 + 8192 + 1024; }
+size_t mlp_pack_bytes(int nv, int M) {
+  const int ng = 5 * nv * ((M + 7) / 8);
+  return (size_t)((ng + 7) / 8) * 8192 + 8192 + 1024;
+}
+size_t mlp_work_bytes(const Mesh& ms, int nv) { return (size_t)ms.ntx * ms.ny * nv * 32 * sizeof(unsigned long long); }
 
 namespace {
 unsigned short bf16_bits(float f) {  // round to nearest even, as __float2bfloat16_rn
@@ -546,14 +651,21 @@ void put_bf16(unsigned char* base, int off, float f) {
 }
 }  // namespace
 
-void mlp_pack(const float* prm, int nin, unsigned char* out) {
+void mlp_pack(const float* prm, int nv, int M, unsigned char* out) {
+  const int nin = 5 * nv * M, gpb = (M + 7) / 8, ng = 5 * nv * gpb, nc = (ng + 7) / 8;
   const Offs o = offs(nin);
-  const int nc = (nin + TC_KC - 1) / TC_KC;
-  memset(out, 0, mlp_pack_bytes(nin));
+  memset(out, 0, mlp_pack_bytes(nv, M));
+  // input k' = (sv * gpb + kk / 8) * 8 + kk % 8 of group sv = s * nv + v is
+  // input (s * nv + v) * M + kk of the network (zero for the padding kk >= M)
   for (int c = 0; c < nc; c++)
-    for (int n = 0; n < H; n++)
-      for (int k = 0; k < TC_KC; k++)
-        if (c * TC_KC + k < nin) put_bf16(out + (size_t)c * 8192, tc_off(H, n, k), prm[o.W1 + (size_t)n * nin + c * TC_KC + k]);
+    for (int kc = 0; kc < TC_KC; kc++) {
+      const int kp = c * TC_KC + kc, G = kp / 8;
+      if (G >= ng) continue;
+      const int sv = G / gpb, kk = (G - sv * gpb) * 8 + kp % 8;
+      if (kk >= M) continue;
+      const int in = sv * M + kk;
+      for (int n = 0; n < H; n++) put_bf16(out + (size_t)c * 8192, tc_off(H, n, kc), prm[o.W1 + (size_t)n * nin + in]);
+    }
   unsigned char* w2 = out + (size_t)nc * 8192;
   for (int u = 0; u < H; u++)
     for (int q = 0; q < H; q++) put_bf16(w2, tc_off(H, u, q), prm[o.W2 + u * H + q]);
