@@ -103,15 +103,29 @@ def test_training_lowers_the_loss_on_tvb_labels():
         g.close()
 
 
-def test_fused_inference_matches_reference():
-    cfg, o = ring_state(40, 3, 5, 1)
+@pytest.mark.parametrize("maker,p,bc,ny", [
+    ("shock_ring", 3, 1, 40), ("shock_ring", 1, 1, 35), ("shock_ring", 2, 0, 40), ("shock_ring", 4, 2, 35),
+    ("disc_small", 1, 1, 40), ("disc_small", 3, 3, 35), ("disc_small", 4, 0, 40)])
+def test_fused_inference_matches_reference(maker, p, bc, ny):
+    """The tensor-core pass (features on the fly, BF16 hi + lo activations
+    against BF16 weights, FP32 accumulators) against the FP64 network on the
+    oracle's features: 4 (adiabatic) and 3 (isothermal) variables, every
+    degree, each boundary kind, a row count that leaves the last CTA's four
+    tiles partly empty and ragged 32-element tiles (nx = 40)."""
+    cfg = getattr(inputs, maker)(40, p)
+    cfg["mesh"]["bc"] = bc
+    cfg["mesh"]["ny"] = ny
+    o = oracle.Oracle(cfg)
+    o.step(3)
+    nv = o.fetch().shape[0]
+    nin = 5 * nv * (p + 1) ** 2
     g = dg.Disc(cfg)
-    net = dg.Mlp(320, seed=3)
+    net = dg.Mlp(nin, seed=3)
     try:
         g.set_state(o.fetch(), *o.get_time()[::2])
         g.set_indicator(net, threshold=0.1)
         z, f = g.indicator_logits()
-        zr = ref.forward(net.get_params(), ref.features(o), 320).reshape(z.shape)
+        zr = ref.forward(net.get_params(), ref.features(o), nin).reshape(z.shape)
         assert np.abs(z - zr).max() <= 1e-4 + 1e-4 * np.abs(zr).max()
         sure = np.abs(zr - 0.1) > 1e-3
         np.testing.assert_array_equal(f[sure], (zr[sure] > 0.1).astype(np.uint8))
