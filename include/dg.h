@@ -182,7 +182,10 @@ int dg_torque_series(dg_handle *h, double *out, int cap, int *n);
 int dg_fetch(dg_handle *h, double *coeffs);
 
 /* Replace the modes (canonical host array), the time and the step counter,
-   clear the device status and recompute the CFL step.  Synchronises. */
+   clear the device status and recompute the CFL step.  Synchronises.
+   Page-locked host memory that is mapped into the device's address space
+   (cudaHostAlloc, pinned tensors) is read in place by the conversion kernel;
+   any other host memory is first copied to a device staging buffer. */
 int dg_set_state(dg_handle *h, const double *coeffs, double t, long step);
 
 /* Current time, the time step of the next step, and the step counter. */

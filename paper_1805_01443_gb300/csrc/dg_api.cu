@@ -971,10 +971,20 @@ int dg_set_state(dg_handle* h, const double* coeffs, double t, long step) {
   if (!isfinite(t)) return fail(h, DG_ERR_ARG, "t must be finite");
   const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
   CU(h, cudaStreamSynchronize(h->stream));
-  CU(h, cudaMemcpyAsync(h->S, coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  // page-locked host memory mapped into the device's address space is read in
+  // place by the conversion kernel (the host link is the bound either way;
+  // this hides the layout change and the delta under it); other host memory
+  // is staged by a copy first
+  const double* src = h->S;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, coeffs) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+    src = static_cast<const double*>(at.devicePointer);
+  else
+    CU(h, cudaMemcpyAsync(h->S, coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  cudaGetLastError();  // a pointer query on unregistered memory may leave an error behind
   double* full = h->prec == 1 ? h->Z : h->B[0];
-  CU(h, launch_to_tiled(h->S, full, h->dm, h->nv, h->M, h->stream));
-  if (h->prec == 1) CU(h, launch_delta_from_full(full, h->BG, h->D[0], tiled_count(h), h->stream));
+  CU(h, launch_ingest(src, full, h->prec == 1 ? h->BG : nullptr, h->prec == 1 ? h->D[0] : nullptr, h->dm, h->nv,
+                      h->M, h->stream));
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
   h->cur = h->cur0 = 0;
   h->step0 = step;

@@ -146,6 +146,24 @@ __global__ void k_to_tiled(const double* canon, double* tiled, const Mesh ms, in
   }
 }
 
+// canonical modes (device memory, or mapped page-locked host memory read in
+// place) -> tiled FP64 state and, for the precision form, delta = u - u_b in
+// FP32, in one pass
+__global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ tiled,
+                         const double* __restrict__ bg, float* __restrict__ d, const Mesh ms, int nv, int M) {
+  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ms.nx);
+    const size_t r1 = e / ms.nx;
+    const int j = (int)(r1 % ms.ny);
+    const size_t vk = r1 / ms.ny;
+    const size_t t = (((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31);
+    const double x = canon[e];
+    tiled[t] = x;
+    if (d) d[t] = (float)(x - bg[t]);
+  }
+}
+
 __global__ void k_to_canon(const double* tiled, double* canon, const Mesh ms, int nv, int M) {
   const size_t n = (size_t)nv * M * ms.nx * ms.ny;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -267,6 +285,12 @@ cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStrea
 cudaError_t launch_to_tiled(const double* canon, double* tiled, const Mesh& mesh, int nv, int M,
                             cudaStream_t s) {
   k_to_tiled<<<1216, 256, 0, s>>>(canon, tiled, mesh, nv, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
+                          int nv, int M, cudaStream_t s) {
+  k_ingest<<<1216, 256, 0, s>>>(canon, tiled, bg, d, mesh, nv, M);
   return cudaGetLastError();
 }
 

@@ -166,6 +166,10 @@ cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Ph
 cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
                           double fixed_dt, int advance, int planet32, double r_p, double omega_p,
                           double phi0, cudaStream_t s);
+// canonical modes -> tiled FP64 state (and delta = u - u_b in FP32 when d is
+// set) in one pass; canon may be mapped page-locked host memory
+cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
+                          int nv, int M, cudaStream_t s);
 cudaError_t launch_to_tiled(const double* canon, double* tiled, const Mesh& mesh, int nv, int M,
                             cudaStream_t s);
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
