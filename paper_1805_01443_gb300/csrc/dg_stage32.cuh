@@ -101,6 +101,52 @@ __device__ __forceinline__ void dflux32(const Bg32& b, const float* d, float* fx
   fy[2] = fmaf(d[2], vy, fmaf(b.my, dvy, dp));
 }
 
+// ---- two nodes at once: the lanes of packed FP32x2 instructions ------------
+__device__ __forceinline__ float2 m2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 a2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 d2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 n2(float2 a) { return make_float2(-a.x, -a.y); }
+
+struct Bg32x2 {
+  float2 sig, vx, vy, mx, my, c2;
+};
+__device__ __forceinline__ Bg32x2 bg32_at2(const Prec32& pc, float2 x, float2 y, float2& r2, float2& ir) {
+  Bg32x2 b;
+  r2 = f2(x, x, m2(y, y));
+  ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  const float2 r = m2(r2, ir);
+  const float2 sir = m2(ir, make_float2(rsqrtf(ir.x), rsqrtf(ir.y)));  // r^-1/2
+  float2 sig = sir;
+  if (!pc.slope_half)
+    sig = make_float2(exp2f(pc.slope * __log2f(r.x)), exp2f(pc.slope * __log2f(r.y)));
+  sig = make_float2(fmaxf(sig.x, pc.sig_floor), fmaxf(sig.y, pc.sig_floor));
+  const float2 omA = m2(m2(d2(pc.sqk_out), ir), sir), vkB = m2(r2, d2(pc.irs3));
+  const float2 om = make_float2(r.x >= pc.rs ? omA.x : pc.om_in, r.y >= pc.rs ? omA.y : pc.om_in);
+  const float2 vk2 = make_float2(r.x >= pc.rs ? ir.x : vkB.x, r.y >= pc.rs ? ir.y : vkB.y);
+  b.sig = sig;
+  b.vx = m2(n2(om), y);
+  b.vy = m2(om, x);
+  b.mx = m2(sig, b.vx);
+  b.my = m2(sig, b.vy);
+  b.c2 = m2(d2(pc.h2), vk2);
+  return b;
+}
+__device__ __forceinline__ void dflux32x2(const Bg32x2& b, const float2* d, float2* fx, float2* fy) {
+  const float2 sg = a2(b.sig, d[0]);
+  const float2 is = make_float2(__fdividef(1.0f, sg.x), __fdividef(1.0f, sg.y));
+  const float2 dvx = m2(f2(n2(b.vx), d[0], d[1]), is);
+  const float2 dvy = m2(f2(n2(b.vy), d[0], d[2]), is);
+  const float2 vx = a2(b.vx, dvx), vy = a2(b.vy, dvy);
+  const float2 dp = m2(b.c2, d[0]);
+  fx[0] = d[1];
+  fx[1] = f2(d[1], vx, f2(b.mx, dvx, dp));
+  fx[2] = f2(d[2], vx, m2(b.my, dvx));
+  fy[0] = d[2];
+  fy[1] = f2(d[1], vy, m2(b.mx, dvy));
+  fy[2] = f2(d[2], vy, f2(b.my, dvy, dp));
+}
+
 // LLF flux difference through a face with normal +DIR, with background traces
 // bL, bR on the two sides (equal for the analytic background).
 template <int DIR>
@@ -473,52 +519,62 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   // round-robin over the three threads of an element), then face fluxes ------
   {
     const float pdx0 = fmaf(lanef, pc.dx, sF[0]);
+    // two nodes per iteration, n0 = v + 3 kk and n1 = n0 + 3 (an odd last node
+    // pairs with itself and its second lane is not stored)
+    constexpr int KN = (M + 2) / 3;
 #pragma unroll 1
-    for (int kk = 0; kk < (M + 2) / 3; kk++) {
-      const int n = v + 3 * kk;
-      if (n < M) {
-        const int q = n / m, r = n - q * m;
-        float d[3];
+    for (int kk = 0; kk < KN; kk += 2) {
+      const int n0 = v + 3 * kk;
+      if (n0 >= M) break;  // warp-uniform
+      const bool two = n0 + 3 < M;
+      const int n1 = two ? n0 + 3 : n0;
+      const int q0 = n0 / m, r0 = n0 - q0 * m, q1 = n1 / m, r1 = n1 - q1 * m;
+      float2 d[3];
 #pragma unroll
-        for (int w3 = 0; w3 < 3; w3++) d[w3] = sU[(w3 * M + n) * 32 + lane];
-        const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
-        const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
-        Bg32 bgn = bg32_at(pc, xq, y);
-        if (exact) bgn = bg32_poly<P>(bgOwn, c32t[P].phi[q], c32t[P].phi[r], bgn.c2);
-        float fx[3], fy[3], vx, vy;
-        dflux32(bgn, d, fx, fy, vx, vy);
-        // star: -dSigma grad Phi_*; planet: -Sigma grad Phi_p
-        float src1 = 0.0f, src2 = 0.0f;
-        if (pc.star) {
-          const float r2 = fmaf(xq, xq, y * y);
-          float inv;
-          if (r2 >= pc.rs * pc.rs) {
-            const float irr = rsqrtf(r2);
-            inv = irr * irr * irr;
-          } else {
-            inv = pc.irs3;
-          }
-          src1 = -d[0] * xq * inv;
-          src2 = -d[0] * y * inv;
-        }
-        if (pc.planet) {
-          const float pdx = pdx0 + fmaf(pc.hdx, c32t[P].xi[q], sF[4]);
-          const float pdy = sF[1] + fmaf(pc.hdy, c32t[P].xi[r], sF[5]);
-          const float d2 = fmaf(pdx, pdx, fmaf(pdy, pdy, pc.eps2));
-          const float id = rsqrtf(d2);
-          const float f = pc.q * id * id * id * (bgn.sig + d[0]);
-          src1 = fmaf(-f, pdx, src1);
-          src2 = fmaf(-f, pdy, src2);
-        }
-        float* o = sFl + n * 32 + lane;
-        o[0 * M * 32] = fx[0];
-        o[1 * M * 32] = fx[1];
-        o[2 * M * 32] = fx[2];
-        o[3 * M * 32] = fy[0] * pc.s2y;
-        o[4 * M * 32] = fy[1] * pc.s2y;
-        o[5 * M * 32] = fy[2] * pc.s2y;
-        o[6 * M * 32] = src1;
-        o[7 * M * 32] = src2;
+      for (int w3 = 0; w3 < 3; w3++) d[w3] = make_float2(sU[(w3 * M + n0) * 32 + lane], sU[(w3 * M + n1) * 32 + lane]);
+      const float2 xiq = make_float2(c32t[P].xi[q0], c32t[P].xi[q1]), xir = make_float2(c32t[P].xi[r0], c32t[P].xi[r1]);
+      const float2 xq = f2(d2(pc.hdx), xiq, d2(xcf));
+      const float2 y = f2(d2(pc.hdy), xir, d2(ycf));
+      float2 r2, ir;
+      Bg32x2 bgn = bg32_at2(pc, xq, y, r2, ir);
+      if (exact) {
+        const Bg32 b0 = bg32_poly<P>(bgOwn, c32t[P].phi[q0], c32t[P].phi[r0], bgn.c2.x);
+        const Bg32 b1 = bg32_poly<P>(bgOwn, c32t[P].phi[q1], c32t[P].phi[r1], bgn.c2.y);
+        bgn.sig = make_float2(b0.sig, b1.sig);
+        bgn.vx = make_float2(b0.vx, b1.vx);
+        bgn.vy = make_float2(b0.vy, b1.vy);
+        bgn.mx = make_float2(b0.mx, b1.mx);
+        bgn.my = make_float2(b0.my, b1.my);
+      }
+      float2 fx[3], fy[3];
+      dflux32x2(bgn, d, fx, fy);
+      // star: -dSigma grad Phi_*; planet: -Sigma grad Phi_p
+      float2 src1 = d2(0.0f), src2 = d2(0.0f);
+      if (pc.star) {
+        const float rs2 = pc.rs * pc.rs;
+        const float2 ir3 = m2(m2(ir, ir), ir);
+        const float2 inv = make_float2(r2.x >= rs2 ? ir3.x : pc.irs3, r2.y >= rs2 ? ir3.y : pc.irs3);
+        src1 = m2(m2(n2(d[0]), xq), inv);
+        src2 = m2(m2(n2(d[0]), y), inv);
+      }
+      if (pc.planet) {
+        const float2 pdx = a2(d2(pdx0), f2(d2(pc.hdx), xiq, d2(sF[4])));
+        const float2 pdy = a2(d2(sF[1]), f2(d2(pc.hdy), xir, d2(sF[5])));
+        const float2 dd = f2(pdx, pdx, f2(pdy, pdy, d2(pc.eps2)));
+        const float2 id = make_float2(rsqrtf(dd.x), rsqrtf(dd.y));
+        const float2 f = m2(m2(m2(m2(d2(pc.q), id), id), id), a2(bgn.sig, d[0]));
+        src1 = f2(n2(f), pdx, src1);
+        src2 = f2(n2(f), pdy, src2);
+      }
+      const float2 s2y = d2(pc.s2y);
+      const float2 o2[8] = {fx[0], fx[1], fx[2], m2(fy[0], s2y), m2(fy[1], s2y), m2(fy[2], s2y), src1, src2};
+      float* o0 = sFl + n0 * 32 + lane;
+#pragma unroll
+      for (int t = 0; t < 8; t++) o0[t * M * 32] = o2[t].x;
+      if (two) {
+        float* o1 = sFl + n1 * 32 + lane;
+#pragma unroll
+        for (int t = 0; t < 8; t++) o1[t * M * 32] = o2[t].y;
       }
     }
     // y faces of the element: bottom (below | own) and top (own | above)
