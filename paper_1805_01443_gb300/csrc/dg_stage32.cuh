@@ -83,25 +83,7 @@ __device__ __forceinline__ Bg32 bg32_at(const Prec32& pc, float x, float y) {
   return b;
 }
 
-// flux differences f(u_b + d) - f(u_b) (isothermal, 3 variables)
-__device__ __forceinline__ void dflux32(const Bg32& b, const float* d, float* fx, float* fy,
-                                        float& vx, float& vy) {
-  const float sg = b.sig + d[0];
-  const float is = __fdividef(1.0f, sg);
-  const float dvx = (d[1] - b.vx * d[0]) * is;
-  const float dvy = (d[2] - b.vy * d[0]) * is;
-  vx = b.vx + dvx;
-  vy = b.vy + dvy;
-  const float dp = b.c2 * d[0];
-  fx[0] = d[1];
-  fx[1] = fmaf(d[1], vx, fmaf(b.mx, dvx, dp));
-  fx[2] = fmaf(d[2], vx, b.my * dvx);
-  fy[0] = d[2];
-  fy[1] = fmaf(d[1], vy, b.mx * dvy);
-  fy[2] = fmaf(d[2], vy, fmaf(b.my, dvy, dp));
-}
-
-// ---- two nodes at once: the lanes of packed FP32x2 instructions ------------
+// ---- two evaluations at once: the lanes of packed FP32x2 instructions ------
 __device__ __forceinline__ float2 m2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 a2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -132,12 +114,15 @@ __device__ __forceinline__ Bg32x2 bg32_at2(const Prec32& pc, float2 x, float2 y,
   b.c2 = m2(d2(pc.h2), vk2);
   return b;
 }
-__device__ __forceinline__ void dflux32x2(const Bg32x2& b, const float2* d, float2* fx, float2* fy) {
+// flux differences f(u_b + d) - f(u_b) (isothermal, 3 variables) at two points
+__device__ __forceinline__ void dflux32x2(const Bg32x2& b, const float2* d, float2* fx, float2* fy, float2& vx,
+                                          float2& vy) {
   const float2 sg = a2(b.sig, d[0]);
   const float2 is = make_float2(__fdividef(1.0f, sg.x), __fdividef(1.0f, sg.y));
   const float2 dvx = m2(f2(n2(b.vx), d[0], d[1]), is);
   const float2 dvy = m2(f2(n2(b.vy), d[0], d[2]), is);
-  const float2 vx = a2(b.vx, dvx), vy = a2(b.vy, dvy);
+  vx = a2(b.vx, dvx);
+  vy = a2(b.vy, dvy);
   const float2 dp = m2(b.c2, d[0]);
   fx[0] = d[1];
   fx[1] = f2(d[1], vx, f2(b.mx, dvx, dp));
@@ -148,22 +133,30 @@ __device__ __forceinline__ void dflux32x2(const Bg32x2& b, const float2* d, floa
 }
 
 // LLF flux difference through a face with normal +DIR, with background traces
-// bL, bR on the two sides (equal for the analytic background).
+// bL, bR on the two sides (equal for the analytic background); the flux
+// differences of the two sides are the lanes of one packed pass.
 template <int DIR>
 __device__ __forceinline__ void dllf32(const Bg32& bL, const Bg32& bR, const float* dL,
                                        const float* dR, float* h) {
-  float fxL[3], fyL[3], fxR[3], fyR[3], vxL, vyL, vxR, vyR;
-  dflux32(bL, dL, fxL, fyL, vxL, vyL);
-  dflux32(bR, dR, fxR, fyR, vxR, vyR);
-  const float* fL = DIR == 0 ? fxL : fyL;
-  const float* fR = DIR == 0 ? fxR : fyR;
+  Bg32x2 b;
+  b.sig = make_float2(bL.sig, bR.sig);
+  b.vx = make_float2(bL.vx, bR.vx);
+  b.vy = make_float2(bL.vy, bR.vy);
+  b.mx = make_float2(bL.mx, bR.mx);
+  b.my = make_float2(bL.my, bR.my);
+  b.c2 = make_float2(bL.c2, bR.c2);
+  const float2 d[3] = {make_float2(dL[0], dR[0]), make_float2(dL[1], dR[1]), make_float2(dL[2], dR[2])};
+  float2 fx[3], fy[3], vx, vy;
+  dflux32x2(b, d, fx, fy, vx, vy);
+  const float2* fn = DIR == 0 ? fx : fy;
+  const float2 vn = DIR == 0 ? vx : vy;
   const float c = sqrt_fast(bL.c2);
-  const float al = fmaxf(fabsf(DIR == 0 ? vxL : vyL), fabsf(DIR == 0 ? vxR : vyR)) + c;
+  const float al = fmaxf(fabsf(vn.x), fabsf(vn.y)) + c;
   const float alb = fmaxf(fabsf(DIR == 0 ? bL.vx : bL.vy), fabsf(DIR == 0 ? bR.vx : bR.vy)) + c;
   const float jb[3] = {bR.sig - bL.sig, bR.mx - bL.mx, bR.my - bL.my};
 #pragma unroll
   for (int v = 0; v < 3; v++)
-    h[v] = 0.5f * (fL[v] + fR[v]) - 0.5f * fmaf(al, dR[v] - dL[v], (al - alb) * jb[v]);
+    h[v] = 0.5f * (fn[v].x + fn[v].y) - 0.5f * fmaf(al, dR[v] - dL[v], (al - alb) * jb[v]);
 }
 
 // Exact projected background at a point of one element from its FP32 modes
@@ -546,8 +539,8 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
         bgn.mx = make_float2(b0.mx, b1.mx);
         bgn.my = make_float2(b0.my, b1.my);
       }
-      float2 fx[3], fy[3];
-      dflux32x2(bgn, d, fx, fy);
+      float2 fx[3], fy[3], vxn, vyn;
+      dflux32x2(bgn, d, fx, fy, vxn, vyn);
       // star: -dSigma grad Phi_*; planet: -Sigma grad Phi_p
       float2 src1 = d2(0.0f), src2 = d2(0.0f);
       if (pc.star) {
