@@ -305,7 +305,12 @@ int dg_mlp_train_step(dg_mlp *net, const float *x_dev, const float *y_dev, int B
    of the current state (FP64 form).  Synchronises. */
 int dg_features(dg_handle *h, const int *elems_dev, int n, float *out_dev);
 /* Hand a copy of the network (BF16) to the handle for limiter 2; flags where
-   the logit exceeds threshold.  net = NULL removes it (the TVB test again). */
+   the logit exceeds threshold.  net = NULL removes it (the TVB test again).
+   The handle's inference runs on the tensor cores: activations split into
+   BF16 hi + lo against the BF16 weights, FP32 accumulation (logits within
+   ~1e-6 of an FP32 evaluation); dg_mlp_forward stays FP32 on the CUDA
+   cores.  The weights are packed once here (own device allocation, with
+   scratch of 32 nv bytes per element). */
 int dg_set_indicator(dg_handle *h, const dg_mlp *net, float threshold);
 /* Logits and/or flags ([j][i], host buffers) of the learned indicator on the
    current state.  Synchronises. */
