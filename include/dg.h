@@ -310,7 +310,7 @@ int dg_features(dg_handle *h, const int *elems_dev, int n, float *out_dev);
    BF16 hi + lo against the BF16 weights, FP32 accumulation (logits within
    ~1e-6 of an FP32 evaluation); dg_mlp_forward stays FP32 on the CUDA
    cores.  The weights are packed once here (own device allocation, with
-   scratch of 32 nv bytes per element). */
+   scratch of 8 nv bytes per element). */
 int dg_set_indicator(dg_handle *h, const dg_mlp *net, float threshold);
 /* Logits and/or flags ([j][i], host buffers) of the learned indicator on the
    current state.  Synchronises. */
