@@ -132,11 +132,22 @@ def cpu_baseline_sample(cfg, seconds=15.0):
     t0 = time.perf_counter()
     o.step(nsteps)
     el = time.perf_counter() - t0
-    return {"value": dof * 3 * nsteps / el, "unit": UNIT, "cores": oracle.nthreads(),
+    cores = oracle.nthreads()
+    # the same oracle on one core: one step of the full mesh
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        o.step(1)
+        el1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    return {"value": dof * 3 * nsteps / el, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "%d SSP(3,3) steps (%d stages) of the full %dx%d P%d workload, FP64, "
                       "OpenMP over elements" % (nsteps, 3 * nsteps, cfg["mesh"]["nx"],
-                                                cfg["mesh"]["ny"], cfg["order"])}
+                                                cfg["mesh"]["ny"], cfg["order"]),
+            "one_core": {"value": dof * 3 / el1, "unit": UNIT, "cores": 1,
+                         "sample": "1 SSP(3,3) step (3 stages) of the same workload"}}
 
 
 def run_reference(args, cfg):

@@ -76,6 +76,8 @@ def lib():
         L.ref_rk_linear.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, _DP, _DP]
         L.ref_nthreads.argtypes = []
+        L.ref_set_threads.argtypes = [ctypes.c_int]
+        L.ref_set_threads.restype = None
         _lib = L
     return _lib
 
@@ -119,6 +121,11 @@ def rk_linear(rk, a, b, dt):
 
 def nthreads():
     return lib().ref_nthreads()
+
+
+def set_threads(n):
+    """Threads of the oracle's element loops (results are independent of it)."""
+    lib().ref_set_threads(int(n))
 
 
 def _fill(struct_cls, d):

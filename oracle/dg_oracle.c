@@ -1022,6 +1022,16 @@ int ref_nthreads(void) {
 #endif
 }
 
+/* threads of the element loops (results do not depend on it: every element
+   writes only itself and the reductions are serial) */
+void ref_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int ref_init(ref_state **out, const ref_mesh *mesh, int order, const ref_eos *eos,
              const ref_planet *pl, const ref_disc *disc) {
   if (!out || !mesh || !eos || !pl || !disc) return -1;

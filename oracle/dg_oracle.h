@@ -97,6 +97,7 @@ int  ref_nodal(ref_state *s, double *out);               /* [var][q*m+r][j][i] a
 int  ref_l1_wave(ref_state *s, double t, int var, double *err); /* Sec. 4.1 L1 norm vs exact wave */
 int  ref_ghosts(ref_state *s, double *out);              /* bc 1 ghost coefficients: [side][var][k][n] */
 int  ref_nthreads(void);
+void ref_set_threads(int n);
 /* troubled-cell flags (1 byte per element, [j][i]) of the current state by the
    TVB-modified minmod test with constant M */
 int  ref_indicator(ref_state *s, double M, unsigned char *flags);
