@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -59,6 +60,7 @@ struct dg_handle {
   float* Bmodes;       // u_b modes in FP32 (exact-background tiles)
   float* Disc;         // per-element projected-vs-analytic background discrepancy
   int* TileFlag;
+  int* TileOrder;
   Tables tab;
   double* K[5];           // stage slopes of the 5- and 6-stage Butcher tableaux
   double* W;              // partial sum of their update
@@ -401,7 +403,7 @@ Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec, in
   // and the partial sum of the update
   L.rkx = rk >= 4 ? (size_t)rk_tableau(rk)->s * L.state : 0;
   L.total += L.rkx;
-  if (prec == 1) L.total += L.state + 5 * L.state32 + L.nodes32 + L.db32 + L.bm032 + L.disc32 + L.flags;
+  if (prec == 1) L.total += L.state + 5 * L.state32 + L.nodes32 + L.db32 + L.bm032 + L.disc32 + 2 * L.flags;
   return L;
 }
 
@@ -444,6 +446,7 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
   a.Bm0 = h->Bm0;
   a.Bmodes = h->Bmodes;
   a.TileFlag = h->TileFlag;
+  a.TileOrder = h->TileOrder;
   a.ts = h->ts;
   a.part = h->part;
   a.mesh = h->dm;
@@ -766,6 +769,7 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     h->Bmodes = (float*)take(L.state32);
     h->Disc = (float*)take(L.disc32);
     h->TileFlag = (int*)take(L.flags);
+    h->TileOrder = (int*)take(L.flags);
   }
 
   auto bail = [&](int code) {
@@ -835,6 +839,27 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
       e = launch_bg_nodes(h->BG, h->SigbN, h->Db, h->Bm0, h->Disc, dm, ph, h->tab, order, h->stream);
     if (e == cudaSuccess) e = launch_f64_to_f32(h->BG, h->Bmodes, tiled_count(h), h->stream);
     if (e == cudaSuccess) e = launch_tile_flags(h->Disc, h->TileFlag, dm, 1e-6f, h->stream);
+    if (e == cudaSuccess) {
+      // schedule of the last stage: the tiles whose box touches a damping zone
+      // (they run the damping branch) first, then the others, each in row order
+      std::vector<int> order;
+      order.reserve((size_t)dm.ntx * dm.ny);
+      const double rin2 = h->disc.rdamp_in * h->disc.rdamp_in, rout2 = h->disc.rdamp_out * h->disc.rdamp_out;
+      for (int pass = 0; pass < 2; pass++)
+        for (int j = 0; j < dm.ny; j++)
+          for (int bx = 0; bx < dm.ntx; bx++) {
+            const int nval = std::min(32, dm.nx - bx * 32);
+            const double xlo = dm.x0 + bx * 32 * dm.dx, xhi = xlo + nval * dm.dx;
+            const double ylo = dm.y0 + j * dm.dy, yhi = ylo + dm.dy;
+            const double cx = std::min(std::max(0.0, xlo), xhi), cy = std::min(std::max(0.0, ylo), yhi);
+            const double rmin2 = cx * cx + cy * cy;
+            const double rmax2 = std::max(xlo * xlo, xhi * xhi) + std::max(ylo * ylo, yhi * yhi);
+            const bool zone = (h->disc.rdamp_in > 0.0 && rmin2 < 1.001 * rin2) ||
+                              (h->disc.rdamp_out > 0.0 && rmax2 > 0.999 * rout2);
+            if (zone == (pass == 0)) order.push_back(j * dm.ntx + bx);
+          }
+      e = cudaMemcpy(h->TileOrder, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = launch_delta_from_full(h->B[0], h->BG, h->D[0], tiled_count(h), h->stream);
     if (e != cudaSuccess) {
       fail(h, DG_ERR_CUDA, "precision-form setup: %s", cudaGetErrorString(e));
@@ -886,7 +911,7 @@ int dg_rhs(dg_handle* h, double* out) {
     a.Bm0 = h->Bm0;
     a.Bmodes = h->Bmodes;
     a.TileFlag = h->TileFlag;
-      a.ts = h->ts;
+    a.ts = h->ts;
     a.part = h->part;
     a.mesh = h->dm;
     a.pc = h->pc;
@@ -1534,6 +1559,7 @@ int dg_batch_create(dg_batch** out, dg_handle* const* hs, int n) {
     I.a.Bm0 = h->Bm0;
     I.a.Bmodes = h->Bmodes;
     I.a.TileFlag = h->TileFlag;
+    I.a.TileOrder = nullptr;
     I.a.ts = h->ts;
     I.a.part = h->part;
     I.a.mesh = h->dm;

@@ -113,6 +113,7 @@ struct StageArgs32 {
   const float* Bm0;    // element averages of u_b [tile][3][32] (CFL)
   const float* Bmodes; // u_b modes in FP32 [tile][var][mode][32] (exact-background tiles)
   const int* TileFlag; // 1: the tile uses the exact projected background
+  const int* TileOrder;  // last stage: CTA -> tile (tiles that touch a damping zone first), or null
   DevState* ts;
   double* part;
   Mesh mesh;

@@ -843,7 +843,14 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
 template <int P, bool LAST>
 __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const StageArgs32 a) {
   extern __shared__ double smd[];
-  stage32_tile<P, LAST>(a, a.D, a.Dn, a.Out, a.alpha, a.beta, a.pidx, a.mode, blockIdx.x, blockIdx.y, smd);
+  int bx = blockIdx.x, j = blockIdx.y;
+  if (LAST && a.TileOrder) {
+    // CTAs in an order that keeps the tiles running the damping branch together
+    const int t = a.TileOrder[blockIdx.y * gridDim.x + blockIdx.x];
+    j = t / a.mesh.ntx;
+    bx = t - j * a.mesh.ntx;
+  }
+  stage32_tile<P, LAST>(a, a.D, a.Dn, a.Out, a.alpha, a.beta, a.pidx, a.mode, bx, j, smd);
 }
 
 // Torque on the planet at t^{n+1} from the new state (Sec. 5.1 torque with the
