@@ -1387,7 +1387,7 @@ struct dg_batch {
   cudaEvent_t ev_in, ev_out;
   BatchLaunch32* L;   // host copy of the launch arguments (captured by value)
   int* d_counter;     // work counters of the three stages
-  int* d_items;       // work order
+  int* d_items;       // work order of stages 1-2, then of the last stage (nitems each)
   int policy, dynamic, ctas_per_sm, sms;
   cudaGraphExec_t exec;
   bool graph_ok;
@@ -1438,7 +1438,26 @@ int batch_items(dg_batch* b) {
       for (int t = 0; t < L.tile0[k + 1] - L.tile0[k]; t++) items.push_back((k << 25) | t);
   }
   if ((int)items.size() != L.nitems) return fail(nullptr, DG_ERR_ARG, "batch: work table size");
+  // the last stage: within each instance, its tiles in the handle's last-stage
+  // order (the tiles that run the damping branch first)
+  std::vector<int> last(items.size());
+  {
+    std::vector<std::vector<int>> tord(b->n);
+    for (int k = 0; k < b->n; k++) {
+      tord[k].resize(L.tile0[k + 1] - L.tile0[k]);
+      cudaError_t e = cudaMemcpy(tord[k].data(), b->h[k]->TileOrder, tord[k].size() * sizeof(int),
+                                 cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return fail(nullptr, DG_ERR_CUDA, "batch: %s", cudaGetErrorString(e));
+    }
+    std::vector<int> next(b->n, 0);
+    for (size_t q = 0; q < items.size(); q++) {
+      const int k = items[q] >> 25;
+      last[q] = (k << 25) | tord[k][next[k]++];
+    }
+  }
   cudaError_t e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_items + L.nitems, last.data(), last.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(nullptr, DG_ERR_CUDA, "batch: %s", cudaGetErrorString(e));
   return DG_OK;
 }
@@ -1468,8 +1487,10 @@ cudaError_t batch_enqueue_step(dg_batch* b) {
   for (int st = 0; st < 3 && e == cudaSuccess; st++) {
     L.stage = st;
     L.counter = b->d_counter + st;
+    L.items = b->d_items + (st == 2 ? L.nitems : 0);
     e = launch_batch_stage32(L, batch_grid(b), b->stream);
   }
+  L.items = b->d_items;
   if (e == cudaSuccess) e = launch_batch_torque32(L, b->stream);
   if (e == cudaSuccess) e = launch_batch_finish(L, b->stream);
   return e;
@@ -1588,7 +1609,7 @@ int dg_batch_create(dg_batch** out, dg_handle* const* hs, int n) {
   if (e == cudaSuccess) e = batch_upload_tables32(tabs);
   b->ctas_per_sm = batch_stage32_ctas_per_sm();
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, 3 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, (size_t)L.nitems * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, 2 * (size_t)L.nitems * sizeof(int));
   int rc = e == cudaSuccess ? DG_OK : fail(nullptr, DG_ERR_CUDA, "batch: %s", cudaGetErrorString(e));
   if (!rc && b->ctas_per_sm < 1) rc = fail(nullptr, DG_ERR_CUDA, "batch: stage kernel does not fit an SM");
   if (!rc) {
