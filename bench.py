@@ -43,6 +43,10 @@ BYTES_PER_ELEM_STAGE_FP64 = 1600.0
 # nodes as a float pair (200 B) once per step.
 BYTES_PER_ELEM_STAGE_PREC = 1157.0
 BYTES_PER_ELEM_TORQUE_PREC = 300.0
+# DRAM bytes (read + write) per stage launch of k_stage32<4> at 512^2, the mean
+# over the three stages of one step from one ncu capture of the current kernel
+# (profiles/k_stage32_p4_disc512.md: 215.0, 300.5 and 365.4 MB)
+TRAFFIC_PER_STAGE_PREC = 293.6e6
 # FP64 peak of GB300 derived from unit counts and clock: 2 FP64 FMA / clk / SM
 # x 152 SMs x 2 flop x 2.07 GHz = 1.26 TFLOP/s
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
@@ -370,7 +374,8 @@ def main():
     if args.form == "prec":
         gbs = BYTES_PER_ELEM_STAGE_PREC * n_el / stage_s / 1e9
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": gbs / hbm_peak, "traffic": None,
+                    "frac": gbs / hbm_peak,
+                    "traffic": TRAFFIC_PER_STAGE_PREC if (n_el == 512 * 512 and cfg["order"] == 4) else None,
                     "kernel": "k_stage32<4> (precision-form fused RK stage)",
                     "peak_source": hbm_src, "stage_us": stage_s * 1e6,
                     "algorithmic_bytes_per_element": BYTES_PER_ELEM_STAGE_PREC}
