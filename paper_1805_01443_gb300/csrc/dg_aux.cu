@@ -101,7 +101,7 @@ __global__ void k_cfl(const double* U, DevState* ts, const Mesh ms, const Phys p
       c = ph.h * sqrt(vk2_of(ph, sqrt(xc * xc + yc * yc)));
     }
     dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
-    bad = !(rho > 0.0) || !(dtk > 0.0) || !isfinite(dtk);
+    bad = !(rho > 0.0) || !(dtk > 0.0);  // +inf (no wave speed) is no constraint; NaN fails
     if (bad) dtk = __longlong_as_double((long long)INF_BITS);
   }
   for (int o = 16; o > 0; o >>= 1) {

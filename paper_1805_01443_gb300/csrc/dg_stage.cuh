@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
         c = sqrt(cs2_at<KIND>(ph, xc, yc));
       }
       dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
-      bad = !(rho > 0.0) || !(dtk > 0.0) || !isfinite(dtk);
+      bad = !(rho > 0.0) || !(dtk > 0.0);  // +inf (no wave speed) is no constraint; NaN fails
       if (bad) dtk = __longlong_as_double(0x7ff0000000000000LL);
     }
 #pragma unroll

@@ -60,7 +60,7 @@ __device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrtf(x); }
 
 __device__ __forceinline__ Bg32 bg32_at(const Prec32& pc, float x, float y) {
   Bg32 b;
-  const float r2 = fmaf(x, x, y * y);
+  const float r2 = fmaxf(fmaf(x, x, y * y), 1e-24f);  // r >= 1e-12: a node at the origin
   const float ir = rsqrtf(r2);
   const float r = r2 * ir;
   const float sir = sqrt_fast(ir);  // r^-1/2
@@ -96,6 +96,7 @@ struct Bg32x2 {
 __device__ __forceinline__ Bg32x2 bg32_at2(const Prec32& pc, float2 x, float2 y, float2& r2, float2& ir) {
   Bg32x2 b;
   r2 = f2(x, x, m2(y, y));
+  r2 = make_float2(fmaxf(r2.x, 1e-24f), fmaxf(r2.y, 1e-24f));  // r >= 1e-12: a node at the origin
   ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
   const float2 r = m2(r2, ir);
   const float2 sir = m2(ir, make_float2(rsqrtf(ir.x), rsqrtf(ir.y)));  // r^-1/2
@@ -745,7 +746,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
       const int q = n / m, r = n - q * m;
       const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
       const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
-      const float rr = sqrt_fast(fmaf(xq, xq, y * y));
+      const float rr = sqrt_fast(fmaxf(fmaf(xq, xq, y * y), 1e-24f));
       float R = 0.0f, rd = 0.0f;
       if (pc.rd_in > 0.0f && rr < pc.rd_in) {
         rd = pc.rd_in;
@@ -824,7 +825,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
       const float vy = (b0[2 * 32 + lane] + sB0[2 * 32 + lane]) * irho;
       const float c = sqrtf(bg32_at(pc, xcf, ycf).c2);
       dtf = pc.cfl_fac / ((fabsf(vx) + c) / pc.dx + (fabsf(vy) + c) / pc.dy);
-      bad = !(rho > 0.0f) || !(dtf > 0.0f) || !isfinite(dtf);
+      bad = !(rho > 0.0f) || !(dtf > 0.0f);  // +inf (no wave speed) is no constraint; NaN fails
       if (bad) dtf = __int_as_float(0x7f800000);
     }
 #pragma unroll

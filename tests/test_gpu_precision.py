@@ -38,7 +38,7 @@ def background_sigma(cfg):
     return oracle.Oracle(bg).fetch()[0]
 
 
-@pytest.mark.parametrize("n,p", [(64, 4), (48, 3), (40, 2)])
+@pytest.mark.parametrize("n,p", [(64, 4), (48, 3), (40, 2), (33, 1)])
 def test_precision_operator(n, p):
     cfg = inputs.disc_planet(n, p)
     o = oracle.Oracle(cfg)
@@ -73,6 +73,57 @@ def test_precision_planet_disc_p4_128_vs_oracle():
         assert rel(ug[0] - sb, uo[0] - sb) <= 1e-3
         assert rel(tg, np.array(tq)) <= 1e-6
         assert g.get_time()[2] == 200
+
+
+def strip(p, nx, ny, yc):
+    """The planet disc on a strip of square elements centred at height yc."""
+    cfg = inputs.disc_planet(nx, p, q=3e-5)
+    cfg["mesh"]["ny"] = ny
+    h = 0.5 * 5.0 * ny / nx
+    cfg["mesh"]["y0"], cfg["mesh"]["y1"] = yc - h, yc + h
+    return cfg
+
+
+@pytest.mark.parametrize("p,nx,ny,yc", [(3, 38, 10, 0.0), (4, 70, 6, 0.0), (2, 34, 1, 1.3), (1, 66, 2, -1.0)])
+def test_precision_steps_ragged_meshes(p, nx, ny, yc):
+    """Strips with ragged 32-element tiles (tails of 6, 6, 2 and 2 elements),
+    one or a few rows, damping zones and the planet: 20 steps against the FP64
+    oracle (the last stage's zone-first CTA order, the tail tiles' torque
+    partials and boundary rows that are both bottom and top all take part).
+    Even element counts, as in every configuration of the method: an odd
+    count in both directions centres an element on the star, whose
+    r^-1/2 density cusp then blows the solution up (in the oracle too)."""
+    cfg = strip(p, nx, ny, yc)
+    o = oracle.Oracle(cfg)
+    with dg.Disc(prec_cfg(cfg)) as g:
+        g.set_state(o.fetch())
+        tq = []
+        for _ in range(20):
+            o.step(1)
+            tq.append(o.torque()[0])
+        g.step(20)
+        uo, ug = o.fetch(), g.fetch()
+        assert rel(ug[0], uo[0]) <= 1e-5
+        assert max(rel(ug[1], uo[1]), rel(ug[2], uo[2])) <= 1e-5
+        assert rel(g.torque_series(), np.array(tq)) <= 1e-6
+        assert g.get_time()[2] == 20
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_zero_wave_speed_element_is_no_cfl_constraint(prec):
+    """An element centred on the star (odd counts in both directions) has no
+    sound speed at its centre and no mean velocity: its CFL bound is +inf,
+    which the step minimum ignores, as in the oracle; the time step matches."""
+    cfg = strip(3, 37, 9, 0.0)
+    o = oracle.Oracle(cfg)
+    u = o.fetch()
+    u[1:3, 0, 4, 18] = 0.0  # the element at the origin: no mean momentum (and c_s = 0 at its centre)
+    o.set_state(u)
+    with dg.Disc(dict(cfg, disc=dict(cfg["disc"], prec=prec))) as g:
+        g.set_state(u)
+        dt = g.get_time()[1]
+        assert np.isfinite(dt) and dt > 0.0
+        assert dt == pytest.approx(o.cfl_dt(), rel=1e-12)
 
 
 def test_precision_planet_disc_p4_512_thousand_steps():
