@@ -201,14 +201,16 @@ int dg_set_stream(dg_handle *h, void *stream);
 /* Number of variables (3 or 4) and of modes per variable (m*m) of a handle. */
 int dg_shape(dg_handle *h, int *nv, int *nmodes, int *nx, int *ny);
 
-/* Kernel timing for benchmarks: while enabled, every RK-stage kernel launch of
-   the handle is bracketed by a pair of CUDA events recorded on the handle's
-   stream (no extra synchronisation).  Enabling or disabling synchronises and
-   discards earlier records. */
+/* Kernel timing for benchmarks: while enabled, the RK-stage kernel launches of
+   the handle are bracketed by pairs of CUDA events recorded on the handle's
+   stream (no extra synchronisation): each launch of the FP64 form, the
+   back-to-back stage launches of one step of the precision form.  Enabling
+   or disabling synchronises and discards earlier records. */
 int dg_set_timing(dg_handle *h, int enable);
 
 /* Sum of the recorded stage-kernel durations in milliseconds and the number of
-   recorded launches since the previous call; synchronises and clears the records. */
+   stage launches they cover since the previous call; synchronises and clears
+   the records. */
 int dg_timing(dg_handle *h, double *stage_ms, long long *nstage);
 
 /* Largest input of dg_conserved_static, in elements (nx * ny). */

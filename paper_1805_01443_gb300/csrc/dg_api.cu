@@ -72,6 +72,7 @@ struct dg_handle {
   float ind_thr;          // flag when the logit exceeds this
   int timing;                                   // bracket stage launches with events
   std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
+  std::vector<int>* ev_n;                       // stage launches each pair brackets
   size_t ev_used;
   char err[256];
 };
@@ -234,8 +235,11 @@ cudaError_t record_start(dg_handle* h) {
   return cudaEventRecord(ev[2 * h->ev_used], h->stream);
 }
 
-cudaError_t record_end(dg_handle* h) {
+cudaError_t record_end(dg_handle* h, int nlaunch = 1) {
   cudaError_t r = cudaEventRecord((*h->ev)[2 * h->ev_used + 1], h->stream);
+  if (!h->ev_n) h->ev_n = new std::vector<int>();
+  if (h->ev_n->size() < h->ev_used + 1) h->ev_n->resize(h->ev_used + 1);
+  (*h->ev_n)[h->ev_used] = nlaunch;
   h->ev_used++;
   return r;
 }
@@ -251,18 +255,9 @@ cudaError_t launch_stage32_h(dg_handle* h, const StageArgs32& a) {
 // stage launch, bracketed by a pair of events when timing is on
 cudaError_t launch_stage_h(dg_handle* h, const StageArgs& a) {
   if (!h->timing) return launch_stage_raw(a, h->p, h->stream);
-  if (!h->ev) h->ev = new std::vector<cudaEvent_t>();
-  std::vector<cudaEvent_t>& ev = *h->ev;
-  while (ev.size() < 2 * (h->ev_used + 1)) {
-    cudaEvent_t e;
-    cudaError_t r = cudaEventCreate(&e);
-    if (r != cudaSuccess) return r;
-    ev.push_back(e);
-  }
-  cudaError_t r = cudaEventRecord(ev[2 * h->ev_used], h->stream);
+  cudaError_t r = record_start(h);
   if (r == cudaSuccess) r = launch_stage_raw(a, h->p, h->stream);
-  if (r == cudaSuccess) r = cudaEventRecord(ev[2 * h->ev_used + 1], h->stream);
-  h->ev_used++;
+  if (r == cudaSuccess) r = record_end(h);
   return r;
 }
 
@@ -456,19 +451,23 @@ int do_steps32(dg_handle* h, int n, double fixed_dt) {
     float* un = h->D[h->cur];
     float* nx = h->D[1 - h->cur];
     a.Dn = un;
+    // with timing on, one pair of events brackets the step's back-to-back
+    // stage launches (events between them would add their own gaps)
+    if (h->timing) CU(h, record_start(h));
     if (h->disc.rk == 3) {
       a.D = un; a.Out = nx; a.alpha = 0.0f; a.beta = 1.0f; a.pidx = 0; a.mode = 1;
-      CU(h, launch_stage32_h(h, a));
+      CU(h, launch_stage32_raw(a, h->p, h->stream));
       a.D = nx; a.Out = h->DZ; a.alpha = 0.75f; a.beta = 0.25f; a.pidx = 2; a.mode = 1;
-      CU(h, launch_stage32_h(h, a));
+      CU(h, launch_stage32_raw(a, h->p, h->stream));
       a.D = h->DZ; a.Out = nx; a.alpha = 1.0f / 3.0f; a.beta = 2.0f / 3.0f; a.pidx = 1; a.mode = 2;
-      CU(h, launch_stage32_h(h, a));
+      CU(h, launch_stage32_raw(a, h->p, h->stream));
     } else {
       a.D = un; a.Out = h->DZ; a.alpha = 0.0f; a.beta = 1.0f; a.pidx = 0; a.mode = 1;
-      CU(h, launch_stage32_h(h, a));
+      CU(h, launch_stage32_raw(a, h->p, h->stream));
       a.D = h->DZ; a.Out = nx; a.alpha = 0.5f; a.beta = 0.5f; a.pidx = 2; a.mode = 2;
-      CU(h, launch_stage32_h(h, a));
+      CU(h, launch_stage32_raw(a, h->p, h->stream));
     }
+    if (h->timing) CU(h, record_end(h, h->disc.rk == 3 ? 3 : 2));
     CU(h, launch_torque32_h(h, nx));
     CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, fixed_dt, 1, 1, h->ph.r_p,
                         h->ph.omega_p, h->ph.phi0, h->stream));
@@ -1072,13 +1071,15 @@ int dg_timing(dg_handle* h, double* stage_ms, long long* nstage) {
   if (!h || !stage_ms || !nstage) return fail(h, DG_ERR_ARG, "null argument");
   CU(h, cudaStreamSynchronize(h->stream));
   double tot = 0.0;
+  long long n = 0;
   for (size_t k = 0; k < h->ev_used; k++) {
     float ms = 0.0f;
     CU(h, cudaEventElapsedTime(&ms, (*h->ev)[2 * k], (*h->ev)[2 * k + 1]));
     tot += ms;
+    n += (h->ev_n && k < h->ev_n->size()) ? (*h->ev_n)[k] : 1;
   }
   *stage_ms = tot;
-  *nstage = (long long)h->ev_used;
+  *nstage = n;
   h->ev_used = 0;
   return DG_OK;
 }
@@ -1091,6 +1092,7 @@ int dg_destroy(dg_handle* h) {
     for (cudaEvent_t e : *h->ev) cudaEventDestroy(e);
     delete h->ev;
   }
+  delete h->ev_n;
   if (h->owns) cudaFree(h->ws);
   delete h;
   return DG_OK;

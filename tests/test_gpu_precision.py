@@ -212,3 +212,27 @@ def test_set_state_from_pinned_memory_reads_in_place(prec):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_stage_timing_counts_every_stage_launch(prec):
+    """dg_set_timing / dg_timing: the records cover every stage launch (three
+    per SSP(3,3) step in both forms) and the kernel time is a part of the
+    step time."""
+    cfg = inputs.disc_planet(64, 3)
+    cfg["disc"]["prec"] = prec
+    with dg.Disc(cfg) as g:
+        g.step(1)
+        g.sync()
+        g.set_timing(True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.step(5)
+        b.record()
+        b.synchronize()
+        ms, n = g.timing()
+        g.set_timing(False)
+        assert n == 15
+        assert 0.0 < ms <= a.elapsed_time(b)
+        assert g.timing() == (0.0, 0)
