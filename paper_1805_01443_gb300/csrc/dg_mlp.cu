@@ -14,6 +14,11 @@
 // identity.  Loss: mean over the batch of the weighted binary cross entropy
 // w_y (softplus(z) - y z), w_1 = pos_weight, w_0 = 1.  Optimiser: Adam
 // (beta 0.9, 0.999, eps 1e-8) on the master copy.
+//
+// Training (forward, backward, Adam) runs on the CUDA cores in FP32; the
+// inference inside the limiter (k_mlp_tc) runs its two dense layers on the
+// tensor cores, the activations split into BF16 hi + lo against the BF16
+// weights with FP32 accumulators in tensor memory.
 #include <cuda_bf16.h>
 
 #include <string.h>
@@ -140,7 +145,7 @@ unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-// ---- features and fused inference on the FP64 tiled state -------------------
+// ---- features of the FP64 tiled state -----------------------------------------
 
 namespace {
 
