@@ -21,9 +21,13 @@
 // no shared-memory operand); shared memory only exchanges the nodal values,
 // face traces, pointwise fluxes and face fluxes between the three variable
 // threads of an element.  Pointwise and face work is dealt round-robin over
-// the three threads.  The last stage adds damping in delta form (tiles that
-// touch a zone) and the CFL minimum; the torque of the new state is a
-// separate one-variable pass (k_torque32 below).
+// the three threads.  Independent evaluations that share their operation
+// sequence (two quadrature nodes, the two sides of a face, sums with a common
+// weight) run as the lanes of packed FP32x2 instructions, each lane in its
+// scalar order.  The last stage adds damping in delta form (tiles that touch
+// a zone, scheduled first so that an SM holds CTAs on one code path) and the
+// CFL minimum; the torque of the new state is a separate one-variable pass
+// (k_torque32 below).
 #pragma once
 #include "dg_async.cuh"
 #include "dg_internal.cuh"
