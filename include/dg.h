@@ -188,6 +188,23 @@ int dg_fetch(dg_handle *h, double *coeffs);
    any other host memory is first copied to a device staging buffer. */
 int dg_set_state(dg_handle *h, const double *coeffs, double t, long step);
 
+/* dg_set_state without waiting: queue the replacement of the modes (a
+   canonical array in page-locked host memory), the time and the step counter,
+   and return.  The copy runs on the handle's own copy stream into one of two
+   staging buffers (device memory of the handle, allocated at the first call),
+   so it overlaps the work already queued on the handle's stream (the step
+   before); the conversion, the status reset and the CFL step follow on the
+   handle's stream once the copy has landed.  The host array must stay
+   unchanged until the next synchronising call on the handle.  Errors of the
+   queued work are reported by the next synchronising call.  DG_ERR_ARG for
+   host memory that is not page-locked. */
+int dg_set_state_async(dg_handle *h, const double *coeffs, double t, long step);
+
+/* dg_torque without waiting: queue the copy of the torque of the last step
+   queued before it into *gz (page-locked host memory), valid after the next
+   synchronising call.  DG_ERR_ARG for memory that is not page-locked. */
+int dg_torque_async(dg_handle *h, double *gz);
+
 /* Current time, the time step of the next step, and the step counter. */
 int dg_get_time(dg_handle *h, double *t, double *dt, long *step);
 

@@ -74,6 +74,12 @@ struct dg_handle {
   std::vector<cudaEvent_t>* ev;                 // event pool (start, end pairs)
   std::vector<int>* ev_n;                       // stage launches each pair brackets
   size_t ev_used;
+  // asynchronous state upload: own copy stream, two staging buffers (own
+  // allocations, null until the first dg_set_state_async) and their events
+  cudaStream_t cstream;
+  double* SA[2];
+  cudaEvent_t ev_copied[2], ev_consumed[2];
+  int apar;
   char err[256];
 };
 
@@ -1019,6 +1025,54 @@ int dg_set_state(dg_handle* h, const double* coeffs, double t, long step) {
   return read_state(h, &st);
 }
 
+namespace {
+bool page_locked(const void* p) {
+  cudaPointerAttributes at;
+  const bool ok = cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost;
+  cudaGetLastError();  // a pointer query on unregistered memory may leave an error behind
+  return ok;
+}
+}  // namespace
+
+int dg_set_state_async(dg_handle* h, const double* coeffs, double t, long step) {
+  if (!h || !coeffs) return fail(h, DG_ERR_ARG, "null argument");
+  if (!isfinite(t)) return fail(h, DG_ERR_ARG, "t must be finite");
+  if (!page_locked(coeffs)) return fail(h, DG_ERR_ARG, "dg_set_state_async needs page-locked host memory");
+  const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
+  if (!h->cstream) {
+    CU(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; k++) {
+      CU(h, cudaEventCreateWithFlags(&h->ev_copied[k], cudaEventDisableTiming));
+      CU(h, cudaEventCreateWithFlags(&h->ev_consumed[k], cudaEventDisableTiming));
+      CU(h, cudaMalloc((void**)&h->SA[k], n * sizeof(double)));
+    }
+  }
+  // the copy into this staging buffer waits for the conversion that read it
+  // last; the conversion waits for the copy
+  const int k = h->apar;
+  CU(h, cudaStreamWaitEvent(h->cstream, h->ev_consumed[k], 0));
+  CU(h, cudaMemcpyAsync(h->SA[k], coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->cstream));
+  CU(h, cudaEventRecord(h->ev_copied[k], h->cstream));
+  CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
+  double* full = h->prec == 1 ? h->Z : h->B[0];
+  CU(h, launch_ingest(h->SA[k], full, h->prec == 1 ? h->BG : nullptr, h->prec == 1 ? h->D[0] : nullptr, h->dm,
+                      h->nv, h->M, h->stream));
+  CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
+  CU(h, launch_reset_state(h->ts, t, step, h->stream));
+  h->cur = h->cur0 = 0;
+  h->step0 = step;
+  h->series_read = 0;
+  h->apar = 1 - k;
+  return launch_cfl_and_dt(h, full);
+}
+
+int dg_torque_async(dg_handle* h, double* gz) {
+  if (!h || !gz) return fail(h, DG_ERR_ARG, "null argument");
+  if (!page_locked(gz)) return fail(h, DG_ERR_ARG, "dg_torque_async needs page-locked host memory");
+  CU(h, cudaMemcpyAsync(gz, &h->ts->torque, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return DG_OK;
+}
+
 int dg_get_time(dg_handle* h, double* t, double* dt, long* step) {
   if (!h) return fail(nullptr, DG_ERR_ARG, "null handle");
   DevState st;
@@ -1087,6 +1141,15 @@ int dg_timing(dg_handle* h, double* stage_ms, long long* nstage) {
 int dg_destroy(dg_handle* h) {
   if (!h) return DG_OK;
   cudaStreamSynchronize(h->stream);
+  if (h->cstream) {
+    cudaStreamSynchronize(h->cstream);
+    for (int k = 0; k < 2; k++) {
+      cudaEventDestroy(h->ev_copied[k]);
+      cudaEventDestroy(h->ev_consumed[k]);
+      cudaFree(h->SA[k]);
+    }
+    cudaStreamDestroy(h->cstream);
+  }
   if (h->ind_w) cudaFree(h->ind_w);
   if (h->ev) {
     for (cudaEvent_t e : *h->ev) cudaEventDestroy(e);

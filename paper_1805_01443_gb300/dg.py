@@ -25,6 +25,7 @@ DG_ERR_NOMEM = -6
 
 EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_dt", "dg_sync",
             "dg_rhs", "dg_torque", "dg_torque_series", "dg_fetch", "dg_set_state", "dg_get_time",
+            "dg_set_state_async", "dg_torque_async",
             "dg_conserved", "dg_set_stream", "dg_shape", "dg_destroy", "dg_last_error",
             "dg_set_timing", "dg_timing", "dg_conserved_static", "dg_batch_create",
             "dg_batch_config", "dg_batch_get_config", "dg_batch_tune", "dg_batch_step",
@@ -92,6 +93,8 @@ def lib(build_if_missing=True):
         L.dg_torque_series.argtypes = [_VP, _DP, ctypes.c_int, P(ctypes.c_int)]
         L.dg_fetch.argtypes = [_VP, _DP]
         L.dg_set_state.argtypes = [_VP, _DP, ctypes.c_double, ctypes.c_long]
+        L.dg_set_state_async.argtypes = [_VP, _DP, ctypes.c_double, ctypes.c_long]
+        L.dg_torque_async.argtypes = [_VP, _DP]
         L.dg_get_time.argtypes = [_VP, _DP, _DP, P(ctypes.c_long)]
         L.dg_conserved.argtypes = [_VP, _DP]
         L.dg_set_stream.argtypes = [_VP, _VP]
@@ -201,6 +204,7 @@ class Disc:
             _check(L.dg_init(ctypes.byref(h), ctypes.byref(mesh), order, ctypes.byref(eos),
                              ctypes.byref(planet), ctypes.byref(disc)))
         self.h = h
+        self._keep = []  # host arrays that queued asynchronous copies still read
 
     # -- lifecycle ---------------------------------------------------------
     def close(self):
@@ -208,6 +212,7 @@ class Disc:
             lib().dg_destroy(self.h)
             self.h = None
         self._ws = None
+        self._keep = []
 
     def __del__(self):
         try:
@@ -230,6 +235,24 @@ class Disc:
 
     def sync(self):
         _check(lib().dg_sync(self.h), self.h)
+        self._keep = []
+
+    def set_state_async(self, coeffs, t=0.0, step=0):
+        """dg_set_state_async: `coeffs`, a C-contiguous float64 array of the
+        state's shape in page-locked memory (e.g. a pinned torch tensor's
+        .numpy()), is kept referenced until the next sync()."""
+        if coeffs.size != int(np.prod(self.shape)):
+            raise ValueError("set_state_async: the array must hold the full state")
+        _check(lib().dg_set_state_async(self.h, _ptr(coeffs), t, step), self.h)
+        self._keep.append(coeffs)
+
+    def torque_async(self, out, index=0):
+        """dg_torque_async into out[index] (a float64 array in page-locked
+        memory), valid after the next sync()."""
+        if not (out.dtype == np.float64 and out.flags["C_CONTIGUOUS"] and 0 <= index < out.size):
+            raise ValueError("torque_async: a C-contiguous float64 array and an index inside it")
+        _check(lib().dg_torque_async(self.h, ctypes.cast(out.ctypes.data + 8 * index, _DP)), self.h)
+        self._keep.append(out)
 
     def rhs(self):
         out = np.empty(self.shape)

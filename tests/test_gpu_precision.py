@@ -236,3 +236,41 @@ def test_stage_timing_counts_every_stage_launch(prec):
         assert n == 15
         assert 0.0 < ms <= a.elapsed_time(b)
         assert g.timing() == (0.0, 0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_async_upload_pipeline_matches_synchronous_calls(prec):
+    """dg_set_state_async / dg_torque_async in a pipelined loop (the upload of
+    step k+1 queued while step k runs, each step's torque read without
+    waiting) give the same torques, state and time as dg_set_state, dg_step
+    and dg_torque called in turn, bit for bit; ordinary host memory is
+    refused."""
+    cfg = inputs.disc_planet(64, 3)
+    cfg["disc"]["prec"] = prec
+    with dg.Disc(cfg) as a, dg.Disc(cfg) as b:
+        a.step(2)
+        u = a.fetch()
+        t, _, st = a.get_time()
+        ups = []
+        for k in range(3):
+            pin = torch.empty(u.shape, dtype=torch.float64, pin_memory=True).numpy()
+            pin[...] = u + 1e-8 * k * np.cos(np.arange(u.size)).reshape(u.shape)
+            ups.append(pin)
+        tq = torch.empty(3, dtype=torch.float64, pin_memory=True).numpy()
+        a.set_state_async(ups[0], t, st)
+        for k in range(3):
+            a.step(1)
+            a.torque_async(tq, k)
+            if k + 1 < 3:
+                a.set_state_async(ups[k + 1], t, st)
+        a.sync()
+        ref = []
+        for k in range(3):
+            b.set_state(ups[k].copy(), t, st)
+            b.step(1)
+            ref.append(b.torque())
+        np.testing.assert_array_equal(tq, np.array(ref))
+        np.testing.assert_array_equal(a.fetch(), b.fetch())
+        assert a.get_time() == b.get_time()
+        with pytest.raises(dg.DgError):
+            a.set_state_async(np.zeros(u.shape), t, st)
