@@ -135,17 +135,6 @@ __global__ void k_reset(DevState* ts, double t, long long step) {
   ts->series_count = 0;
 }
 
-__global__ void k_to_tiled(const double* canon, double* tiled, const Mesh ms, int nv, int M) {
-  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % ms.nx);
-    const size_t r1 = e / ms.nx;
-    const int j = (int)(r1 % ms.ny);
-    const size_t vk = r1 / ms.ny;
-    tiled[(((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31)] = canon[e];
-  }
-}
-
 // canonical modes (device memory, or mapped page-locked host memory read in
 // place) -> tiled FP64 state and, for the precision form, delta = u - u_b in
 // FP32, in one pass
@@ -279,12 +268,6 @@ cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double om
 
 cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s) {
   k_reset<<<1, 1, 0, s>>>(ts, t, step);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_to_tiled(const double* canon, double* tiled, const Mesh& mesh, int nv, int M,
-                            cudaStream_t s) {
-  k_to_tiled<<<1216, 256, 0, s>>>(canon, tiled, mesh, nv, M);
   return cudaGetLastError();
 }
 

@@ -171,8 +171,6 @@ cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* 
 // set) in one pass; canon may be mapped page-locked host memory
 cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
                           int nv, int M, cudaStream_t s);
-cudaError_t launch_to_tiled(const double* canon, double* tiled, const Mesh& mesh, int nv, int M,
-                            cudaStream_t s);
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
                             cudaStream_t s);
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,

@@ -241,16 +241,10 @@ __device__ __forceinline__ F2 f2_norm(float s, float e) {  // |e| small against 
   r.l = __fsub_rn(e, __fsub_rn(r.h, s));
   return r;
 }
-__device__ __forceinline__ F2 f2_make(float h, float l) { return f2_norm(h, l); }
 __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
   float s, e;
   two_sum(a.h, b.h, s, e);
   return f2_norm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ F2 f2_addf(F2 a, float b) {
-  float s, e;
-  two_sum(a.h, b, s, e);
-  return f2_norm(s, __fadd_rn(e, a.l));
 }
 __device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {  // exact product of the heads by an FMA
   const float p = __fmul_rn(a.h, b.h);
