@@ -114,6 +114,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, pg, device="cuda"):
+    """The largest of the ranks' values of x (x itself with one rank): the
+    whole job's time is the slowest rank's."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` in `seconds` (the slowest rank's time)."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -208,10 +225,7 @@ def timed_run(dg, torch, cfg, steps, warmup, local, pg):
     stage_ms, nstage = disc.timing()
     disc.set_timing(False)
     disc.sync()
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, pg)
     return disc, ms, stage_ms / max(nstage, 1) / 1e3, clk.summary()
 
 
@@ -339,7 +353,7 @@ def main():
 
     # headline form
     disc, ms, stage_s, clocks = timed_run(dg, torch, head_cfg, args.steps, args.warmup, local, pg)
-    value = world * dof * stages_per_step * args.steps / (ms / 1e3)
+    value = job_rate(world, dof * stages_per_step * args.steps, ms / 1e3)
 
     # end to end through the C ABI with host buffers: every step uploads the
     # state from pinned host memory, advances one step and reads the torque
@@ -365,11 +379,8 @@ def main():
     if not (np.all(np.isfinite(tq)) and np.all(tq == tq[0])):
         raise RuntimeError("end-to-end steps from the same uploaded state disagree")
     disc.close()
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * dof * stages_per_step / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, pg)
+    e2e = {"value": job_rate(world, dof * stages_per_step, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": 8}
 
     def fp64_roofline(stage64):
