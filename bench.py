@@ -315,7 +315,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--err-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--n", type=int, default=512, help="mesh size (profiling cases only)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-disc batched workload")
     ap.add_argument("--no-indicator", action="store_true", help="skip the learned-indicator workload")
