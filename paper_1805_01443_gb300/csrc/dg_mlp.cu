@@ -443,7 +443,9 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     }
 #pragma unroll 1
     for (int g = 0; g < 4; g += 2) {
-      float x[16];
+      // the two groups' 16 coefficients are loaded first (all in flight at
+      // once), then scaled and rounded
+      double cv[16], rv2[2];
 #pragma unroll
       for (int h8 = 0; h8 < 2; h8++) {
         const int G = c * 8 + half * 4 + g + h8;
@@ -459,11 +461,15 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
         double rv = R[0];
 #pragma unroll
         for (int w = 1; w < NV; w++) rv = (v == w) ? R[w] : rv;
+        rv2[h8] = rv;
         const bool on = valid && G < NG;
         q += (size_t)(v * M + kk0) * qs;
 #pragma unroll
-        for (int e = 0; e < 8; e++) x[h8 * 8 + e] = (on && kk0 + e < M) ? d2f_rn(q[e * qs] * rv) : 0.0f;
+        for (int e = 0; e < 8; e++) cv[h8 * 8 + e] = (on && kk0 + e < M) ? q[e * qs] : 0.0;
       }
+      float x[16];
+#pragma unroll
+      for (int t = 0; t < 16; t++) x[t] = d2f_rn(cv[t] * rv2[t >> 3]);
       // the previous chunk's MMAs have read the A buffer
       if (c > 0 && g == 0) ok &= mbar_wait(&bar[0], (c - 1) & 1);
 #pragma unroll
