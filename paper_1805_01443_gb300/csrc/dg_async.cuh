@@ -48,4 +48,31 @@ __device__ __forceinline__ bool mbar_wait(void* bar, unsigned parity) {
   return false;
 }
 
+// ---- programmatic dependent launch (consecutive kernels on one stream) ----
+// Wait until the grid this launch depends on has completed and its writes are
+// visible (an ordinary launch returns at once); called first in a kernel, so
+// nothing of the previous kernel's output is read before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the next launch on the stream start its CTAs (which then wait in
+// pdl_wait) once every CTA of this grid has started.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// host: launch `kern` so that it may start while the previous kernel on the
+// stream drains (the kernel calls pdl_wait before touching its inputs)
+template <typename... Exp, typename... Act>
+static cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Act&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Act&&>(args)...);
+}
+
 }  // namespace dg

@@ -2,6 +2,7 @@
 // layout transforms and conserved sums.
 #include <math.h>
 
+#include "dg_async.cuh"
 #include "dg_finish.cuh"
 #include "dg_internal.cuh"
 #include "dg_physics.cuh"
@@ -121,6 +122,8 @@ __global__ void k_planet32(DevState* ts, double fixed_dt, double r_p, double ome
 __global__ void k_finish(DevState* ts, const double* part, int nparts, double* series,
                          double fixed_dt, int advance, int planet32, double r_p, double omega_p,
                          double phi0) {
+  pdl_wait();
+  pdl_trigger();
   finish_step(ts, part, nparts, series, fixed_dt, advance, planet32, r_p, omega_p, phi0);
 }
 
@@ -222,8 +225,8 @@ cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Ph
 cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
                           double fixed_dt, int advance, int planet32, double r_p, double omega_p,
                           double phi0, cudaStream_t s) {
-  k_finish<<<1, 256, 0, s>>>(ts, part, nparts, series, fixed_dt, advance, planet32, r_p, omega_p, phi0);
-  return cudaGetLastError();
+  return launch_pdl(k_finish, dim3(1), dim3(256), 0, s, ts, part, nparts, series, fixed_dt, advance, planet32,
+                    r_p, omega_p, phi0);
 }
 
 // out = u0 + dt sum_{j<nk} c_j k_j + cx X (dt the step in use)

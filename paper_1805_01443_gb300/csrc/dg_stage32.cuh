@@ -842,6 +842,8 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
 template <int P, bool LAST>
 __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const StageArgs32 a) {
   extern __shared__ double smd[];
+  pdl_wait();
+  pdl_trigger();
   int bx = blockIdx.x, j = blockIdx.y;
   if (LAST && a.TileOrder) {
     // CTAs in an order that keeps the tiles running the damping branch together
@@ -972,6 +974,8 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
 template <int P>
 __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* SigbN, const DevState* ts,
                                                    double* part, const Mesh ms, const Prec32 pc) {
+  pdl_wait();
+  pdl_trigger();
   const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (tile < ms.ntx * ms.ny) torque32_tile<P>(D, SigbN, ts, part, ms, pc, tile);  // warp-uniform
 }
@@ -986,9 +990,7 @@ static cudaError_t launch_stage32_kind(const StageArgs32& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid(a.mesh.ntx, a.mesh.ny);
-  k_stage32<P, LAST><<<grid, 96, bytes, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_stage32<P, LAST>, dim3(a.mesh.ntx, a.mesh.ny), dim3(96), bytes, s, a);
 }
 
 template <int P>
@@ -1000,8 +1002,7 @@ template <int P>
 static cudaError_t launch_torque32_impl(const float* D, const float* SigbN, const DevState* ts, double* part,
                                  const Mesh& ms, const Prec32& pc, cudaStream_t s) {
   const int ntiles = ms.ntx * ms.ny;
-  k_torque32<P><<<(ntiles + 3) / 4, 128, 0, s>>>(D, SigbN, ts, part, ms, pc);
-  return cudaGetLastError();
+  return launch_pdl(k_torque32<P>, dim3((ntiles + 3) / 4), dim3(128), 0, s, D, SigbN, ts, part, ms, pc);
 }
 
 template <int P>
