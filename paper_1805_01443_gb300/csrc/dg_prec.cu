@@ -105,7 +105,11 @@ __global__ void k_bg_nodes(const double* __restrict__ bg, float* __restrict__ si
 
 // A tile takes the exact background when it, or one of its four neighbour
 // tiles, holds an element whose projected background departs from the
-// analytic one by more than `thr` (relative).
+// analytic one by more than `thr` (relative).  Under periodic (bc 0) and
+// copied-element (bc 3) boundaries the tiles along the box edge take it too:
+// the neighbour across the edge is an element elsewhere (or the edge element
+// itself, extended outward), whose background at the shared face is its own
+// projection, not the analytic background at the face point.
 __global__ void k_tile_flags(const float* __restrict__ disc, int* __restrict__ flags, const Mesh ms,
                              float thr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,6 +123,7 @@ __global__ void k_tile_flags(const float* __restrict__ disc, int* __restrict__ f
     const int nval = min(TILE, ms.nx - tx * TILE);
     for (int l = 0; l < nval; l++) f |= disc[((size_t)ty * ms.ntx + tx) * TILE + l] > thr;
   }
+  if ((ms.bc == 0 || ms.bc == 3) && (bx == 0 || bx + 1 == ms.ntx || j == 0 || j + 1 == ms.ny)) f = 1;
   flags[t] = f;
 }
 

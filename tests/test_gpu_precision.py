@@ -38,9 +38,15 @@ def background_sigma(cfg):
     return oracle.Oracle(bg).fetch()[0]
 
 
-@pytest.mark.parametrize("n,p", [(64, 4), (48, 3), (40, 2), (33, 1)])
-def test_precision_operator(n, p):
+@pytest.mark.parametrize("n,p,bc", [(64, 4, 1), (48, 3, 1), (40, 2, 1), (33, 1, 1), (40, 3, 0), (36, 4, 2),
+                                    (40, 2, 3), (34, 4, 0)])
+def test_precision_operator(n, p, bc):
+    """L(u) of the precision form against the oracle for every boundary kind:
+    background ghosts (1), the periodic wrap (0: the neighbour's background
+    is the far edge's), mirrored traces (2) and copied boundary elements (3:
+    the copy's background is at the element's opposite face)."""
     cfg = inputs.disc_planet(n, p)
+    cfg["mesh"]["bc"] = bc
     o = oracle.Oracle(cfg)
     with dg.Disc(prec_cfg(cfg)) as g:
         u0 = o.fetch() + inputs.modal_perturbation(o.shape, seed=4, amp=1e-4)
