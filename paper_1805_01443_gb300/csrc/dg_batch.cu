@@ -63,8 +63,11 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_batch_stage32(const
 }
 
 __global__ void __launch_bounds__(128) k_batch_torque32(const __grid_constant__ BatchLaunch32 L) {
-  const int item = blockIdx.x * 4 + (threadIdx.x >> 5);  // warp-uniform
+  __shared__ float sD[4][2 * MAXM * MAXM * 32];  // per warp: nodal delta Sigma of its tile
+  const int w = threadIdx.x >> 5;
+  const int item = blockIdx.x * 4 + w;  // warp-uniform
   if (item >= L.nitems) return;
+  float* sd = sD[w] + (threadIdx.x & 31);
   const int k = upper_tile0(L, item), tile = item - L.tile0[k];
   const BatchInst32& I = L.inst[k];
   // the new state: the last stage wrote buf[cur ^ 1]; the step counter
@@ -72,10 +75,10 @@ __global__ void __launch_bounds__(128) k_batch_torque32(const __grid_constant__ 
   const int cur = I.cur0 ^ (int)((I.a.ts->step - I.step0) & 1);
   const float* nx = I.buf[cur ^ 1];
   switch (I.p) {
-    case 1: torque32_tile<1>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
-    case 2: torque32_tile<2>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
-    case 3: torque32_tile<3>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
-    default: torque32_tile<4>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
+    case 1: torque32_tile<1>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
+    case 2: torque32_tile<2>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
+    case 3: torque32_tile<3>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
+    default: torque32_tile<4>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
   }
 }
 

@@ -12,8 +12,10 @@
 //   h(uL,uR) - h_b  = (df_L + df_R)/2 - [alpha (dR - dL) + (alpha - alpha_b)(uR_b - uL_b)]/2
 // The background coefficients come from the analytic equilibrium at the point,
 // except in tiles flagged at set-up (the singular centre Sigma ~ r^-1/2 and the
-// solid-body-core edge), where the analytic and projected backgrounds differ
-// and the projected one is contracted from its FP32 modes.
+// solid-body-core edge, where the analytic and projected backgrounds differ;
+// the box edge under periodic or copied-element boundaries, where the
+// neighbour's background is its own projection), where the projected one is
+// contracted from its FP32 modes.
 //
 // Work decomposition: one CTA per 32-element tile of one mesh row, three warps;
 // thread (v, e) owns variable v of element e.  Its m*m modes, nodal values and
@@ -266,6 +268,37 @@ __device__ __forceinline__ F2 f2_rsqrt(F2 d) {
   const F2 t = f2_mul(d, y2);
   const float r = __fsub_rn(__fsub_rn(1.0f, t.h), t.l);  // 1 - t.h exact: t.h within [1/2, 2]
   return f2_norm(y, __fmul_rn(__fmul_rn(0.5f, y), r));
+}
+
+// Unnormalised forms for the torque sums: the result h + l has |l| within a
+// few ulp(h) but is not re-split into head and tail.  Every consumer accepts
+// that: a product reads a tail only through FMAs, and a sum splits the heads
+// exactly and adds the tails.  Each saves the three-instruction
+// renormalisation.
+__device__ __forceinline__ F2 f2_mul_u(F2 a, F2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  return F2{p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
+}
+__device__ __forceinline__ F2 f2_add_u(F2 a, F2 b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return F2{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+// d^{-3/2}, d > 0: from the hardware estimate y of d^{-1/2}, r = 1 - d y^2 is
+// formed in float-float and d^{-3/2} = y^3 (1 - r)^{-3/2}
+// = y^3 (1 + 3r/2 + 15r^2/8 + O(r^3)) by the binomial series.  With |r| ~
+// 2^-22 the truncation is ~2^-63 and the rounding of the correction ~2^-45 of
+// the result; y^3 is formed as an exact-head pair.
+__device__ __forceinline__ F2 f2_rsqrt3_u(F2 d) {
+  const float y = rsqrtf(d.h);
+  const float y2h = __fmul_rn(y, y);
+  const float y2l = fmaf(y, y, -y2h);
+  const F2 t = f2_mul_u(d, F2{y2h, y2l});
+  const float r = __fsub_rn(__fsub_rn(1.0f, t.h), t.l);  // 1 - t.h exact: t.h within [1/2, 2]
+  const float c = __fmul_rn(r, fmaf(1.875f, r, 1.5f));
+  const float p = __fmul_rn(y2h, y);
+  const float e = fmaf(y2l, y, fmaf(y2h, y, -p));
+  return F2{p, fmaf(p, c, e)};
 }
 
 // x0 + k dx - p as a normalised (hi, lo) float pair, from the float pairs of
@@ -862,14 +895,19 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
 // is evaluated and summed in float-float arithmetic (~2^-44 relative): node
 // mass Sigma_b (a float pair from the FP64 background) + delta Sigma, offsets
 // from the planet as float pairs from the FP64 position, the inverse cube by
-// a float-float Newton step.  delta Sigma at the nodes is contracted in FP32
-// (its rounding is ~1e-7 of delta, far below the mass where delta << Sigma_b)
-// and in float-float within sqrt(near2) of the planet, where delta ~ Sigma_b.
-// The per-tile pair is stored as a double; the finish kernel sums the tiles
-// in FP64.
+// one float-float Newton correction.  delta Sigma at the nodes is contracted
+// in FP32 (its rounding is ~1e-7 of delta, far below the mass where delta <<
+// Sigma_b) and in float-float within sqrt(near2) of the planet, where delta ~
+// Sigma_b; it waits in this lane's column of shared memory (sD[n * 32], tail
+// at sD[(M + n) * 32]) so that no contraction operand stays live through the
+// node loop.  The x offset depends on the node row q only and the y offset on
+// the node column r only, so the force sums as sum_q dx_q (sum_r f_qr) and
+// sum_r dy_r (sum_q f_qr).  The per-tile pair is stored as a double; the
+// finish kernel sums the tiles in FP64.
 template <int P>
 __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN, const DevState* ts,
-                                              double* part, const Mesh& ms, const Prec32& pc, int tile) {
+                                              double* part, const Mesh& ms, const Prec32& pc, int tile,
+                                              float* sD) {
   constexpr int m = P + 1, M = m * m, NVM = 3 * M;
   if (ts->status != 0) return;
   const int lane = threadIdx.x & 31;
@@ -886,30 +924,54 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
   ff_offset(i2f(j) + 0.5f, pc.y0p, pc.dyp, p1[2], p1[3], oy.h, oy.l);
   const bool near = valid && fmaf(ox.h, ox.h, oy.h * oy.h) < pc.near2;
   const bool ffw = __any_sync(0xffffffffu, near);  // float-float delta contraction in this warp
-  // T[a][r] = sum_b c_ab phi_b(eta_r) (head, and tail in a float-float warp)
-  float Th[m][m], Tl[m][m];
+  float* sDl = sD + M * 32;
   {
+    // T[a][r] = sum_b c_ab phi_b(eta_r), then delta Sigma(q, r) = sum_a phi_a(xi_q) T[a][r]
     float c[M];
 #pragma unroll
     for (int k = 0; k < M; k++) c[k] = dsig[k * 32];
+    if (ffw) {
+      F2 T[m][m];
 #pragma unroll
-    for (int aa = 0; aa < m; aa++)
+      for (int aa = 0; aa < m; aa++)
 #pragma unroll
-      for (int r = 0; r < m; r++) {
-        if (ffw) {
+        for (int r = 0; r < m; r++) {
           F2 acc{0.0f, 0.0f};
 #pragma unroll
           for (int b = 0; b < m; b++) acc = f2_add(acc, f2_mulf(F2{c32t[P].phi[r][b], c32t[P].phil[r][b]}, c[aa * m + b]));
-          Th[aa][r] = acc.h;
-          Tl[aa][r] = acc.l;
-        } else {
+          T[aa][r] = acc;
+        }
+#pragma unroll
+      for (int q = 0; q < m; q++)
+#pragma unroll
+        for (int r = 0; r < m; r++) {
+          F2 ds{0.0f, 0.0f};
+#pragma unroll
+          for (int aa = 0; aa < m; aa++) ds = f2_add(ds, f2_mul(F2{c32t[P].phi[q][aa], c32t[P].phil[q][aa]}, T[aa][r]));
+          sD[(q * m + r) * 32] = ds.h;
+          sDl[(q * m + r) * 32] = ds.l;
+        }
+    } else {
+      float T[m][m];
+#pragma unroll
+      for (int aa = 0; aa < m; aa++)
+#pragma unroll
+        for (int r = 0; r < m; r++) {
           float acc = 0.0f;
 #pragma unroll
           for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32t[P].phi[r][b], acc);
-          Th[aa][r] = acc;
-          Tl[aa][r] = 0.0f;
+          T[aa][r] = acc;
         }
-      }
+#pragma unroll
+      for (int q = 0; q < m; q++)
+#pragma unroll
+        for (int r = 0; r < m; r++) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], T[aa][r], acc);
+          sD[(q * m + r) * 32] = acc;
+        }
+    }
   }
   const F2 hdx{0.5f * pc.dxp[0], 0.5f * pc.dxp[1]}, hdy{0.5f * pc.dyp[0], 0.5f * pc.dyp[1]};
   const F2 eps2{pc.eps2p[0], pc.eps2p[1]};
@@ -922,6 +984,9 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
   }
   F2 gx{0.0f, 0.0f}, gy{0.0f, 0.0f};
   if (valid) {
+    F2 C[m];  // column sums sum_q f_qr
+#pragma unroll
+    for (int r = 0; r < m; r++) C[r] = F2{0.0f, 0.0f};
     // one node row q per iteration (rolled: the float-float body is long)
 #pragma unroll 1
     for (int q = 0; q < m; q++) {
@@ -932,30 +997,22 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
         sl[r] = sbl[(q * m + r) * 32];
       }
       const F2 px = f2_add(ox, f2_mul(hdx, F2{c32t[P].xi[q], c32t[P].xil[q]}));
-      const F2 px2 = f2_mul(px, px);
+      const F2 px2 = f2_mul_u(px, px);
+      F2 S{0.0f, 0.0f};  // row sum sum_r f_qr
 #pragma unroll
       for (int r = 0; r < m; r++) {
-        // delta Sigma at node (q, r)
-        F2 ds{0.0f, 0.0f};
-        if (ffw) {
-#pragma unroll
-          for (int aa = 0; aa < m; aa++)
-            ds = f2_add(ds, f2_mul(F2{c32t[P].phi[q][aa], c32t[P].phil[q][aa]}, F2{Th[aa][r], Tl[aa][r]}));
-        } else {
-          float acc = 0.0f;
-#pragma unroll
-          for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], Th[aa][r], acc);
-          ds.h = acc;
-        }
-        // w_n (Sigma_b + delta Sigma) / (d^2 + eps^2)^{3/2}
         const int n = q * m + r;
-        const F2 mass = f2_mul(f2_add(F2{sh[r], sl[r]}, ds), F2{c32t[P].w2h[n], c32t[P].w2l[n]});
-        const F2 id = f2_rsqrt(f2_add(px2, pye[r]));
-        const F2 f = f2_mul(mass, f2_mul(f2_mul(id, id), id));
-        gx = f2_add(gx, f2_mul(f, px));
-        gy = f2_add(gy, f2_mul(f, py[r]));
+        const F2 ds{sD[n * 32], ffw ? sDl[n * 32] : 0.0f};
+        // w_n (Sigma_b + delta Sigma) / (d^2 + eps^2)^{3/2}
+        const F2 mass = f2_mul_u(f2_add_u(F2{sh[r], sl[r]}, ds), F2{c32t[P].w2h[n], c32t[P].w2l[n]});
+        const F2 f = f2_mul_u(mass, f2_rsqrt3_u(f2_add_u(px2, pye[r])));
+        S = r ? f2_add_u(S, f) : f;
+        C[r] = f2_add_u(C[r], f);
       }
+      gx = f2_add_u(gx, f2_mul_u(S, px));
     }
+#pragma unroll
+    for (int r = 0; r < m; r++) gy = f2_add_u(gy, f2_mul_u(C[r], py[r]));
   }
   // warp sum of the pairs
 #pragma unroll
@@ -970,14 +1027,18 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
   }
 }
 
-// four tiles (warps) per CTA
+// four tiles (warps) per CTA; each lane keeps its element's nodal delta Sigma
+// (head and tail) in shared memory
 template <int P>
 __global__ void __launch_bounds__(128) k_torque32(const float* D, const float* SigbN, const DevState* ts,
                                                    double* part, const Mesh ms, const Prec32 pc) {
+  constexpr int M = (P + 1) * (P + 1);
+  __shared__ float sD[4][2 * M * 32];
   pdl_wait();
   pdl_trigger();
-  const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (tile < ms.ntx * ms.ny) torque32_tile<P>(D, SigbN, ts, part, ms, pc, tile);  // warp-uniform
+  const int w = threadIdx.x >> 5;
+  const int tile = blockIdx.x * 4 + w;
+  if (tile < ms.ntx * ms.ny) torque32_tile<P>(D, SigbN, ts, part, ms, pc, tile, sD[w] + (threadIdx.x & 31));  // warp-uniform
 }
 
 template <int P, bool LAST>
