@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_batch_stage32(const
   }
 }
 
-__global__ void __launch_bounds__(128) k_batch_torque32(const __grid_constant__ BatchLaunch32 L) {
+__global__ void __launch_bounds__(128, 7) k_batch_torque32(const __grid_constant__ BatchLaunch32 L) {
   __shared__ float sD[4][2 * MAXM * MAXM * 32];  // per warp: nodal delta Sigma of its tile
   const int w = threadIdx.x >> 5;
   const int item = blockIdx.x * 4 + w;  // warp-uniform

@@ -1030,7 +1030,7 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
 // four tiles (warps) per CTA; each lane keeps its element's nodal delta Sigma
 // (head and tail) in shared memory
 template <int P>
-__global__ void __launch_bounds__(128) k_torque32(const float* D, const float* SigbN, const DevState* ts,
+__global__ void __launch_bounds__(128, 7) k_torque32(const float* D, const float* SigbN, const DevState* ts,
                                                    double* part, const Mesh ms, const Prec32 pc) {
   constexpr int M = (P + 1) * (P + 1);
   __shared__ float sD[4][2 * M * 32];
