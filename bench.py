@@ -4,14 +4,16 @@ zones r < 0.4 and r > 2.1, SSP(3,3), torque on the planet every step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-One timed step = one full RK step of the hot path (3 fused stage kernels +
-the finish kernel: damping, torque, CFL) on device-resident inputs.  The state
+One timed step = one full RK step of the hot path (3 fused stage kernels, the
+last with damping and CFL, then the torque pass and the finish kernel) on
+device-resident inputs.  The state
 buffers (157 MB each, 3 of them) are larger than the 129 MB L2, so no flush is
 needed between steps.  DOF = nx * ny * (p+1)^2 per stage (Sec. 3.1).
 For N > 1 (torchrun) every rank advances an independent replica (no data-path
 collective); value = DOF-updates of all ranks / max-over-ranks time.
 `--impl reference` times the FP64 CPU oracle (the reference arm of this
-project) on this host's cores.
+project) on this host's cores: K steps of the full mesh, or of the same disc on
+a coarser mesh where K full steps would take more than two minutes.
 """
 import argparse
 import json
@@ -171,15 +173,42 @@ def cpu_baseline_sample(cfg, seconds=15.0):
                          "sample": "1 SSP(3,3) step (3 stages) of the same workload"}}
 
 
-def run_reference(args, cfg):
+def reference_sample(cfg, steps, t_step, budget_s=120.0):
+    """The workload the reference arm times: the full mesh while `steps` steps
+    of it fit in `budget_s` (one step took `t_step` s), otherwise the same disc
+    on a coarser mesh, the element count scaled to fit (even sides, at least
+    64 unless the mesh is smaller), so that the run stays within a few
+    minutes; returns (cfg, note)."""
+    import copy
+
+    n = cfg["mesh"]["nx"]
+    if steps * t_step <= budget_s:
+        return cfg, "the full %dx%d mesh" % (n, cfg["mesh"]["ny"])
+    frac = budget_s / (steps * t_step)
+    ns = max(int(n * frac ** 0.5) // 2 * 2, min(n, 64))
+    if ns >= n:
+        return cfg, "the full %dx%d mesh" % (n, cfg["mesh"]["ny"])
+    small = copy.deepcopy(cfg)
+    small["mesh"]["nx"] = small["mesh"]["ny"] = ns
+    return small, "the same disc on a %dx%d mesh (the full %dx%d mesh would take %.0f s)" % (
+        ns, ns, n, cfg["mesh"]["ny"], steps * t_step)
+
+
+def run_reference(args, cfg, budget_s=120.0):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
 
     o = oracle.Oracle(cfg)
-    n_el = cfg["mesh"]["nx"] * cfg["mesh"]["ny"]
-    dof = n_el * (cfg["order"] + 1) ** 2
+    t0 = time.perf_counter()
+    o.step(1)
+    t_step = time.perf_counter() - t0
+    cfg_s, note = reference_sample(cfg, args.steps, t_step, budget_s)
+    if cfg_s is not cfg:
+        o = oracle.Oracle(cfg_s)
+    n_el = cfg_s["mesh"]["nx"] * cfg_s["mesh"]["ny"]
+    dof = n_el * (cfg_s["order"] + 1) ** 2
     o.step(max(args.warmup, 0))
     t0 = time.perf_counter()
     o.step(args.steps)
@@ -191,8 +220,7 @@ def run_reference(args, cfg):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.nthreads(), "kind": "oracle",
-                         "sample": "%d SSP(3,3) steps of the full workload per timed run"
-                                   % args.steps},
+                         "sample": "%d SSP(3,3) steps per timed run, each over %s" % (args.steps, note)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

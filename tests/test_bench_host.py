@@ -1,0 +1,86 @@
+"""The host-side arms of bench.py on CPU: the reference arm's JSON line and
+its bounded sample, and the oracle baseline that rides on the GPU line."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_1805_01443_gb300 import inputs  # noqa: E402
+
+
+class Args:
+    steps = 2
+    warmup = 1
+
+
+def test_reference_sample_keeps_the_full_mesh_when_it_fits():
+    import bench
+    cfg = inputs.disc_planet_512()
+    got, note = bench.reference_sample(cfg, 100, 0.5)
+    assert got is cfg
+    assert "512x512" in note
+
+
+def test_reference_sample_shrinks_to_the_budget():
+    import bench
+    cfg = inputs.disc_planet_512()
+    got, note = bench.reference_sample(cfg, 1000, 0.5)  # 500 s of full steps against 120 s
+    assert got is not cfg and cfg["mesh"]["nx"] == 512  # the caller's configuration stays
+    n = got["mesh"]["nx"]
+    assert n == got["mesh"]["ny"] and n % 2 == 0
+    assert (n / 512) ** 2 * 500 <= 120 < ((n + 2) / 512) ** 2 * 500
+    assert got["order"] == cfg["order"] and got["mesh"]["x0"] == cfg["mesh"]["x0"]
+    assert "%dx%d" % (n, n) in note
+
+
+def test_reference_sample_never_grows_a_small_mesh():
+    import bench
+    cfg = inputs.disc_planet(16, 2)
+    got, _ = bench.reference_sample(cfg, 10 ** 6, 1.0)
+    assert got is cfg
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    cfg = inputs.disc_planet(16, 2)
+    assert bench.run_reference(Args(), cfg) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"]
+    assert line["steps"] == 2 and line["value"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert "16x16" in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_takes_the_coarse_sample_over_budget(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    cfg = inputs.disc_planet(80, 1)
+    assert bench.run_reference(Args(), cfg, budget_s=0.0) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert "64x64" in line["cpu_baseline"]["sample"] and line["value"] > 0
+
+
+def test_cpu_baseline_sample_fields():
+    import bench
+    import oracle
+    cfg = inputs.disc_planet(16, 2)
+    cb = bench.cpu_baseline_sample(cfg, seconds=0.05)
+    assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT and cb["value"] > 0
+    assert cb["cores"] == oracle.nthreads()
+    assert cb["one_core"]["cores"] == 1 and cb["one_core"]["value"] > 0
+    assert oracle.nthreads() == cb["cores"]  # the thread count is restored
+    assert "16x16" in cb["sample"]
