@@ -4,8 +4,10 @@ Each test checks the oracle against something other than itself: closed forms
 (Gauss-Legendre tables, Legendre polynomials, spherical-Bessel projections,
 RK stability polynomials), published generator vectors, invariants (constant
 states, conservation, mirror symmetry), exact weak forms of polynomial states
-computed here with numpy quadrature, and measured convergence order p+1
-(Sec. 4.1).  None of these tests needs a GPU.
+computed here with numpy quadrature, measured convergence order p+1
+(Sec. 4.1), and every outer boundary kind against the same operator on a
+wider mesh that holds its ghost elements explicitly.  None of these tests
+needs a GPU.
 """
 import math
 
@@ -454,3 +456,90 @@ def test_isentropic_vortex_translates_exactly():
             o.step_dt(1, min(dt, T - t))
         errs.append(measures.vortex_l1_density(o.fetch(), cfg, T))
     assert np.log2(errs[0] / errs[1]) >= 1.5
+
+
+# ----------------------------------------------------------------------------
+# outer boundaries: a ghost element is an explicit element
+#
+# L of an element reads only its own coefficients and its four face
+# neighbours' (the flux is local per face node, Eq. 2 with the LLF flux).  So
+# L on a mesh with boundary kind bc must equal, on its elements, L on the mesh
+# one element wider on every side whose outer ring holds the ghost elements
+# explicitly: the far edge's element (bc 0), the boundary element reflected in
+# the face normal (bc 2: its trace at the shared face is the element's own),
+# the boundary element itself (bc 3), or the projected background there (bc 1).
+# The wider mesh keeps every inner element at the same physical position, so
+# the star and planet gravity and the local sound speed see the same points.
+
+
+def _wider(cfg):
+    w = {k: (dict(v) if isinstance(v, dict) else v) for k, v in cfg.items()}
+    mesh = cfg["mesh"]
+    dx = (mesh["x1"] - mesh["x0"]) / mesh["nx"]
+    dy = (mesh["y1"] - mesh["y0"]) / mesh["ny"]
+    w["mesh"].update({"nx": mesh["nx"] + 2, "ny": mesh["ny"] + 2, "x0": mesh["x0"] - dx,
+                      "x1": mesh["x1"] + dx, "y0": mesh["y0"] - dy, "y1": mesh["y1"] + dy, "bc": 1})
+    return w
+
+
+def _reflect(c, p, axis):
+    """An element polynomial reflected in x (axis 0) or y (axis 1): the Legendre
+    mode of degree d changes sign with (-1)^d; modes are [..., a*m + b, ...]."""
+    m = p + 1
+    a, b = np.divmod(np.arange(m * m), m)
+    sign = (-1.0) ** (a if axis == 0 else b)
+    return c * sign[None, :, None]
+
+
+@pytest.mark.parametrize("bc", [0, 1, 2, 3])
+def test_boundary_kinds_equal_an_explicit_ghost_ring(bc):
+    p = 3
+    cfg = inputs.disc_planet(12, p, q=1e-4)
+    cfg["mesh"]["bc"] = bc
+    o = oracle.Oracle(cfg)
+    u = o.fetch() + inputs.modal_perturbation(o.shape, seed=11, amp=1e-2)
+    o.set_state(u)
+    L = o.rhs()
+    nv, M, ny, nx = o.shape
+
+    W = np.empty((nv, M, ny + 2, nx + 2))
+    W[:, :, 1:-1, 1:-1] = u
+    if bc == 0:
+        left, right, bottom, top = u[:, :, :, -1], u[:, :, :, 0], u[:, :, -1, :], u[:, :, 0, :]
+    elif bc == 3:
+        left, right, bottom, top = u[:, :, :, 0], u[:, :, :, -1], u[:, :, 0, :], u[:, :, -1, :]
+    elif bc == 2:
+        left, right = _reflect(u[:, :, :, 0], p, 0), _reflect(u[:, :, :, -1], p, 0)
+        bottom, top = _reflect(u[:, :, 0, :], p, 1), _reflect(u[:, :, -1, :], p, 1)
+    else:
+        left, right, bottom, top = o.ghosts()
+    W[:, :, 1:-1, 0], W[:, :, 1:-1, -1] = left, right
+    W[:, :, 0, 1:-1], W[:, :, -1, 1:-1] = bottom, top
+    for jj, ii in ((0, 0), (0, -1), (-1, 0), (-1, -1)):  # corners: read by no inner element
+        W[:, :, jj, ii] = W[:, :, jj, 1 if ii == 0 else -2]
+    ow = oracle.Oracle(_wider(cfg))
+    ow.set_state(W)
+    Lw = ow.rhs()[:, :, 1:-1, 1:-1]
+    for v in range(nv):
+        scale = np.abs(L[v]).max()
+        assert np.abs(Lw[v] - L[v]).max() <= 1e-9 * scale, (bc, v)
+    # the boundary elements do see their ghosts: a different ring changes them
+    W2 = W.copy()
+    W2[:, 1:, 1:-1, 0] *= 1.5
+    ow.set_state(W2)
+    assert np.abs(ow.rhs()[:, :, 1:-1, 1] - L[:, :, :, 0]).max() > 1e-6 * np.abs(L).max()
+
+
+def test_background_ghosts_are_the_projected_background_there():
+    """bc 1: the ghost ring holds the background projected onto the elements
+    just outside the mesh, as the wider mesh's own noise-free initial state
+    does there."""
+    cfg = inputs.disc_planet(12, 3, q=1e-4)
+    cfg["mesh"]["bc"] = 1
+    left, right, bottom, top = oracle.Oracle(cfg).ghosts()
+    w = _wider(cfg)
+    w["disc"]["noise_amp"] = 0.0
+    B = oracle.Oracle(w).fetch()
+    for got, ref in ((left, B[:, :, 1:-1, 0]), (right, B[:, :, 1:-1, -1]),
+                     (bottom, B[:, :, 0, 1:-1]), (top, B[:, :, -1, 1:-1])):
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
