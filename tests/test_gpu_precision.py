@@ -155,6 +155,29 @@ def test_precision_planet_disc_p4_512_thousand_steps():
     assert e_tq <= 1e-6
 
 
+def test_precision_planet_disc_p4_512_full_size_step_vs_oracle():
+    """The benchmark's workload and launch configuration (P4 512x512, q = 3e-5,
+    precision form), one SSP(3,3) step at the oracle's CFL step, against the
+    oracle directly: the whole state within the form's bounds, every element's
+    density mean within 1e-7 of the largest one, and the torque within 1e-6."""
+    cfg = inputs.disc_planet_512()
+    o = oracle.Oracle(cfg)
+    dt = o.cfl_dt()
+    with dg.Disc(prec_cfg(cfg)) as g:
+        u0 = o.fetch()
+        g.set_state(u0)
+        o.step_dt(1, dt)
+        g.step_dt(1, dt)
+        uo, ug = o.fetch(), g.fetch()
+        tg = g.torque()
+    to = o.torque()[0]
+    assert rel(ug[0], uo[0]) <= 1e-5
+    assert max(rel(ug[1], uo[1]), rel(ug[2], uo[2])) <= 1e-5
+    assert rel(ug[0] - u0[0], uo[0] - u0[0]) <= 1e-3
+    assert np.abs(ug[0, 0] - uo[0, 0]).max() <= 1e-7 * np.abs(uo[0, 0]).max()
+    assert abs(tg - to) <= 1e-6 * abs(to)
+
+
 @pytest.mark.parametrize("n,p,q", [(128, 4, 3e-5), (96, 3, 1e-4), (64, 2, 1e-3), (40, 1, 1e-3)])
 def test_precision_torque_same_state(n, p, q):
     """The torque kernel alone: the precision form's torque of its own state
