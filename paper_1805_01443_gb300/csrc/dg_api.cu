@@ -543,7 +543,7 @@ int do_steps_butcher(dg_handle* h, int n, double fixed_dt) {
 cudaError_t limit_state(dg_handle* h, double* U, const unsigned char* given) {
   if (!given && h->ph.limiter == 2 && h->ind_w) {
     // the learned indicator flags the stage value; the TVB test still runs
-    // beside it (its flags are the judge, dg_last_flags)
+    // beside it (its flags are the reference, dg_last_flags)
     cudaError_t e = launch_mlp_flags(U, h->GL, h->GR, h->GB, h->GT, h->dm, h->p, h->nv, h->ind_w,
                                      h->ind_w + h->ind_work, h->ind_thr, h->ts, h->gflags, nullptr, h->stream);
     if (e != cudaSuccess) return e;

@@ -1,6 +1,6 @@
 """The learned troubled-cell indicator, end to end: labels from the TVB test on
 the method's own runs, training on the GPU with libdg's kernels, and the
-measures that judge it against the TVB test it stands in for.
+measures that compare it with the TVB test it stands in for.
 
 Labels.  A TVB-limited run (limiter 1, positivity) of the disc is sampled
 every few steps; each sampled state takes one step without troubled-cell
