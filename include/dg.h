@@ -131,7 +131,7 @@ typedef struct {
                          no network is set */
   double tvb_m;       /* TVB constant M (|slope| <= M h^2 is never limited); 0: minmod */
   int positivity;     /* 1: Zhang-Shu positivity limiter after every stage
-                         (Sec. 2.3; density, and pressure for the adiabatic
+                         (Sec. 2.4; density, and pressure for the adiabatic
                          EOS, >= 1e-13 at the volume and face quadrature points),
                          with the time-step factor min(1/(2p+1), w_1/2) */
   double ring_r, ring_p; /* ic 3 ring radius and pressure factor */
@@ -266,7 +266,7 @@ int dg_conserved_static(const double *coeffs, int nv, int nmodes, int nx, int ny
 
 /* ---- Troubled cells and limiters (FP64 form; DG_ERR_UNSUPPORTED otherwise) --
    The TVB-modified minmod test of Cockburn & Shu, the limited-P1 reduction of
-   troubled elements and the positivity limiter of Sec. 2.3 (Zhang & Shu), as
+   troubled elements and the positivity limiter of Sec. 2.4 (Zhang & Shu), as
    dg_disc.limiter / tvb_m / positivity describe them.  Flags are one byte per
    element, 1 = troubled, layout [j][i] (nx*ny bytes, caller-owned host
    buffers).  All four synchronise. */
@@ -288,7 +288,7 @@ int dg_last_flags(dg_handle *h, unsigned char *flags);
 
 /* ---- Learned troubled-cell indicator ----------------------------------------
    No counterpart in the paper (its only limiter is the positivity limiter of
-   Sec. 2.3): a multilayer perceptron nin -> 64 (GELU) -> 64 (GELU) -> 1 logit
+   Sec. 2.4): a multilayer perceptron nin -> 64 (GELU) -> 64 (GELU) -> 1 logit
    that stands in for the TVB test as the limiter's flagging step
    (dg_disc.limiter = 2), trained on the TVB test's own flags (dg_last_flags).
    BF16 weights (round to nearest even of an FP32 master copy), FP32

@@ -626,7 +626,7 @@ static void rhs_eval(void *vctx, double t, const double *u, double *out) {
    averages (mode 0), global minimum.  READING: for the isothermal EOS c_s is
    taken at the element centre. */
 /* the factor of C in the CFL step (Sec. 2.3): 1/(2p+1), and with the
-   positivity limiter min(1/(2p+1), w_1/2) where w_1 is the first weight of the
+   positivity limiter (Sec. 2.4) min(1/(2p+1), w_1/2) where w_1 is the first weight of the
    N-point Gauss-Lobatto rule normalised to sum 1.  READING: N is the smallest
    count with 2N - 3 >= p (the rule Zhang & Shu use for degree p), and the
    endpoint weight of that rule is 2/(N(N-1)) on [-1,1], i.e. 1/(N(N-1)). */
@@ -886,7 +886,7 @@ static void eval_point(const ref_state *s, double c[MAXV][MAXN], int n, double *
   }
 }
 
-/* Zhang & Shu's positivity limiter (Sec. 2.3) on one element.  READING: the
+/* Zhang & Shu's positivity limiter (Sec. 2.4) on one element.  READING: the
    check points are the points where the operator evaluates the solution (the
    m x m volume nodes and the 4m face points), eps = 1e-13; density first
    (theta = (mean - eps)/(mean - min)), then pressure with

@@ -74,7 +74,7 @@ typedef struct {
   double amp, vx0, vy0;       /* wave amplitude and uniform velocity (ic 1, 2) */
   int limiter;                /* 0 none; 1 TVB-minmod troubled cells reduced to limited P1 after each stage */
   double tvb_m;               /* TVB constant M of the modified minmod (0: plain minmod) */
-  int positivity;             /* 1: Zhang-Shu positivity limiter after each stage (Sec. 2.3) */
+  int positivity;             /* 1: Zhang-Shu positivity limiter after each stage (Sec. 2.4) */
   double ring_r, ring_p;      /* ic 3: the disc of ic 0 with pressure x ring_p inside r < ring_r */
 } ref_disc;
 

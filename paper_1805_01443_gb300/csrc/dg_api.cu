@@ -361,7 +361,7 @@ const Tableau* rk_tableau(int rk) {
 }
 
 // factor of C in the CFL step (Sec. 2.3): 1/(2p+1); with the positivity
-// limiter min(1/(2p+1), w_1/2), w_1 = 1/(N(N-1)) the first weight (sum 1) of
+// limiter (Sec. 2.4) min(1/(2p+1), w_1/2), w_1 = 1/(N(N-1)) the first weight (sum 1) of
 // the N-point Gauss-Lobatto rule with the smallest N such that 2N - 3 >= p
 double cfl_factor(int p, int positivity) {
   double f = 1.0 / (2.0 * p + 1.0);

@@ -8,7 +8,7 @@
 // limited.  The element is troubled when any increment would change.  (2) A
 // troubled element (by the test, or by given flags from the learned
 // indicator) keeps its mean and the limited linear modes, every other mode
-// zero.  (3) The positivity limiter of Sec. 2.3 (Zhang & Shu): density, then
+// zero.  (3) The positivity limiter of Sec. 2.4 (Zhang & Shu): density, then
 // pressure (adiabatic), >= 1e-13 at the m x m volume nodes and the 4m face
 // points, by scaling the non-mean modes towards the mean.  Limiting never
 // writes mode 0, so reading the neighbours' means while they are limited in

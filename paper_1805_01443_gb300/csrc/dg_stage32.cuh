@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
   stage32_tile<P, LAST>(a, a.D, a.Dn, a.Out, a.alpha, a.beta, a.pidx, a.mode, bx, j, smd);
 }
 
-// Torque on the planet at t^{n+1} from the new state (Sec. 5.1 torque with the
+// Torque on the planet at t^{n+1} from the new state (Sec. 5.2 torque with the
 // quadrature-node masses).  One warp per tile, lane e owns element e.  The
 // terms w_n m_n (r_n - r_p) / (|r_n - r_p|^2 + eps^2)^{3/2} are large and
 // cancel to a few 1e-5 of their absolute sum, and their absolute sum is

@@ -5,7 +5,7 @@ cases with a known answer (a linear field is never troubled; a large TVB
 constant flags nothing), invariants the method guarantees (means are kept;
 the limited state passes its own test; positivity holds at every check point;
 mass is conserved by a limited run), the closed form of the positivity time
-step (Sec. 2.3), and the limited Shu-Osher driver against the pinned Butcher
+step (Sec. 2.4), and the limited Shu-Osher driver against the pinned Butcher
 form of SSP(3,3) when no limiter acts.
 """
 import math
@@ -149,7 +149,7 @@ def test_positivity_limiter_restores_positive_points(p):
 
 @pytest.mark.parametrize("p,expect", [(1, 1 / 4), (2, 1 / 12), (3, 1 / 12), (4, 1 / 24)])
 def test_positivity_time_step_closed_form(p, expect):
-    """Sec. 2.3: C min(1/(2p+1), w_1/2), w_1 the endpoint weight of the
+    """Sec. 2.4: C min(1/(2p+1), w_1/2), w_1 the endpoint weight of the
     N-point Gauss-Lobatto rule (N = 2, 3, 3, 4 for p = 1..4: weights 1/2,
     1/6, 1/6, 1/12 normalised to sum 1)."""
     cfg = inputs.uniform_state(10, p, kind=1, vx0=0.3, vy0=-0.2)
