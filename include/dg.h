@@ -100,7 +100,10 @@ typedef struct {
                          r < ring_r (an imposed shock ring); 4 the isentropic
                          vortex of Sec. 4.1 (strength amp, free stream rho = p = 1,
                          v = (vx0, vy0), centred in the box); 5 the Gresho vortex
-                         of Sec. 4.2 (centred in the box); 4 and 5 adiabatic */
+                         of Sec. 4.2 (centred in the box); 4 and 5 adiabatic.
+                         Other values, among them 6 (the paper's own disc of
+                         Sec. 5.1, which the oracle has), give
+                         DG_ERR_UNSUPPORTED. */
   int star;           /* 1: softened point-mass star at the origin in the source;
                          Phi_* = -1/r for r >= r_soft, solid-body core inside */
   double r_soft;      /* star softening radius (> 0 for kind 0, star or ic 0) */

@@ -364,6 +364,27 @@ static void background_prim(const ref_state *s, double x, double y, double *w) {
     /* READING (config 5): the imposed shock ring is a pressure step, p x ring_p
        inside r < ring_r, on the same disc (sharp at the nodes, then projected) */
     if (s->d.ic == 3 && r < s->d.ring_r) w[3] *= s->d.ring_p;
+  } else if (s->d.ic == 6) {
+    /* Sec. 5.1, the paper's own disc: Sigma = Sigma_0 / (1 + f), p = p_0 / (1 + f),
+       f = exp((r - r_ex) / (r_p h)), in rotational equilibrium
+       v_phi^2 = r^2 Omega^2 + (r / Sigma) d(c_s,iso^2 Sigma)/dr with Omega solid-body
+       inside r_in and Keplerian outside.  READINGS: the printed first term
+       "Omega^2" is r^2 Omega^2 (the first equality and the units say so);
+       Sigma_0 = r_p = 1 and c_s,iso = h (p_0 = h^2 Sigma_0, the printed
+       2.5e-3 for h = 0.05); r_in is the star's solid-body core r_s, so that
+       r^2 Omega^2 = v_K^2; r_ex is the outer damping radius times 1.15^(3/2)
+       (the paper places r_d = r_ex 1.15^(-3/2)).  p / Sigma = h^2 everywhere,
+       so d(c_s,iso^2 Sigma)/dr = h^2 dSigma/dr = -h f Sigma / (1 + f). */
+    double r = sqrt(x * x + y * y);
+    if (r < 1e-12) r = 1e-12;
+    const double h = s->eos.h, rex = s->d.rdamp_out * pow(1.15, 1.5);
+    const double f = exp((r - rex) / h), g = f / (1.0 + f);
+    const double vphi2 = vk2_at(s, r) - r * h * g;
+    const double vphi = sqrt(vphi2 > 0.0 ? vphi2 : 0.0);
+    w[0] = 1.0 / (1.0 + f);
+    w[1] = -vphi * y / r;
+    w[2] = vphi * x / r;
+    w[3] = h * h / (1.0 + f);
   } else if (s->d.ic == 4) {
     /* Sec. 4.1 isentropic vortex (Yee et al.) about (x0 + x1, y0 + y1)/2 in
        the free stream rho = p = 1, v = (vx0, vy0); READING: the vortex
@@ -1042,8 +1063,10 @@ int ref_init(ref_state **out, const ref_mesh *mesh, int order, const ref_eos *eo
   if (eos->kind < 0 || eos->kind > 2) return -2;
   if (eos->kind == 1 && !(eos->gamma > 1.0)) return -1;
   if ((eos->kind == 0 || disc->star || disc->ic == 0 || disc->ic == 3) && !(disc->r_soft > 0.0)) return -1;
-  if (disc->ic < 0 || disc->ic > 5) return -2;
-  if ((disc->ic == 4 || disc->ic == 5) && eos->kind != 1) return -1;
+  if (disc->ic < 0 || disc->ic > 6) return -2;
+  if ((disc->ic == 4 || disc->ic == 5 || disc->ic == 6) && eos->kind != 1) return -1;
+  if (disc->ic == 6 && (!disc->star || !(disc->r_soft > 0.0) || !(disc->rdamp_out > 0.0) || !(eos->h > 0.0)))
+    return -1;
   if (disc->ic == 3 && (eos->kind != 1 || !(disc->ring_p > 0.0))) return -1;
   if (disc->limiter < 0 || disc->limiter > 1 || disc->positivity < 0 || disc->positivity > 1) return -1;
   if ((disc->limiter || disc->positivity) && disc->rk != 3) return -2;

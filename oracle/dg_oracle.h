@@ -60,7 +60,8 @@ typedef struct {
 
 typedef struct {
   int ic;                     /* 0 Keplerian disc, 1 density wave, 2 uniform state, 3 disc with a pressure ring,
-                                 4 isentropic vortex (strength amp), 5 Gresho vortex (adiabatic) */
+                                 4 isentropic vortex (strength amp), 5 Gresho vortex (adiabatic),
+                                 6 the paper's disc of Sec. 5.1 (adiabatic; r_ex from rdamp_out) */
   int star;                   /* 1: softened point-mass star potential in the source */
   double r_soft;              /* star softening radius r_s */
   double sigma_slope;         /* Sigma ~ r^slope */

@@ -108,6 +108,21 @@ def gresho_vortex(n=40, order=3, cfl=0.1):
     return cfg
 
 
+def paper_disc(n=128, order=4, q=6e-5, positivity=1):
+    """The paper's own planet disc (Sec. 5.1): box [-2.25, 2.25]^2, adiabatic
+    gamma = 1.4, uniform Sigma_0 = 1 and p_0 = h^2 = 2.5e-3 tapered beyond
+    r_ex = 1.75, solid-body rotation inside r_in = 0.4 (the star's core
+    radius), planet q = 6e-5 on the fixed orbit r_p = 1 with eps = 0.03,
+    damping radii r_in 1.15^(3/2) and r_ex 1.15^(-3/2), the positivity
+    limiter on; no seeded noise (the disc starts smooth)."""
+    cfg = _disc_base(n, order, 0, planet_q=q, damping=True)
+    cfg["mesh"].update({"x0": -2.25, "x1": 2.25, "y0": -2.25, "y1": 2.25})
+    cfg["eos"].update({"kind": 1, "gamma": 1.4})
+    cfg["disc"].update({"ic": 6, "r_soft": 0.4, "noise_amp": 0.0, "rdamp_in": 0.4 * 1.15 ** 1.5,
+                        "rdamp_out": 1.75 * 1.15 ** -1.5, "positivity": positivity})
+    return cfg
+
+
 def batch_discs(n=48, seed0=100, prec=1):
     """Batched workload: n independent planet discs (damping zones as above),
     instance k with seed seed0 + k, mesh {128, 256, 384, 512}^2 cycling with k,

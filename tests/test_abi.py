@@ -57,6 +57,11 @@ def test_argument_validation_without_gpu(L):
     with pytest.raises(dg.DgError) as e:
         dg.dg_workspace_bytes(bad)
     assert e.value.code == dg.DG_ERR_ARG
+    # the paper's own disc (ic 6) is built in the oracle only so far
+    bad = inputs.paper_disc(16, 2)
+    with pytest.raises(dg.DgError) as e:
+        dg.dg_workspace_bytes(bad)
+    assert e.value.code == dg.DG_ERR_UNSUPPORTED
     assert dg.dg_workspace_bytes(cfg) > 0
 
 

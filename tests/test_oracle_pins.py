@@ -543,3 +543,93 @@ def test_background_ghosts_are_the_projected_background_there():
     for got, ref in ((left, B[:, :, 1:-1, 0]), (right, B[:, :, 1:-1, -1]),
                      (bottom, B[:, :, 0, 1:-1]), (top, B[:, :, -1, 1:-1])):
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------
+# the paper's own disc (Sec. 5.1, ic 6)
+
+PD_H, PD_REX, PD_RIN, PD_GAMMA = 0.05, 1.75, 0.4, 1.4
+
+
+def _paper_disc_fields(X, Y, pressure_term=True):
+    """Conserved fields of the Sec. 5.1 disc written out here from the paper:
+    Sigma = Sigma_0/(1+f), p = p_0/(1+f), f = exp((r - r_ex)/(r_p h)), Sigma_0 = 1,
+    p_0 = 2.5e-3, v_phi^2 = r^2 Omega^2 + (r/Sigma) d(c_s,iso^2 Sigma)/dr with
+    c_s,iso^2 = p_0/Sigma_0, Omega^2 = 1/r_in^3 inside r_in and 1/r^3 outside."""
+    r = np.hypot(X, Y)
+    f = np.exp((r - PD_REX) / PD_H)
+    sig = 1.0 / (1.0 + f)
+    p = 2.5e-3 / (1.0 + f)
+    om2 = np.where(r <= PD_RIN, 1.0 / PD_RIN ** 3, 1.0 / r ** 3)
+    c2 = 2.5e-3 / 1.0
+    dsig = -(f / PD_H) / (1.0 + f) ** 2  # dSigma/dr
+    vphi2 = r * r * om2 + (r * c2 * dsig / sig if pressure_term else 0.0)
+    vphi = np.sqrt(vphi2)
+    vx, vy = -vphi * Y / r, vphi * X / r
+    return [sig, sig * vx, sig * vy, p / (PD_GAMMA - 1.0) + 0.5 * sig * (vx * vx + vy * vy)]
+
+
+def _project_all(cfg, fields, npts):
+    """Every element's mean-normalised projection with an npts^2 numpy GL rule,
+    vectorised over the mesh; returns [var][a*m+b][j][i]."""
+    p = cfg["order"]
+    m = p + 1
+    mesh = cfg["mesh"]
+    nx, ny = mesh["nx"], mesh["ny"]
+    dx = (mesh["x1"] - mesh["x0"]) / nx
+    dy = (mesh["y1"] - mesh["y0"]) / ny
+    xg, wg = np.polynomial.legendre.leggauss(npts)
+    xc = mesh["x0"] + (np.arange(nx) + 0.5) * dx
+    yc = mesh["y0"] + (np.arange(ny) + 0.5) * dy
+    X = xc[None, :, None, None] + 0.5 * dx * xg[None, None, :, None]
+    Y = yc[:, None, None, None] + 0.5 * dy * xg[None, None, None, :]
+    X, Y = np.broadcast_arrays(X, Y)
+    B = np_basis(p, xg)
+    return np.array([0.25 * np.einsum("q,r,jiqr,qa,rb->abji", wg, wg, F, B, B).reshape(m * m, ny, nx)
+                     for F in fields(X, Y)])
+
+
+def test_paper_disc_initial_state_is_the_printed_profile():
+    """The oracle's initial state of ic 6 equals the projection (same (m+1)-point
+    rule) of the profile as printed, written out independently above."""
+    cfg = inputs.paper_disc(24, 3, positivity=0)
+    u = oracle.Oracle(cfg).fetch()
+    ref = _project_all(cfg, _paper_disc_fields, cfg["order"] + 2)
+    assert np.abs(u - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_paper_disc_sound_speeds_are_the_printed_ones():
+    """At the planet's orbit the disc has Sigma_0 = 1, c_s,iso = 0.05 and
+    c_s,adi = sqrt(gamma p_0/Sigma_0) ~ 0.059 (the values printed in Sec. 5.1),
+    read at the quadrature nodes of the element that holds (r_p, 0)."""
+    cfg = inputs.paper_disc(96, 3, positivity=0)
+    o = oracle.Oracle(cfg)
+    nod = o.nodal()
+    dx = 4.5 / 96
+    i = int((1.0 + 2.25) / dx)
+    j = int((0.0 + 2.25) / dx)
+    sig, mx, my, E = (nod[v, :, j, i] for v in range(4))
+    p = (PD_GAMMA - 1.0) * (E - 0.5 * (mx * mx + my * my) / sig)
+    np.testing.assert_allclose(sig, 1.0, rtol=1e-6)
+    np.testing.assert_allclose(np.sqrt(p / sig), 0.05, rtol=1e-3)
+    assert np.all(np.round(np.sqrt(PD_GAMMA * p / sig), 3) == 0.059)
+
+
+def test_paper_disc_is_in_equilibrium_only_with_its_pressure_term():
+    """Without the planet, L of the projected disc shrinks at order ~p where the
+    taper bends the pressure (1.5 < r < 2), and stalls if v_phi drops the
+    pressure-gradient term of the printed equilibrium."""
+    good, bad = [], []
+    for n in (96, 192):
+        cfg = inputs.paper_disc(n, 3, positivity=0)
+        cfg["planet"]["enabled"] = 0
+        o = oracle.Oracle(cfg)
+        dx = 4.5 / n
+        xc = -2.25 + (np.arange(n) + 0.5) * dx
+        R = np.hypot(xc[None, :], xc[:, None])
+        mask = (R > 1.5) & (R < 2.0)
+        good.append(np.sqrt(np.mean(o.rhs()[:, :, mask] ** 2)))
+        o.set_state(_project_all(cfg, lambda X, Y: _paper_disc_fields(X, Y, False), cfg["order"] + 2))
+        bad.append(np.sqrt(np.mean(o.rhs()[:, :, mask] ** 2)))
+    assert math.log2(good[0] / good[1]) > 2.5, good
+    assert bad[1] > 30.0 * good[1] and bad[1] > 0.8 * bad[0], (good, bad)
