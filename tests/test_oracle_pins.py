@@ -633,3 +633,60 @@ def test_paper_disc_is_in_equilibrium_only_with_its_pressure_term():
         bad.append(np.sqrt(np.mean(o.rhs()[:, :, mask] ** 2)))
     assert math.log2(good[0] / good[1]) > 2.5, good
     assert bad[1] > 30.0 * good[1] and bad[1] > 0.8 * bad[0], (good, bad)
+
+
+def test_damping_of_the_adiabatic_disc_relaxes_density_velocity_and_temperature():
+    """Sec. 5.1: density, velocities and temperature T = p/Sigma relax at each
+    damped node by Q = (dt Q0 + tau Q)/(tau + dt) towards the unperturbed disc,
+    tau = 2 pi sqrt(r_d^3)/R(r) with R = ((r - r_d)/(r_in/ex - r_d))^2 (at most 1);
+    nodes between the zones keep their values.  The paper's disc (ic 6):
+    zones inside r_d = 0.4 * 1.15^1.5 and outside r_d = 1.75 / 1.15^1.5."""
+    cfg = inputs.paper_disc(20, 2, positivity=0)
+    o = oracle.Oracle(cfg)
+    u = o.fetch()
+    u[0] *= 1.02
+    u[1:3] *= 1.01
+    u[3] *= 1.03
+    o.set_state(u)
+    n0 = o.nodal()
+    dt = 0.05
+    o.damp(dt)
+    n1 = o.nodal()
+    m = cfg["order"] + 1
+    xg, _ = np.polynomial.legendre.leggauss(m)
+    dx = 4.5 / 20
+    rd_in, rb_in = 0.4 * 1.15 ** 1.5, 0.4
+    rd_out, rb_out = 1.75 / 1.15 ** 1.5, 1.75
+
+    def prim(nv):
+        sig = nv[0]
+        vx, vy = nv[1] / sig, nv[2] / sig
+        p = (PD_GAMMA - 1.0) * (nv[3] - 0.5 * sig * (vx * vx + vy * vy))
+        return np.array([sig, vx, vy, p / sig])
+
+    seen = set()
+    for (i, j) in [(10, 10), (9, 10), (0, 0), (17, 10), (16, 12), (14, 10), (4, 15)]:
+        for q in range(m):
+            for r in range(m):
+                X = -2.25 + (i + 0.5) * dx + 0.5 * dx * xg[q]
+                Y = -2.25 + (j + 0.5) * dx + 0.5 * dx * xg[r]
+                rr = math.hypot(X, Y)
+                k = q * m + r
+                before, after = prim(n0[:, k, j, i]), prim(n1[:, k, j, i])
+                if rr < rd_in:
+                    rd, rb = rd_in, rb_in
+                elif rr > rd_out:
+                    rd, rb = rd_out, rb_out
+                else:
+                    seen.add("none")
+                    np.testing.assert_allclose(after, before, rtol=1e-12, atol=1e-14)
+                    continue
+                seen.add("inner" if rd == rd_in else "outer")
+                R = min(((rr - rd) / (rb - rd)) ** 2, 1.0)
+                tau = 2.0 * math.pi * math.sqrt(rd ** 3) / R
+                F = _paper_disc_fields(np.array(X), np.array(Y))
+                sig0 = float(F[0])
+                target = np.array([sig0, float(F[1]) / sig0, float(F[2]) / sig0, 2.5e-3])
+                expect = (dt * target + tau * before) / (tau + dt)
+                np.testing.assert_allclose(after, expect, rtol=1e-10, atol=1e-13)
+    assert seen == {"inner", "outer", "none"}
