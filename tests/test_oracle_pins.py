@@ -263,6 +263,37 @@ def test_gravity_source_matches_exact_integral(p):
     np.testing.assert_allclose(L, same_rule, atol=1e-14 * scale)
 
 
+def test_energy_source_is_minus_rho_v_dot_grad_phi():
+    """Adiabatic gas, uniform rho = p = 1 moving at v = (0.3, -0.2) near the star
+    and the planet: the fluxes are constant, so L(u) is the projected source
+    (0, -rho grad Phi, -rho v . grad Phi) of Eq. 1, compared with numpy's m-point
+    projection of the closed-form gravity."""
+    p = 3
+    vx, vy = 0.3, -0.2
+    cfg = inputs.uniform_state(6, p, kind=1, vx0=vx, vy0=vy, bc=2)
+    cfg["mesh"].update({"x0": 0.8, "x1": 1.1, "y0": 0.1, "y1": 0.4})
+    cfg["disc"].update({"star": 1, "r_soft": 0.2})
+    cfg["planet"].update({"enabled": 1, "q": 1e-3, "eps": 0.03, "phi0": math.pi})
+    xp, yp = -1.0, 0.0
+
+    def gphi(X, Y):
+        r3 = (X**2 + Y**2) ** 1.5
+        d2 = (X - xp) ** 2 + (Y - yp) ** 2 + 0.03**2
+        f = 1e-3 / d2**1.5
+        return X / r3 + f * (X - xp), Y / r3 + f * (Y - yp)
+
+    o = oracle.Oracle(cfg)
+    L = o.rhs()
+    ex = project_field(lambda X, Y: -gphi(X, Y)[0], cfg, npts=p + 1)
+    ey = project_field(lambda X, Y: -gphi(X, Y)[1], cfg, npts=p + 1)
+    ee = project_field(lambda X, Y: -(vx * gphi(X, Y)[0] + vy * gphi(X, Y)[1]), cfg, npts=p + 1)
+    scale = np.abs(ex).max()
+    np.testing.assert_allclose(L[0], 0.0, atol=1e-13 * scale)
+    np.testing.assert_allclose(L[1], ex, atol=1e-13 * scale)
+    np.testing.assert_allclose(L[2], ey, atol=1e-13 * scale)
+    np.testing.assert_allclose(L[3], ee, atol=1e-13 * scale)
+
+
 def test_conservation_periodic():
     """Periodic adiabatic gas without gravity: total mass, momentum and energy
     (sum of element averages times |K|) are constant to round-off."""
