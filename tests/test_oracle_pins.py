@@ -294,6 +294,47 @@ def test_energy_source_is_minus_rho_v_dot_grad_phi():
     np.testing.assert_allclose(L[3], ee, atol=1e-13 * scale)
 
 
+def test_mode0_update_is_the_rusanov_finite_volume_scheme():
+    """Piecewise-constant adiabatic data (mode 0 only), uniform in y, periodic,
+    no gravity: the mode-0 row of L is the finite-volume update
+    -(F_{i+1/2} - F_{i-1/2})/dx with the textbook Rusanov flux
+    F = (f(u_L) + f(u_R))/2 - alpha (u_R - u_L)/2, alpha = max(|v_x| + c) over the
+    two sides, c = sqrt(gamma p/rho) (the LLF flux of Eq. 2)."""
+    nx, g = 8, 1.4
+    cfg = inputs.uniform_state(nx, 2, kind=1, bc=0)
+    cfg["mesh"]["ny"] = 2
+    cfg["mesh"]["x1"] = 2.0
+    dx = 2.0 / nx
+    rng = np.random.Generator(np.random.PCG64(9))
+    rho = rng.uniform(0.5, 1.5, nx)
+    vx = rng.uniform(-0.5, 0.5, nx)
+    vy = rng.uniform(-0.2, 0.2, nx)
+    pr = rng.uniform(0.5, 1.5, nx)
+    E = pr / (g - 1.0) + 0.5 * rho * (vx * vx + vy * vy)
+    U = np.stack([rho, rho * vx, rho * vy, E])  # [var][i]
+    o = oracle.Oracle(cfg)
+    state = np.zeros(o.shape)
+    state[:, 0] = U[:, None, :]
+    o.set_state(state)
+    L = o.rhs()
+
+    def fx(u):
+        r, mx, my, e = u
+        v = mx / r
+        p_ = (g - 1.0) * (e - 0.5 * (mx * mx + my * my) / r)
+        return np.array([mx, mx * v + p_, my * v, (e + p_) * v]), np.abs(v) + np.sqrt(g * p_ / r)
+
+    F = np.zeros((4, nx))  # F[:, i] at the face between i-1 and i
+    for i in range(nx):
+        uL, uR = U[:, i - 1], U[:, i]
+        fL, aL = fx(uL)
+        fR, aR = fx(uR)
+        F[:, i] = 0.5 * (fL + fR) - 0.5 * max(aL, aR) * (uR - uL)
+    expect = -(np.roll(F, -1, axis=1) - F) / dx
+    for j in range(2):
+        np.testing.assert_allclose(L[:, 0, j, :], expect, rtol=0, atol=1e-13 * np.abs(expect).max())
+
+
 def test_conservation_periodic():
     """Periodic adiabatic gas without gravity: total mass, momentum and energy
     (sum of element averages times |K|) are constant to round-off."""
