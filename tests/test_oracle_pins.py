@@ -335,6 +335,66 @@ def test_mode0_update_is_the_rusanov_finite_volume_scheme():
         np.testing.assert_allclose(L[:, 0, j, :], expect, rtol=0, atol=1e-13 * np.abs(expect).max())
 
 
+def test_mode0_update_locally_isothermal_face_quadrature():
+    """Locally isothermal gas, c_s^2 = h^2 v_K^2(r) with the softened star's v_K
+    (r^2/r_s^3 inside r_s), piecewise-constant data, no gravity: the mode-0 row
+    of L is -(1/dx) sum_r (w_r/2) [h_x(x_{i+1}, y_r) - h_x(x_i, y_r)] minus the
+    same over the y faces, with the LLF flux of Eq. 2 taking c_s at each face
+    node (numpy's Gauss-Legendre nodes and weights)."""
+    p, n, hh, rs = 2, 8, 0.05, 0.2
+    m = p + 1
+    cfg = inputs.uniform_state(n, p, kind=0, bc=0, h=hh)
+    cfg["mesh"].update({"x0": -0.5, "x1": 0.5, "y0": -0.45, "y1": 0.55})
+    cfg["disc"].update({"star": 0, "r_soft": rs})
+    dx, dy = 1.0 / n, 1.0 / n
+    rng = np.random.Generator(np.random.PCG64(21))
+    S = rng.uniform(0.5, 1.5, (n, n))
+    mx = S * rng.uniform(-0.3, 0.3, (n, n))
+    my = S * rng.uniform(-0.3, 0.3, (n, n))
+    o = oracle.Oracle(cfg)
+    state = np.zeros(o.shape)
+    state[0, 0], state[1, 0], state[2, 0] = S, mx, my
+    o.set_state(state)
+    L = o.rhs()
+
+    def c2(X, Y):
+        r = math.hypot(X, Y)
+        return hh * hh * (1.0 / r if r >= rs else r * r / rs ** 3)
+
+    def llf(uL, uR, d, X, Y):
+        cc = c2(X, Y)
+
+        def f(u):
+            v = u[1 + d] / u[0]
+            out = np.array([u[1 + d], u[1] * v, u[2] * v])
+            out[1 + d] += cc * u[0]
+            return out, abs(v) + math.sqrt(cc)
+        fL, aL = f(uL)
+        fR, aR = f(uR)
+        return 0.5 * (fL + fR) - 0.5 * max(aL, aR) * (uR - uL)
+
+    xg, wg = np.polynomial.legendre.leggauss(m)
+    U = np.stack([S, mx, my])  # [var][j][i]
+    expect = np.zeros((3, n, n))
+    for j in range(n):
+        for i in range(n):
+            yc = -0.45 + (j + 0.5) * dy
+            xc = -0.5 + (i + 0.5) * dx
+            acc = np.zeros(3)
+            for r in range(m):
+                y = yc + 0.5 * dy * xg[r]
+                hl = llf(U[:, j, (i - 1) % n], U[:, j, i], 0, -0.5 + i * dx, y)
+                hr = llf(U[:, j, i], U[:, j, (i + 1) % n], 0, -0.5 + (i + 1) * dx, y)
+                acc -= 0.5 * wg[r] * (hr - hl) / dx
+            for q in range(m):
+                x = xc + 0.5 * dx * xg[q]
+                hb = llf(U[:, (j - 1) % n, i], U[:, j, i], 1, x, -0.45 + j * dy)
+                ht = llf(U[:, j, i], U[:, (j + 1) % n, i], 1, x, -0.45 + (j + 1) * dy)
+                acc -= 0.5 * wg[q] * (ht - hb) / dy
+            expect[:, j, i] = acc
+    np.testing.assert_allclose(L[:, 0], expect, rtol=0, atol=1e-12 * np.abs(expect).max())
+
+
 def test_conservation_periodic():
     """Periodic adiabatic gas without gravity: total mass, momentum and energy
     (sum of element averages times |K|) are constant to round-off."""
