@@ -395,6 +395,39 @@ def test_mode0_update_locally_isothermal_face_quadrature():
     np.testing.assert_allclose(L[:, 0], expect, rtol=0, atol=1e-12 * np.abs(expect).max())
 
 
+def test_planet_moves_with_the_stage_times():
+    """SSP(3,3) evaluates the planet at t^n + c_i dt with c = (0, 1, 1/2) (reading
+    R4) and weighs the stages by b = (1/6, 1/6, 2/3).  Cold resting gas near the
+    planet: after one step the momentum is -dt sum_i b_i rho grad Phi_p(t_i),
+    projected with the m-point rule, up to O(dt^3) couplings through the flux,
+    i.e. O(dt^2) relative to the O(dt) momentum: halving dt cuts the relative
+    mismatch by ~4.  With c_3 = 3/4 it would be ~30x larger at dt = 0.01 and
+    fall only as dt."""
+    p, q, eps = 2, 1e-3, 0.03
+    cfg = inputs.uniform_state(6, p, kind=2, h=0.0, bc=2)
+    cfg["mesh"].update({"x0": 0.85, "x1": 1.15, "y0": -0.15, "y1": 0.15})
+    cfg["planet"].update({"enabled": 1, "q": q, "eps": eps, "r_p": 1.0, "omega_p": 1.0, "phi0": 0.0})
+
+    def source(t):
+        xp, yp = math.cos(t), math.sin(t)
+
+        def g(X, Y, c):
+            d2 = (X - xp) ** 2 + (Y - yp) ** 2 + eps * eps
+            return -q * ((X - xp) if c == 0 else (Y - yp)) / d2 ** 1.5
+        return np.stack([project_field(lambda X, Y: g(X, Y, 0), cfg, npts=p + 1),
+                         project_field(lambda X, Y: g(X, Y, 1), cfg, npts=p + 1)])
+
+    err = []
+    for dt in (0.02, 0.01):
+        o = oracle.Oracle(cfg)
+        o.step_dt(1, dt)
+        m = o.fetch()[1:3]
+        expect = dt * (source(0.0) / 6.0 + source(dt) / 6.0 + 2.0 * source(0.5 * dt) / 3.0)
+        err.append(np.abs(m - expect).max() / np.abs(expect).max())
+    assert err[0] / err[1] > 3.3, err
+    assert err[1] < 2e-3, err
+
+
 def test_conservation_periodic():
     """Periodic adiabatic gas without gravity: total mass, momentum and energy
     (sum of element averages times |K|) are constant to round-off."""
