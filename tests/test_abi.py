@@ -70,3 +70,42 @@ def test_workspace_size_scales_with_mesh(L):
     a = dg.dg_workspace_bytes(inputs.disc_planet(64, 4))
     b = dg.dg_workspace_bytes(inputs.disc_planet(128, 4))
     assert 3.5 < b / a < 4.5
+
+
+def _bad(edit):
+    from paper_1805_01443_gb300 import inputs
+    cfg = inputs.disc_small(8, 2)
+    edit(cfg)
+    return cfg
+
+
+def _set(section, **kw):
+    return lambda c: c[section].update(kw)
+
+
+@pytest.mark.parametrize("edit,code", [
+    (_set("mesh", nx=70000), dg.DG_ERR_ARG),                         # side outside 1..65535
+    (_set("mesh", nx=20000, ny=20000), dg.DG_ERR_ARG),               # more than 2^28 elements
+    (_set("mesh", x1=-3.0), dg.DG_ERR_ARG),                          # empty box
+    (_set("mesh", bc=4), dg.DG_ERR_ARG),
+    (lambda c: c.update(order=0), dg.DG_ERR_UNSUPPORTED),
+    (_set("eos", kind=3), dg.DG_ERR_UNSUPPORTED),
+    (_set("eos", kind=1, gamma=1.0), dg.DG_ERR_ARG),
+    (_set("disc", ic=7), dg.DG_ERR_UNSUPPORTED),
+    (_set("disc", ic=4), dg.DG_ERR_ARG),                             # vortex needs the adiabatic EOS
+    (lambda c: (c["eos"].update(kind=1), c["disc"].update(ic=3, ring_p=0.0)), dg.DG_ERR_ARG),
+    (_set("disc", limiter=3), dg.DG_ERR_ARG),
+    (_set("disc", positivity=1, rk=2), dg.DG_ERR_UNSUPPORTED),       # limiters need SSP(3,3)
+    (_set("disc", limiter=1, tvb_m=-1.0), dg.DG_ERR_ARG),
+    (_set("disc", rk=6), dg.DG_ERR_UNSUPPORTED),
+    (_set("disc", rk=4, prec=1), dg.DG_ERR_UNSUPPORTED),             # RK(4,5) in the FP64 form only
+    (_set("disc", prec=2), dg.DG_ERR_UNSUPPORTED),                   # only FP64 and the FP32 form
+    (lambda c: (c["eos"].update(kind=1), c["disc"].update(prec=1)), dg.DG_ERR_UNSUPPORTED),
+    (_set("disc", cfl=0.0), dg.DG_ERR_ARG),
+])
+def test_every_validation_rule_returns_its_documented_code(L, edit, code):
+    """Each host-side check of dg_init (run here through dg_workspace_bytes,
+    before any CUDA call) rejects with the code include/dg.h documents."""
+    with pytest.raises(dg.DgError) as e:
+        dg.dg_workspace_bytes(_bad(edit))
+    assert e.value.code == code
