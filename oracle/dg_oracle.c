@@ -374,17 +374,27 @@ static void background_prim(const ref_state *s, double x, double y, double *w) {
        2.5e-3 for h = 0.05); r_in is the star's solid-body core r_s, so that
        r^2 Omega^2 = v_K^2; r_ex is the outer damping radius times 1.15^(3/2)
        (the paper places r_d = r_ex 1.15^(-3/2)).  p / Sigma = h^2 everywhere,
-       so d(c_s,iso^2 Sigma)/dr = h^2 dSigma/dr = -h f Sigma / (1 + f). */
+       so d(c_s,iso^2 Sigma)/dr = h^2 dSigma/dr = -h f Sigma / (1 + f).
+       READING: Sigma is floored at sigma_floor (1e-4 in the configurations,
+       as for the other discs), beyond r ~ r_ex + h ln(1/floor); unfloored the
+       box corners hold Sigma ~ 4e-13 and p ~ 1e-15, below the positivity
+       limiter's absolute floor.  Where the floor holds there is no pressure
+       gradient and v_phi is the star's alone. */
     double r = sqrt(x * x + y * y);
     if (r < 1e-12) r = 1e-12;
     const double h = s->eos.h, rex = s->d.rdamp_out * pow(1.15, 1.5);
-    const double f = exp((r - rex) / h), g = f / (1.0 + f);
+    const double f = exp((r - rex) / h);
+    double sig = 1.0 / (1.0 + f), g = f / (1.0 + f);
+    if (sig < s->d.sigma_floor) {
+      sig = s->d.sigma_floor;
+      g = 0.0;
+    }
     const double vphi2 = vk2_at(s, r) - r * h * g;
     const double vphi = sqrt(vphi2 > 0.0 ? vphi2 : 0.0);
-    w[0] = 1.0 / (1.0 + f);
+    w[0] = sig;
     w[1] = -vphi * y / r;
     w[2] = vphi * x / r;
-    w[3] = h * h / (1.0 + f);
+    w[3] = h * h * sig;
   } else if (s->d.ic == 4) {
     /* Sec. 4.1 isentropic vortex (Yee et al.) about (x0 + x1, y0 + y1)/2 in
        the free stream rho = p = 1, v = (vx0, vy0); READING: the vortex
