@@ -100,10 +100,13 @@ typedef struct {
                          r < ring_r (an imposed shock ring); 4 the isentropic
                          vortex of Sec. 4.1 (strength amp, free stream rho = p = 1,
                          v = (vx0, vy0), centred in the box); 5 the Gresho vortex
-                         of Sec. 4.2 (centred in the box); 4 and 5 adiabatic.
-                         Other values, among them 6 (the paper's own disc of
-                         Sec. 5.1, which the oracle has), give
-                         DG_ERR_UNSUPPORTED. */
+                         of Sec. 4.2 (centred in the box); 6 the paper's own
+                         disc of Sec. 5.1: Sigma = max(1/(1+f), sigma_floor),
+                         p = h^2 Sigma, f = exp((r - r_ex)/h), r_ex =
+                         rdamp_out * 1.15^(3/2), rotational equilibrium with
+                         solid-body rotation inside r_soft (needs the star and
+                         rdamp_out > 0); 4, 5 and 6 adiabatic.  Other values
+                         give DG_ERR_UNSUPPORTED. */
   int star;           /* 1: softened point-mass star at the origin in the source;
                          Phi_* = -1/r for r >= r_soft, solid-body core inside */
   double r_soft;      /* star softening radius (> 0 for kind 0, star or ic 0) */

@@ -290,8 +290,10 @@ int validate(const dg_mesh* mesh, int order, const dg_eos* eos, const dg_disc* d
   if (eos->kind == 1 && !(eos->gamma > 1.0)) return fail(nullptr, DG_ERR_ARG, "gamma must be > 1");
   if ((eos->kind == 0 || disc->star || disc->ic == 0 || disc->ic == 3) && !(disc->r_soft > 0.0))
     return fail(nullptr, DG_ERR_ARG, "r_soft must be > 0");
-  if (disc->ic < 0 || disc->ic > 5) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
-  if ((disc->ic == 4 || disc->ic == 5) && eos->kind != 1)
+  if (disc->ic < 0 || disc->ic > 6) return fail(nullptr, DG_ERR_UNSUPPORTED, "ic %d", disc->ic);
+  if (disc->ic == 6 && (!disc->star || !(disc->rdamp_out > 0.0) || !(eos->h > 0.0)))
+    return fail(nullptr, DG_ERR_ARG, "ic 6 needs the star, an outer damping radius and h > 0");
+  if ((disc->ic == 4 || disc->ic == 5 || disc->ic == 6) && eos->kind != 1)
     return fail(nullptr, DG_ERR_ARG, "ic %d needs the adiabatic EOS", disc->ic);
   if (disc->ic == 3 && (eos->kind != 1 || !(disc->ring_p > 0.0)))
     return fail(nullptr, DG_ERR_ARG, "ic 3 needs the adiabatic EOS and ring_p > 0");

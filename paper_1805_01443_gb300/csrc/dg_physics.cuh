@@ -16,7 +16,8 @@ __device__ __forceinline__ double vk2_of(const Phys& ph, double r) {
 // ic 0 the rotational-equilibrium disc Sigma = max(r^s, floor),
 // v_phi^2 = (1 + (s-1) h^2)/r outside r_s and (1 + (s+2) h^2) r^2/r_s^3
 // inside, p = h^2 v_K^2 Sigma; ic 3 the same with p x ring_p inside r < ring_r;
-// ic 1 the density wave; ic 2 a uniform state.
+// ic 1 the density wave; ic 2 a uniform state; ic 4 and 5 the vortices of
+// Sec. 4; ic 6 the paper's own disc of Sec. 5.1.
 __device__ __forceinline__ void ic_prim(const Phys& ph, const Mesh& ms, double x, double y,
                                         double* w) {
   if (ph.ic == 0 || ph.ic == 3) {
@@ -61,6 +62,24 @@ __device__ __forceinline__ void ic_prim(const Phys& ph, const Mesh& ms, double x
     w[1] = r > 0.0 ? -vphi * dy / r : 0.0;
     w[2] = r > 0.0 ? vphi * dx / r : 0.0;
     w[3] = p;
+  } else if (ph.ic == 6) {
+    // the paper's own disc (Sec. 5.1): Sigma = max(1/(1+f), floor),
+    // p = h^2 Sigma, f = exp((r - r_ex)/h), v_phi^2 = r^2 Omega^2 - r h f/(1+f)
+    // with the softened star's r^2 Omega^2 (no pressure term where the floor
+    // holds); r_ex = the outer damping radius x 1.15^(3/2)
+    const double r = fmax(sqrt(x * x + y * y), 1e-12);
+    const double rex = ph.rd_out * ph.damp_ratio;
+    const double f = exp((r - rex) / ph.h);
+    double sig = 1.0 / (1.0 + f), g = f / (1.0 + f);
+    if (sig < ph.sig_floor) {
+      sig = ph.sig_floor;
+      g = 0.0;
+    }
+    const double vphi = sqrt(fmax(vk2_of(ph, r) - r * ph.h * g, 0.0));
+    w[0] = sig;
+    w[1] = -vphi * y / r;
+    w[2] = vphi * x / r;
+    w[3] = ph.h * ph.h * sig;
   } else if (ph.ic == 1) {
     double lx = ms.x1 - ms.x0, ly = ms.y1 - ms.y0;
     w[0] = 1.0 + ph.amp * sin(6.283185307179586476925286766559 * ((x - ms.x0) / lx + (y - ms.y0) / ly));

@@ -57,11 +57,18 @@ def test_argument_validation_without_gpu(L):
     with pytest.raises(dg.DgError) as e:
         dg.dg_workspace_bytes(bad)
     assert e.value.code == dg.DG_ERR_ARG
-    # the paper's own disc (ic 6) is built in the oracle only so far
+    # the paper's own disc (ic 6) needs the adiabatic EOS and the star
+    assert dg.dg_workspace_bytes(inputs.paper_disc(16, 2)) > 0
     bad = inputs.paper_disc(16, 2)
+    bad["eos"]["kind"] = 0
     with pytest.raises(dg.DgError) as e:
         dg.dg_workspace_bytes(bad)
-    assert e.value.code == dg.DG_ERR_UNSUPPORTED
+    assert e.value.code == dg.DG_ERR_ARG
+    bad = inputs.paper_disc(16, 2)
+    bad["disc"]["star"] = 0
+    with pytest.raises(dg.DgError) as e:
+        dg.dg_workspace_bytes(bad)
+    assert e.value.code == dg.DG_ERR_ARG
     assert dg.dg_workspace_bytes(cfg) > 0
 
 

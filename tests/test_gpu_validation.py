@@ -103,3 +103,22 @@ def test_isentropic_vortex_convergence(p, bar):
     print(p, errs, rates)
     assert errs[0] > errs[1] > errs[2]
     assert rates[-1] >= bar
+
+
+def test_paper_disc_parity():
+    """The paper's own disc of Sec. 5.1 (ic 6: adiabatic, tapered beyond r_ex,
+    damping zones, positivity limiter, planet q = 6e-5): initial state and 20
+    steps on 48 x 48 P3 against the oracle (1e-12), torque included."""
+    cfg = inputs.paper_disc(48, 3)
+    o = oracle.Oracle(cfg)
+    with dg.Disc(cfg) as g:
+        u0 = o.fetch()
+        assert np.abs(g.fetch() - u0).max() <= 1e-12 * np.abs(u0).max()
+        o.step(20)
+        g.step(20)
+        uo, ug = o.fetch(), g.fetch()
+        for v in range(uo.shape[0]):
+            assert np.abs(ug[v] - uo[v]).max() <= 1e-12 * np.abs(uo[v]).max(), v
+        to, ab = o.torque()
+        assert abs(g.torque() - to) <= 1e-12 * ab
+        assert g.get_time()[0] == pytest.approx(o.get_time()[0], rel=1e-12)
