@@ -9,7 +9,9 @@ computed here with numpy quadrature, measured convergence order p+1
 wider mesh that holds its ghost elements explicitly.  None of these tests
 needs a GPU.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -395,11 +397,27 @@ def test_mode0_update_locally_isothermal_face_quadrature():
     np.testing.assert_allclose(L[:, 0], expect, rtol=0, atol=1e-12 * np.abs(expect).max())
 
 
-@pytest.mark.parametrize("rk", [3, 2])
+def _stage_times_and_weights(rk):
+    """(c, b) of each scheme: SSP(3,3) and SSP(2,2) by readings R4 and R5, the
+    5- and 6-stage schemes as printed in Tables A1 and A2 (tests/golden)."""
+    from fractions import Fraction
+    if rk == 3:
+        return [0.0, 1.0, 0.5], [1 / 6, 1 / 6, 2 / 3]
+    if rk == 2:
+        return [0.0, 1.0], [0.5, 0.5]
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "rk_appendix_tables.json")) as f:
+        g = json.load(f)
+    t = g["ssp_rk45_table_a1" if rk == 4 else "cash_karp_table_a2"]
+    return [float(Fraction(x)) for x in t["c"]], [float(Fraction(x)) for x in t["b"]]
+
+
+@pytest.mark.parametrize("rk", [3, 2, 4, 5])
 def test_planet_moves_with_the_stage_times(rk):
     """SSP(3,3) evaluates the planet at t^n + c_i dt with c = (0, 1, 1/2) (reading
     R4) and weighs the stages by b = (1/6, 1/6, 2/3); SSP(2,2) is Heun's
-    c = (0, 1), b = (1/2, 1/2) (reading R5).  Cold resting gas near the
+    c = (0, 1), b = (1/2, 1/2) (reading R5); SSP-RK(4,5) and Cash-Karp use the
+    c and b printed in Tables A1 and A2.  Cold resting gas near the
     planet: after one step the momentum is -dt sum_i b_i rho grad Phi_p(t_i),
     projected with the m-point rule, up to O(dt^3) couplings through the flux,
     i.e. O(dt^2) relative to the O(dt) momentum: halving dt cuts the relative
@@ -425,10 +443,8 @@ def test_planet_moves_with_the_stage_times(rk):
         o = oracle.Oracle(cfg)
         o.step_dt(1, dt)
         m = o.fetch()[1:3]
-        if rk == 3:
-            expect = dt * (source(0.0) / 6.0 + source(dt) / 6.0 + 2.0 * source(0.5 * dt) / 3.0)
-        else:
-            expect = dt * (source(0.0) / 2.0 + source(dt) / 2.0)
+        c, b = _stage_times_and_weights(rk)
+        expect = dt * sum(bi * source(ci * dt) for ci, bi in zip(c, b))
         err.append(np.abs(m - expect).max() / np.abs(expect).max())
     assert err[0] / err[1] > 3.3, err
     assert err[1] < 2e-3, err
