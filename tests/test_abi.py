@@ -116,3 +116,18 @@ def test_every_validation_rule_returns_its_documented_code(L, edit, code):
     with pytest.raises(dg.DgError) as e:
         dg.dg_workspace_bytes(_bad(edit))
     assert e.value.code == code
+
+
+def test_no_cpu_fallback_without_a_device(L):
+    """Without a CUDA device the binding raises instead of computing anything:
+    through PyTorch's allocator, and through dg_init's own allocation."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1805_01443_gb300 import inputs
+    cfg = inputs.disc_small(8, 2)
+    with pytest.raises(RuntimeError, match="no CPU path"):
+        dg.Disc(cfg)
+    with pytest.raises(dg.DgError) as e:
+        dg.Disc(cfg, torch_memory=False)
+    assert e.value.code in (dg.DG_ERR_NOMEM, dg.DG_ERR_CUDA)
