@@ -901,3 +901,22 @@ def test_paper_disc_steps_under_the_positivity_limiter():
     gz, ab = o.torque()
     assert np.isfinite(gz) and np.isfinite(ab) and ab > 0.0
     assert abs(o.fetch()[0, 0].sum() / m0 - 1.0) < 1e-3
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle parallelises over elements and reduces (CFL minimum, torque,
+    conserved sums) in a fixed element order: one thread and all threads give
+    bit-identical states, time steps and torques."""
+    cfg = inputs.disc_planet(24, 3, q=1e-4)
+    cores = oracle.nthreads()
+    out = []
+    try:
+        for nt in (1, max(cores, 2)):
+            oracle.set_threads(nt)
+            o = oracle.Oracle(cfg)
+            o.step(3)
+            out.append((o.fetch(), o.get_time(), o.torque()))
+    finally:
+        oracle.set_threads(cores)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
