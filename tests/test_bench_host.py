@@ -84,3 +84,24 @@ def test_cpu_baseline_sample_fields():
     assert cb["one_core"]["cores"] == 1 and cb["one_core"]["value"] > 0
     assert oracle.nthreads() == cb["cores"]  # the thread count is restored
     assert "16x16" in cb["sample"]
+
+
+def test_clock_summary_reads_the_median_and_the_throttle_reasons():
+    """The clocks record of the bench line: the median SM clock of the samples
+    taken under load, the maximum clock, and every throttle reason seen Active
+    (nvidia-smi csv,noheader,nounits lines in the sampler's field order)."""
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1400.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = ["0, 1200, 2070, 300, 0x8, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
