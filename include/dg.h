@@ -38,7 +38,8 @@
  *
  * Errors.  Every call returns DG_OK (0) or a negative DG_ERR_* code; a
  * description of the last error of a handle is returned by dg_last_error(h)
- * (or of the last failed dg_init by dg_last_error(NULL)).
+ * (or of the last failed call without a handle -- dg_init, dg_batch_*,
+ * dg_conserved_static -- of this thread by dg_last_error(NULL)).
  */
 #ifndef DG_H
 #define DG_H
@@ -256,17 +257,25 @@ int dg_timing(dg_handle *h, double *stage_ms, long long *nstage);
      out     device pointer to nv doubles, written
      stream  cudaStream_t the two kernels are launched on (NULL: legacy default)
    Its scratch space is a fixed array of 4096 x 4 doubles (128 KiB) inside
-   libdg.so, held by every GPU that loads the library until the process exits;
-   it limits nx*ny to DG_STATIC_MAX_ELEMENTS, and larger inputs return
-   DG_ERR_ARG without launching anything.  The first call on a device, with that
-   device current, looks up the array's device address (cudaGetSymbolAddress);
-   make that first call before any stream capture.  All calls share the one
-   array and each call overwrites every slot it later reads, so nothing needs
-   clearing between calls, but calls whose kernels overlap on the GPU (on
-   different streams or from different host threads) race on it and return
-   wrong sums: serialise them.  Asynchronous: returns once the kernels are
-   enqueued.  Errors: DG_ERR_ARG for a null pointer or a bad size, DG_ERR_CUDA
-   if the address lookup or a launch fails. */
+   libdg.so; it limits nx*ny to DG_STATIC_MAX_ELEMENTS, and larger inputs return
+   DG_ERR_ARG without launching anything.  When CUDA loads modules lazily
+   (CUDA_MODULE_LOADING=LAZY, the default of recent CUDA releases), the array
+   is committed in a device's memory by the first call made with that device
+   current -- that call looks up its device address (cudaGetSymbolAddress),
+   which loads this part of the library -- and the GPU then holds it until the
+   process exits.  So a caller that reserves all GPU memory for its own pool
+   must make one call on each device before it reserves the pool, and that
+   first call must also come before any stream capture; later calls allocate
+   nothing.  Both pointers are checked before any launch: host memory (pageable
+   or page-locked), memory of another device or an address the runtime does not
+   know returns DG_ERR_ARG.  All calls share the one array and each call
+   overwrites every slot it later reads, so nothing needs clearing between
+   calls, but calls whose kernels overlap on the GPU (on different streams or
+   from different host threads) race on it and return wrong sums: serialise
+   them.  Asynchronous: returns once the kernels are enqueued.  Errors:
+   DG_ERR_ARG for a null or non-device pointer, a bad size or no current
+   device, DG_ERR_CUDA if the address lookup or a launch fails; the reason is
+   in dg_last_error(NULL). */
 int dg_conserved_static(const double *coeffs, int nv, int nmodes, int nx, int ny, double dx,
                         double dy, double *out, void *stream);
 

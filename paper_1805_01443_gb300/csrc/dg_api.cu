@@ -603,6 +603,8 @@ int do_steps(dg_handle* h, int n, double fixed_dt) {
 
 }  // namespace
 
+int dg::set_thread_error(int code, const char* msg) { return fail(nullptr, code, "%s", msg); }
+
 extern "C" {
 
 const char* dg_last_error(dg_handle* h) { return h ? h->err : g_err; }

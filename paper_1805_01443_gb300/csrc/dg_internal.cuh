@@ -282,4 +282,7 @@ cudaError_t launch_batch_torque32(const BatchLaunch32& L, cudaStream_t s);
 cudaError_t launch_batch_finish(const BatchLaunch32& L, cudaStream_t s);
 cudaError_t launch_batch_planet32(const BatchLaunch32& L, cudaStream_t s);
 
+// Record msg as this thread's last error (dg_last_error(NULL)); returns code.
+int set_thread_error(int code, const char* msg);
+
 }  // namespace dg

@@ -2,13 +2,17 @@
 // coefficient array without any device allocation.
 //
 // Its per-block partial sums live in the file-scope device array below instead
-// of memory from cudaMalloc.  The array is part of the library image: every GPU
-// that loads libdg.so holds it (4096 blocks x 4 doubles = 128 KiB)
-// until the process exits.  In host code `g_partials` only names a host-side
-// stand-in for the symbol, so the kernels are given the device address that
+// of memory from cudaMalloc.  The array belongs to this file's module of
+// libdg.so (4096 blocks x 4 doubles = 128 KiB).  Under lazy module loading
+// (CUDA_MODULE_LOADING=LAZY, the default of recent CUDA releases) the module,
+// and with it the array, is loaded into a device's memory at the first call
+// made with that device current; from then on that GPU holds it until the
+// process exits.  In host code `g_partials` only names a host-side stand-in
+// for the symbol, so the kernels are given the device address that
 // cudaGetSymbolAddress returns, looked up once per device.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "dg_internal.cuh"
@@ -64,18 +68,47 @@ __global__ void k_static_final(const double* __restrict__ partials, int nblk, in
     for (int v = 0; v < nv; v++) out[v] = s[v][0];
 }
 
-// Device address of g_partials on the current device, looked up on the first
-// call made with that device current.
-int scratch_address(double** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DG_ERR_CUDA;
+// Device address of g_partials on device `dev` (the current device), looked
+// up on the first call made with that device current.  That lookup also loads
+// this file's module on the device when modules are loaded lazily.
+int scratch_address(int dev, double** out) {
+  if (dev >= kMaxDevices) return dg::set_thread_error(DG_ERR_CUDA, "dg_conserved_static: device index");
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return DG_ERR_CUDA;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
+    if (e != cudaSuccess || !p) {
+      char msg[160];
+      snprintf(msg, sizeof(msg), "dg_conserved_static: scratch address: %s", cudaGetErrorString(e));
+      return dg::set_thread_error(DG_ERR_CUDA, msg);
+    }
     g_addr[dev] = static_cast<double*>(p);
   }
   *out = g_addr[dev];
+  return DG_OK;
+}
+
+// DG_OK if p is device (or managed) memory that kernels on device `dev` can
+// read and write; anything else -- pageable or page-locked host memory, memory
+// of another device, an address the runtime does not know -- is refused before
+// a kernel could fault on it.
+int check_device_pointer(const void* p, int dev, const char* what) {
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // the failed query is this call's own; do not leave it behind
+    char msg[160];
+    snprintf(msg, sizeof(msg), "dg_conserved_static: %s: pointer attributes unavailable (%s)", what,
+             cudaGetErrorString(e));
+    return dg::set_thread_error(DG_ERR_ARG, msg);
+  }
+  const bool device_mem = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (!device_mem || (at.type == cudaMemoryTypeDevice && at.device != dev)) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "dg_conserved_static: %s is not device memory of the current device %d",
+             what, dev);
+    return dg::set_thread_error(DG_ERR_ARG, msg);
+  }
   return DG_OK;
 }
 
@@ -83,17 +116,41 @@ int scratch_address(double** out) {
 
 extern "C" int dg_conserved_static(const double* coeffs, int nv, int nmodes, int nx, int ny,
                                    double dx, double dy, double* out, void* stream) {
-  if (!coeffs || !out) return DG_ERR_ARG;
-  if (nv < 1 || nv > 4 || nmodes < 1 || nx < 1 || ny < 1) return DG_ERR_ARG;
-  if (!(dx > 0.0) || !(dy > 0.0)) return DG_ERR_ARG;
+  if (!coeffs || !out) return dg::set_thread_error(DG_ERR_ARG, "dg_conserved_static: null pointer");
+  if (nv < 1 || nv > 4 || nmodes < 1 || nx < 1 || ny < 1)
+    return dg::set_thread_error(DG_ERR_ARG, "dg_conserved_static: bad nv, nmodes, nx or ny");
+  if (!(dx > 0.0) || !(dy > 0.0))
+    return dg::set_thread_error(DG_ERR_ARG, "dg_conserved_static: dx and dy must be > 0");
   const long long nel = (long long)nx * ny;
-  if (nel > (long long)DG_STATIC_MAX_ELEMENTS) return DG_ERR_ARG;
+  if (nel > (long long)DG_STATIC_MAX_ELEMENTS)
+    return dg::set_thread_error(DG_ERR_ARG,
+                                "dg_conserved_static: nx * ny above DG_STATIC_MAX_ELEMENTS (1048576)");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+    cudaGetLastError();
+    return dg::set_thread_error(DG_ERR_ARG, "dg_conserved_static: no current CUDA device");
+  }
+  int rc = check_device_pointer(coeffs, dev, "coeffs");
+  if (rc == DG_OK) rc = check_device_pointer(out, dev, "out");
+  if (rc != DG_OK) return rc;
   const int nblk = (int)((nel + kThreads - 1) / kThreads);
   double* partials = nullptr;
-  int rc = scratch_address(&partials);
+  rc = scratch_address(dev, &partials);
   if (rc != DG_OK) return rc;
+  // launched through cudaLaunchKernel so that each launch's own status is
+  // returned, not an earlier, unrelated error left in the runtime's record
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_static_part<<<nblk, kThreads, 0, s>>>(coeffs, nv, nmodes, nel, dx * dy, partials);
-  k_static_final<<<1, kThreads, 0, s>>>(partials, nblk, nv, out);
-  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+  double area = dx * dy;
+  void* a1[] = {(void*)&coeffs, (void*)&nv, (void*)&nmodes, (void*)&nel, (void*)&area, (void*)&partials};
+  cudaError_t e = cudaLaunchKernel((const void*)k_static_part, dim3(nblk), dim3(kThreads), a1, 0, s);
+  if (e == cudaSuccess) {
+    void* a2[] = {(void*)&partials, (void*)&nblk, (void*)&nv, (void*)&out};
+    e = cudaLaunchKernel((const void*)k_static_final, dim3(1), dim3(kThreads), a2, 0, s);
+  }
+  if (e != cudaSuccess) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "dg_conserved_static: launch: %s", cudaGetErrorString(e));
+    return dg::set_thread_error(DG_ERR_CUDA, msg);
+  }
+  return DG_OK;
 }

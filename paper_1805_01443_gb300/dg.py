@@ -398,17 +398,20 @@ def dg_timing(d):
 
 def dg_conserved_static(coeffs, dx, dy, out, stream=None):
     """Allocation-free conserved sums of a canonical FP64 device tensor `coeffs`
-    of shape (nv, nmodes, ny, nx) into the FP64 device tensor `out` (nv values),
-    enqueued on `stream` (default: PyTorch's current stream).  Raises DgError
-    on a bad argument or a CUDA failure."""
+    of shape (nv, nmodes, ny, nx) into the FP64 device tensor `out` (nv values,
+    on the same device), enqueued on `stream` (default: PyTorch's current
+    stream of that device).  The call is made with coeffs' device current.
+    Raises DgError on a bad argument or a CUDA failure."""
     import torch
     nv, nmodes, ny, nx = coeffs.shape
     assert coeffs.dtype == torch.float64 and coeffs.is_cuda and coeffs.is_contiguous()
     assert out.dtype == torch.float64 and out.is_cuda and out.numel() >= nv
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
-    rc = lib().dg_conserved_static(ctypes.c_void_p(coeffs.data_ptr()), nv, nmodes, nx, ny, dx, dy,
-                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
+    assert out.device == coeffs.device, "coeffs and out on different devices"
+    with torch.cuda.device(coeffs.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(coeffs.device).cuda_stream
+        rc = lib().dg_conserved_static(ctypes.c_void_p(coeffs.data_ptr()), nv, nmodes, nx, ny, dx, dy,
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream or 0))
     if rc != DG_OK:
         raise DgError(rc, "dg_conserved_static")
 

@@ -50,6 +50,43 @@ def test_conserved_static_matches_dg_conserved_on_two_calls_in_a_row():
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
 
 
+@pytest.mark.gpu
+def test_conserved_static_allocates_nothing_after_the_first_call():
+    """The property the call exists for: once a first call has loaded the
+    library's scratch array on the device, a call changes neither the device's
+    free memory (cudaMemGetInfo) nor PyTorch's allocator counters."""
+    import torch
+
+    L = dg.lib()
+    cfg = inputs.disc_planet(64, 2)
+    with dg.Disc(cfg) as d:
+        d.step(1)
+        ref = d.conserved()
+        host = d.fetch()
+    dev = torch.from_numpy(host).to("cuda")
+    out = torch.zeros(host.shape[0], dtype=torch.float64, device="cuda")
+    nv, nmodes, ny, nx = dev.shape
+    dx, dy = _spacing(cfg)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (ctypes.c_void_p(dev.data_ptr()), nv, nmodes, nx, ny, dx, dy, ctypes.c_void_p(out.data_ptr()),
+            stream)
+    assert L.dg_conserved_static(*args) == dg.DG_OK  # the warm-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    allocated0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert L.dg_conserved_static(*args) == dg.DG_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == allocated0
+    for key in ("allocation.all.allocated", "segment.all.allocated"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
 def test_conserved_static_rejects_bad_sizes_before_any_launch():
     """Sizes above DG_STATIC_MAX_ELEMENTS and null pointers are refused on the host
     (no CUDA call is made, so this runs without a GPU)."""
@@ -59,3 +96,17 @@ def test_conserved_static_rejects_bad_sizes_before_any_launch():
     assert L.dg_conserved_static(None, 3, 25, 8, 8, 1.0, 1.0, fake, None) == dg.DG_ERR_ARG
     assert L.dg_conserved_static(fake, 5, 25, 8, 8, 1.0, 1.0, fake, None) == dg.DG_ERR_ARG
     assert L.dg_conserved_static(fake, 3, 25, 8, 8, 0.0, 1.0, fake, None) == dg.DG_ERR_ARG
+
+
+def test_conserved_static_refuses_host_memory():
+    """Host arrays (here numpy's) are refused with DG_ERR_ARG before any launch,
+    with a GPU (the pointer is not device memory) and without one (there is no
+    current device)."""
+    L = dg.lib()
+    coeffs = np.zeros((3, 9, 8, 8))
+    out = np.zeros(3)
+    rc = L.dg_conserved_static(coeffs.ctypes.data_as(ctypes.c_void_p), 3, 9, 8, 8, 1.0, 1.0,
+                               out.ctypes.data_as(ctypes.c_void_p), None)
+    assert rc == dg.DG_ERR_ARG
+    assert b"dg_conserved_static" in L.dg_last_error(None)
+    assert np.all(out == 0.0)
