@@ -36,18 +36,22 @@ WORKLOAD = "planet-disc P4 512x512 (q=3e-5, damping 0.4/2.1, SSP(3,3), torque ev
 # u^(s+1) written on average over the 3 SSP(3,3) stages)
 FLOP_PER_ELEM_STAGE = 10.0e3
 BYTES_PER_ELEM_STAGE_FP64 = 1600.0
-# precision form (FP32 delta, 75 floats = 300 B per element and array): a stage
-# reads delta^(s), delta^n (stages 2, 3) and R_b and writes delta^(s+1); the
-# last stage also reads the background averages (12 B) and, in the tiles that
-# touch a damping zone (53.5 % of the 32-element tiles at 512^2), the damping
-# offsets (300 B): (900 + 1200 + 1200 + 12 + 160) / 3 = 1157 B per element and
-# stage launch.  The torque pass reads delta Sigma (100 B) and Sigma_b at the
-# nodes as a float pair (200 B) once per step.
-BYTES_PER_ELEM_STAGE_PREC = 1157.0
+# precision form, algorithmic bytes: the FP32 state of 75 floats = 300 B per
+# element, read u^(s) (and u^n in stages 2 and 3) and written u^(s+1):
+# (2 + 3 + 3) / 3 x 300 = 800 B per element and stage launch, half the FP64
+# figure.  The background residual R_b, the background averages and the
+# damping offsets are static data of this design, not algorithmic bytes:
+# every stage also reads R_b (RB_BYTES_PER_ELEM), the last stage the
+# background averages (12 B) and, in the tiles that touch a damping zone
+# (53.5 % of the 32-element tiles at 512^2), the damping offsets (300 B).
+BYTES_PER_ELEM_STAGE_PREC = 800.0
+RB_BYTES_PER_ELEM = 300.0
+DESIGN_BYTES_PER_ELEM_STAGE_PREC = (BYTES_PER_ELEM_STAGE_PREC + RB_BYTES_PER_ELEM
+                                    + (12.0 + 0.535 * 300.0) / 3.0)
 BYTES_PER_ELEM_TORQUE_PREC = 300.0
 # DRAM bytes (read + write) per stage launch of k_stage32<4> at 512^2, the mean
 # over the three stages of one step from one ncu capture of the current kernel
-# (profiles/k_stage32_p4_disc512.md: 214.8, 301.0 and 365.6 MB)
+# (214.8, 301.0 and 365.6 MB)
 TRAFFIC_PER_STAGE_PREC = 293.8e6
 # FP64 peak of GB300 derived from unit counts and clock: 2 FP64 FMA / clk / SM
 # x 152 SMs x 2 flop x 2.07 GHz = 1.26 TFLOP/s
@@ -332,6 +336,17 @@ def indicator_run():
     return rec
 
 
+def indicator_pass(n, reps, warmup):
+    """The learned indicator's limit pass alone (the profiling case of its
+    inference kernel): mean ms per pass on the n^2 P3 shock-ring disc."""
+    import torch  # noqa: F401
+    from paper_1805_01443_gb300 import indicator
+    ms = indicator.limit_pass_ms(n=n, order=3, reps=reps, warmup=warmup)
+    print(json.dumps({"workload": "limit pass, learned indicator, P3 %d^2 shock ring" % n,
+                      "elements": n * n, "ms_per_pass": ms}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,7 +362,12 @@ def main():
     ap.add_argument("--n", type=int, default=512, help="mesh size (profiling cases only)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-disc batched workload")
     ap.add_argument("--no-indicator", action="store_true", help="skip the learned-indicator workload")
+    ap.add_argument("--indicator-pass", type=int, default=0, metavar="N",
+                    help="profiling case: time `--steps` limit passes of the learned indicator on the "
+                         "N^2 P3 shock-ring disc, print one JSON line and exit")
     args = ap.parse_args()
+    if args.indicator_pass > 0:
+        return indicator_pass(args.indicator_pass, args.steps, args.warmup)
 
     import copy
 
@@ -428,7 +448,9 @@ def main():
                     "traffic": TRAFFIC_PER_STAGE_PREC if (n_el == 512 * 512 and cfg["order"] == 4) else None,
                     "kernel": "k_stage32<4> (precision-form fused RK stage)",
                     "peak_source": hbm_src, "stage_us": stage_s * 1e6,
-                    "algorithmic_bytes_per_element": BYTES_PER_ELEM_STAGE_PREC}
+                    "algorithmic_bytes_per_element": BYTES_PER_ELEM_STAGE_PREC,
+                    "design_bytes_per_element": DESIGN_BYTES_PER_ELEM_STAGE_PREC,
+                    "design_achieved": DESIGN_BYTES_PER_ELEM_STAGE_PREC * n_el / stage_s / 1e9}
         d64, ms64, stage64, clocks64 = timed_run(dg, torch, cfg, args.fp64_steps, 2, local, pg)
         d64.close()
         fp64 = {"value": world * dof * stages_per_step * args.fp64_steps / (ms64 / 1e3),

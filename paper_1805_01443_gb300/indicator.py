@@ -191,45 +191,32 @@ def induced_error(net, cfg, steps, threshold=0.0):
     return out
 
 
-def _main(argv=None):
-    """`python -m paper_1805_01443_gb300.indicator pass --n N --order P --reps K`:
-    K limit passes with a seeded untrained network (limiter 2) on the N^2
-    shock-ring disc, timed with CUDA events; prints one JSON line."""
-    import argparse
-    import json
+def limit_pass_ms(n=1024, order=3, reps=5, warmup=2):
+    """Mean time in ms of one limit pass with a seeded untrained network
+    (limiter 2; the kernels' work does not depend on the weights) on the n^2
+    shock-ring disc of degree `order`, timed with CUDA events over `reps`
+    passes after `warmup` untimed ones."""
     import torch
     from . import inputs
-    ap = argparse.ArgumentParser(prog="python -m paper_1805_01443_gb300.indicator")
-    ap.add_argument("what", choices=["pass"])
-    ap.add_argument("--n", type=int, default=1024)
-    ap.add_argument("--order", type=int, default=3)
-    ap.add_argument("--reps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=2)
-    args = ap.parse_args(argv)
-    cfg = inputs.shock_ring(args.n, args.order)
+    cfg = inputs.shock_ring(n, order)
     cfg["disc"]["limiter"] = 2
     d = dg.Disc(cfg)
-    net = dg.Mlp(5 * 4 * (args.order + 1) ** 2, seed=1)
+    net = dg.Mlp(5 * 4 * (order + 1) ** 2, seed=1)
     try:
         d.set_indicator(net, 0.0)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             d.limit()
         d.sync()
         torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(args.reps):
+        a.record(stream)
+        for _ in range(reps):
             d.limit()
-        b.record()
+        b.record(stream)
         b.synchronize()
-        ms = a.elapsed_time(b) / max(args.reps, 1)
+        return a.elapsed_time(b) / max(reps, 1)
     finally:
         net.close()
         d.close()
-    print(json.dumps({"workload": "limit pass, learned indicator, P%d %d^2 shock ring" % (args.order, args.n),
-                      "elements": args.n * args.n, "ms_per_pass": ms}))
-
-
-if __name__ == "__main__":
-    _main()
