@@ -209,3 +209,129 @@ def test_shock_ring_pressure_step():
             elif R[j, i] > 1.5 + dx:
                 assert np.array_equal(ur[3, :, j, i], ud[3, :, j, i])
     assert checked > 50
+
+
+# ---- worked cases: the values the limiters produce, computed by hand ----------
+#
+# A periodic 3 x 3 mesh of elements dx = 0.5 by dy = 0.25 (box [0, 1.5] x
+# [0, 0.75]).  Element means rho(i, j) = a_i + b_j with a = (1.0, 1.5, 1.7) and
+# b = (0.0, 0.4, 0.5), so the centre element (1, 1) sees
+#   x: forward difference 1.7 - 1.5 = 0.2, backward 1.5 - 1.0 = 0.5
+#   y: forward difference 0.5 - 0.4 = 0.1, backward 0.4 - 0.0 = 0.4
+# Its face increments (the linear mode times phi_1(+1) = sqrt(3)) are 0.35 in x
+# and -0.3 in y; every other element has no linear mode and is never troubled.
+# Plain minmod (M = 0) gives minmod(0.35, 0.2, 0.5) = 0.2 in x and
+# minmod(-0.3, 0.1, 0.4) = 0 in y.  The TVB bound M h^2 keeps the x increment
+# for M >= 0.35 / 0.5^2 = 1.4 and the y increment for M >= 0.3 / 0.25^2 = 4.8.
+
+SQ3 = math.sqrt(3.0)
+
+
+def tvb_worked_case(p, tvb_m):
+    cfg = inputs.uniform_state(3, p, kind=1)
+    cfg["mesh"].update({"x1": 1.5, "y1": 0.75, "bc": 0})
+    cfg["disc"].update({"limiter": 1, "tvb_m": tvb_m, "positivity": 0})
+    o = oracle.Oracle(cfg)
+    m = p + 1
+    rng = np.random.default_rng(11)
+    u = np.zeros(o.shape)
+    u[:, 1:] = rng.uniform(-0.05, 0.05, size=u[:, 1:].shape)  # higher modes everywhere
+    u[:, m] = 0.0   # no linear modes ...
+    u[:, 1] = 0.0
+    a, b = np.array([1.0, 1.5, 1.7]), np.array([0.0, 0.4, 0.5])
+    u[0, 0] = a[None, :] + b[:, None]
+    u[1:, 0] = np.array([0.1, -0.2, 3.0])[:, None, None]
+    u[0, m, 1, 1] = 0.35 / SQ3   # ... except the centre element's density
+    u[0, 1, 1, 1] = -0.3 / SQ3
+    o.set_state(u)
+    return o, u
+
+
+@pytest.mark.parametrize("tvb_m,flag", [(0.0, 1), (1.39, 1), (1.41, 1), (4.79, 1), (4.81, 0), (50.0, 0)])
+def test_tvb_flag_flips_at_m_h_squared(tvb_m, flag):
+    o, _ = tvb_worked_case(2, tvb_m)
+    f = o.indicator(tvb_m)
+    expect = np.zeros((3, 3), np.uint8)
+    expect[1, 1] = flag
+    np.testing.assert_array_equal(f, expect)
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+@pytest.mark.parametrize("tvb_m,sx,sy", [(0.0, 0.2, 0.0), (1.39, 0.2, 0.0), (3.0, 0.35, 0.0)])
+def test_tvb_limited_linear_modes_worked_case(p, tvb_m, sx, sy):
+    """The troubled centre element becomes its means plus the limited face
+    increments divided by sqrt(3); all its other modes vanish, in every
+    variable; the other elements are untouched."""
+    o, u = tvb_worked_case(p, tvb_m)
+    o.limit()
+    v = o.fetch()
+    m = p + 1
+    c = v[:, :, 1, 1]
+    np.testing.assert_array_equal(c[:, 0], u[:, 0, 1, 1])
+    assert c[0, m] == pytest.approx(sx / SQ3, rel=1e-15, abs=1e-17)
+    assert c[0, 1] == pytest.approx(sy / SQ3, abs=1e-17)
+    rest = np.ones(m * m, bool)
+    rest[[0, 1, m]] = False
+    assert np.all(c[:, rest] == 0.0)
+    assert np.all(c[1:, [1, m]] == 0.0)
+    others = np.ones((3, 3), bool)
+    others[1, 1] = False
+    np.testing.assert_array_equal(v[..., others], u[..., others])
+
+
+# A single P1 element (periodic 1 x 1 mesh, so it is its own neighbour) with
+# mean density 1 and face increment sqrt(3) u_10 = 1.5 in x: the density is
+# negative at the face x = -1 (a check point) but positive at the volume
+# nodes xi = +-1/sqrt(3).  Zhang & Shu's scaling (Sec. 2.4) with eps = 1e-13
+# is theta = (1 - eps) / (1 - rho_min), applied to every non-mean mode of the
+# density.  Then the pressure: uniform density 1, no momentum,
+# energy mean 1 and energy increment 2 give p = 0.4 (1 + 2 xi), -0.4 at
+# x = -1 against a mean pressure 0.4: theta = (0.4 - eps) / (0.4 + 0.4) on
+# the non-mean modes of every variable.
+
+def positivity_element_case():
+    cfg = inputs.uniform_state(1, 1, kind=1)
+    cfg["disc"].update({"positivity": 1, "limiter": 0})
+    o = oracle.Oracle(cfg)
+    return o
+
+
+def test_positivity_theta_for_the_density_closed_form():
+    o = positivity_element_case()
+    u = np.zeros(o.shape)
+    u[0, 0] = 1.0
+    u[0, 2] = 1.5 / SQ3          # mode (1, 0) of the density
+    u[0, 1] = 0.01               # mode (0, 1): +-0.01 sqrt(3) at the face points
+    u[3, 0] = 5.0                # plenty of energy: the pressure stays positive
+    o.set_state(u)
+    o.limit()
+    v = o.fetch()
+    # rho = 1 + 1.5 xi + 0.01 sqrt(3) eta; its smallest check-point value is at
+    # the face x = -1, eta = -1/sqrt(3): 1 - 1.5 - 0.01 = -0.51 (the face
+    # y = -1 gives 1 - 1.5/sqrt(3) - 0.01 sqrt(3) > 0, the volume nodes more)
+    theta = (1.0 - 1e-13) / (1.0 + 0.51)
+    assert theta == pytest.approx(0.66225165563, rel=1e-10)
+    np.testing.assert_allclose(v[0, 1:], theta * u[0, 1:], rtol=1e-14, atol=0)
+    assert v[0, 0] == 1.0
+    np.testing.assert_array_equal(v[1:], u[1:])
+
+
+def test_positivity_theta_for_the_pressure_closed_form():
+    o = positivity_element_case()
+    u = np.zeros(o.shape)
+    u[0, 0] = 1.0
+    u[3, 0] = 1.0
+    u[3, 2] = 2.0 / SQ3          # energy increment 2 in x
+    u[3, 1] = 0.1                # and a y mode that the scaling shrinks too
+    u[1, 3] = 0.02               # a momentum mode (1, 1), small enough to keep rho v^2 tiny
+    o.set_state(u)
+    o.limit()
+    v = o.fetch()
+    # at the check point x = -1, eta = -1/sqrt(3): E = 1 - 2 - 0.1 = -1.1 and
+    # the kinetic term 0.5 (0.02 * sqrt(3) * (-1) * (-1))^2 = 0.0006, so
+    # p = 0.4 (-1.1 - 0.0006); the mean pressure is 0.4
+    pmin = 0.4 * (-1.1 - 0.5 * (0.02 * 3.0 * (-1.0 / SQ3) * (-1.0)) ** 2)
+    theta = (0.4 - 1e-13) / (0.4 - pmin)
+    assert theta == pytest.approx(0.4 / (0.4 + 0.44024), rel=1e-10)
+    np.testing.assert_allclose(v[:, 1:], theta * u[:, 1:], rtol=1e-13, atol=0)
+    np.testing.assert_array_equal(v[:, 0], u[:, 0])

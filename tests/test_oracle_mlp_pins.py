@@ -87,3 +87,59 @@ def test_features_scale_invariance_and_periodic_shift():
         for i in range(8):
             np.testing.assert_array_equal(f1[j * nx + (i + 1) % nx], f0[j * nx + i])
     assert np.abs(f0).max() == 1.0
+
+
+def _hand_net(nin):
+    """A hand-set network whose logit is worked out below: only a few weights
+    and biases are non-zero, and every pre-activation is either 0, 1, far
+    above zero (GELU(x) = x to ~1e-40 for x >= 14) or far below it (GELU(x)
+    ~ 0 for x <= -20)."""
+    H = mlp.H
+    W1 = np.zeros((H, nin), np.float32)
+    b1 = np.zeros(H, np.float32)
+    W2 = np.zeros((H, H), np.float32)
+    b2 = np.zeros(H, np.float32)
+    w3 = np.zeros(H, np.float32)
+    W1[0, 0] = 1.0
+    W1[1, 0] = 3.0
+    W1[2, 1] = -1.0       # reads the second input only (catches a transposed W1)
+    b1[0] = 2.0
+    W2[0, 0] = 0.5 + 2.0 ** -12   # not a BF16 value: rounds to 0.5
+    W2[0, 1] = 0.25
+    W2[1, 0] = -2.0
+    W2[2, 2] = 1.0
+    b2[0] = 5.0
+    b2[2] = 1.0
+    w3[0] = -0.25
+    w3[1] = 1.0
+    w3[2] = 2.0
+    b3 = np.array([0.5], np.float32)
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, w3, b3])
+
+
+def test_forward_of_a_hand_set_network():
+    """Worked by hand.  x = (12, 0, ...):
+         layer 1: a = (12 + 2, 36, 0, ...)            -> h1 = (14, 36, 0, ...)
+         layer 2: a = (0.5*14 + 0.25*36 + 5, -2*14, 0 + 1) = (21, -28, 1)
+                                                      -> h2 = (21, ~0, Phi(1))
+         logit:   -0.25*21 + 1*~0 + 2*Phi(1) + 0.5
+       (GELU(1) = Phi(1), the standard normal CDF at 1, a table value).
+       x = (12, -14): unit 2 of layer 1 sees 14, so unit 2 of layer 2 sees
+       14 + 1 = 15 and the logit is -5.25 + 2*15 + 0.5 = 25.25.
+       x = (12, 20): unit 2 of layer 1 sees -20, GELU(-20) ~ -6e-88, and the
+       logit is the first case's.
+       A dropped bias, GELU on the logit, no GELU on a hidden layer, W1 or W2
+       read transposed, or weights not rounded to BF16 (W2[0, 0] = 0.5 + 2^-12
+       would add 14 * 2^-12 / 4 to the logit) each change one of the three."""
+    nin = 5
+    params = _hand_net(nin)
+    x = np.zeros((3, nin))
+    x[:, 0] = 12.0
+    x[1, 1] = -14.0
+    x[2, 1] = 20.0
+    z = mlp.forward(params, x, nin)
+    phi1 = 0.8413447460685429  # standard normal CDF at 1 (table value)
+    z0 = -0.25 * 21.0 + 2.0 * phi1 + 0.5
+    assert z[0] == pytest.approx(z0, rel=0, abs=1e-15)
+    assert z[1] == pytest.approx(25.25, rel=0, abs=1e-14)
+    assert z[2] == pytest.approx(z0, rel=0, abs=1e-15)
