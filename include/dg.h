@@ -279,6 +279,30 @@ int dg_timing(dg_handle *h, double *stage_ms, long long *nstage);
 int dg_conserved_static(const double *coeffs, int nv, int nmodes, int nx, int ny, double dx,
                         double dy, double *out, void *stream);
 
+/* dg_selftest_wait -- a check of the library's bounded device-side waits.  The
+   paper has no counterpart.  Every wait of a libdg kernel on something another
+   agent completes (a bulk copy landing on an mbarrier, tensor-core MMAs
+   committing to one, CTAs of the same persistent launch advancing a counter)
+   gives up after a limit, records DG_ERR_TIMEOUT in the handle's status word
+   and lets the kernel exit, so a defect cannot hang the GPU.  This call makes
+   such a wait run out on purpose: one CTA waits, with the product kernels'
+   own wait helper, on something nothing will complete, and reports how it
+   ended.
+     kind  0: an mbarrier that no copy and no thread arrives on (the stage
+              kernel's wait on its damping-offset copy, about 0.3 s);
+           1: the same while the CTA holds tensor memory (the tensor-core
+              inference kernel's waits), which the CTA frees before it exits;
+           2: a counter in global memory that one CTA of a two-CTA cooperative
+              launch never advances (the persistent batched kernel's waits
+              between stages, 0.5 s).
+     freed receives 1 if the CTA freed its tensor memory (kind 1), else 0
+           (may be NULL).
+   Returns DG_ERR_TIMEOUT when the wait gave up as designed (the expected
+   result), DG_OK if it did not, DG_ERR_ARG for another kind and DG_ERR_CUDA
+   if a CUDA call failed.  Uses the legacy default stream and synchronises the
+   device. */
+int dg_selftest_wait(int kind, int *freed);
+
 /* ---- Troubled cells and limiters (FP64 form; DG_ERR_UNSUPPORTED otherwise) --
    The TVB-modified minmod test of Cockburn & Shu, the limited-P1 reduction of
    troubled elements and the positivity limiter of Sec. 2.4 (Zhang & Shu), as

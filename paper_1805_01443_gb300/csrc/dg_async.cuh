@@ -48,6 +48,40 @@ __device__ __forceinline__ bool mbar_wait(void* bar, unsigned parity) {
   return false;
 }
 
+// ---- counters in global memory (waits between CTAs of one launch) ---------
+// Only for CTAs that are resident together: a cooperative launch, or CTAs of
+// one launch that wait only for work other running CTAs have already taken.
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// add 1 to *ctr with release semantics (this CTA's earlier writes, made
+// visible to the GPU by the caller's __threadfence, are ordered before it)
+__device__ __forceinline__ void counter_signal(int* ctr) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");
+}
+__device__ __forceinline__ int counter_load(const int* ctr) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+  return v;
+}
+// bounded wait until *ctr >= target: false once ~limit_ns have passed on the
+// GPU's global timer (or 2^26 polls, whichever comes first), so that a
+// counter nobody advances cannot hang the GPU
+__device__ __forceinline__ bool counter_wait(const int* ctr, int target, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < (1 << 26); i++) {
+    if (counter_load(ctr) >= target) return true;
+    if (i >= 16) {
+      __nanosleep(128);
+      if ((i & 63) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
+  }
+  return false;
+}
+
 // ---- programmatic dependent launch (consecutive kernels on one stream) ----
 // Wait until the grid this launch depends on has completed and its writes are
 // visible (an ordinary launch returns at once); called first in a kernel, so

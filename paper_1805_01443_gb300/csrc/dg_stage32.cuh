@@ -892,7 +892,8 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
 // terms w_n m_n (r_n - r_p) / (|r_n - r_p|^2 + eps^2)^{3/2} are large and
 // cancel to a few 1e-5 of their absolute sum, and their absolute sum is
 // spread evenly over the decades of distance from the planet, so every term
-// is evaluated and summed in float-float arithmetic (~2^-44 relative): node
+// is evaluated, and summed over the element's nodes, in float-float
+// arithmetic (~2^-44 relative); the sums over elements are FP64: node
 // mass Sigma_b (a float pair from the FP64 background) + delta Sigma, offsets
 // from the planet as float pairs from the FP64 position, the inverse cube by
 // one float-float Newton correction.  delta Sigma at the nodes is contracted
@@ -902,8 +903,9 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
 // at sD[(M + n) * 32]) so that no contraction operand stays live through the
 // node loop.  The x offset depends on the node row q only and the y offset on
 // the node column r only, so the force sums as sum_q dx_q (sum_r f_qr) and
-// sum_r dy_r (sum_q f_qr).  The per-tile pair is stored as a double; the
-// finish kernel sums the tiles in FP64.
+// sum_r dy_r (sum_q f_qr).  Each element's pair is rounded to a double and
+// the warp sums its elements in FP64; the finish kernel sums the tiles in
+// FP64.
 template <int P>
 __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN, const DevState* ts,
                                               double* part, const Mesh& ms, const Prec32& pc, int tile,
@@ -1014,16 +1016,17 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
 #pragma unroll
     for (int r = 0; r < m; r++) gy = f2_add_u(gy, f2_mul_u(C[r], py[r]));
   }
-  // warp sum of the pairs
+  // the element's sums to FP64, then the warp's sum over its elements in FP64
+  double ex = (double)gx.h + (double)gx.l, ey = (double)gy.h + (double)gy.l;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    gx = f2_add(gx, F2{__shfl_xor_sync(0xffffffffu, gx.h, o), __shfl_xor_sync(0xffffffffu, gx.l, o)});
-    gy = f2_add(gy, F2{__shfl_xor_sync(0xffffffffu, gy.h, o), __shfl_xor_sync(0xffffffffu, gy.l, o)});
+    ex += __shfl_xor_sync(0xffffffffu, ex, o);
+    ey += __shfl_xor_sync(0xffffffffu, ey, o);
   }
   if (lane == 0) {
     const double area = ms.dx * ms.dy;
-    part[2 * tile] = ((double)gx.h + (double)gx.l) * area;
-    part[2 * tile + 1] = ((double)gy.h + (double)gy.l) * area;
+    part[2 * tile] = ex * area;
+    part[2 * tile + 1] = ey * area;
   }
 }
 

@@ -32,7 +32,7 @@ EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_d
             "dg_batch_sync", "dg_batch_destroy", "dg_indicator", "dg_limit", "dg_limit_flags",
             "dg_last_flags", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_nparams", "dg_mlp_get_params",
             "dg_mlp_set_params", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step", "dg_features",
-            "dg_set_indicator", "dg_indicator_logits"]
+            "dg_set_indicator", "dg_indicator_logits", "dg_selftest_wait"]
 
 
 class DgMesh(ctypes.Structure):
@@ -130,6 +130,7 @@ def lib(build_if_missing=True):
         L.dg_batch_step.argtypes = [_VP, ctypes.c_int]
         L.dg_batch_sync.argtypes = [_VP]
         L.dg_batch_destroy.argtypes = [_VP]
+        L.dg_selftest_wait.argtypes = [ctypes.c_int, P(ctypes.c_int)]
         _lib = L
     return _lib
 

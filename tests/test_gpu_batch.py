@@ -1,12 +1,17 @@
 """Batched precision form (dg_batch_*): many discs of mixed size and degree in
-one launch per stage, against each disc stepped on its own with dg_step.
+one launch per stage, against the FP64 oracle run of each disc and against
+each disc stepped on its own with dg_step.
 
-The batched kernels run the same per-tile code on the same data in the same
-per-instance order of reductions, so the results are compared bit for bit.
+Against the oracle the precision form's stated bounds hold per instance
+(relative L2 of Sigma and momentum <= 1e-5, of the torque series <= 1e-6).
+Against per-instance steps the batched kernels run the same per-tile code on
+the same data in the same per-instance order of reductions, so the results are
+compared bit for bit.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1805_01443_gb300 import dg, inputs
 
 pytestmark = pytest.mark.gpu
@@ -27,6 +32,61 @@ def assert_same(a, b):
     np.testing.assert_array_equal(a.torque_series(), b.torque_series())
 
 
+SCHEDULES = [(0, 1, 0), (1, 1, 0), (2, 1, 0), (1, 0, 0), (2, 1, 1)]
+ORACLE_STEPS = 12
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    """Each instance of the small mixed batch (degrees 1-4, ragged tiles),
+    ORACLE_STEPS steps of the FP64 oracle: initial and final state, torque
+    series, time, and the noise-free background density."""
+    cfgs = inputs.batch_small()
+    runs = []
+    for cfg in cfgs:
+        o = oracle.Oracle(cfg)
+        u0 = o.fetch()
+        tq = []
+        for _ in range(ORACLE_STEPS):
+            o.step(1)
+            tq.append(o.torque()[0])
+        bg = dict(cfg, disc=dict(cfg["disc"], noise_amp=0.0))
+        runs.append({"u0": u0, "u": o.fetch(), "tq": np.array(tq), "t": o.get_time(),
+                     "sig_bg": oracle.Oracle(bg).fetch()[0]})
+        o.close()
+    return cfgs, runs
+
+
+@pytest.mark.parametrize("policy,dynamic,ctas", SCHEDULES)
+def test_batch_matches_the_oracle(oracle_runs, policy, dynamic, ctas):
+    """Every instance of a batched run against its own FP64 oracle run, under
+    every schedule of the batched launches."""
+    cfgs, runs = oracle_runs
+    bat = make(cfgs)
+    try:
+        for d, r in zip(bat, runs):
+            d.set_state(r["u0"])
+        with dg.Batch(bat) as b:
+            b.config(policy, dynamic, ctas)
+            b.step(ORACLE_STEPS)
+            b.sync()
+        for k, (d, r) in enumerate(zip(bat, runs)):
+            ug, uo = d.fetch(), r["u"]
+            assert rel(ug[0], uo[0]) <= 1e-5, k
+            assert max(rel(ug[1], uo[1]), rel(ug[2], uo[2])) <= 1e-5, k
+            assert rel(ug[0] - r["sig_bg"], uo[0] - r["sig_bg"]) <= 1e-4, k
+            assert rel(d.torque_series(), r["tq"]) <= 1e-6, k
+            t, _, st = d.get_time()
+            assert st == ORACLE_STEPS
+            assert abs(t - r["t"][0]) <= 1e-6 * r["t"][0], k
+    finally:
+        close(bat)
+
+
 def test_batch_equals_individual_steps():
     cfgs = inputs.batch_small()
     solo, bat = make(cfgs), make(cfgs)
@@ -43,7 +103,7 @@ def test_batch_equals_individual_steps():
         close(solo + bat)
 
 
-@pytest.mark.parametrize("policy,dynamic,ctas", [(0, 1, 0), (1, 1, 0), (2, 1, 0), (1, 0, 0), (2, 1, 1)])
+@pytest.mark.parametrize("policy,dynamic,ctas", SCHEDULES)
 def test_batch_schedules_give_identical_results(policy, dynamic, ctas):
     cfgs = inputs.batch_small()
     ref, bat = make(cfgs), make(cfgs)
