@@ -6,7 +6,12 @@ in the decision), so they are compared bit for bit on the same state.  The
 limited and positivity-limited states are compared element by element: the
 point values inside the positivity limiter are sums of products whose rounding
 order differs (<= 1e-13 of the largest coefficient).  Limited runs of the
-shock-ring disc are compared after several steps at 1e-10.
+shock-ring disc are compared after several steps element by element at 1e-12
+of the largest coefficient, with the torque at the FP64 bar (1e-12 of the sum
+of |terms|) and the TVB flags of the final state equal: no minmod decision
+flips between the two sides on these runs (measured on the GB300: at most
+1.2e-14 after 20 steps, torque within 7e-12 relative, no flag differs), so
+the FP64 bar applies unchanged.
 """
 import numpy as np
 import pytest
@@ -130,9 +135,12 @@ def test_limited_shock_ring_run_matches_oracle(p, n, steps):
         assert relmax(g.fetch(), o.fetch()) <= 1e-13
         o.step(steps)
         g.step(steps)
-        assert relmax(g.fetch(), o.fetch()) <= 1e-10
+        assert relmax(g.fetch(), o.fetch()) <= 1e-12
         assert g.get_time()[0] == pytest.approx(o.get_time()[0], rel=1e-12)
-        assert g.torque() == pytest.approx(o.torque()[0], rel=1e-8, abs=1e-12)
+        gz, asum = o.torque()
+        assert abs(g.torque() - gz) <= 1e-12 * asum
+        M = cfg["disc"]["tvb_m"]
+        np.testing.assert_array_equal(g.indicator(M), o.indicator(M))
     finally:
         g.close()
 

@@ -3,9 +3,14 @@
 Both sides receive the same seeded inputs (the oracle's projected initial data,
 plus seeded modal perturbations from paper_1805_01443_gb300.inputs) through
 dg_set_state / ref_set_state.  Tolerances (FP64 path):
-  * states: relative L2 per variable <= 1e-12;
-  * operator L(u): ||dL|| <= 1e-12 ||u|| / dt_CFL per variable (the size of the
-    stage update dt L relative to u);
+  * states: relative L2 per variable <= 1e-12, and element by element
+    max |du| <= 1e-12 max |u| per variable;
+  * operator L(u): ||dL|| <= 1e-12 ||L|| + 1e-15 ||u|| / dt_CFL per variable,
+    and the same element by element in the max norm.  L is a near-cancelling
+    sum of flux and source terms of size ~||u|| / dt_CFL (the stage update
+    dt L relative to u), whose rounding differs between the two sides; the
+    second term bounds that rounding (measured ~5e-17 of it on the GB300,
+    with ||dL|| / ||L|| at most 4e-13);
   * torque: |dGamma| <= 1e-12 sum_n |Gamma_n| (the torque is a near-cancelling sum);
   * initial projection: relative L2 <= 1e-13.
 """
@@ -49,10 +54,17 @@ def run_pair(o, g, nsteps):
     return np.array(gz_o), np.array(ab_o)
 
 
+def max_rel(a, b):
+    """Per variable: the largest element difference over the largest |element|."""
+    return np.array([np.abs(a[v] - b[v]).max() / max(np.abs(b[v]).max(), 1e-300) for v in range(a.shape[0])])
+
+
 def assert_state_parity(o, g, tol=TOL):
     uo, ug = o.fetch(), g.fetch()
     err = rel_l2(ug, uo)
     assert np.all(err <= tol), err
+    emax = max_rel(ug, uo)
+    assert np.all(emax <= tol), emax
     to, dto, so = o.get_time()
     tg, dtg, sg = g.get_time()
     assert so == sg
@@ -111,8 +123,10 @@ def test_operator_parity(kind, p, nx, ny):
     Lo, Lg = o.rhs(), g.rhs()
     dt = o.cfl_dt()
     for v in range(u0.shape[0]):
-        scale = np.linalg.norm(u0[v]) / dt
-        assert np.linalg.norm(Lg[v] - Lo[v]) <= TOL * scale, (v, np.linalg.norm(Lg[v] - Lo[v]) / scale)
+        bound = TOL * np.linalg.norm(Lo[v]) + 1e-15 * np.linalg.norm(u0[v]) / dt
+        assert np.linalg.norm(Lg[v] - Lo[v]) <= bound, (v, np.linalg.norm(Lg[v] - Lo[v]), bound)
+        bmax = TOL * np.abs(Lo[v]).max() + 1e-15 * np.abs(u0[v]).max() / dt
+        assert np.abs(Lg[v] - Lo[v]).max() <= bmax, (v, np.abs(Lg[v] - Lo[v]).max(), bmax)
     g.close()
 
 

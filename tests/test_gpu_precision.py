@@ -9,7 +9,10 @@ sums).  Stated bounds, per result:
   * torque: relative L2 of the per-step torque series <= 1e-6; on the same
     state, the precision-form torque (float-float terms) matches the FP64
     oracle to <= 1e-7 relative and <= 1e-11 of the sum of |terms|;
-  * the perturbation itself, Sigma - Sigma_bg: relative L2 <= 1e-3.
+  * the perturbation itself, Sigma - Sigma_bg, the honest measure of the
+    form's error: relative L2 <= 3e-5 after 200 steps at 128^2 (measured
+    3.8e-6 on the GB300), <= 1e-4 after 1000 steps at 512^2 (3.1e-5), and the
+    change of Sigma over one full-size 512^2 step <= 2e-5 (1.6e-6).
 """
 import numpy as np
 import pytest
@@ -76,7 +79,8 @@ def test_precision_planet_disc_p4_128_vs_oracle():
         sb = background_sigma(cfg)
         assert rel(ug[0], uo[0]) <= 1e-5
         assert max(rel(ug[1], uo[1]), rel(ug[2], uo[2])) <= 1e-5
-        assert rel(ug[0] - sb, uo[0] - sb) <= 1e-3
+        assert rel(ug[0] - sb, uo[0] - sb) <= 3e-5
+        assert np.abs(ug[0] - uo[0]).max() <= 3e-5 * np.abs(uo[0] - sb).max()
         assert rel(tg, np.array(tq)) <= 1e-6
         assert g.get_time()[2] == 200
 
@@ -151,15 +155,18 @@ def test_precision_planet_disc_p4_512_thousand_steps():
           % (e_sig, e_pert, e_tq))
     assert e_sig <= 1e-5
     assert max(rel(up[1], ua[1]), rel(up[2], ua[2])) <= 1e-5
-    assert e_pert <= 1e-3
+    assert e_pert <= 1e-4
     assert e_tq <= 1e-6
 
 
 def test_precision_planet_disc_p4_512_full_size_step_vs_oracle():
     """The benchmark's workload and launch configuration (P4 512x512, q = 3e-5,
     precision form), one SSP(3,3) step at the oracle's CFL step, against the
-    oracle directly: the whole state within the form's bounds, every element's
-    density mean within 1e-7 of the largest one, and the torque within 1e-6."""
+    oracle directly: the whole state within the form's bounds, element by
+    element within 1e-9 of each variable's largest coefficient, every
+    element's density mean within 1e-10 of the largest one, the change of
+    Sigma over the step within 2e-5, and the torque within 1e-6 (measured on
+    the GB300: 1.3e-11, 7.4e-13, 1.6e-6 and 3.5e-8)."""
     cfg = inputs.disc_planet_512()
     o = oracle.Oracle(cfg)
     dt = o.cfl_dt()
@@ -173,8 +180,10 @@ def test_precision_planet_disc_p4_512_full_size_step_vs_oracle():
     to = o.torque()[0]
     assert rel(ug[0], uo[0]) <= 1e-5
     assert max(rel(ug[1], uo[1]), rel(ug[2], uo[2])) <= 1e-5
-    assert rel(ug[0] - u0[0], uo[0] - u0[0]) <= 1e-3
-    assert np.abs(ug[0, 0] - uo[0, 0]).max() <= 1e-7 * np.abs(uo[0, 0]).max()
+    for v in range(3):
+        assert np.abs(ug[v] - uo[v]).max() <= 1e-9 * np.abs(uo[v]).max(), v
+    assert rel(ug[0] - u0[0], uo[0] - u0[0]) <= 2e-5
+    assert np.abs(ug[0, 0] - uo[0, 0]).max() <= 1e-10 * np.abs(uo[0, 0]).max()
     assert abs(tg - to) <= 1e-6 * abs(to)
 
 
