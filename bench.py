@@ -41,13 +41,20 @@ BYTES_PER_ELEM_STAGE_FP64 = 1600.0
 # (2 + 3 + 3) / 3 x 300 = 800 B per element and stage launch, half the FP64
 # figure.  The background residual R_b, the background averages and the
 # damping offsets are static data of this design, not algorithmic bytes:
-# every stage also reads R_b (RB_BYTES_PER_ELEM), the last stage the
-# background averages (12 B) and, in the tiles that touch a damping zone
-# (53.5 % of the 32-element tiles at 512^2), the damping offsets (300 B).
+# a stage also reads R_b (300 B per element) in the tiles that keep it, the
+# last stage the background averages (12 B) and, in the tiles that touch a
+# damping zone, the damping offsets (300 B); design_bytes() counts them from
+# the handle's own tile counts.
 BYTES_PER_ELEM_STAGE_PREC = 800.0
-RB_BYTES_PER_ELEM = 300.0
-DESIGN_BYTES_PER_ELEM_STAGE_PREC = (BYTES_PER_ELEM_STAGE_PREC + RB_BYTES_PER_ELEM
-                                    + (12.0 + 0.535 * 300.0) / 3.0)
+
+
+def design_bytes(ntiles, rb_tiles, zone_tiles):
+    """Bytes per element and stage launch of the precision-form stage kernel
+    with its static data (see above), averaged over the three stages."""
+    return (BYTES_PER_ELEM_STAGE_PREC + 300.0 * rb_tiles / ntiles
+            + (12.0 + 300.0 * zone_tiles / ntiles) / 3.0)
+
+
 BYTES_PER_ELEM_TORQUE_PREC = 300.0
 # DRAM bytes (read + write) per stage launch of k_stage32<4> at 512^2, the mean
 # over the three stages of one step from one ncu capture of the current kernel
@@ -313,9 +320,11 @@ def batched_run(dg, torch, steps=10, tune_steps=3):
             "sequential": {"value": dof * 3 / (seq_ms / 1e3), "ms_per_step": seq_ms,
                            "how": "per-instance dg_step launches in turn on one stream"},
             "speedup_vs_sequential": seq_ms / bat_ms, "steps": steps,
-            "schedule": {"policy": dg.Batch.POLICIES[tuned["policy"]], "dynamic": tuned["dynamic"],
-                         "ctas_per_sm": tuned["ctas_per_sm"]},
-            "gpu_launches_per_step": 5,
+            "schedule": {"policy": dg.Batch.POLICIES[tuned["policy"]],
+                         "launches": ["one CTA per tile per stage", "persistent CTAs per stage",
+                                      "one persistent launch per step"][tuned["dynamic"]],
+                         "ctas_per_sm": tuned["ctas_per_sm"], "tiles_per_item": tuned["tiles_per_item"]},
+            "gpu_launches_per_step": 1 if tuned["dynamic"] == 2 else 5,
             "config": {"workload": "48 planet discs, sizes 128/256/384/512^2 and degrees 2/3/4 "
                                    "cycling, q = 10^U(-6,-4), seeds 100-147, precision form",
                        "instances": len(cfgs), "dof_per_stage": dof}}
@@ -401,6 +410,8 @@ def main():
 
     # headline form
     disc, ms, stage_s, clocks = timed_run(dg, torch, head_cfg, args.steps, args.warmup, local, pg)
+    tiles = disc.prec_tiles() if args.form == "prec" else None
+    dbytes = design_bytes(*tiles) if tiles else None
     value = job_rate(world, dof * stages_per_step * args.steps, ms / 1e3)
 
     # end to end through the C ABI with host buffers: every step uploads the
@@ -449,8 +460,9 @@ def main():
                     "kernel": "k_stage32<4> (precision-form fused RK stage)",
                     "peak_source": hbm_src, "stage_us": stage_s * 1e6,
                     "algorithmic_bytes_per_element": BYTES_PER_ELEM_STAGE_PREC,
-                    "design_bytes_per_element": DESIGN_BYTES_PER_ELEM_STAGE_PREC,
-                    "design_achieved": DESIGN_BYTES_PER_ELEM_STAGE_PREC * n_el / stage_s / 1e9}
+                    "design_bytes_per_element": dbytes,
+                    "design_achieved": dbytes * n_el / stage_s / 1e9,
+                    "tiles": {"all": tiles[0], "keeping_R_b": tiles[1], "damping": tiles[2]}}
         d64, ms64, stage64, clocks64 = timed_run(dg, torch, cfg, args.fp64_steps, 2, local, pg)
         d64.close()
         fp64 = {"value": world * dof * stages_per_step * args.fp64_steps / (ms64 / 1e3),

@@ -225,6 +225,13 @@ int dg_set_stream(dg_handle *h, void *stream);
 /* Number of variables (3 or 4) and of modes per variable (m*m) of a handle. */
 int dg_shape(dg_handle *h, int *nv, int *nmodes, int *nx, int *ny);
 
+/* Static data of the precision form's stage kernel, for its traffic figures:
+   the number of 32-element tiles, of tiles that keep the background residual
+   R_b (the others hold no coefficient above 1e-10 of max |R_b| and read none),
+   and of tiles whose box touches a damping zone (they read the damping
+   offsets in the last stage).  DG_ERR_UNSUPPORTED for the FP64 form. */
+int dg_prec_tiles(dg_handle *h, long long *ntiles, long long *rb_tiles, long long *zone_tiles);
+
 /* Kernel timing for benchmarks: while enabled, the RK-stage kernel launches of
    the handle are bracketed by pairs of CUDA events recorded on the handle's
    stream (no extra synchronisation): each launch of the FP64 form, the
@@ -384,21 +391,33 @@ const char *dg_last_error(dg_handle *h);
 /* ---- Batched precision form ------------------------------------------------
    Many independent discs (the Sec. 5.1 problem with its own mesh size, degree,
    planet mass and seed each) advanced together on one GPU.  The paper runs one
-   disc over many GPUs (Sec. 3.1); it has no batched form.  Each RK stage of
-   every instance is one launch over the 32-element tiles of all instances
-   (mixed degrees), with persistent CTAs that take (instance, tile) work items
-   from a device counter in a tuned order; the torque of every instance and
-   its end-of-step work (torque sum, time advance, CFL step) are one launch
-   each.  One step is captured as a CUDA graph and replayed.  Every instance
-   keeps its own CFL step, time, torque series and error status, and gives the
-   same results as dg_step on its own handle (same kernels, same arithmetic);
-   after batched steps the handles are used as usual (dg_fetch, dg_torque...).
+   disc over many GPUs (Sec. 3.1); it has no batched form.  Two kinds of
+   schedule, chosen by dg_batch_config or the autotuner:
+   - per-stage launches: each RK stage of every instance is one launch over the
+     32-element tiles of all instances (mixed degrees), with persistent CTAs
+     that take (instance, tile) work items from a device counter in a tuned
+     order (or one CTA per tile); the torque of every instance and its
+     end-of-step work (torque sum, time advance, CFL step) are one launch each;
+   - the flow schedule: one persistent cooperative launch per step.  Its CTAs
+     take work items (runs of up to tiles_per_item tiles of one row) from one
+     queue holding every instance's first-stage items, then the second, the
+     last, then the torque; an item waits only until the rows it reads (its own
+     and the two neighbouring rows) are finished by the stage before, and the
+     CTA that finishes an instance's last torque tile does that instance's
+     end-of-step work.  Every wait is bounded (one second); one that gives up
+     voids the step of its instance, which keeps its state and reports
+     DG_ERR_TIMEOUT.
+   One step is captured as a CUDA graph and replayed.  Every instance keeps its
+   own CFL step, time, torque series and error status, and gives the same
+   results as dg_step on its own handle under every schedule (same per-tile
+   code, same arithmetic, same order of every sum); after batched steps the
+   handles are used as usual (dg_fetch, dg_torque...).
 
    Requirements: 1 <= n <= DG_BATCH_MAX handles, each created with
    disc.prec = 1 and disc.rk = 3 (locally isothermal), all on the same stream
    and device, each in at most one batch.  The batch keeps pointers to the
    handles, which must outlive it; it owns a CUDA stream, two events, its
-   work table and three counters.  Batched work is ordered after everything
+   work tables and counters.  Batched work is ordered after everything
    queued on the handles' stream before the call and before everything queued
    there after it.  Errors: DG_ERR_ARG (bad argument), DG_ERR_UNSUPPORTED
    (a handle not in the precision form or not SSP(3,3)), DG_ERR_CUDA,
@@ -409,25 +428,31 @@ typedef struct dg_batch dg_batch;
 
 int dg_batch_create(dg_batch **b, dg_handle *const *handles, int n);
 
-/* Schedule of the batched stage launches:
-     policy       work order: 0 instances as given, 1 costliest tiles first
-                  (highest degree, then largest instance), 2 one tile row of
-                  each instance in turn
-     dynamic      1: persistent CTAs (ctas_per_sm per SM) take items from a
-                  counter; 0: one CTA per tile in work order
-     ctas_per_sm  resident CTAs per SM of the persistent grid (0 or above the
-                  occupancy limit: the limit)
-   Default: policy 1, dynamic 1, the occupancy limit. */
-int dg_batch_config(dg_batch *b, int policy, int dynamic, int ctas_per_sm);
-int dg_batch_get_config(const dg_batch *b, int *policy, int *dynamic, int *ctas_per_sm);
+/* Schedule of the batched steps:
+     policy          work order: 0 instances as given, 1 costliest tiles first
+                     (highest degree, then largest instance), 2 one tile row of
+                     each instance in turn
+     dynamic         0: one CTA per tile in each stage launch; 1: persistent
+                     CTAs (ctas_per_sm per SM) take items from a counter in
+                     each stage launch; 2: the flow schedule (one persistent
+                     launch per step)
+     ctas_per_sm     resident CTAs per SM of the persistent grid (0 or above the
+                     occupancy limit: the limit)
+     tiles_per_item  1, 2 or 4: tiles (32 elements each) of one row per work
+                     item of the flow schedule (ignored by the others)
+   Default: policy 1, dynamic 1, the occupancy limit, 1 tile per item. */
+int dg_batch_config(dg_batch *b, int policy, int dynamic, int ctas_per_sm, int tiles_per_item);
+int dg_batch_get_config(const dg_batch *b, int *policy, int *dynamic, int *ctas_per_sm,
+                        int *tiles_per_item);
 
 /* Autotuner: times `steps` batched steps under each schedule (3 work orders x
-   {persistent at the occupancy limit, one CTA below it, one CTA per tile}),
-   keeps the fastest and returns it (any output pointer may be NULL; best_ms
-   is the time of one batched step).  The instances are restored afterwards
-   (state, time, step count), so tuning does not advance them.  Synchronous. */
+   {persistent per-stage launches at the occupancy limit and one CTA below it,
+   one CTA per tile, the flow schedule with 1, 2 and 4 tiles per item}), keeps
+   the fastest and returns it (any output pointer may be NULL; best_ms is the
+   time of one batched step).  The instances are restored afterwards (state,
+   time, step count), so tuning does not advance them.  Synchronous. */
 int dg_batch_tune(dg_batch *b, int steps, int *policy, int *dynamic, int *ctas_per_sm,
-                  double *best_ms);
+                  int *tiles_per_item, double *best_ms);
 
 /* nsteps SSP(3,3) steps of every instance, each with its own CFL step.
    Asynchronous. */

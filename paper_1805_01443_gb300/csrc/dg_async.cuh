@@ -68,15 +68,17 @@ __device__ __forceinline__ int counter_load(const int* ctr) {
   return v;
 }
 // bounded wait until *ctr >= target: false once ~limit_ns have passed on the
-// GPU's global timer (or 2^26 polls, whichever comes first), so that a
-// counter nobody advances cannot hang the GPU
-__device__ __forceinline__ bool counter_wait(const int* ctr, int target, unsigned long long limit_ns) {
+// GPU's global timer (or 2^26 polls, whichever comes first), or soon after
+// *abort (if given) becomes non-zero, so that a counter nobody advances cannot
+// hang the GPU
+__device__ __forceinline__ bool counter_wait(const int* ctr, int target, unsigned long long limit_ns,
+                                             const int* abort = nullptr) {
   const unsigned long long t0 = global_ns();
   for (int i = 0; i < (1 << 26); i++) {
     if (counter_load(ctr) >= target) return true;
     if (i >= 16) {
       __nanosleep(128);
-      if ((i & 63) == 0 && global_ns() - t0 > limit_ns) return false;
+      if ((i & 63) == 0 && ((abort && counter_load(abort) != 0) || global_ns() - t0 > limit_ns)) return false;
     }
   }
   return false;

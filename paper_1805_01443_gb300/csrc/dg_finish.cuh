@@ -34,36 +34,42 @@ __device__ __forceinline__ void store_planet32(DevState* ts, double dt, double r
   ts->dtf = (float)dt;
 }
 
-// End of a step, by one CTA of 256 threads: fixed-order sum of the per-tile
+// End of a step, by one CTA of NT threads: fixed-order sum of the per-tile
 // torque partials, torque on the planet at t^{n+1} (Sec. 5.2), time advance,
 // the next CFL step and (planet32) the next step's planet positions, one per
 // thread.  With advance = 0 only the CFL slot is turned into ts->dt.  With
 // planet32 the position at t^{n+1} is the one stored for this step (pl1, the
-// same expression), so no trigonometry runs before the torque.
-__device__ __forceinline__ void finish_step(DevState* ts, const double* part, int nparts, double* series,
-                                            double fixed_dt, int advance, int planet32, double r_p,
-                                            double omega_p, double phi0) {
-  __shared__ double sx[256], sy[256];
+// same expression), so no trigonometry runs before the torque.  The sum is
+// the same for every NT: 256 virtual lanes (lane v adds partials v, v + 256,
+// ... in order, then a pairwise tree over the lanes), the real threads taking
+// lanes tid, tid + NT, ...; sx and sy are 256 doubles of shared scratch each.
+template <int NT>
+__device__ __forceinline__ void finish_step_nt(double* sx, double* sy, DevState* ts, const double* part,
+                                               int nparts, double* series, double fixed_dt, int advance,
+                                               int planet32, double r_p, double omega_p, double phi0) {
   __shared__ double s_t, s_dt;
   __shared__ int s_go;
+  constexpr int NL = 256;
   const int tid = threadIdx.x;
   if (ts->status != 0) return;
   if (advance) {
-    double gx = 0.0, gy = 0.0;
     const double2* p2 = reinterpret_cast<const double2*>(part);
+    for (int v = tid; v < NL; v += NT) {
+      double gx = 0.0, gy = 0.0;
 #pragma unroll 4
-    for (int k = tid; k < nparts; k += 256) {
-      const double2 g = p2[k];
-      gx += g.x;
-      gy += g.y;
+      for (int k = v; k < nparts; k += NL) {
+        const double2 g = p2[k];
+        gx += g.x;
+        gy += g.y;
+      }
+      sx[v] = gx;
+      sy[v] = gy;
     }
-    sx[tid] = gx;
-    sy[tid] = gy;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s) {
-        sx[tid] += sx[tid + s];
-        sy[tid] += sy[tid + s];
+    for (int s = NL / 2; s > 0; s >>= 1) {
+      for (int v = tid; v < s; v += NT) {
+        sx[v] += sx[v + s];
+        sy[v] += sy[v + s];
       }
       __syncthreads();
     }
@@ -111,6 +117,14 @@ __device__ __forceinline__ void finish_step(DevState* ts, const double* part, in
   }
   __syncthreads();
   if (s_go && tid < 3) store_planet32_k(ts, tid, s_t, s_dt, r_p, omega_p, phi0);
+}
+
+// the same by one CTA of 256 threads with its own scratch
+__device__ __forceinline__ void finish_step(DevState* ts, const double* part, int nparts, double* series,
+                                            double fixed_dt, int advance, int planet32, double r_p,
+                                            double omega_p, double phi0) {
+  __shared__ double sx[256], sy[256];
+  finish_step_nt<256>(sx, sy, ts, part, nparts, series, fixed_dt, advance, planet32, r_p, omega_p, phi0);
 }
 
 }  // namespace dg

@@ -108,7 +108,8 @@ struct StageArgs32 {
   const float* D;      // delta^(s)
   const float* Dn;     // delta^n
   float* Out;
-  const float* Rb;     // R_b = L(u_b), evaluated in FP64, stored FP32 [tile][var][mode][32]
+  const float* Rb;     // R_b = L(u_b), evaluated in FP64, stored FP32 [slot][var][mode][32]
+  const int* RbIdx;    // tile -> its slot in Rb, or -1 (R_b dropped: below 1e-10 of its maximum)
   const float* Db;     // Q0 - Q_b at the nodes for (Sigma, vx, vy) [tile][3][node][32] (damping)
   const float* Bm0;    // element averages of u_b [tile][3][32] (CFL)
   const float* Bmodes; // u_b modes in FP32 [tile][var][mode][32] (exact-background tiles)
@@ -262,6 +263,27 @@ struct BatchInst32 {
   int cur0, p, nparts;
 };
 
+// One persistent launch per step (the flow schedule): CTAs take work items
+// from one queue -- every stage-1 item, then every stage-2 item, every
+// stage-3 item, then the torque groups -- and an item waits, with a bounded
+// spin, only for the tile rows it reads to be finished by the stage before.
+// The counters live in one int array that is cleared before every step.
+struct BatchFlow32 {
+  int* ctr;             // [0] queue, [1] abort flag, [2] CTAs done, [FLOW_TQ + k] torque
+                        // tiles done of instance k, [FLOW_ROWS + 3 r + s] tiles of global row
+                        // r finished by stage s
+  const int2* items;    // stage work items {(instance << 25) | first tile, tiles}, stages 1-2 order
+  const int2* last;     // the same for the last stage
+  const int* tq;        // torque groups: (instance << 25) | first tile (3 tiles, one per warp)
+  int nq;               // stage work items of stages 1 and 2
+  int nql;              // stage work items of the last stage
+  int ntq;              // torque groups
+  unsigned long long limit_ns;  // bound of one wait
+  int rowbase[BATCH_MAX + 1];   // first global row of each instance
+};
+constexpr int FLOW_TQ = 4;
+constexpr int FLOW_ROWS = FLOW_TQ + BATCH_MAX;
+
 struct BatchLaunch32 {
   int n;                // instances
   int nitems;           // tiles over all instances
@@ -270,6 +292,7 @@ struct BatchLaunch32 {
   int* counter;         // work counter of this stage (reset every step)
   const int* items;     // work order: (instance << 25) | tile
   int tile0[BATCH_MAX + 1];  // prefix sums of the instances' tile counts
+  BatchFlow32 flow;
   BatchInst32 inst[BATCH_MAX];
 };
 
@@ -281,6 +304,9 @@ cudaError_t launch_batch_stage32(const BatchLaunch32& L, int grid, cudaStream_t 
 cudaError_t launch_batch_torque32(const BatchLaunch32& L, cudaStream_t s);
 cudaError_t launch_batch_finish(const BatchLaunch32& L, cudaStream_t s);
 cudaError_t launch_batch_planet32(const BatchLaunch32& L, cudaStream_t s);
+// the flow schedule: one cooperative launch of `grid` CTAs per step
+int batch_flow_ctas_per_sm();
+cudaError_t launch_batch_flow32(const BatchLaunch32& L, int grid, cudaStream_t s);
 
 // Record msg as this thread's last error (dg_last_error(NULL)); returns code.
 int set_thread_error(int code, const char* msg);

@@ -40,7 +40,8 @@ __global__ void k_selftest_mbar(int hold_tmem, int* out) {
   if (threadIdx.x == 0 && any_timeout) atomicAdd(&out[0], 1);
 }
 
-// two CTAs; CTA 1 never signals the counter that CTA 0 waits for
+// two CTAs; CTA 1 never signals the counter that CTA 0 waits for (ctr[1] is
+// an abort word that stays zero, as in the persistent batched kernel)
 __global__ void k_selftest_counter(int* ctr, int* out) {
   if (blockIdx.x == 1) return;
   if (threadIdx.x == 0) {
@@ -48,7 +49,7 @@ __global__ void k_selftest_counter(int* ctr, int* out) {
     counter_signal(ctr);
   }
   bool ok = true;
-  if (threadIdx.x == 0) ok = counter_wait(ctr, 2, 500000000ull);
+  if (threadIdx.x == 0) ok = counter_wait(ctr, 2, 500000000ull, ctr + 1);
   if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicAdd(&out[0], 1);
 }
 
@@ -59,8 +60,8 @@ extern "C" int dg_selftest_wait(int kind, int* freed) {
   using namespace dg;
   if (kind < 0 || kind > 2) return set_thread_error(DG_ERR_ARG, "dg_selftest_wait: kind is 0, 1 or 2");
   int* d = nullptr;
-  cudaError_t e = cudaMalloc((void**)&d, 3 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(d, 0, 3 * sizeof(int));
+  cudaError_t e = cudaMalloc((void**)&d, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, 4 * sizeof(int));
   if (e == cudaSuccess) {
     if (kind < 2) {
       k_selftest_mbar<<<1, 64>>>(kind == 1 ? 1 : 0, d);

@@ -712,10 +712,15 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
         L[aa * m + b] = fmaf(pc.idx, lx, fmaf(pc.idy, ly, L[aa * m + b]));
       }
   }
-  // background residual R_b, then the Shu-Osher combination
+  // background residual R_b (only in the tiles that keep it), then the
+  // Shu-Osher combination
   const size_t gbase = tile * NVM * 32 + voff;
+  const int rbs = a.RbIdx[tile];
+  if (rbs >= 0) {
+    const float* rb = a.Rb + (size_t)rbs * NVM * 32 + voff + lc;
 #pragma unroll
-  for (int k = 0; k < M; k++) L[k] += a.Rb[gbase + k * 32 + lc];
+    for (int k = 0; k < M; k++) L[k] += rb[k * 32];
+  }
   if (mode == 0) {
     if (valid) {
 #pragma unroll

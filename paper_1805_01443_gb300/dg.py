@@ -32,7 +32,7 @@ EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_d
             "dg_batch_sync", "dg_batch_destroy", "dg_indicator", "dg_limit", "dg_limit_flags",
             "dg_last_flags", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_nparams", "dg_mlp_get_params",
             "dg_mlp_set_params", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step", "dg_features",
-            "dg_set_indicator", "dg_indicator_logits", "dg_selftest_wait"]
+            "dg_set_indicator", "dg_indicator_logits", "dg_selftest_wait", "dg_prec_tiles"]
 
 
 class DgMesh(ctypes.Structure):
@@ -123,14 +123,16 @@ def lib(build_if_missing=True):
         L.dg_set_indicator.argtypes = [_VP, _VP, ctypes.c_float]
         L.dg_indicator_logits.argtypes = [_VP, _VP, _VP]
         L.dg_batch_create.argtypes = [P(_VP), P(_VP), ctypes.c_int]
-        L.dg_batch_config.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-        L.dg_batch_get_config.argtypes = [_VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]
+        L.dg_batch_config.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.dg_batch_get_config.argtypes = [_VP, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                                          P(ctypes.c_int)]
         L.dg_batch_tune.argtypes = [_VP, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
-                                    P(ctypes.c_int), _DP]
+                                    P(ctypes.c_int), P(ctypes.c_int), _DP]
         L.dg_batch_step.argtypes = [_VP, ctypes.c_int]
         L.dg_batch_sync.argtypes = [_VP]
         L.dg_batch_destroy.argtypes = [_VP]
         L.dg_selftest_wait.argtypes = [ctypes.c_int, P(ctypes.c_int)]
+        L.dg_prec_tiles.argtypes = [_VP, P(ctypes.c_longlong), P(ctypes.c_longlong), P(ctypes.c_longlong)]
         _lib = L
     return _lib
 
@@ -340,6 +342,12 @@ class Disc:
         _check(lib().dg_timing(self.h, ctypes.byref(ms), ctypes.byref(n)), self.h)
         return ms.value, n.value
 
+    def prec_tiles(self):
+        """Precision form: (tiles, tiles that keep R_b, tiles touching a damping zone)."""
+        n, r, z = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().dg_prec_tiles(self.h, ctypes.byref(n), ctypes.byref(r), ctypes.byref(z)), self.h)
+        return n.value, r.value, z.value
+
     def set_stream(self, stream):
         _check(lib().dg_set_stream(self.h, ctypes.c_void_p(stream or 0)), self.h)
 
@@ -435,20 +443,25 @@ class Batch:
         _check(L.dg_batch_create(ctypes.byref(b), arr, len(self.discs)))
         self.b = b
 
-    def config(self, policy=1, dynamic=1, ctas_per_sm=0):
-        _check(lib().dg_batch_config(self.b, policy, dynamic, ctas_per_sm))
+    def config(self, policy=1, dynamic=1, ctas_per_sm=0, tiles_per_item=1):
+        """dynamic: 0 one CTA per tile, 1 persistent CTAs in each stage launch,
+        2 one persistent launch per step (flow schedule, work items of
+        tiles_per_item tiles)."""
+        _check(lib().dg_batch_config(self.b, policy, dynamic, ctas_per_sm, tiles_per_item))
 
     def get_config(self):
-        p, d, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(lib().dg_batch_get_config(self.b, ctypes.byref(p), ctypes.byref(d), ctypes.byref(c)))
-        return {"policy": p.value, "dynamic": d.value, "ctas_per_sm": c.value}
+        p, d, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().dg_batch_get_config(self.b, ctypes.byref(p), ctypes.byref(d), ctypes.byref(c),
+                                         ctypes.byref(t)))
+        return {"policy": p.value, "dynamic": d.value, "ctas_per_sm": c.value, "tiles_per_item": t.value}
 
     def tune(self, steps=3):
-        p, d, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        p, d, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ms = ctypes.c_double()
         _check(lib().dg_batch_tune(self.b, steps, ctypes.byref(p), ctypes.byref(d), ctypes.byref(c),
-                                   ctypes.byref(ms)))
-        return {"policy": p.value, "dynamic": d.value, "ctas_per_sm": c.value, "ms_per_step": ms.value}
+                                   ctypes.byref(t), ctypes.byref(ms)))
+        return {"policy": p.value, "dynamic": d.value, "ctas_per_sm": c.value, "tiles_per_item": t.value,
+                "ms_per_step": ms.value}
 
     def step(self, n=1):
         _check(lib().dg_batch_step(self.b, n))

@@ -3,7 +3,8 @@ one launch per stage, against the FP64 oracle run of each disc and against
 each disc stepped on its own with dg_step.
 
 Against the oracle the precision form's stated bounds hold per instance
-(relative L2 of Sigma and momentum <= 1e-5, of the torque series <= 1e-6).
+(relative L2 of Sigma and momentum <= 1e-5, of the torque series <= 1e-6,
+of Sigma - Sigma_bg <= 5e-6 after 12 steps: measured at most 4e-7).
 Against per-instance steps the batched kernels run the same per-tile code on
 the same data in the same per-instance order of reductions, so the results are
 compared bit for bit.
@@ -32,7 +33,10 @@ def assert_same(a, b):
     np.testing.assert_array_equal(a.torque_series(), b.torque_series())
 
 
-SCHEDULES = [(0, 1, 0), (1, 1, 0), (2, 1, 0), (1, 0, 0), (2, 1, 1)]
+# (policy, dynamic, ctas_per_sm, tiles_per_item): persistent per-stage
+# launches, one CTA per tile, and the flow schedule (one launch per step)
+SCHEDULES = [(0, 1, 0, 1), (1, 1, 0, 1), (2, 1, 0, 1), (1, 0, 0, 1), (2, 1, 1, 1), (1, 2, 0, 1), (0, 2, 0, 2),
+             (2, 2, 0, 4), (1, 2, 1, 4)]
 ORACLE_STEPS = 12
 
 
@@ -61,8 +65,8 @@ def oracle_runs():
     return cfgs, runs
 
 
-@pytest.mark.parametrize("policy,dynamic,ctas", SCHEDULES)
-def test_batch_matches_the_oracle(oracle_runs, policy, dynamic, ctas):
+@pytest.mark.parametrize("policy,dynamic,ctas,tpi", SCHEDULES)
+def test_batch_matches_the_oracle(oracle_runs, policy, dynamic, ctas, tpi):
     """Every instance of a batched run against its own FP64 oracle run, under
     every schedule of the batched launches."""
     cfgs, runs = oracle_runs
@@ -71,14 +75,14 @@ def test_batch_matches_the_oracle(oracle_runs, policy, dynamic, ctas):
         for d, r in zip(bat, runs):
             d.set_state(r["u0"])
         with dg.Batch(bat) as b:
-            b.config(policy, dynamic, ctas)
+            b.config(policy, dynamic, ctas, tpi)
             b.step(ORACLE_STEPS)
             b.sync()
         for k, (d, r) in enumerate(zip(bat, runs)):
             ug, uo = d.fetch(), r["u"]
             assert rel(ug[0], uo[0]) <= 1e-5, k
             assert max(rel(ug[1], uo[1]), rel(ug[2], uo[2])) <= 1e-5, k
-            assert rel(ug[0] - r["sig_bg"], uo[0] - r["sig_bg"]) <= 1e-4, k
+            assert rel(ug[0] - r["sig_bg"], uo[0] - r["sig_bg"]) <= 5e-6, k
             assert rel(d.torque_series(), r["tq"]) <= 1e-6, k
             t, _, st = d.get_time()
             assert st == ORACLE_STEPS
@@ -103,15 +107,15 @@ def test_batch_equals_individual_steps():
         close(solo + bat)
 
 
-@pytest.mark.parametrize("policy,dynamic,ctas", SCHEDULES)
-def test_batch_schedules_give_identical_results(policy, dynamic, ctas):
+@pytest.mark.parametrize("policy,dynamic,ctas,tpi", SCHEDULES)
+def test_batch_schedules_give_identical_results(policy, dynamic, ctas, tpi):
     cfgs = inputs.batch_small()
     ref, bat = make(cfgs), make(cfgs)
     try:
         for d in ref:
             d.step(5)
         with dg.Batch(bat) as b:
-            b.config(policy, dynamic, ctas)
+            b.config(policy, dynamic, ctas, tpi)
             b.step(5)
         for a, c in zip(bat, ref):
             assert_same(a, c)
@@ -131,6 +135,7 @@ def test_batch_tune_does_not_advance_and_then_matches():
         with dg.Batch(bat) as b:
             best = b.tune(steps=2)
             assert best["policy"] in (0, 1, 2) and best["ms_per_step"] > 0
+            assert best["dynamic"] in (0, 1, 2) and best["tiles_per_item"] in (1, 2, 4)
             for d, u in zip(bat, u0):
                 np.testing.assert_array_equal(d.fetch(), u)
                 assert d.get_time()[2] == 2
@@ -182,3 +187,38 @@ def test_batch_rejects_fp64_and_bad_counts():
         assert e.value.code == dg.DG_ERR_ARG
     finally:
         fp64.close()
+
+
+def test_flow_schedule_continues_after_odd_step_counts():
+    """One persistent launch per step: odd step counts, a switch of schedule in
+    the middle and dg_step afterwards give the per-instance results."""
+    cfgs = inputs.batch_small()[2:5]
+    ref, bat = make(cfgs), make(cfgs)
+    try:
+        for d in ref:
+            d.step(6)
+        with dg.Batch(bat) as b:
+            b.config(1, 2, 0, 2)
+            b.step(3)
+            b.config(0, 1, 0, 1)
+            b.step(1)
+            b.config(2, 2, 0, 1)
+            b.step(1)
+        for d in bat:
+            d.step(1)
+        for a, c in zip(bat, ref):
+            assert_same(a, c)
+    finally:
+        close(ref + bat)
+
+
+def test_batch_config_rejects_bad_schedules():
+    bat = make(inputs.batch_small()[:1])
+    try:
+        with dg.Batch(bat) as b:
+            for args in [(3, 1, 0, 1), (1, 3, 0, 1), (1, 2, 0, 3), (1, 2, -1, 1)]:
+                with pytest.raises(dg.DgError) as e:
+                    b.config(*args)
+                assert e.value.code == dg.DG_ERR_ARG
+    finally:
+        close(bat)

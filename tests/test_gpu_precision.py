@@ -312,3 +312,25 @@ def test_async_upload_pipeline_matches_synchronous_calls(prec):
         assert a.get_time() == b.get_time()
         with pytest.raises(dg.DgError):
             a.set_state_async(np.zeros(u.shape), t, st)
+
+
+def test_background_residual_kept_only_where_it_matters():
+    """R_b = L(u_b) is kept only in tiles holding a coefficient above 1e-10 of
+    its maximum (the singular centre, the softened core, the box edge); the
+    precision form's operator on the noise-free background then equals the
+    oracle's L(u_b) element by element within the FP32 rounding of R_b, the
+    dropped part and the FP64 rounding of the operator's cancelling terms."""
+    cfg = inputs.disc_planet(128, 4)
+    cfg["disc"]["noise_amp"] = 0.0
+    cfg["planet"]["enabled"] = 0
+    o = oracle.Oracle(cfg)
+    with dg.Disc(prec_cfg(cfg)) as g:
+        n, r, z = g.prec_tiles()
+        assert n == 128 * 4 and 0 < r < n and 0 < z < n
+        u = o.fetch()
+        g.set_state(u)
+        Lo, Lg = o.rhs(), g.rhs()
+        dt = o.cfl_dt()
+    rmax = np.abs(Lo).max()
+    bound = 1.2e-7 * np.abs(Lo) + 1.01e-10 * rmax + 1e-15 * np.abs(u).max() / dt
+    assert np.all(np.abs(Lg - Lo) <= bound), float((np.abs(Lg - Lo) / bound).max())
