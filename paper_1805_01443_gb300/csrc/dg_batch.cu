@@ -158,9 +158,13 @@ __device__ __forceinline__ void flow_stage_item(const BatchLaunch32& L, int stag
       __syncthreads();  // the tile's shared memory is free for the next one
     }
   }
-  __threadfence();
+  // every thread's writes are ordered before thread 0's fence by the barrier
+  // (the pattern of a grid barrier); then the rows' counter
   __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(rows + 3 * j + stage, len);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(rows + 3 * j + stage, len);
+  }
 }
 
 // torque of up to three tiles of instance k (one warp each), each once its
@@ -187,9 +191,9 @@ __device__ __forceinline__ void flow_torque_item(const BatchLaunch32& L, int cod
       batch_torque_tile(L, k, tile, sd);
     }
   }
-  __threadfence();
   const bool fail = __syncthreads_or(!ok);
   if (threadIdx.x == 0) {
+    __threadfence();
     if (fail) flow_fail(L, k);
     const int cnt = min(3, nt - t0);
     s_last = atomicAdd(F.ctr + FLOW_TQ + k, cnt) + cnt == nt;

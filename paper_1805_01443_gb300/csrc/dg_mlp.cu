@@ -6,7 +6,11 @@
 // 2 right, 3 below, 4 above (outside elements by the boundary rule), variable
 // v and mode k, x[(s * nv + v) * M + k] = c_s[v][k] * (1 / S_v) with S_v the
 // largest |c_s[v][k]| over the stencil and the modes (1 when all vanish): the
-// reciprocal and the product in FP64, the product rounded once to FP32.
+// reciprocal and the product in FP64, the product rounded once to FP32
+// (dg_features, the training inputs).  The inference kernel on the tensor
+// cores forms the same inputs in FP32 -- the coefficient and the reciprocal
+// each rounded to FP32, then their FP32 product -- within three FP32 roundings
+// of those (relative 2^-22) and without an FP64 instruction per input.
 //
 // Parameters (FP32 master copy, flat): W1 [64][nin], b1 [64], W2 [64][64],
 // b2 [64], w3 [64], b3.  The products use the weights rounded to BF16
@@ -374,8 +378,9 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     i = (int)(tile - (long long)j * a.ms.ntx) * 32 + (row & 31);
     valid = i < a.ms.nx;
   }
-  // 1 / S_v over the stencil, from the per-element maxima (fixed ghost elements scanned here)
-  double R[NV];
+  // 1 / S_v over the stencil, from the per-element maxima (fixed ghost elements
+  // scanned here), rounded to FP32
+  float R[NV];
   {
     unsigned long long mx[NV];
 #pragma unroll
@@ -404,7 +409,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
       }
     }
 #pragma unroll
-    for (int v = 0; v < NV; v++) R[v] = mx[v] ? 1.0 / __longlong_as_double((long long)mx[v]) : 1.0;
+    for (int v = 0; v < NV; v++) R[v] = mx[v] ? d2f_rn(1.0 / __longlong_as_double((long long)mx[v])) : 1.0f;
   }
 
   // base address and stride (elements) of each stencil element's coefficients
@@ -445,7 +450,8 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     for (int g = 0; g < 4; g += 2) {
       // the two groups' 16 coefficients are loaded first (all in flight at
       // once), then scaled and rounded
-      double cv[16], rv2[2];
+      double cv[16];
+      float rv2[2];
 #pragma unroll
       for (int h8 = 0; h8 < 2; h8++) {
         const int G = c * 8 + half * 4 + g + h8;
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
             q = sp[w];
             qs = sst[w];
           }
-        double rv = R[0];
+        float rv = R[0];
 #pragma unroll
         for (int w = 1; w < NV; w++) rv = (v == w) ? R[w] : rv;
         rv2[h8] = rv;
@@ -467,9 +473,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
 #pragma unroll
         for (int e = 0; e < 8; e++) cv[h8 * 8 + e] = (on && kk0 + e < M) ? q[e * qs] : 0.0;
       }
+      // each coefficient rounded to FP32 on the integer pipe, then scaled in
+      // FP32: within two FP32 roundings of the features of the FP64 product
+      // (dg_features), and no FP64 instruction per input
       float x[16];
 #pragma unroll
-      for (int t = 0; t < 16; t++) x[t] = d2f_rn(cv[t] * rv2[t >> 3]);
+      for (int t = 0; t < 16; t++) x[t] = d2f_rn(cv[t]) * rv2[t >> 3];
       // the previous chunk's MMAs have read the A buffer
       if (c > 0 && g == 0) ok &= mbar_wait(&bar[0], (c - 1) & 1);
 #pragma unroll

@@ -195,7 +195,11 @@ __device__ __noinline__ Bg32 bg32_poly(const float* bm, const float* fa, const f
   return r;
 }
 
-// Shared-memory plan (floats) of the precision-form stage kernel.
+// Shared-memory plan (floats) of the precision-form stage kernel.  The face
+// fluxes are formed before the pointwise terms, so the traces that are dead
+// once the fluxes exist (own y traces, left x traces) sit in the planes of
+// the pointwise terms that are written after them: 32.0 KB at P4, seven CTAs
+// per SM.
 template <int P>
 struct Smem32 {
   static constexpr int m = P + 1, M = m * m;
@@ -204,18 +208,20 @@ struct Smem32 {
   // values are read and replaced by the one thread that owns the node)
   static constexpr int U = 0;
   static constexpr int F = 0;
-  static constexpr int XT = F + 8 * M * 32;        // x traces [2][3][m][33]: 0 right (slot e+1), 1 left (slot e)
-  static constexpr int YT = XT + 2 * 3 * m * 33;   // own y traces [2][3][m][32]: 0 top, 1 bottom
-  static constexpr int YN = YT + 2 * 3 * m * 32;   // neighbour traces [2][3][m][32]: 0 below's top, 1 above's bottom
+  static constexpr int YT = F + 3 * M * 32;        // own y traces [2][3][m][32]: 0 top, 1 bottom (in planes 3..)
+  static constexpr int XL = YT + 2 * 3 * m * 32;   // left x traces [3][m][33], slot e (in planes 3..)
+  static constexpr int XR = F + 8 * M * 32;        // right x traces [3][m][33], slot e+1
+  static constexpr int YN = XR + 3 * m * 33;       // neighbour traces [2][3][m][32]: 0 below's top, 1 above's bottom
   // face fluxes overwrite the traces they are formed from (each face point's
   // traces are read and replaced by the one thread that owns the point):
-  static constexpr int FX = XT;                    // x-face flux differences [3][m][33] on plane 0 of XT
-  static constexpr int FY = YN;                    // y-face flux differences [2][3][m][32] on YN
+  static constexpr int FX = XR;                    // x-face flux differences [3][m][33]
+  static constexpr int FY = YN;                    // y-face flux differences [2][3][m][32]
   static constexpr int B0 = YN + 2 * 3 * m * 32;   // element averages of the new state [3][32]
   static constexpr int FLAGS = B0 + 3 * 32;        // 32 ints
   static constexpr int TOTAL = FLAGS + 32;
   static constexpr int ND = 8;                     // 8-byte words: offsets, dt, mbarrier
   static constexpr size_t BYTES = (size_t)ND * sizeof(double) + (size_t)TOTAL * sizeof(float);
+  static_assert(XL + 3 * m * 33 <= F + 8 * M * 32, "traces exceed the pointwise planes");
 };
 
 // exact int -> float for 0 <= x < 2^23 on the integer and FP32 pipes (this
@@ -374,10 +380,20 @@ __device__ __forceinline__ void ytrace32(const float* c, const float* f, float* 
   }
 }
 
-// minimum resident CTAs per SM asked of the register allocator
+// minimum resident CTAs per SM asked of the register allocator (96
+// registers and 32.0 KB of shared memory at P4 fit seven)
 #ifndef DG_STAGE32_MIN_CTAS
-#define DG_STAGE32_MIN_CTAS 6
+#define DG_STAGE32_MIN_CTAS 7
 #endif
+// 1: each warp asks the L2 for the lines of u^n (and R_b) that its update
+// reads at the end of the tile, when the tile starts
+#ifndef DG_STAGE32_PREFETCH
+#define DG_STAGE32_PREFETCH 1
+#endif
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // LAST = false: modes 0 (operator only) and 1 (RK stage); LAST = true: mode 2
 // (last RK stage with damping, torque and CFL), compiled apart so that the
@@ -395,7 +411,8 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   float* sm = reinterpret_cast<float*>(smd + S::ND);
   float* sU = sm + S::U;
   float* sFl = sm + S::F;
-  float* sXT = sm + S::XT;
+  float* sXR = sm + S::XR;
+  float* sXL = sm + S::XL;
   float* sYT = sm + S::YT;
   float* sYN = sm + S::YN;
   float* sFX = sm + S::FX;
@@ -459,6 +476,17 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   else if (ms.bc == 1) zR = true;
   else if (ms.bc == 3) { const int ie = ms.nx - 1; pR = Dcur + ((size_t)j * ms.ntx + (ie >> 5)) * NVM * 32 + voff + (ie & 31); }
   const bool trL = !pL && !zL, trR = !pR && !zR;
+#if DG_STAGE32_PREFETCH
+  {
+    // lane k < M: the 128-byte row of mode k of this warp's variable
+    const size_t row = tile * NVM * 32 + voff + (size_t)lane * 32;
+    if (lane < M) {
+      if (mode == 1 && alpha != 0.0f) prefetch_l2(Dn0 + row);
+      const int rb = a.RbIdx[tile];
+      if (rb >= 0) prefetch_l2(a.Rb + (size_t)rb * NVM * 32 + voff + (size_t)lane * 32);
+    }
+  }
+#endif
   // tiles near the singular centre use the exact projected background (FP32
   // modes of u_b, same tiled layout as delta, all three variables)
   const int exact = a.TileFlag[tile];
@@ -480,8 +508,8 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
 #pragma unroll
     for (int k = 0; k < M; k++) c[k] = own[k * 32];
     // x traces: right trace of element e at slot e+1, left trace at slot e
-    float* xr = sXT + (0 * 3 + v) * m * 33;
-    float* xl = sXT + (1 * 3 + v) * m * 33;
+    float* xr = sXR + v * m * 33;
+    float* xl = sXL + v * m * 33;
     float tr_r[m], tr_l[m];
     nodal32<P, true>(c, sU + voff + lane, tr_r, tr_l);
 #pragma unroll
@@ -533,15 +561,68 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
             acc = fmaf(right ? c32t[P].pm[aa] : c32t[P].pp[aa], t, acc);
           }
         }
-        if (right) sXT[((1 * 3 + v) * m + r) * 33 + nvalid] = acc;
-        else sXT[((0 * 3 + v) * m + r) * 33] = acc;
+        if (right) sXL[(v * m + r) * 33 + nvalid] = acc;
+        else sXR[(v * m + r) * 33] = acc;
       }
     }
   }
   __syncthreads();
   const float dt = sF[8];
-  // ---- P2: pointwise flux differences and sources at the nodes (dealt
-  // round-robin over the three threads of an element), then face fluxes ------
+  // ---- P2: face fluxes, then the pointwise flux differences and sources at
+  // the nodes (both dealt round-robin over the three threads of an element);
+  // the pointwise terms overwrite the traces the face fluxes were formed from
+  {
+    // y faces of the element: bottom (below | own) and top (own | above)
+    for (int kk = v; kk < 2 * m; kk += 3) {
+      const int side = kk >= m, q = kk - side * m;
+      const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
+      float dL[3], dR[3], hf[3];
+#pragma unroll
+      for (int w3 = 0; w3 < 3; w3++) {
+        const int o = ((w3)*m + q) * 32 + lane;
+        dL[w3] = side ? sYT[0 * 3 * m * 32 + o] : sYN[0 * 3 * m * 32 + o];
+        dR[w3] = side ? sYN[1 * 3 * m * 32 + o] : sYT[1 * 3 * m * 32 + o];
+      }
+      Bg32 bO = bg32_at(pc, xq, side ? yTf : yBf), bN = bO;
+      if (exact) {
+        const float c2 = bO.c2;
+        bO = bg32_poly<P>(bgOwn, c32t[P].phi[q], side ? c32t[P].pp : c32t[P].pm, c2);
+        const float* nb = side ? bgT : bgB;
+        if (nb) bN = bg32_poly<P>(nb, c32t[P].phi[q], side ? c32t[P].pm : c32t[P].pp, c2);
+        else if (side ? trT : trB) bN = bO;
+      }
+      dllf32<1>(side ? bO : bN, side ? bN : bO, dL, dR, hf);
+#pragma unroll
+      for (int w3 = 0; w3 < 3; w3++) sFY[((side * 3 + w3) * m + q) * 32 + lane] = hf[w3];
+    }
+    // x faces f = 0..nvalid of the tile row (face f between elements f-1 and f)
+    for (int idx = tid; idx < m * 33; idx += 96) {
+      const int r = idx / 33, f = idx - 33 * r;
+      if (f <= nvalid) {
+        float dL[3], dR[3], hf[3];
+#pragma unroll
+        for (int w3 = 0; w3 < 3; w3++) {
+          dL[w3] = sXR[(w3 * m + r) * 33 + f];
+          dR[w3] = sXL[(w3 * m + r) * 33 + f];
+        }
+        const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
+        Bg32 bL = bg32_at(pc, fmaf(i2f(f), pc.dx, xt0), y), bR = bL;
+        if (exact) {
+          const float* eL = (f > 0) ? bgOwn - lc + (f - 1) : bgL;
+          const float* eR = (f < nvalid) ? bgOwn - lc + f : bgR;
+          const float c2 = bL.c2;
+          if (eL) bL = bg32_poly<P>(eL, c32t[P].pp, c32t[P].phi[r], c2);
+          if (eR) bR = bg32_poly<P>(eR, c32t[P].pm, c32t[P].phi[r], c2);
+          if (!eL && trL && f == 0) bL = bR;
+          if (!eR && trR && f == nvalid) bR = bL;
+        }
+        dllf32<0>(bL, bR, dL, dR, hf);
+#pragma unroll
+        for (int w3 = 0; w3 < 3; w3++) sFX[(w3 * m + r) * 33 + f] = hf[w3];
+      }
+    }
+  }
+  __syncthreads();
   {
     const float pdx0 = fmaf(lanef, pc.dx, sF[0]);
     // two nodes per iteration, n0 = v + 3 kk and n1 = n0 + 3 (an odd last node
@@ -600,55 +681,6 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
         float* o1 = sFl + n1 * 32 + lane;
 #pragma unroll
         for (int t = 0; t < 8; t++) o1[t * M * 32] = o2[t].y;
-      }
-    }
-    // y faces of the element: bottom (below | own) and top (own | above)
-    for (int kk = v; kk < 2 * m; kk += 3) {
-      const int side = kk >= m, q = kk - side * m;
-      const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
-      float dL[3], dR[3], hf[3];
-#pragma unroll
-      for (int w3 = 0; w3 < 3; w3++) {
-        const int o = ((w3)*m + q) * 32 + lane;
-        dL[w3] = side ? sYT[0 * 3 * m * 32 + o] : sYN[0 * 3 * m * 32 + o];
-        dR[w3] = side ? sYN[1 * 3 * m * 32 + o] : sYT[1 * 3 * m * 32 + o];
-      }
-      Bg32 bO = bg32_at(pc, xq, side ? yTf : yBf), bN = bO;
-      if (exact) {
-        const float c2 = bO.c2;
-        bO = bg32_poly<P>(bgOwn, c32t[P].phi[q], side ? c32t[P].pp : c32t[P].pm, c2);
-        const float* nb = side ? bgT : bgB;
-        if (nb) bN = bg32_poly<P>(nb, c32t[P].phi[q], side ? c32t[P].pm : c32t[P].pp, c2);
-        else if (side ? trT : trB) bN = bO;
-      }
-      dllf32<1>(side ? bO : bN, side ? bN : bO, dL, dR, hf);
-#pragma unroll
-      for (int w3 = 0; w3 < 3; w3++) sFY[((side * 3 + w3) * m + q) * 32 + lane] = hf[w3];
-    }
-    // x faces f = 0..nvalid of the tile row (face f between elements f-1 and f)
-    for (int idx = tid; idx < m * 33; idx += 96) {
-      const int r = idx / 33, f = idx - 33 * r;
-      if (f <= nvalid) {
-        float dL[3], dR[3], hf[3];
-#pragma unroll
-        for (int w3 = 0; w3 < 3; w3++) {
-          dL[w3] = sXT[((0 * 3 + w3) * m + r) * 33 + f];
-          dR[w3] = sXT[((1 * 3 + w3) * m + r) * 33 + f];
-        }
-        const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
-        Bg32 bL = bg32_at(pc, fmaf(i2f(f), pc.dx, xt0), y), bR = bL;
-        if (exact) {
-          const float* eL = (f > 0) ? bgOwn - lc + (f - 1) : bgL;
-          const float* eR = (f < nvalid) ? bgOwn - lc + f : bgR;
-          const float c2 = bL.c2;
-          if (eL) bL = bg32_poly<P>(eL, c32t[P].pp, c32t[P].phi[r], c2);
-          if (eR) bR = bg32_poly<P>(eR, c32t[P].pm, c32t[P].phi[r], c2);
-          if (!eL && trL && f == 0) bL = bR;
-          if (!eR && trR && f == nvalid) bR = bL;
-        }
-        dllf32<0>(bL, bR, dL, dR, hf);
-#pragma unroll
-        for (int w3 = 0; w3 < 3; w3++) sFX[(w3 * m + r) * 33 + f] = hf[w3];
       }
     }
   }
@@ -755,10 +787,10 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   }
   if (zones) {
     // the damping targets Q0 - Q_b at the nodes are copied by the TMA unit
-    // into the face buffers, dead from here on, while the nodal values of the
-    // new state are formed
-    float* sDb = sXT;
-    static_assert(3 * M * 32 <= S::B0 - S::XT, "prefetch buffer exceeds the face buffers");
+    // into planes 3-5 of the pointwise terms, dead from here on, while the
+    // nodal values of the new state are formed in planes 0-2
+    float* sDb = sm + S::F + 3 * M * 32;
+    static_assert(3 * M * 32 <= 5 * M * 32, "prefetch buffer exceeds the dead pointwise planes");
     fence_proxy_async_smem();
     __syncthreads();  // every read of the pointwise terms and face fluxes by P3 is done
     if (tid == 0) {

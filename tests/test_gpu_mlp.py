@@ -1,11 +1,13 @@
 """The learned troubled-cell indicator's kernels against the FP64 reference
 network (oracle/mlp.py).
 
-Features are formed in FP64 and rounded once on both sides: bit for bit.
-Logits and gradients accumulate in FP32 on the GPU (BF16 weights, the same
-on both sides): logits to 1e-4 absolute plus 1e-4 relative, the gradient to
-1e-4 relative L2, the loss to 1e-5.  Fused inference on the state (features
-on the fly) against the reference on the oracle's features.  Training on the
+Features (dg_features, the training inputs) are formed in FP64 and rounded
+once on both sides: bit for bit.  Logits and gradients accumulate in FP32 on
+the GPU (BF16 weights, the same on both sides): logits to 1e-4 absolute plus
+1e-4 relative, the gradient to 1e-4 relative L2, the loss to 1e-5.  Fused
+inference on the state, which forms its inputs on the fly in FP32 (within
+2^-22 relative of the FP64-product features), against the reference network
+on the oracle's features, at the same logit tolerance.  Training on the
 GPU lowers the loss; limiter 2 without a network is the TVB limiter.
 """
 import numpy as np
