@@ -56,6 +56,7 @@ struct dg_handle {
   float* DZ;
   float* Rb;           // R_b = L(u_b) from the FP64 kernel, stored FP32: the tiles that keep it, packed
   int* RbIdx;          // per tile: its slot in Rb, or -1 (every |R_b| of the tile below the threshold)
+  double *SN, *SXF, *SYF;  // FP64 form, locally isothermal disc with the star: static fields (StageArgs)
   float* SigbN;
   float* Db;
   float* Bm0;
@@ -276,6 +277,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t state, canon, gcol, grow, tsb, part, series, cpart, csum, flags8, rkx;
   size_t state32, nodes32, db32, bm032, disc32, flags;  // precision form only (0 otherwise)
+  size_t sfn, sfx, sfy;  // static fields of the FP64 locally isothermal disc with the star (0 otherwise)
   size_t total;
 };
 
@@ -380,7 +382,7 @@ double cfl_factor(int p, int positivity) {
   return f;
 }
 
-Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec, int rk) {
+Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec, int rk, int star) {
   Layout L;
   const int m = order + 1, M = m * m, nv = eos->kind == 1 ? 4 : 3;
   const size_t ntx = (mesh->nx + TILE - 1) / TILE;
@@ -403,6 +405,12 @@ Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec, in
     L.disc32 = align256((size_t)mesh->ny * ntx * TILE * sizeof(float));
     L.flags = align256((size_t)mesh->ny * ntx * sizeof(int));
   }
+  L.sfn = L.sfx = L.sfy = 0;
+  if (prec == 0 && eos->kind == 0 && star) {
+    L.sfn = align256((size_t)mesh->ny * ntx * 3 * M * TILE * sizeof(double));
+    L.sfx = align256((size_t)mesh->ny * m * (mesh->nx + 1) * 2 * sizeof(double));
+    L.sfy = align256((size_t)(mesh->ny + 1) * mesh->nx * m * 2 * sizeof(double));
+  }
   L.flags8 = align256((size_t)mesh->nx * mesh->ny);
   L.total = 3 * L.state + L.canon + 2 * L.gcol + 2 * L.grow + L.tsb + L.part + L.series + L.cpart + L.csum +
             2 * L.flags8;
@@ -411,6 +419,7 @@ Layout layout_of(const dg_mesh* mesh, int order, const dg_eos* eos, int prec, in
   L.rkx = rk >= 4 ? (size_t)rk_tableau(rk)->s * L.state : 0;
   L.total += L.rkx;
   if (prec == 1) L.total += L.state + 5 * L.state32 + L.nodes32 + L.db32 + L.bm032 + L.disc32 + 3 * L.flags;
+  L.total += L.sfn + L.sfx + L.sfy;
   return L;
 }
 
@@ -541,6 +550,9 @@ int do_steps_butcher(dg_handle* h, int n, double fixed_dt) {
   a.GR = h->GR;
   a.GB = h->GB;
   a.GT = h->GT;
+  a.SN = h->SN;
+  a.SXF = h->SXF;
+  a.SYF = h->SYF;
   a.ts = h->ts;
   a.part = h->part;
   a.mesh = h->dm;
@@ -608,6 +620,9 @@ int do_steps(dg_handle* h, int n, double fixed_dt) {
   a.GR = h->GR;
   a.GB = h->GB;
   a.GT = h->GT;
+  a.SN = h->SN;
+  a.SXF = h->SXF;
+  a.SYF = h->SYF;
   a.ts = h->ts;
   a.part = h->part;
   a.mesh = h->dm;
@@ -657,7 +672,7 @@ int dg_workspace_bytes(const dg_mesh* mesh, int order, const dg_eos* eos, const 
   int rc = validate(mesh, order, eos, disc);
   if (rc) return rc;
   if (!bytes) return fail(nullptr, DG_ERR_ARG, "null bytes");
-  *bytes = layout_of(mesh, order, eos, disc->prec, disc->rk).total;
+  *bytes = layout_of(mesh, order, eos, disc->prec, disc->rk, disc->star).total;
   return DG_OK;
 }
 
@@ -669,7 +684,7 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   int rc = validate(mesh, order, eos, disc);
   if (rc) return rc;
   if (planet->enabled && !(planet->eps > 0.0)) return fail(nullptr, DG_ERR_ARG, "planet eps must be > 0");
-  const Layout L = layout_of(mesh, order, eos, disc->prec, disc->rk);
+  const Layout L = layout_of(mesh, order, eos, disc->prec, disc->rk, disc->star);
   if (workspace && ((uintptr_t)workspace & 255))
     return fail(nullptr, DG_ERR_ARG, "workspace must be 256-byte aligned");
   if (workspace && workspace_bytes < L.total)
@@ -809,6 +824,11 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
   }
   h->tflags = (unsigned char*)take(L.flags8);
   h->gflags = (unsigned char*)take(L.flags8);
+  if (L.sfn) {
+    h->SN = (double*)take(L.sfn);
+    h->SXF = (double*)take(L.sfx);
+    h->SYF = (double*)take(L.sfy);
+  }
   if (h->prec == 1) {
     h->BG = (double*)take(L.state);
     h->D[0] = (float*)take(L.state32);
@@ -860,6 +880,14 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     if (e == cudaSuccess) { ia.out = h->GT; ia.target = 4; e = launch_init(ia, mesh->nx, h->stream); }
   }
   // with the limiters on they also act on the projected initial data
+  if (e == cudaSuccess && h->SN) {
+    switch (order) {
+      case 1: e = launch_static_p1(dm, ph, h->SN, h->SXF, h->SYF, h->stream); break;
+      case 2: e = launch_static_p2(dm, ph, h->SN, h->SXF, h->SYF, h->stream); break;
+      case 3: e = launch_static_p3(dm, ph, h->SN, h->SXF, h->SYF, h->stream); break;
+      default: e = launch_static_p4(dm, ph, h->SN, h->SXF, h->SYF, h->stream); break;
+    }
+  }
   if (e == cudaSuccess && (ph.limiter || ph.positivity)) e = limit_state(h, h->B[0], nullptr);
   if (e != cudaSuccess) {
     fail(h, DG_ERR_CUDA, "init kernels: %s", cudaGetErrorString(e));
@@ -880,6 +908,9 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     a.GR = h->GR;
     a.GB = h->GB;
     a.GT = h->GT;
+    a.SN = h->SN;
+    a.SXF = h->SXF;
+    a.SYF = h->SYF;
     a.ts = h->ts;
     a.part = h->part;
     a.mesh = dm;
@@ -985,6 +1016,9 @@ int dg_rhs(dg_handle* h, double* out) {
     a.GR = h->GR;
     a.GB = h->GB;
     a.GT = h->GT;
+    a.SN = h->SN;
+    a.SXF = h->SXF;
+    a.SYF = h->SYF;
     a.ts = h->ts;
     a.part = h->part;
     a.mesh = h->dm;

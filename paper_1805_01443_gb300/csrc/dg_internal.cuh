@@ -83,6 +83,13 @@ struct StageArgs {
   double cstage;      // stage time t^n + cstage dt
   double fixed_dt;    // > 0: use instead of ts->dt
   int mode;           // 0: Out = L(U); 1: RK stage; 2: last RK stage (+ damping, torque, CFL)
+  // static fields of the locally isothermal disc with the star (null
+  // otherwise): at the nodes [tile][3][M][32] c_s^2 and the star's gradient
+  // (x, y); at the x-face points [ny][m][nx+1][2] and the y-face points
+  // [ny+1][nx][m][2] c_s^2 and c_s
+  const double* SN;
+  const double* SXF;
+  const double* SYF;
 };
 
 // Parameters of the precision form (FP32 operator on delta = u - u_b).
@@ -142,7 +149,9 @@ struct Tables {
   cudaError_t launch_stage32_p##P(const StageArgs32& a, cudaStream_t s);          \
   cudaError_t launch_torque32_p##P(const float* D, const float* SigbN, const DevState* ts, double* part, \
                                    const Mesh& ms, const Prec32& pc, cudaStream_t s);               \
-  cudaError_t upload_tables32_p##P(const Tables& t);
+  cudaError_t upload_tables32_p##P(const Tables& t);                               \
+  cudaError_t launch_static_p##P(const Mesh& ms, const Phys& ph, double* SN, double* SXF, double* SYF, \
+                                 cudaStream_t s);
 DG_DECLARE_ORDER(1)
 DG_DECLARE_ORDER(2)
 DG_DECLARE_ORDER(3)

@@ -80,7 +80,7 @@ __device__ __forceinline__ void phys_flux(const double* u, double cs2, double ga
 // Local Lax-Friedrichs flux through a face with normal +DIR (0: x, 1: y):
 // h = (f(uL) + f(uR))/2 - alpha (uR - uL)/2, alpha = max(|v_n| + c) of the two sides.
 template <int KIND, int DIR>
-__device__ __forceinline__ void llf(const double* uL, const double* uR, double cs2, double gam,
+__device__ __forceinline__ void llf(const double* uL, const double* uR, double cs2, double cs, double gam,
                                     double* h) {
   constexpr int NV = NVar<KIND>::value;
   double f[2][NV], s[2];
@@ -104,7 +104,7 @@ __device__ __forceinline__ void llf(const double* uL, const double* uR, double c
     f[side][1] = DIR == 0 ? fma(mx, vx, p) : mx * vy;
     f[side][2] = DIR == 0 ? my * vx : fma(my, vy, p);
     if (KIND == 1) f[side][3] = (u[3] + p) * vn;
-    s[side] = fabs(vn) + sqrt(c2);
+    s[side] = fabs(vn) + (KIND == 1 ? sqrt(c2) : cs);
   }
   const double al = fmax(s[0], s[1]);
 #pragma unroll
@@ -113,8 +113,7 @@ __device__ __forceinline__ void llf(const double* uL, const double* uR, double c
 
 // grad(Phi_* + Phi_p) at (x, y): softened star (solid-body core inside r_s)
 // plus Plummer planet at (px, py).
-__device__ __forceinline__ void grad_phi(const Phys& ph, double x, double y, double px, double py,
-                                         double& gx, double& gy) {
+__device__ __forceinline__ void grad_star(const Phys& ph, double x, double y, double& gx, double& gy) {
   gx = 0.0;
   gy = 0.0;
   if (ph.star) {
@@ -129,6 +128,9 @@ __device__ __forceinline__ void grad_phi(const Phys& ph, double x, double y, dou
     gx = x * inv;
     gy = y * inv;
   }
+}
+__device__ __forceinline__ void grad_planet(const Phys& ph, double x, double y, double px, double py,
+                                            double& gx, double& gy) {
   if (ph.planet) {
     double ddx = x - px, ddy = y - py;
     double d2 = fma(ddx, ddx, fma(ddy, ddy, ph.eps2));
@@ -379,10 +381,24 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
         na[v] = trT ? s0 : s3;
       }
       double hf[NV];
-      llf<KIND, 1>(nb, yb, cs2_at<KIND>(ph, xq, ms.y0 + j * ms.dy), ph.gamma, hf);
+      double c2b, cb, c2t, ct;
+      if (KIND == 0 && a.SYF) {
+        const size_t o = ((size_t)j * ms.nx + i0 + lc) * m + q;
+        const size_t stride = (size_t)ms.nx * m;
+        c2b = a.SYF[2 * o];
+        cb = a.SYF[2 * o + 1];
+        c2t = a.SYF[2 * (o + stride)];
+        ct = a.SYF[2 * (o + stride) + 1];
+      } else {
+        c2b = cs2_at<KIND>(ph, xq, ms.y0 + j * ms.dy);
+        cb = sqrt(c2b);
+        c2t = cs2_at<KIND>(ph, xq, ms.y0 + (j + 1) * ms.dy);
+        ct = sqrt(c2t);
+      }
+      llf<KIND, 1>(nb, yb, c2b, cb, ph.gamma, hf);
 #pragma unroll
       for (int v = 0; v < NV; v++) sFYB[(v * m + q) * 32 + lane] = hf[v];
-      llf<KIND, 1>(yt, na, cs2_at<KIND>(ph, xq, ms.y0 + (j + 1) * ms.dy), ph.gamma, hf);
+      llf<KIND, 1>(yt, na, c2t, ct, ph.gamma, hf);
 #pragma unroll
       for (int v = 0; v < NV; v++) sFYT[(v * m + q) * 32 + lane] = hf[v];
     }
@@ -403,9 +419,18 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
       double uu[NV], fx[NV], fy[NV], src[NV];
 #pragma unroll
       for (int v = 0; v < NV; v++) uu[v] = u[v][r];
-      phys_flux<KIND>(uu, cs2_at<KIND>(ph, xq, y), ph.gamma, fx, fy);
-      double gx, gy;
-      grad_phi(ph, xq, y, px, py, gx, gy);
+      double gx, gy, c2n;
+      if (KIND == 0 && a.SN) {
+        const double* sn = a.SN + tile * 3 * M * 32 + (size_t)(q * m + r) * 32 + lane;
+        c2n = sn[0];
+        gx = sn[M * 32];
+        gy = sn[2 * M * 32];
+      } else {
+        c2n = cs2_at<KIND>(ph, xq, y);
+        grad_star(ph, xq, y, gx, gy);
+      }
+      phys_flux<KIND>(uu, c2n, ph.gamma, fx, fy);
+      grad_planet(ph, xq, y, px, py, gx, gy);
       src[0] = 0.0;
       src[1] = -uu[0] * gx;
       src[2] = -uu[0] * gy;
@@ -442,7 +467,16 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
         uL[v] = sXR[(v * m + r) * 33 + f];
         uR[v] = sXL[(v * m + r) * 33 + f];
       }
-      llf<KIND, 0>(uL, uR, cs2_at<KIND>(ph, ms.x0 + (i0 + f) * ms.dx, y), ph.gamma, hf);
+      double c2f, cf;
+      if (KIND == 0 && a.SXF) {
+        const size_t o = ((size_t)j * m + r) * (ms.nx + 1) + i0 + f;
+        c2f = a.SXF[2 * o];
+        cf = a.SXF[2 * o + 1];
+      } else {
+        c2f = cs2_at<KIND>(ph, ms.x0 + (i0 + f) * ms.dx, y);
+        cf = sqrt(c2f);
+      }
+      llf<KIND, 0>(uL, uR, c2f, cf, ph.gamma, hf);
 #pragma unroll
       for (int v = 0; v < NV; v++) sFX[(v * m + r) * 33 + f] = hf[v];
     }
@@ -696,6 +730,67 @@ __global__ void __launch_bounds__(32 * (P + 1)) k_stage(const StageArgs a) {
     a.part[2 * tile] = gx;
     a.part[2 * tile + 1] = gy;
   }
+}
+
+// Static fields of the locally isothermal disc with the star, evaluated
+// once with the expressions (and the operand order) the stage kernel uses
+// without them, so a kernel that reads them computes the same values: at the
+// nodes c_s^2 and the star's gradient, at the face points c_s^2 and c_s.
+template <int P>
+__global__ void k_static_fields(const Mesh ms, const Phys ph, double* SN, double* SXF, double* SYF) {
+  constexpr int m = P + 1, M = m * m;
+  const long long nn = (long long)ms.ny * ms.ntx * M * 32;
+  const long long nxf = (long long)ms.ny * m * (ms.nx + 1);
+  const long long nyf = (long long)(ms.ny + 1) * ms.nx * m;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn + nxf + nyf;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (t < nn) {
+      // [tile][field][q m + r][lane]
+      const int lane = (int)(t & 31);
+      const int n = (int)((t >> 5) % M);
+      const long long tile = (t >> 5) / M;
+      const int j = (int)(tile / ms.ntx), i0 = (int)(tile % ms.ntx) * 32;
+      const int q = n / m, r = n - q * m;
+      const double xq = ms.x0 + (i0 + lane + 0.5) * ms.dx + 0.5 * ms.dx * c_tab.xi[q];
+      const double yc = ms.y0 + (j + 0.5) * ms.dy;
+      const double y = yc + 0.5 * ms.dy * c_tab.xi[r];
+      double gx, gy;
+      grad_star(ph, xq, y, gx, gy);
+      double* o = SN + tile * 3 * M * 32 + (size_t)n * 32 + lane;
+      o[0] = cs2_at<0>(ph, xq, y);
+      o[M * 32] = gx;
+      o[2 * M * 32] = gy;
+    } else if (t < nn + nxf) {
+      // [j][r][f]: face f of row j at y-node r
+      const long long u = t - nn;
+      const int f = (int)(u % (ms.nx + 1));
+      const int r = (int)((u / (ms.nx + 1)) % m);
+      const int j = (int)(u / ((long long)(ms.nx + 1) * m));
+      const int i0 = (f / 32) * 32, ff = f - i0;
+      const double y = ms.y0 + (j + 0.5) * ms.dy + 0.5 * ms.dy * c_tab.xi[r];
+      const double c2 = cs2_at<0>(ph, ms.x0 + (i0 + ff) * ms.dx, y);
+      SXF[2 * u] = c2;
+      SXF[2 * u + 1] = sqrt(c2);
+    } else {
+      // [j'][i][q]: the face y = y0 + j' dy at x-node q of element i
+      const long long u = t - nn - nxf;
+      const int q = (int)(u % m);
+      const int i = (int)((u / m) % ms.nx);
+      const int jf = (int)(u / ((long long)m * ms.nx));
+      const int i0 = (i / 32) * 32, lane = i - i0;
+      const double xq = ms.x0 + (i0 + lane + 0.5) * ms.dx + 0.5 * ms.dx * c_tab.xi[q];
+      const double c2 = cs2_at<0>(ph, xq, ms.y0 + jf * ms.dy);
+      SYF[2 * u] = c2;
+      SYF[2 * u + 1] = sqrt(c2);
+    }
+  }
+}
+
+template <int P>
+static cudaError_t launch_static_impl(const Mesh& ms, const Phys& ph, double* SN, double* SXF, double* SYF,
+                                      cudaStream_t s) {
+  k_static_fields<P><<<1216, 256, 0, s>>>(ms, ph, SN, SXF, SYF);
+  return cudaGetLastError();
 }
 
 template <int P>
