@@ -207,6 +207,18 @@ int dg_set_state(dg_handle *h, const double *coeffs, double t, long step);
    host memory that is not page-locked. */
 int dg_set_state_async(dg_handle *h, const double *coeffs, double t, long step);
 
+/* Precision form only (DG_ERR_UNSUPPORTED otherwise): its state is the FP32
+   perturbation delta = u - u_b about the projected background u_b, so a caller
+   that holds delta can exchange it directly, at half the bytes of the FP64
+   state.  Layout: canonical, FP32, [var][a*m+b][j][i].
+   dg_set_delta_async: as dg_set_state_async with u = u_b + delta (the same
+   copy stream, staging buffers and ordering; page-locked host memory only,
+   unchanged until the next synchronising call).
+   dg_fetch_delta: copy the current delta to the caller's host array;
+   synchronises. */
+int dg_set_delta_async(dg_handle *h, const float *delta, double t, long step);
+int dg_fetch_delta(dg_handle *h, float *delta);
+
 /* dg_torque without waiting: queue the copy of the torque of the last step
    queued before it into *gz (page-locked host memory), valid after the next
    synchronising call.  DG_ERR_ARG for memory that is not page-locked. */

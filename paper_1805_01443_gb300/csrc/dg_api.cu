@@ -1151,6 +1151,51 @@ int dg_set_state_async(dg_handle* h, const double* coeffs, double t, long step) 
   return launch_cfl_and_dt(h, full);
 }
 
+int dg_set_delta_async(dg_handle* h, const float* delta, double t, long step) {
+  if (!h || !delta) return fail(h, DG_ERR_ARG, "null argument");
+  if (h->prec != 1) return fail(h, DG_ERR_UNSUPPORTED, "dg_set_delta_async: the precision form only");
+  if (!isfinite(t)) return fail(h, DG_ERR_ARG, "t must be finite");
+  if (!page_locked(delta)) return fail(h, DG_ERR_ARG, "dg_set_delta_async needs page-locked host memory");
+  const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
+  if (!h->cstream) {
+    CU(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; k++) {
+      CU(h, cudaEventCreateWithFlags(&h->ev_copied[k], cudaEventDisableTiming));
+      CU(h, cudaEventCreateWithFlags(&h->ev_consumed[k], cudaEventDisableTiming));
+      CU(h, cudaMalloc((void**)&h->SA[k], n * sizeof(double)));
+    }
+  }
+  // the staging buffers hold n doubles; the FP32 delta takes half of one
+  const int k = h->apar;
+  float* stage = reinterpret_cast<float*>(h->SA[k]);
+  CU(h, cudaStreamWaitEvent(h->cstream, h->ev_consumed[k], 0));
+  CU(h, cudaMemcpyAsync(stage, delta, n * sizeof(float), cudaMemcpyHostToDevice, h->cstream));
+  CU(h, cudaEventRecord(h->ev_copied[k], h->cstream));
+  CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
+  CU(h, launch_ingest_delta(stage, h->D[0], h->BG, h->Z, h->dm, h->nv, h->M, h->stream));
+  CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
+  CU(h, launch_reset_state(h->ts, t, step, h->stream));
+  h->cur = h->cur0 = 0;
+  h->step0 = step;
+  h->series_read = 0;
+  h->apar = 1 - k;
+  return launch_cfl_and_dt(h, h->Z);
+}
+
+int dg_fetch_delta(dg_handle* h, float* delta) {
+  if (!h || !delta) return fail(h, DG_ERR_ARG, "null argument");
+  if (h->prec != 1) return fail(h, DG_ERR_UNSUPPORTED, "dg_fetch_delta: the precision form only");
+  DevState st;
+  int rc = read_state(h, &st);
+  if (rc && rc != DG_ERR_NUMERIC) return rc;
+  float* canon = reinterpret_cast<float*>(h->S);
+  CU(h, launch_to_canon_f32(h->D[h->cur], canon, h->dm, h->nv, h->M, h->stream));
+  const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
+  CU(h, cudaMemcpyAsync(delta, canon, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
 int dg_torque_async(dg_handle* h, double* gz) {
   if (!h || !gz) return fail(h, DG_ERR_ARG, "null argument");
   if (!page_locked(gz)) return fail(h, DG_ERR_ARG, "dg_torque_async needs page-locked host memory");

@@ -156,6 +156,33 @@ __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ 
   }
 }
 
+// canonical FP32 delta -> tiled delta and the tiled FP64 state u_b + delta
+__global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const double* __restrict__ bg,
+                               double* __restrict__ full, const Mesh ms, int nv, int M) {
+  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ms.nx);
+    const size_t r1 = e / ms.nx;
+    const int j = (int)(r1 % ms.ny);
+    const size_t vk = r1 / ms.ny;
+    const size_t t = (((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31);
+    const float x = canon[e];
+    d[t] = x;
+    full[t] = bg[t] + (double)x;
+  }
+}
+
+__global__ void k_to_canon_f32(const float* tiled, float* canon, const Mesh ms, int nv, int M) {
+  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ms.nx);
+    const size_t r1 = e / ms.nx;
+    const int j = (int)(r1 % ms.ny);
+    const size_t vk = r1 / ms.ny;
+    canon[e] = tiled[(((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31)];
+  }
+}
+
 __global__ void k_to_canon(const double* tiled, double* canon, const Mesh ms, int nv, int M) {
   const size_t n = (size_t)nv * M * ms.nx * ms.ny;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -277,6 +304,18 @@ cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStrea
 cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
                           int nv, int M, cudaStream_t s) {
   k_ingest<<<1216, 256, 0, s>>>(canon, tiled, bg, d, mesh, nv, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_delta(const float* canon, float* d, const double* bg, double* full, const Mesh& mesh,
+                                int nv, int M, cudaStream_t s) {
+  k_ingest_delta<<<1216, 256, 0, s>>>(canon, d, bg, full, mesh, nv, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
+                                cudaStream_t s) {
+  k_to_canon_f32<<<1216, 256, 0, s>>>(tiled, canon, mesh, nv, M);
   return cudaGetLastError();
 }
 

@@ -183,6 +183,11 @@ cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, 
                           int nv, int M, cudaStream_t s);
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
                             cudaStream_t s);
+// precision form: canonical FP32 delta -> tiled delta d and tiled FP64 u_b + delta
+cudaError_t launch_ingest_delta(const float* canon, float* d, const double* bg, double* full, const Mesh& mesh,
+                                int nv, int M, cudaStream_t s);
+cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
+                                cudaStream_t s);
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,
                              int M, cudaStream_t s);
 cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s);

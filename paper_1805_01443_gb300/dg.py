@@ -32,7 +32,8 @@ EXPORTED = ["dg_init", "dg_init_ex", "dg_workspace_bytes", "dg_step", "dg_step_d
             "dg_batch_sync", "dg_batch_destroy", "dg_indicator", "dg_limit", "dg_limit_flags",
             "dg_last_flags", "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_nparams", "dg_mlp_get_params",
             "dg_mlp_set_params", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step", "dg_features",
-            "dg_set_indicator", "dg_indicator_logits", "dg_selftest_wait", "dg_prec_tiles"]
+            "dg_set_indicator", "dg_indicator_logits", "dg_selftest_wait", "dg_prec_tiles",
+            "dg_set_delta_async", "dg_fetch_delta"]
 
 
 class DgMesh(ctypes.Structure):
@@ -133,6 +134,8 @@ def lib(build_if_missing=True):
         L.dg_batch_destroy.argtypes = [_VP]
         L.dg_selftest_wait.argtypes = [ctypes.c_int, P(ctypes.c_int)]
         L.dg_prec_tiles.argtypes = [_VP, P(ctypes.c_longlong), P(ctypes.c_longlong), P(ctypes.c_longlong)]
+        L.dg_set_delta_async.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_long]
+        L.dg_fetch_delta.argtypes = [_VP, _VP]
         _lib = L
     return _lib
 
@@ -248,6 +251,23 @@ class Disc:
             raise ValueError("set_state_async: the array must hold the full state")
         _check(lib().dg_set_state_async(self.h, _ptr(coeffs), t, step), self.h)
         self._keep.append(coeffs)
+
+    def set_delta_async(self, delta, t=0.0, step=0):
+        """dg_set_delta_async (precision form): `delta`, a C-contiguous float32
+        array of the state's shape in page-locked memory, is kept referenced
+        until the next sync()."""
+        if not (delta.dtype == np.float32 and delta.flags["C_CONTIGUOUS"] and
+                delta.size == int(np.prod(self.shape))):
+            raise ValueError("set_delta_async: a C-contiguous float32 array of the state's shape")
+        _check(lib().dg_set_delta_async(self.h, delta.ctypes.data_as(_VP), t, step), self.h)
+        self._keep.append(delta)
+
+    def fetch_delta(self, out=None):
+        """dg_fetch_delta (precision form): delta = u - u_b as float32."""
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        _check(lib().dg_fetch_delta(self.h, out.ctypes.data_as(_VP)), self.h)
+        return out
 
     def torque_async(self, out, index=0):
         """dg_torque_async into out[index] (a float64 array in page-locked

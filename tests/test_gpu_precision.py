@@ -334,3 +334,42 @@ def test_background_residual_kept_only_where_it_matters():
     rmax = np.abs(Lo).max()
     bound = 1.2e-7 * np.abs(Lo) + 1.01e-10 * rmax + 1e-15 * np.abs(u).max() / dt
     assert np.all(np.abs(Lg - Lo) <= bound), float((np.abs(Lg - Lo) / bound).max())
+
+
+def test_delta_upload_matches_the_fp64_upload():
+    """dg_set_delta_async (the FP32 perturbation, half the bytes) gives the
+    steps of dg_set_state_async of u_b + delta, and dg_fetch_delta returns the
+    delta the steps leave.  The FP64 upload recovers delta as
+    (float)((u_b + delta) - u_b), which can move a coefficient far smaller
+    than u_b by a few of its own FP32 units: the results agree to FP32
+    rounding of delta."""
+    cfg = prec_cfg(inputs.disc_planet(64, 4, q=3e-5))
+    with dg.Disc(cfg) as a, dg.Disc(cfg) as b:
+        a.step(3)
+        delta = torch.from_numpy(a.fetch_delta()).pin_memory().numpy()
+        full = torch.from_numpy(a.fetch()).pin_memory().numpy()
+        t, _, st = a.get_time()
+        a.set_delta_async(delta, t, st)
+        b.set_state_async(full, t, st)
+        a.step(4)
+        b.step(4)
+        a.sync()
+        b.sync()
+        da, db = a.fetch_delta(), b.fetch_delta()
+        for v in range(3):
+            assert np.abs(da[v] - db[v]).max() <= 1e-6 * np.abs(db[v]).max(), v
+        assert a.get_time()[0] == pytest.approx(b.get_time()[0], rel=1e-12)
+        assert a.get_time()[2] == b.get_time()[2]
+        assert rel(a.torque_series(), b.torque_series()) <= 1e-7
+        assert rel(a.fetch()[0], b.fetch()[0]) <= 1e-10
+        # the fetched delta is the state the handle steps from
+        full = a.fetch()
+        c = torch.from_numpy(a.fetch_delta()).pin_memory().numpy()
+        t, _, st = a.get_time()
+        b.set_delta_async(c, t, st)
+        b.sync()
+        np.testing.assert_array_equal(b.fetch(), full)
+    with dg.Disc(inputs.disc_small(16, 2)) as f64:
+        with pytest.raises(dg.DgError) as e:
+            f64.fetch_delta()
+        assert e.value.code == dg.DG_ERR_UNSUPPORTED
