@@ -385,15 +385,7 @@ __device__ __forceinline__ void ytrace32(const float* c, const float* f, float* 
 #ifndef DG_STAGE32_MIN_CTAS
 #define DG_STAGE32_MIN_CTAS 7
 #endif
-// 1: each warp asks the L2 for the lines of u^n (and R_b) that its update
-// reads at the end of the tile, when the tile starts
-#ifndef DG_STAGE32_PREFETCH
-#define DG_STAGE32_PREFETCH 1
-#endif
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
 
 // LAST = false: modes 0 (operator only) and 1 (RK stage); LAST = true: mode 2
 // (last RK stage with damping, torque and CFL), compiled apart so that the
@@ -476,17 +468,6 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   else if (ms.bc == 1) zR = true;
   else if (ms.bc == 3) { const int ie = ms.nx - 1; pR = Dcur + ((size_t)j * ms.ntx + (ie >> 5)) * NVM * 32 + voff + (ie & 31); }
   const bool trL = !pL && !zL, trR = !pR && !zR;
-#if DG_STAGE32_PREFETCH
-  {
-    // lane k < M: the 128-byte row of mode k of this warp's variable
-    const size_t row = tile * NVM * 32 + voff + (size_t)lane * 32;
-    if (lane < M) {
-      if (mode == 1 && alpha != 0.0f) prefetch_l2(Dn0 + row);
-      const int rb = a.RbIdx[tile];
-      if (rb >= 0) prefetch_l2(a.Rb + (size_t)rb * NVM * 32 + voff + (size_t)lane * 32);
-    }
-  }
-#endif
   // tiles near the singular centre use the exact projected background (FP32
   // modes of u_b, same tiled layout as delta, all three variables)
   const int exact = a.TileFlag[tile];
@@ -790,7 +771,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
     // into planes 3-5 of the pointwise terms, dead from here on, while the
     // nodal values of the new state are formed in planes 0-2
     float* sDb = sm + S::F + 3 * M * 32;
-    static_assert(3 * M * 32 <= 5 * M * 32, "prefetch buffer exceeds the dead pointwise planes");
+    static_assert(3 * M * 32 <= 5 * M * 32, "damping offsets exceed the dead pointwise planes");
     fence_proxy_async_smem();
     __syncthreads();  // every read of the pointwise terms and face fluxes by P3 is done
     if (tid == 0) {
