@@ -8,9 +8,9 @@
 // largest |c_s[v][k]| over the stencil and the modes (1 when all vanish): the
 // reciprocal and the product in FP64, the product rounded once to FP32
 // (dg_features, the training inputs).  The inference kernel on the tensor
-// cores forms the same inputs in FP32 -- the coefficient and the reciprocal
-// each rounded to FP32, then their FP32 product -- within three FP32 roundings
-// of those (relative 2^-22) and without an FP64 instruction per input.
+// cores forms the same inputs in FP32 -- the coefficient truncated and the
+// reciprocal rounded to FP32, then their FP32 product -- within 2^-22
+// relative of those and without an FP64 instruction per input.
 //
 // Parameters (FP32 master copy, flat): W1 [64][nin], b1 [64], W2 [64][64],
 // b2 [64], w3 [64], b3.  The products use the weights rounded to BF16
@@ -291,6 +291,16 @@ __device__ __forceinline__ float d2f_rn(double x) {
   return __uint_as_float(f | (hi & 0x80000000u));
 }
 
+// double -> float by truncation of the 29 dropped fraction bits, branch-free on
+// the integer pipe: |x| in [2^-126, 2^128) keeps its exponent and top 23
+// fraction bits (within one FP32 unit, toward zero), smaller |x| gives zero
+__device__ __forceinline__ float d2f_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ah = hi & 0x7FFFFFFFu;
+  const unsigned f = ah >= (897u << 20) ? (((ah - (896u << 20)) << 3) | (lo >> 29)) : 0u;
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
 // the mesh element standing for stencil element (ii, jj) of element (ci, cj):
 // false for a fixed ghost element (bc 1)
 __device__ __forceinline__ bool mesh_elem(const Mesh& ms, int ii, int jj, int ci, int cj, long long& tile,
@@ -473,12 +483,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
 #pragma unroll
         for (int e = 0; e < 8; e++) cv[h8 * 8 + e] = (on && kk0 + e < M) ? q[e * qs] : 0.0;
       }
-      // each coefficient rounded to FP32 on the integer pipe, then scaled in
-      // FP32: within two FP32 roundings of the features of the FP64 product
+      // each coefficient truncated to FP32 on the integer pipe, then scaled
+      // in FP32: within 2^-22 of the features of the FP64 product
       // (dg_features), and no FP64 instruction per input
       float x[16];
 #pragma unroll
-      for (int t = 0; t < 16; t++) x[t] = d2f_rn(cv[t]) * rv2[t >> 3];
+      for (int t = 0; t < 16; t++) x[t] = d2f_rz(cv[t]) * rv2[t >> 3];
       // the previous chunk's MMAs have read the A buffer
       if (c > 0 && g == 0) ok &= mbar_wait(&bar[0], (c - 1) & 1);
 #pragma unroll
