@@ -62,6 +62,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void counter_signal(int* ctr) {
   asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");
 }
+__device__ __forceinline__ int counter_load_relaxed(const int* ctr) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+  return v;
+}
 __device__ __forceinline__ int counter_load(const int* ctr) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");

@@ -140,13 +140,22 @@ __device__ __forceinline__ void flow_stage_item(const BatchLaunch32& L, int stag
   int* rows = F.ctr + FLOW_ROWS + 3 * F.rowbase[k];
   bool ok = true;
   if (stage > 0 && threadIdx.x == 0) {
-#pragma unroll 1
-    for (int d = -1; d <= 1 && ok; d++) {
+    // the three rows' counters read together (one round trip); the bounded
+    // waits only for a row that is not finished yet; then the acquiring fence
+    int rr[3];
+#pragma unroll
+    for (int d = -1; d <= 1; d++) {
       int r = j + d;
       if (r < 0) r = ms.bc == 0 ? ms.ny - 1 : -1;
       else if (r >= ms.ny) r = ms.bc == 0 ? 0 : -1;
-      if (r >= 0) ok = flow_wait(F, rows + 3 * r + (stage - 1), ms.ntx);
+      rr[d + 1] = r;
     }
+    int cv[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) cv[d] = rr[d] >= 0 ? counter_load_relaxed(rows + 3 * rr[d] + (stage - 1)) : ms.ntx;
+#pragma unroll 1
+    for (int d = 0; d < 3 && ok; d++)
+      if (cv[d] < ms.ntx) ok = flow_wait(F, rows + 3 * rr[d] + (stage - 1), ms.ntx);
     __threadfence();
   }
   if (__syncthreads_or(!ok)) {

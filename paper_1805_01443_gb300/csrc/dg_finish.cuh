@@ -56,7 +56,8 @@ __device__ __forceinline__ void finish_step_nt(double* sx, double* sy, DevState*
     const double2* p2 = reinterpret_cast<const double2*>(part);
     for (int v = tid; v < NL; v += NT) {
       double gx = 0.0, gy = 0.0;
-#pragma unroll 4
+      // unrolled so that 16 loads are in flight; the additions keep their order
+#pragma unroll 16
       for (int k = v; k < nparts; k += NL) {
         const double2 g = p2[k];
         gx += g.x;
