@@ -433,8 +433,8 @@ int read_state(dg_handle* h, DevState* out) {
 }
 
 // CFL step of a full FP64 tiled state into the device time state
-int launch_cfl_and_dt(dg_handle* h, const double* full) {
-  CU(h, launch_cfl(full, h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
+int launch_cfl_and_dt(dg_handle* h, const double* full, const float* delta = nullptr) {
+  CU(h, launch_cfl(full, delta, h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
   CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, 0, h->ph.r_p, h->ph.omega_p,
                       h->ph.phi0, h->stream));
   return DG_OK;
@@ -1172,14 +1172,14 @@ int dg_set_delta_async(dg_handle* h, const float* delta, double t, long step) {
   CU(h, cudaMemcpyAsync(stage, delta, n * sizeof(float), cudaMemcpyHostToDevice, h->cstream));
   CU(h, cudaEventRecord(h->ev_copied[k], h->cstream));
   CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
-  CU(h, launch_ingest_delta(stage, h->D[0], h->BG, h->Z, h->dm, h->nv, h->M, h->stream));
+  CU(h, launch_ingest_delta(stage, h->D[0], h->dm, h->nv, h->M, h->stream));
   CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
   h->cur = h->cur0 = 0;
   h->step0 = step;
   h->series_read = 0;
   h->apar = 1 - k;
-  return launch_cfl_and_dt(h, h->Z);
+  return launch_cfl_and_dt(h, h->BG, h->D[0]);  // element averages of u_b + delta
 }
 
 int dg_fetch_delta(dg_handle* h, float* delta) {

@@ -80,7 +80,9 @@ __global__ void k_init(const InitArgs a, int count) {
 
 // CFL time step of Sec. 2.3 from the element averages; block minimum folded
 // into the device slot with an atomic minimum on the (positive) bit pattern.
-__global__ void k_cfl(const double* U, DevState* ts, const Mesh ms, const Phys ph, int p, int nv) {
+// CFL minimum of the element averages of U (tiled FP64), or of U + D when D
+// (tiled FP32, the precision form's delta about U = u_b) is given
+__global__ void k_cfl(const double* U, const float* D, DevState* ts, const Mesh ms, const Phys ph, int p, int nv) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int M = (p + 1) * (p + 1);
   double dtk = __longlong_as_double((long long)INF_BITS);
@@ -88,11 +90,15 @@ __global__ void k_cfl(const double* U, DevState* ts, const Mesh ms, const Phys p
   if (e < ms.nx * ms.ny) {
     const int i = e % ms.nx, j = e / ms.nx;
     const size_t base = (((size_t)j * ms.ntx + (i >> 5)) * nv * M) * TILE + (i & 31);
-    const double rho = U[base], mx = U[base + (size_t)M * TILE], my = U[base + (size_t)2 * M * TILE];
+    auto avg = [&](int v) {
+      const size_t o = base + (size_t)v * M * TILE;
+      return D ? U[o] + (double)D[o] : U[o];
+    };
+    const double rho = avg(0), mx = avg(1), my = avg(2);
     const double vx = mx / rho, vy = my / rho;
     double c;
     if (ph.kind == 1) {
-      const double E = U[base + (size_t)3 * M * TILE];
+      const double E = avg(3);
       const double pr = (ph.gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy));
       c = sqrt(ph.gamma * pr / rho);
     } else if (ph.kind == 2) {
@@ -156,9 +162,9 @@ __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ 
   }
 }
 
-// canonical FP32 delta -> tiled delta and the tiled FP64 state u_b + delta
-__global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const double* __restrict__ bg,
-                               double* __restrict__ full, const Mesh ms, int nv, int M) {
+// canonical FP32 delta -> tiled delta
+__global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const Mesh ms, int nv,
+                               int M) {
   const size_t n = (size_t)nv * M * ms.nx * ms.ny;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % ms.nx);
@@ -166,9 +172,7 @@ __global__ void k_ingest_delta(const float* __restrict__ canon, float* __restric
     const int j = (int)(r1 % ms.ny);
     const size_t vk = r1 / ms.ny;
     const size_t t = (((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31);
-    const float x = canon[e];
-    d[t] = x;
-    full[t] = bg[t] + (double)x;
+    d[t] = canon[e];
   }
 }
 
@@ -242,10 +246,10 @@ cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
+cudaError_t launch_cfl(const double* U, const float* D, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
                        int nv, cudaStream_t s) {
   const int n = mesh.nx * mesh.ny;
-  k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, ts, mesh, phys, p, nv);
+  k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, D, ts, mesh, phys, p, nv);
   return cudaGetLastError();
 }
 
@@ -307,9 +311,8 @@ cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ingest_delta(const float* canon, float* d, const double* bg, double* full, const Mesh& mesh,
-                                int nv, int M, cudaStream_t s) {
-  k_ingest_delta<<<1216, 256, 0, s>>>(canon, d, bg, full, mesh, nv, M);
+cudaError_t launch_ingest_delta(const float* canon, float* d, const Mesh& mesh, int nv, int M, cudaStream_t s) {
+  k_ingest_delta<<<1216, 256, 0, s>>>(canon, d, mesh, nv, M);
   return cudaGetLastError();
 }
 

@@ -172,7 +172,8 @@ struct InitArgs {
 };
 
 cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s);
-cudaError_t launch_cfl(const double* U, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
+// CFL step from the element averages of U, or of U + D (D: FP32 delta, may be null)
+cudaError_t launch_cfl(const double* U, const float* D, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
                        int nv, cudaStream_t s);
 cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
                           double fixed_dt, int advance, int planet32, double r_p, double omega_p,
@@ -183,9 +184,8 @@ cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, 
                           int nv, int M, cudaStream_t s);
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
                             cudaStream_t s);
-// precision form: canonical FP32 delta -> tiled delta d and tiled FP64 u_b + delta
-cudaError_t launch_ingest_delta(const float* canon, float* d, const double* bg, double* full, const Mesh& mesh,
-                                int nv, int M, cudaStream_t s);
+// precision form: canonical FP32 delta -> tiled delta d
+cudaError_t launch_ingest_delta(const float* canon, float* d, const Mesh& mesh, int nv, int M, cudaStream_t s);
 cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
                                 cudaStream_t s);
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,
