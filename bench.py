@@ -284,7 +284,11 @@ def error_vs_fp64(dg, cfg, cfg32, nsteps):
             "rel_l2_sigma_minus_bg": rel(up[0] - sig_bg, ua[0] - sig_bg),
             "rel_l2_momentum": max(rel(up[1], ua[1]), rel(up[2], ua[2])),
             "rel_l2_torque_series": rel(tp, ta),
-            "bounds": {"sigma": 1e-5, "torque": 1e-6}}
+            "bounds": {"sigma": 1e-5, "torque": 1e-6},
+            "torque_form": "node terms and their per-element sums in float-float (~2^-44 relative), the "
+                           "reduction over elements and tiles in FP64: the one part of the torque not in "
+                           "FP64; an all-FP64 pass is estimated at ~0.16 ms per step against the "
+                           "float-float pass's ~0.04 ms"}
 
 
 def batched_run(dg, torch, steps=10, tune_steps=3):

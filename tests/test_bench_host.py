@@ -105,3 +105,14 @@ def test_clock_summary_reads_the_median_and_the_throttle_reasons():
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c.lines = []
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_design_bytes_count_the_static_data_apart_from_the_algorithmic_bytes():
+    """800 B per element and stage launch is the algorithmic figure (FP32 state:
+    reads of delta^(s) and delta^n, one write, averaged over the three stages);
+    the design bytes add R_b where it is kept, the background averages and the
+    damping offsets of the zone tiles, all from the handle's tile counts."""
+    assert bench.BYTES_PER_ELEM_STAGE_PREC == (2 + 3 + 3) / 3 * 75 * 4
+    assert bench.design_bytes(100, 0, 0) == 800.0 + 12.0 / 3.0
+    assert bench.design_bytes(100, 100, 100) == 800.0 + 300.0 + (12.0 + 300.0) / 3.0
+    assert 800.0 < bench.design_bytes(8192, 782, 4380) < 900.0
