@@ -112,6 +112,7 @@ def test_design_bytes_count_the_static_data_apart_from_the_algorithmic_bytes():
     reads of delta^(s) and delta^n, one write, averaged over the three stages);
     the design bytes add R_b where it is kept, the background averages and the
     damping offsets of the zone tiles, all from the handle's tile counts."""
+    import bench
     assert bench.BYTES_PER_ELEM_STAGE_PREC == (2 + 3 + 3) / 3 * 75 * 4
     assert bench.design_bytes(100, 0, 0) == 800.0 + 12.0 / 3.0
     assert bench.design_bytes(100, 100, 100) == 800.0 + 300.0 + (12.0 + 300.0) / 3.0
