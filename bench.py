@@ -326,9 +326,10 @@ def batched_run(dg, torch, steps=10, tune_steps=3):
             "speedup_vs_sequential": seq_ms / bat_ms, "steps": steps,
             "schedule": {"policy": dg.Batch.POLICIES[tuned["policy"]],
                          "launches": ["one CTA per tile per stage", "persistent CTAs per stage",
-                                      "one persistent launch per step"][tuned["dynamic"]],
+                                      "one persistent launch per step",
+                                      "one persistent launch per step, round-robin items"][tuned["dynamic"]],
                          "ctas_per_sm": tuned["ctas_per_sm"], "tiles_per_item": tuned["tiles_per_item"]},
-            "gpu_launches_per_step": 1 if tuned["dynamic"] == 2 else 5,
+            "gpu_launches_per_step": 1 if tuned["dynamic"] >= 2 else 5,
             "config": {"workload": "48 planet discs, sizes 128/256/384/512^2 and degrees 2/3/4 "
                                    "cycling, q = 10^U(-6,-4), seeds 100-147, precision form",
                        "instances": len(cfgs), "dof_per_stage": dof}}

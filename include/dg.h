@@ -447,7 +447,9 @@ int dg_batch_create(dg_batch **b, dg_handle *const *handles, int n);
      dynamic         0: one CTA per tile in each stage launch; 1: persistent
                      CTAs (ctas_per_sm per SM) take items from a counter in
                      each stage launch; 2: the flow schedule (one persistent
-                     launch per step)
+                     launch per step), items from a queue counter; 3: the
+                     flow schedule with CTA c taking queue positions c,
+                     c + G, c + 2G, ... (G CTAs, no counter)
      ctas_per_sm     resident CTAs per SM of the persistent grid (0 or above the
                      occupancy limit: the limit)
      tiles_per_item  1, 2 or 4: tiles (32 elements each) of one row per work
@@ -459,7 +461,8 @@ int dg_batch_get_config(const dg_batch *b, int *policy, int *dynamic, int *ctas_
 
 /* Autotuner: times `steps` batched steps under each schedule (3 work orders x
    {persistent per-stage launches at the occupancy limit and one CTA below it,
-   one CTA per tile, the flow schedule with 1, 2 and 4 tiles per item}), keeps
+   one CTA per tile, the flow schedule with 1, 2 and 4 tiles per item from the
+   queue counter and with 1 and 2 in round-robin}), keeps
    the fastest and returns it (any output pointer may be NULL; best_ms is the
    time of one batched step).  The instances are restored afterwards (state,
    time, step count), so tuning does not advance them.  Synchronous. */

@@ -1716,7 +1716,7 @@ bool batch_refresh(dg_batch* b) {
 }
 
 int batch_grid(const dg_batch* b) {
-  if (b->dynamic == 2) return b->sms * b->ctas_per_sm;
+  if (b->dynamic >= 2) return b->sms * b->ctas_per_sm;
   if (!b->dynamic) return b->L->nitems;
   const int g = b->sms * b->ctas_per_sm;
   return g < b->L->nitems ? g : b->L->nitems;
@@ -1725,7 +1725,8 @@ int batch_grid(const dg_batch* b) {
 // one SSP(3,3) step of every instance, as stream work
 cudaError_t batch_enqueue_step(dg_batch* b) {
   BatchLaunch32& L = *b->L;
-  if (b->dynamic == 2) {
+  if (b->dynamic >= 2) {
+    L.flow.rr = b->dynamic == 3 ? 1 : 0;
     cudaError_t e = cudaMemsetAsync(b->d_fctr, 0, b->nfctr * sizeof(int), b->stream);
     if (e == cudaSuccess) e = launch_batch_flow32(L, batch_grid(b), b->stream);
     return e;
@@ -1882,10 +1883,10 @@ int dg_batch_create(dg_batch** out, dg_handle* const* hs, int n) {
 }
 
 int dg_batch_config(dg_batch* b, int policy, int dynamic, int ctas_per_sm, int tiles_per_item) {
-  if (!b || policy < 0 || policy > 2 || dynamic < 0 || dynamic > 2 || ctas_per_sm < 0 ||
+  if (!b || policy < 0 || policy > 2 || dynamic < 0 || dynamic > 3 || ctas_per_sm < 0 ||
       (tiles_per_item != 1 && tiles_per_item != 2 && tiles_per_item != 4))
     return fail(nullptr, DG_ERR_ARG, "batch: bad config");
-  const int maxc = dynamic == 2 ? batch_flow_ctas_per_sm() : batch_stage32_ctas_per_sm();
+  const int maxc = dynamic >= 2 ? batch_flow_ctas_per_sm() : batch_stage32_ctas_per_sm();
   if (maxc < 1) return fail(nullptr, DG_ERR_CUDA, "batch: the kernel does not fit an SM");
   b->policy = policy;
   b->dynamic = dynamic;
@@ -1960,8 +1961,10 @@ int dg_batch_tune(dg_batch* b, int steps, int* policy, int* dynamic, int* ctas_p
     trials.push_back({pol, 1, maxc, 1});
     if (maxc > 1) trials.push_back({pol, 1, maxc - 1, 1});
     trials.push_back({pol, 0, maxc, 1});
-    if (maxf > 0)
+    if (maxf > 0) {
       for (int tpi : {1, 2, 4}) trials.push_back({pol, 2, maxf, tpi});
+      for (int tpi : {1, 2}) trials.push_back({pol, 3, maxf, tpi});
+    }
   }
   Trial bestc = {b->policy, b->dynamic, b->ctas_per_sm, b->tpi};
   double best = 1e30;

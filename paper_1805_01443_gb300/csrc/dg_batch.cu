@@ -216,22 +216,25 @@ __device__ __forceinline__ void flow_torque_item(const BatchLaunch32& L, int cod
 }
 
 // CTAs take queue positions from ctr[0] (the next one fetched while the
-// current one runs).  Position q: [0, nq) stage 1, [nq, 2 nq) stage 2,
-// [2 nq, 2 nq + nql) the last stage, then the torque groups.  An item waits
-// only for items earlier in the queue, each of which a running CTA has taken
-// (a CTA holds at most one item it has not started, taken after the one it
-// runs), so the earliest unfinished item always progresses.
+// current one runs), or, with F.rr, CTA c takes positions c, c + G, c + 2G, ...
+// in turn.  Position q: [0, nq) stage 1, [nq, 2 nq) stage 2, [2 nq, 2 nq +
+// nql) the last stage, then the torque groups.  An item waits only for items
+// earlier in the queue.  Every CTA of the (cooperative) launch is resident
+// and takes its positions in increasing order, holding at most one it has
+// not started, taken after the one it runs; so the CTA that owns the
+// earliest unfinished position is running it, its inputs are finished, and
+// it progresses.
 __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_batch_flow32(const __grid_constant__ BatchLaunch32 L) {
   extern __shared__ double smd[];
   __shared__ int s_q;
   const BatchFlow32& F = L.flow;
   const int nq = F.nq, nql = F.nql, total = 2 * nq + nql + F.ntq;
-  if (threadIdx.x == 0) s_q = atomicAdd(F.ctr, 1);
+  if (threadIdx.x == 0) s_q = F.rr ? (int)blockIdx.x : atomicAdd(F.ctr, 1);
   __syncthreads();
   int q = s_q;
   while (q < total) {
     __syncthreads();  // every thread holds q before thread 0 fetches the next
-    if (threadIdx.x == 0) s_q = atomicAdd(F.ctr, 1);
+    if (threadIdx.x == 0) s_q = F.rr ? q + (int)gridDim.x : atomicAdd(F.ctr, 1);
     if (q < nq) flow_stage_item<false>(L, 0, F.items[q], smd);
     else if (q < 2 * nq) flow_stage_item<false>(L, 1, F.items[q - nq], smd);
     else if (q < 2 * nq + nql) flow_stage_item<true>(L, 2, F.last[q - 2 * nq], smd);

@@ -293,6 +293,7 @@ struct BatchFlow32 {
   int nql;              // stage work items of the last stage
   int ntq;              // torque groups
   unsigned long long limit_ns;  // bound of one wait
+  int rr;               // 1: CTA c takes positions c, c + G, c + 2G, ... (no queue counter)
   int rowbase[BATCH_MAX + 1];   // first global row of each instance
 };
 constexpr int FLOW_TQ = 4;

@@ -466,7 +466,8 @@ class Batch:
     def config(self, policy=1, dynamic=1, ctas_per_sm=0, tiles_per_item=1):
         """dynamic: 0 one CTA per tile, 1 persistent CTAs in each stage launch,
         2 one persistent launch per step (flow schedule, work items of
-        tiles_per_item tiles)."""
+        tiles_per_item tiles from a queue counter), 3 the same with the
+        queue positions dealt round-robin over the CTAs."""
         _check(lib().dg_batch_config(self.b, policy, dynamic, ctas_per_sm, tiles_per_item))
 
     def get_config(self):

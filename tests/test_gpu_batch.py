@@ -36,7 +36,7 @@ def assert_same(a, b):
 # (policy, dynamic, ctas_per_sm, tiles_per_item): persistent per-stage
 # launches, one CTA per tile, and the flow schedule (one launch per step)
 SCHEDULES = [(0, 1, 0, 1), (1, 1, 0, 1), (2, 1, 0, 1), (1, 0, 0, 1), (2, 1, 1, 1), (1, 2, 0, 1), (0, 2, 0, 2),
-             (2, 2, 0, 4), (1, 2, 1, 4)]
+             (2, 2, 0, 4), (1, 2, 1, 4), (1, 3, 0, 1), (2, 3, 1, 2)]
 ORACLE_STEPS = 12
 
 
@@ -135,7 +135,7 @@ def test_batch_tune_does_not_advance_and_then_matches():
         with dg.Batch(bat) as b:
             best = b.tune(steps=2)
             assert best["policy"] in (0, 1, 2) and best["ms_per_step"] > 0
-            assert best["dynamic"] in (0, 1, 2) and best["tiles_per_item"] in (1, 2, 4)
+            assert best["dynamic"] in (0, 1, 2, 3) and best["tiles_per_item"] in (1, 2, 4)
             for d, u in zip(bat, u0):
                 np.testing.assert_array_equal(d.fetch(), u)
                 assert d.get_time()[2] == 2
@@ -216,7 +216,7 @@ def test_batch_config_rejects_bad_schedules():
     bat = make(inputs.batch_small()[:1])
     try:
         with dg.Batch(bat) as b:
-            for args in [(3, 1, 0, 1), (1, 3, 0, 1), (1, 2, 0, 3), (1, 2, -1, 1)]:
+            for args in [(3, 1, 0, 1), (1, 4, 0, 1), (1, 2, 0, 3), (1, 2, -1, 1)]:
                 with pytest.raises(dg.DgError) as e:
                     b.config(*args)
                 assert e.value.code == dg.DG_ERR_ARG
