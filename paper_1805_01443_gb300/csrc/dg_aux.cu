@@ -82,7 +82,8 @@ __global__ void k_init(const InitArgs a, int count) {
 // into the device slot with an atomic minimum on the (positive) bit pattern.
 // CFL minimum of the element averages of U (tiled FP64), or of U + D when D
 // (tiled FP32, the precision form's delta about U = u_b) is given
-__global__ void k_cfl(const double* U, const float* D, DevState* ts, const Mesh ms, const Phys ph, int p, int nv) {
+__global__ void k_cfl(const double* U, const float* D, DevState* ts, const Mesh ms, const Phys ph, int p, int nv,
+                      double idx, double idy) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int M = (p + 1) * (p + 1);
   double dtk = __longlong_as_double((long long)INF_BITS);
@@ -95,19 +96,22 @@ __global__ void k_cfl(const double* U, const float* D, DevState* ts, const Mesh 
       return D ? U[o] + (double)D[o] : U[o];
     };
     const double rho = avg(0), mx = avg(1), my = avg(2);
-    const double vx = mx / rho, vy = my / rho;
+    const double irho = 1.0 / rho;
+    const double vx = mx * irho, vy = my * irho;
     double c;
     if (ph.kind == 1) {
       const double E = avg(3);
       const double pr = (ph.gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy));
-      c = sqrt(ph.gamma * pr / rho);
+      c = sqrt(ph.gamma * pr * irho);
     } else if (ph.kind == 2) {
       c = ph.h;
     } else {
       const double xc = ms.x0 + (i + 0.5) * ms.dx, yc = ms.y0 + (j + 0.5) * ms.dy;
-      c = ph.h * sqrt(vk2_of(ph, sqrt(xc * xc + yc * yc)));
+      const double r = sqrt(xc * xc + yc * yc);
+      // h v_K: h / sqrt(r) outside the softened core, h r / r_s^(3/2) inside
+      c = ph.h * (r >= ph.rs ? rsqrt(r) : sqrt(vk2_of(ph, r)));
     }
-    dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) / ms.dx + (fabs(vy) + c) / ms.dy);
+    dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) * idx + (fabs(vy) + c) * idy);
     bad = !(rho > 0.0) || !(dtk > 0.0);  // +inf (no wave speed) is no constraint; NaN fails
     if (bad) dtk = __longlong_as_double((long long)INF_BITS);
   }
@@ -147,55 +151,37 @@ __global__ void k_reset(DevState* ts, double t, long long step) {
 // canonical modes (device memory, or mapped page-locked host memory read in
 // place) -> tiled FP64 state and, for the precision form, delta = u - u_b in
 // FP32, in one pass
+// canonical <-> tiled layout kernels: block (tile bx, row j, var-mode vk),
+// thread = lane, so both sides move one row of 32 elements per warp
 __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ tiled,
-                         const double* __restrict__ bg, float* __restrict__ d, const Mesh ms, int nv, int M) {
-  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % ms.nx);
-    const size_t r1 = e / ms.nx;
-    const int j = (int)(r1 % ms.ny);
-    const size_t vk = r1 / ms.ny;
-    const size_t t = (((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31);
-    const double x = canon[e];
-    tiled[t] = x;
-    if (d) d[t] = (float)(x - bg[t]);
-  }
+                         const double* __restrict__ bg, float* __restrict__ d, const Mesh ms, int nvm) {
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  if (i >= ms.nx) return;
+  const size_t t = (((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x;
+  const double x = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
+  tiled[t] = x;
+  if (d) d[t] = (float)(x - bg[t]);
 }
 
-// canonical FP32 delta -> tiled delta
-__global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const Mesh ms, int nv,
-                               int M) {
-  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % ms.nx);
-    const size_t r1 = e / ms.nx;
-    const int j = (int)(r1 % ms.ny);
-    const size_t vk = r1 / ms.ny;
-    const size_t t = (((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31);
-    d[t] = canon[e];
-  }
+// canonical FP32 delta -> tiled delta: block (tile bx, row j, var-mode vk),
+// thread = lane, so both sides move one 128-byte row per warp
+__global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const Mesh ms, int nvm) {
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  if (i >= ms.nx) return;
+  d[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x] = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
 }
 
-__global__ void k_to_canon_f32(const float* tiled, float* canon, const Mesh ms, int nv, int M) {
-  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % ms.nx);
-    const size_t r1 = e / ms.nx;
-    const int j = (int)(r1 % ms.ny);
-    const size_t vk = r1 / ms.ny;
-    canon[e] = tiled[(((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31)];
-  }
+__global__ void k_to_canon_f32(const float* tiled, float* canon, const Mesh ms, int nvm) {
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  if (i >= ms.nx) return;
+  canon[((size_t)vk * ms.ny + j) * ms.nx + i] = tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x];
 }
 
-__global__ void k_to_canon(const double* tiled, double* canon, const Mesh ms, int nv, int M) {
-  const size_t n = (size_t)nv * M * ms.nx * ms.ny;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % ms.nx);
-    const size_t r1 = e / ms.nx;
-    const int j = (int)(r1 % ms.ny);
-    const size_t vk = r1 / ms.ny;
-    canon[e] = tiled[(((size_t)j * ms.ntx + (i >> 5)) * nv * M + vk) * TILE + (i & 31)];
-  }
+__global__ void k_to_canon(const double* tiled, double* canon, const Mesh ms, int nvm) {
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  if (i >= ms.nx) return;
+  canon[((size_t)vk * ms.ny + j) * ms.nx + i] = tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x];
+}
 }
 
 // FP64 sums of element average x |K| per variable: per-block partials in a
@@ -249,7 +235,7 @@ cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s) {
 cudaError_t launch_cfl(const double* U, const float* D, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
                        int nv, cudaStream_t s) {
   const int n = mesh.nx * mesh.ny;
-  k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, D, ts, mesh, phys, p, nv);
+  k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, D, ts, mesh, phys, p, nv, 1.0 / mesh.dx, 1.0 / mesh.dy);
   return cudaGetLastError();
 }
 
@@ -307,24 +293,24 @@ cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStrea
 
 cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
                           int nv, int M, cudaStream_t s) {
-  k_ingest<<<1216, 256, 0, s>>>(canon, tiled, bg, d, mesh, nv, M);
+  k_ingest<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(canon, tiled, bg, d, mesh, nv * M);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ingest_delta(const float* canon, float* d, const Mesh& mesh, int nv, int M, cudaStream_t s) {
-  k_ingest_delta<<<1216, 256, 0, s>>>(canon, d, mesh, nv, M);
+  k_ingest_delta<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(canon, d, mesh, nv * M);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
                                 cudaStream_t s) {
-  k_to_canon_f32<<<1216, 256, 0, s>>>(tiled, canon, mesh, nv, M);
+  k_to_canon_f32<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(tiled, canon, mesh, nv * M);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
                             cudaStream_t s) {
-  k_to_canon<<<1216, 256, 0, s>>>(tiled, canon, mesh, nv, M);
+  k_to_canon<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(tiled, canon, mesh, nv * M);
   return cudaGetLastError();
 }
 
