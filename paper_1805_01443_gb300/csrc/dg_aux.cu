@@ -148,11 +148,11 @@ __global__ void k_reset(DevState* ts, double t, long long step) {
   ts->series_count = 0;
 }
 
-// canonical modes (device memory, or mapped page-locked host memory read in
-// place) -> tiled FP64 state and, for the precision form, delta = u - u_b in
-// FP32, in one pass
 // canonical <-> tiled layout kernels: block (tile bx, row j, var-mode vk),
-// thread = lane, so both sides move one row of 32 elements per warp
+// thread = lane, so both sides move one row of 32 elements per warp.
+// k_ingest: canonical modes (device memory, or mapped page-locked host memory
+// read in place) -> tiled FP64 state and, for the precision form, delta =
+// u - u_b in FP32, in one pass
 __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ tiled,
                          const double* __restrict__ bg, float* __restrict__ d, const Mesh ms, int nvm) {
   const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
@@ -181,7 +181,6 @@ __global__ void k_to_canon(const double* tiled, double* canon, const Mesh ms, in
   const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
   if (i >= ms.nx) return;
   canon[((size_t)vk * ms.ny + j) * ms.nx + i] = tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x];
-}
 }
 
 // FP64 sums of element average x |K| per variable: per-block partials in a
