@@ -148,39 +148,44 @@ __global__ void k_reset(DevState* ts, double t, long long step) {
   ts->series_count = 0;
 }
 
-// canonical <-> tiled layout kernels: block (tile bx, row j, var-mode vk),
-// thread = lane, so both sides move one row of 32 elements per warp.
+// canonical <-> tiled layout kernels: a block of 8 warps per (tile bx, row
+// j), thread x = lane, warp y taking var-modes vk = y, y + 8, ...; each warp
+// moves one row of 32 elements of one (var, mode) per iteration on both sides.
 // k_ingest: canonical modes (device memory, or mapped page-locked host memory
 // read in place) -> tiled FP64 state and, for the precision form, delta =
 // u - u_b in FP32, in one pass
 __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ tiled,
                          const double* __restrict__ bg, float* __restrict__ d, const Mesh ms, int nvm) {
-  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y;
   if (i >= ms.nx) return;
-  const size_t t = (((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x;
-  const double x = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
-  tiled[t] = x;
-  if (d) d[t] = (float)(x - bg[t]);
+  for (int vk = threadIdx.y; vk < nvm; vk += blockDim.y) {
+    const size_t t = (((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x;
+    const double x = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
+    tiled[t] = x;
+    if (d) d[t] = (float)(x - bg[t]);
+  }
 }
 
-// canonical FP32 delta -> tiled delta: block (tile bx, row j, var-mode vk),
-// thread = lane, so both sides move one 128-byte row per warp
+// canonical FP32 delta -> tiled delta
 __global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const Mesh ms, int nvm) {
-  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y;
   if (i >= ms.nx) return;
-  d[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x] = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
+  for (int vk = threadIdx.y; vk < nvm; vk += blockDim.y)
+    d[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x] = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
 }
 
 __global__ void k_to_canon_f32(const float* tiled, float* canon, const Mesh ms, int nvm) {
-  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y;
   if (i >= ms.nx) return;
-  canon[((size_t)vk * ms.ny + j) * ms.nx + i] = tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x];
+  for (int vk = threadIdx.y; vk < nvm; vk += blockDim.y)
+    canon[((size_t)vk * ms.ny + j) * ms.nx + i] = tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x];
 }
 
 __global__ void k_to_canon(const double* tiled, double* canon, const Mesh ms, int nvm) {
-  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y, vk = blockIdx.z;
+  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y;
   if (i >= ms.nx) return;
-  canon[((size_t)vk * ms.ny + j) * ms.nx + i] = tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x];
+  for (int vk = threadIdx.y; vk < nvm; vk += blockDim.y)
+    canon[((size_t)vk * ms.ny + j) * ms.nx + i] = tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x];
 }
 
 // FP64 sums of element average x |K| per variable: per-block partials in a
@@ -292,24 +297,24 @@ cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStrea
 
 cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
                           int nv, int M, cudaStream_t s) {
-  k_ingest<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(canon, tiled, bg, d, mesh, nv * M);
+  k_ingest<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 8), 0, s>>>(canon, tiled, bg, d, mesh, nv * M);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ingest_delta(const float* canon, float* d, const Mesh& mesh, int nv, int M, cudaStream_t s) {
-  k_ingest_delta<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(canon, d, mesh, nv * M);
+  k_ingest_delta<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 8), 0, s>>>(canon, d, mesh, nv * M);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
                                 cudaStream_t s) {
-  k_to_canon_f32<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(tiled, canon, mesh, nv * M);
+  k_to_canon_f32<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 8), 0, s>>>(tiled, canon, mesh, nv * M);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
                             cudaStream_t s) {
-  k_to_canon<<<dim3(mesh.ntx, mesh.ny, nv * M), TILE, 0, s>>>(tiled, canon, mesh, nv * M);
+  k_to_canon<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 8), 0, s>>>(tiled, canon, mesh, nv * M);
   return cudaGetLastError();
 }
 
