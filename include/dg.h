@@ -125,8 +125,9 @@ typedef struct {
   int prec;           /* 0: FP64 operator.  1: precision form (locally isothermal
                          disc only): FP32 operator on delta = u - u_b about the
                          projected equilibrium u_b, with R_b = L(u_b) evaluated
-                         in FP64 once, FP64 torque reduction and sums; the
-                         state is exchanged as FP64 u = u_b + delta */
+                         in FP64 once, FP64 torque reduction and sums; delta is
+                         held as its values at the Gauss-Legendre nodes and the
+                         state is exchanged as FP64 modes u = u_b + delta */
   double amp, vx0, vy0;
   int limiter;        /* troubled-cell limiting after every RK stage (FP64 form,
                          SSP(3,3)): 0 none; 1 the TVB-modified minmod test
@@ -210,7 +211,9 @@ int dg_set_state_async(dg_handle *h, const double *coeffs, double t, long step);
 /* Precision form only (DG_ERR_UNSUPPORTED otherwise): its state is the FP32
    perturbation delta = u - u_b about the projected background u_b, so a caller
    that holds delta can exchange it directly, at half the bytes of the FP64
-   state.  Layout: canonical, FP32, [var][a*m+b][j][i].
+   state.  Values: delta at the m x m Gauss-Legendre nodes of each element
+   (the form's own state; the node (xi_q, eta_r) of the m-point rule at index
+   q*m+r), not Legendre modes.  Layout: canonical, FP32, [var][q*m+r][j][i].
    dg_set_delta_async: as dg_set_state_async with u = u_b + delta (the same
    copy stream, staging buffers and ordering; page-locked host memory only,
    unchanged until the next synchronising call).

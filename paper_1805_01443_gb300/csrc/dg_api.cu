@@ -434,7 +434,11 @@ int read_state(dg_handle* h, DevState* out) {
 
 // CFL step of a full FP64 tiled state into the device time state
 int launch_cfl_and_dt(dg_handle* h, const double* full, const float* delta = nullptr) {
-  CU(h, launch_cfl(full, delta, h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
+  double wn[MAXM * MAXM];
+  const int m = h->p + 1;
+  for (int q = 0; q < m; q++)
+    for (int r = 0; r < m; r++) wn[q * m + r] = h->tab.wh[q] * h->tab.wh[r];
+  CU(h, launch_cfl(full, delta, wn, h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
   CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, 0, h->ph.r_p, h->ph.omega_p,
                       h->ph.phi0, h->stream));
   return DG_OK;
@@ -443,13 +447,13 @@ int launch_cfl_and_dt(dg_handle* h, const double* full, const float* delta = nul
 size_t tiled_count(const dg_handle* h) { return (size_t)h->dm.ny * h->dm.ntx * h->nv * h->M * TILE; }
 
 // full FP64 tiled state of the current buffer: the state itself (FP64 form) or
-// u_b + delta written into Z (precision form)
+// u_b + the modes of delta written into Z (precision form)
 int full_state(dg_handle* h, const double** out) {
   if (h->prec == 0) {
     *out = h->B[h->cur];
     return DG_OK;
   }
-  CU(h, launch_full_from_delta(h->BG, h->D[h->cur], h->Z, tiled_count(h), h->stream));
+  CU(h, launch_to_modal64(h->D[h->cur], h->BG, h->Z, h->dm, h->tab, h->p, h->nv, h->stream));
   *out = h->Z;
   return DG_OK;
 }
@@ -461,26 +465,37 @@ int full_state(dg_handle* h, const double** out) {
 // the stage update by at most dt x RB_DROP x max |R_b|, so over a time T the
 // solution moves by at most T x RB_DROP x max |R_b| per coefficient (to first
 // order) -- ~3e-11 over the 1000-step benchmark run, far below the form's FP32
-// error.  The stored tiles are packed at the front of Rb (the same tiled
-// layout) and RbIdx maps a tile to its slot or to -1.
+// error.  The test is on the FP64 modes (zmodal, tiled), so that the bound is
+// stated per Legendre coefficient; the kept tiles' values at the nodes (Rb,
+// FP32) are packed at the front of Rb (the same tiled layout) and RbIdx maps a
+// tile to its slot or to -1.
 constexpr double RB_DROP = 1e-10;
 
-cudaError_t sparse_rb(dg_handle* h) {
+cudaError_t sparse_rb(dg_handle* h, const double* zmodal) {
   const size_t ntiles = (size_t)h->dm.ny * h->dm.ntx, per = (size_t)h->nv * h->M * TILE;
   std::vector<float> rb(ntiles * per);
+  std::vector<double> zm(ntiles * per);
   cudaError_t e = cudaMemcpyAsync(rb.data(), h->Rb, rb.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(zm.data(), zmodal, zm.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return e;
-  float gmax = 0.0f;
-  for (float x : rb) gmax = std::max(gmax, std::fabs(x));
-  const float tau = (float)(RB_DROP * gmax);
+  // tiled padding lanes (past nx) hold no element
+  auto lane_ok = [&](size_t t, size_t i) { return (t % h->dm.ntx) * TILE + (i % TILE) < (size_t)h->dm.nx; };
+  double gmax = 0.0;
+  for (size_t t = 0; t < ntiles; t++)
+    for (size_t i = 0; i < per; i++)
+      if (lane_ok(t, i)) gmax = std::max(gmax, std::fabs(zm[t * per + i]));
+  const double tau = RB_DROP * gmax;
   std::vector<int> idx(ntiles, -1);
   size_t nkeep = 0;
   for (size_t t = 0; t < ntiles; t++) {
-    const float* x = rb.data() + t * per;
-    float m = 0.0f;
-    for (size_t i = 0; i < per; i++) m = std::max(m, std::fabs(x[i]));
+    const double* z = zm.data() + t * per;
+    double m = 0.0;
+    for (size_t i = 0; i < per; i++)
+      if (lane_ok(t, i)) m = std::max(m, std::fabs(z[i]));
     if (m > tau) {
+      const float* x = rb.data() + t * per;
       if (nkeep != t) std::copy(x, x + per, rb.data() + nkeep * per);
       idx[t] = (int)nkeep++;
     }
@@ -767,7 +782,6 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     split(dm.dx, pc.dxp);
     split(dm.dy, pc.dyp);
     split(planet->eps * planet->eps, pc.eps2p);
-    pc.near2 = 0.09f;  // 0.3^2: the planet's envelope, where delta Sigma ~ Sigma_b
     pc.rd_in = (float)disc->rdamp_in;
     pc.rd_out = (float)disc->rdamp_out;
     pc.damp_ratio = (float)pow(1.15, 1.5);
@@ -918,11 +932,11 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     a.phys.planet = 0;
     a.mode = 0;
     if (e == cudaSuccess) e = launch_stage_raw(a, h->p, h->stream);
-    if (e == cudaSuccess) e = launch_f64_to_f32(h->Z, h->Rb, tiled_count(h), h->stream);
-    if (e == cudaSuccess) e = sparse_rb(h);
+    if (e == cudaSuccess) e = launch_to_nodal32(h->Z, 0, nullptr, h->Rb, dm, h->tab, order, 3, 1, h->stream);
+    if (e == cudaSuccess) e = sparse_rb(h, h->Z);
     if (e == cudaSuccess)
       e = launch_bg_nodes(h->BG, h->SigbN, h->Db, h->Bm0, h->Disc, dm, ph, h->tab, order, h->stream);
-    if (e == cudaSuccess) e = launch_f64_to_f32(h->BG, h->Bmodes, tiled_count(h), h->stream);
+    if (e == cudaSuccess) e = launch_to_nodal32(h->BG, 0, nullptr, h->Bmodes, dm, h->tab, order, 3, 1, h->stream);
     if (e == cudaSuccess) e = launch_tile_flags(h->Disc, h->TileFlag, dm, 1e-6f, h->stream);
     if (e == cudaSuccess) {
       // schedule of the last stage: the tiles whose box touches a damping zone
@@ -946,7 +960,7 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
           }
       e = cudaMemcpy(h->TileOrder, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = launch_delta_from_full(h->B[0], h->BG, h->D[0], tiled_count(h), h->stream);
+    if (e == cudaSuccess) e = launch_to_nodal32(h->B[0], 0, h->BG, h->D[0], dm, h->tab, order, 3, 1, h->stream);
     if (e != cudaSuccess) {
       fail(h, DG_ERR_CUDA, "precision-form setup: %s", cudaGetErrorString(e));
       return bail(DG_ERR_CUDA);
@@ -1006,7 +1020,7 @@ int dg_rhs(dg_handle* h, double* out) {
     a.mode = 0;
     CU(h, launch_planet32(h->ts, 0.0, h->ph.r_p, h->ph.omega_p, h->ph.phi0, h->stream));
     CU(h, launch_stage32_h(h, a));
-    CU(h, launch_f32_to_f64(h->DZ, h->Z, tiled_count(h), h->stream));
+    CU(h, launch_to_modal64(h->DZ, nullptr, h->Z, h->dm, h->tab, h->p, h->nv, h->stream));
   } else {
     StageArgs a;
     memset(&a, 0, sizeof(a));
@@ -1098,8 +1112,8 @@ int dg_set_state(dg_handle* h, const double* coeffs, double t, long step) {
     CU(h, cudaMemcpyAsync(h->S, coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   cudaGetLastError();  // a pointer query on unregistered memory may leave an error behind
   double* full = h->prec == 1 ? h->Z : h->B[0];
-  CU(h, launch_ingest(src, full, h->prec == 1 ? h->BG : nullptr, h->prec == 1 ? h->D[0] : nullptr, h->dm, h->nv,
-                      h->M, h->stream));
+  CU(h, launch_ingest(src, full, h->dm, h->nv, h->M, h->stream));
+  if (h->prec == 1) CU(h, launch_to_nodal32(full, 0, h->BG, h->D[0], h->dm, h->tab, h->p, h->nv, 0, h->stream));
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
   h->cur = h->cur0 = 0;
   h->step0 = step;
@@ -1140,8 +1154,8 @@ int dg_set_state_async(dg_handle* h, const double* coeffs, double t, long step) 
   CU(h, cudaEventRecord(h->ev_copied[k], h->cstream));
   CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
   double* full = h->prec == 1 ? h->Z : h->B[0];
-  CU(h, launch_ingest(h->SA[k], full, h->prec == 1 ? h->BG : nullptr, h->prec == 1 ? h->D[0] : nullptr, h->dm,
-                      h->nv, h->M, h->stream));
+  CU(h, launch_ingest(h->SA[k], full, h->dm, h->nv, h->M, h->stream));
+  if (h->prec == 1) CU(h, launch_to_nodal32(full, 0, h->BG, h->D[0], h->dm, h->tab, h->p, h->nv, 0, h->stream));
   CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
   h->cur = h->cur0 = 0;

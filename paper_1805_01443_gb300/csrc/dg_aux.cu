@@ -81,9 +81,13 @@ __global__ void k_init(const InitArgs a, int count) {
 // CFL time step of Sec. 2.3 from the element averages; block minimum folded
 // into the device slot with an atomic minimum on the (positive) bit pattern.
 // CFL minimum of the element averages of U (tiled FP64), or of U + D when D
-// (tiled FP32, the precision form's delta about U = u_b) is given
-__global__ void k_cfl(const double* U, const float* D, DevState* ts, const Mesh ms, const Phys ph, int p, int nv,
-                      double idx, double idy) {
+// (tiled FP32, the precision form's delta about U = u_b, values at the nodes
+// averaged with the weights w) is given
+struct NodeW {
+  double w[MAXM * MAXM];
+};
+__global__ void k_cfl(const double* U, const float* D, const NodeW w, DevState* ts, const Mesh ms, const Phys ph,
+                      int p, int nv, double idx, double idy) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int M = (p + 1) * (p + 1);
   double dtk = __longlong_as_double((long long)INF_BITS);
@@ -93,7 +97,10 @@ __global__ void k_cfl(const double* U, const float* D, DevState* ts, const Mesh 
     const size_t base = (((size_t)j * ms.ntx + (i >> 5)) * nv * M) * TILE + (i & 31);
     auto avg = [&](int v) {
       const size_t o = base + (size_t)v * M * TILE;
-      return D ? U[o] + (double)D[o] : U[o];
+      if (!D) return U[o];
+      double s = 0.0;
+      for (int n = 0; n < M; n++) s += w.w[n] * (double)D[o + (size_t)n * TILE];
+      return U[o] + s;
     };
     const double rho = avg(0), mx = avg(1), my = avg(2);
     const double irho = 1.0 / rho;
@@ -152,21 +159,16 @@ __global__ void k_reset(DevState* ts, double t, long long step) {
 // j), thread x = lane, warp y taking var-modes vk = y, y + 8, ...; each warp
 // moves one row of 32 elements of one (var, mode) per iteration on both sides.
 // k_ingest: canonical modes (device memory, or mapped page-locked host memory
-// read in place) -> tiled FP64 state and, for the precision form, delta =
-// u - u_b in FP32, in one pass
-__global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ tiled,
-                         const double* __restrict__ bg, float* __restrict__ d, const Mesh ms, int nvm) {
+// read in place) -> tiled FP64 state
+__global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ tiled, const Mesh ms, int nvm) {
   const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y;
   if (i >= ms.nx) return;
-  for (int vk = threadIdx.y; vk < nvm; vk += blockDim.y) {
-    const size_t t = (((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x;
-    const double x = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
-    tiled[t] = x;
-    if (d) d[t] = (float)(x - bg[t]);
-  }
+  for (int vk = threadIdx.y; vk < nvm; vk += blockDim.y)
+    tiled[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x] =
+        canon[((size_t)vk * ms.ny + j) * ms.nx + i];
 }
 
-// canonical FP32 delta -> tiled delta
+// canonical FP32 delta (values at the nodes) -> tiled delta
 __global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const Mesh ms, int nvm) {
   const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y;
   if (i >= ms.nx) return;
@@ -236,10 +238,13 @@ cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cfl(const double* U, const float* D, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
-                       int nv, cudaStream_t s) {
+cudaError_t launch_cfl(const double* U, const float* D, const double* wn, DevState* ts, const Mesh& mesh,
+                       const Phys& phys, int p, int nv, cudaStream_t s) {
   const int n = mesh.nx * mesh.ny;
-  k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, D, ts, mesh, phys, p, nv, 1.0 / mesh.dx, 1.0 / mesh.dy);
+  NodeW w{};
+  if (D)
+    for (int k = 0; k < (p + 1) * (p + 1); k++) w.w[k] = wn[k];
+  k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, D, w, ts, mesh, phys, p, nv, 1.0 / mesh.dx, 1.0 / mesh.dy);
   return cudaGetLastError();
 }
 
@@ -295,9 +300,8 @@ cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
-                          int nv, int M, cudaStream_t s) {
-  k_ingest<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 8), 0, s>>>(canon, tiled, bg, d, mesh, nv * M);
+cudaError_t launch_ingest(const double* canon, double* tiled, const Mesh& mesh, int nv, int M, cudaStream_t s) {
+  k_ingest<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 8), 0, s>>>(canon, tiled, mesh, nv * M);
   return cudaGetLastError();
 }
 

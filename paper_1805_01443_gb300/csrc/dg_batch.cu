@@ -70,30 +70,27 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_batch_stage32(const
   }
 }
 
-// torque of tile `tile` of instance k (one warp; sd: this lane's column of
-// the warp's nodal buffer)
-__device__ __forceinline__ void batch_torque_tile(const BatchLaunch32& L, int k, int tile, float* sd) {
+// torque of tile `tile` of instance k (one warp)
+__device__ __forceinline__ void batch_torque_tile(const BatchLaunch32& L, int k, int tile) {
   const BatchInst32& I = L.inst[k];
   // the new state: the last stage wrote buf[cur ^ 1]; the step counter
   // advances in the end-of-step work that follows
   const int cur = I.cur0 ^ (int)((I.a.ts->step - I.step0) & 1);
   const float* nx = I.buf[cur ^ 1];
   switch (I.p) {
-    case 1: torque32_tile<1>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
-    case 2: torque32_tile<2>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
-    case 3: torque32_tile<3>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
-    default: torque32_tile<4>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile, sd); break;
+    case 1: torque32_tile<1>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
+    case 2: torque32_tile<2>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
+    case 3: torque32_tile<3>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
+    default: torque32_tile<4>(nx, I.SigbN, I.a.ts, I.a.part, I.a.mesh, I.a.pc, tile); break;
   }
 }
 
-__global__ void __launch_bounds__(128, 7) k_batch_torque32(const __grid_constant__ BatchLaunch32 L) {
-  __shared__ float sD[4][2 * MAXM * MAXM * 32];  // per warp: nodal delta Sigma of its tile
+__global__ void __launch_bounds__(128, 8) k_batch_torque32(const __grid_constant__ BatchLaunch32 L) {
   const int w = threadIdx.x >> 5;
   const int item = blockIdx.x * 4 + w;  // warp-uniform
   if (item >= L.nitems) return;
-  float* sd = sD[w] + (threadIdx.x & 31);
   const int k = upper_tile0(L, item), tile = item - L.tile0[k];
-  batch_torque_tile(L, k, tile, sd);
+  batch_torque_tile(L, k, tile);
 }
 
 // one CTA of 256 threads per instance
@@ -195,10 +192,7 @@ __device__ __forceinline__ void flow_torque_item(const BatchLaunch32& L, int cod
       __threadfence();
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) {
-      float* sd = reinterpret_cast<float*>(smd + 8) + w * (2 * MAXM * MAXM * 32) + lane;
-      batch_torque_tile(L, k, tile, sd);
-    }
+    if (ok) batch_torque_tile(L, k, tile);
   }
   const bool fail = __syncthreads_or(!ok);
   if (threadIdx.x == 0) {
@@ -245,8 +239,6 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_batch_flow32(const 
 }
 
 size_t smem_bytes() { return Smem32<4>::BYTES; }
-static_assert(8 * sizeof(double) + 3 * 2 * MAXM * MAXM * 32 * sizeof(float) <= Smem32<4>::BYTES,
-              "torque buffers of the flow kernel exceed the stage kernel's shared memory");
 static_assert((8 + 512) * sizeof(double) <= Smem32<4>::BYTES, "end-of-step scratch");
 static_assert(sizeof(BatchLaunch32) <= 32000, "kernel parameter size");
 

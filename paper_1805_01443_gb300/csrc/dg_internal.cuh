@@ -102,7 +102,6 @@ struct Prec32 {
   float q, eps2;
   float x0p[2], y0p[2], dxp[2], dyp[2];  // x0, y0, dx, dy as (hi, lo) float pairs
   float eps2p[2];          // planet smoothing^2 as a float pair (torque)
-  float near2;             // torque: float-float delta contraction within sqrt(near2) of the planet
   float rd_in, rd_out, damp_ratio;
   float cfl_fac;           // C / (2p + 1)
   // mesh geometry in FP32 (coefficients only; offsets from the planet are
@@ -115,11 +114,11 @@ struct StageArgs32 {
   const float* D;      // delta^(s)
   const float* Dn;     // delta^n
   float* Out;
-  const float* Rb;     // R_b = L(u_b), evaluated in FP64, stored FP32 [slot][var][mode][32]
+  const float* Rb;     // R_b = L(u_b), evaluated in FP64, stored FP32 at the nodes [slot][var][node][32]
   const int* RbIdx;    // tile -> its slot in Rb, or -1 (R_b dropped: below 1e-10 of its maximum)
   const float* Db;     // Q0 - Q_b at the nodes for (Sigma, vx, vy) [tile][3][node][32] (damping)
   const float* Bm0;    // element averages of u_b [tile][3][32] (CFL)
-  const float* Bmodes; // u_b modes in FP32 [tile][var][mode][32] (exact-background tiles)
+  const float* Bmodes; // u_b at the nodes in FP32 [tile][var][node][32] (exact-background tiles)
   const int* TileFlag; // 1: the tile uses the exact projected background
   const int* TileOrder;  // last stage: CTA -> tile (tiles that touch a damping zone first), or null
   DevState* ts;
@@ -172,19 +171,19 @@ struct InitArgs {
 };
 
 cudaError_t launch_init(const InitArgs& a, int count, cudaStream_t s);
-// CFL step from the element averages of U, or of U + D (D: FP32 delta, may be null)
-cudaError_t launch_cfl(const double* U, const float* D, DevState* ts, const Mesh& mesh, const Phys& phys, int p,
-                       int nv, cudaStream_t s);
+// CFL step from the element averages of U, or of U + D (D: the precision
+// form's FP32 delta at the nodes, averaged with the weights wn[q*m + r] =
+// (w_q/2)(w_r/2); may be null)
+cudaError_t launch_cfl(const double* U, const float* D, const double* wn, DevState* ts, const Mesh& mesh,
+                       const Phys& phys, int p, int nv, cudaStream_t s);
 cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* series,
                           double fixed_dt, int advance, int planet32, double r_p, double omega_p,
                           double phi0, cudaStream_t s);
-// canonical modes -> tiled FP64 state (and delta = u - u_b in FP32 when d is
-// set) in one pass; canon may be mapped page-locked host memory
-cudaError_t launch_ingest(const double* canon, double* tiled, const double* bg, float* d, const Mesh& mesh,
-                          int nv, int M, cudaStream_t s);
+// canonical modes -> tiled FP64 state; canon may be mapped page-locked host memory
+cudaError_t launch_ingest(const double* canon, double* tiled, const Mesh& mesh, int nv, int M, cudaStream_t s);
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
                             cudaStream_t s);
-// precision form: canonical FP32 delta -> tiled delta d
+// precision form: canonical FP32 delta (values at the nodes) -> tiled delta d
 cudaError_t launch_ingest_delta(const float* canon, float* d, const Mesh& mesh, int nv, int M, cudaStream_t s);
 cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
                                 cudaStream_t s);
@@ -247,12 +246,14 @@ size_t mlp_pack_bytes(int nv, int M);
 void mlp_pack(const float* prm, int nv, int M, unsigned char* out);
 
 // precision-form setup and conversions (dg_prec.cu)
-cudaError_t launch_delta_from_full(const double* full, const double* bg, float* d, size_t n,
-                                   cudaStream_t s);
-cudaError_t launch_full_from_delta(const double* bg, const float* d, double* full, size_t n,
-                                   cudaStream_t s);
-cudaError_t launch_f64_to_f32(const double* x, float* y, size_t n, cudaStream_t s);
-cudaError_t launch_f32_to_f64(const float* x, double* y, size_t n, cudaStream_t s);
+// tiled (or, with canon, canonical) FP64 modes minus sub (tiled FP64, may be
+// null) -> tiled FP32 values at the Gauss-Legendre nodes, the transform in
+// FP64 (fp64 set) or FP32
+cudaError_t launch_to_nodal32(const double* src, int canon, const double* sub, float* dst, const Mesh& mesh,
+                              const Tables& tab, int p, int nv, int fp64, cudaStream_t s);
+// tiled FP32 nodal values -> tiled FP64 modes (+ add, tiled FP64 modes, may be null)
+cudaError_t launch_to_modal64(const float* src, const double* add, double* dst, const Mesh& mesh,
+                              const Tables& tab, int p, int nv, cudaStream_t s);
 cudaError_t launch_bg_nodes(const double* bg, float* sigbn, float* db, float* bm0, float* disc,
                             const Mesh& mesh, const Phys& phys, const Tables& tab, int p,
                             cudaStream_t s);

@@ -1,7 +1,8 @@
 // dg_prec.cu -- setup and conversions of the precision form: delta = u - u_b
-// in FP32 about the FP64 projected background u_b, and the static background
-// fields the FP32 stage kernel reads (nodal Sigma_b for the torque, damping
-// offsets Q0 - Q_b, element averages of u_b for the CFL step).
+// in FP32 about the FP64 projected background u_b, held as its values at the
+// Gauss-Legendre nodes, and the static background fields the FP32 stage
+// kernel reads (nodal Sigma_b for the torque, damping offsets Q0 - Q_b,
+// element averages of u_b for the CFL step).
 #include "dg_internal.cuh"
 #include "dg_physics.cuh"
 
@@ -9,26 +10,77 @@ namespace dg {
 
 namespace {
 
-__global__ void k_delta_from_full(const double* __restrict__ full, const double* __restrict__ bg,
-                                  float* __restrict__ d, size_t n) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    d[e] = (float)(full[e] - bg[e]);
+// Modal <-> nodal transforms of the precision form's tiled arrays (its state,
+// R_b and the exact background are values at the m x m Gauss-Legendre nodes
+// of each element).  One thread per (element, variable): a block of (32, nv)
+// threads per tile, grid (tiles per row, rows); lanes past nx write zeros.
+//   to nodes:  u(q, r) = sum_ab c_ab phi_a(xi_q) phi_b(eta_r), with c the
+//              source modes minus `sub` (both FP64, the difference rounded to
+//              T), summed over b then a in T
+//   to modes:  c_ab = sum_qr (w_q/2)(w_r/2) phi_a(xi_q) phi_b(eta_r) u(q, r) in
+//              FP64 (the discrete orthonormality of the basis on the m-point
+//              rule), plus `add` (FP64 modes) when given
+// The source of k_to_nodal32 is a tiled array or, with canon set, the
+// canonical array [var][a*m+b][j][i].
+template <int P, typename T>
+__global__ void k_to_nodal32(const double* __restrict__ src, int canon, const double* __restrict__ sub,
+                             float* __restrict__ dst, const Mesh ms, const Tables tab, int nv) {
+  constexpr int m = P + 1, M = m * m;
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int i = blockIdx.x * TILE + lane, j = blockIdx.y;
+  const size_t tile = (size_t)j * ms.ntx + blockIdx.x;
+  float* out = dst + (tile * nv + v) * M * TILE + lane;
+  if (i >= ms.nx) {
+    for (int k = 0; k < M; k++) out[k * TILE] = 0.0f;
+    return;
+  }
+  const size_t to = (tile * nv + v) * M * TILE + lane;
+  T c[M];
+  for (int k = 0; k < M; k++) {
+    const double x = canon ? src[((size_t)(v * M + k) * ms.ny + j) * ms.nx + i] : src[to + (size_t)k * TILE];
+    c[k] = (T)(sub ? x - sub[to + (size_t)k * TILE] : x);
+  }
+  T Tm[m][m];
+  for (int a = 0; a < m; a++)
+    for (int r = 0; r < m; r++) {
+      T acc = 0;
+      for (int b = 0; b < m; b++) acc += c[a * m + b] * (T)tab.phi[r][b];
+      Tm[a][r] = acc;
+    }
+  for (int q = 0; q < m; q++)
+    for (int r = 0; r < m; r++) {
+      T acc = 0;
+      for (int a = 0; a < m; a++) acc += (T)tab.phi[q][a] * Tm[a][r];
+      out[(q * m + r) * TILE] = (float)acc;
+    }
 }
 
-__global__ void k_full_from_delta(const double* __restrict__ bg, const float* __restrict__ d,
-                                  double* __restrict__ full, size_t n) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    full[e] = bg[e] + (double)d[e];
-}
-
-__global__ void k_f64_to_f32(const double* __restrict__ x, float* __restrict__ y, size_t n) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    y[e] = (float)x[e];
-}
-
-__global__ void k_f32_to_f64(const float* __restrict__ x, double* __restrict__ y, size_t n) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    y[e] = (double)x[e];
+template <int P>
+__global__ void k_to_modal64(const float* __restrict__ src, const double* __restrict__ add,
+                             double* __restrict__ dst, const Mesh ms, const Tables tab, int nv) {
+  constexpr int m = P + 1, M = m * m;
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int i = blockIdx.x * TILE + lane, j = blockIdx.y;
+  const size_t to = (((size_t)j * ms.ntx + blockIdx.x) * nv + v) * M * TILE + lane;
+  if (i >= ms.nx) {
+    for (int k = 0; k < M; k++) dst[to + (size_t)k * TILE] = 0.0;
+    return;
+  }
+  double u[M];
+  for (int k = 0; k < M; k++) u[k] = (double)src[to + (size_t)k * TILE];
+  double Pq[m][m];  // [b][q] = sum_r (w_r/2) phi_b(eta_r) u(q, r)
+  for (int b = 0; b < m; b++)
+    for (int q = 0; q < m; q++) {
+      double acc = 0.0;
+      for (int r = 0; r < m; r++) acc += tab.wh[r] * tab.phi[r][b] * u[q * m + r];
+      Pq[b][q] = acc;
+    }
+  for (int a = 0; a < m; a++)
+    for (int b = 0; b < m; b++) {
+      double acc = 0.0;
+      for (int q = 0; q < m; q++) acc += tab.wh[q] * tab.phi[q][a] * Pq[b][q];
+      dst[to + (size_t)(a * m + b) * TILE] = add ? add[to + (size_t)(a * m + b) * TILE] + acc : acc;
+    }
 }
 
 // One thread per element: FP64 nodal values of the projected background u_b
@@ -129,25 +181,34 @@ __global__ void k_tile_flags(const float* __restrict__ disc, int* __restrict__ f
 
 }  // namespace
 
-cudaError_t launch_delta_from_full(const double* full, const double* bg, float* d, size_t n,
-                                   cudaStream_t s) {
-  k_delta_from_full<<<1216, 256, 0, s>>>(full, bg, d, n);
+template <typename T>
+static cudaError_t to_nodal32(const double* src, int canon, const double* sub, float* dst, const Mesh& ms,
+                              const Tables& tab, int p, int nv, cudaStream_t s) {
+  const dim3 grid(ms.ntx, ms.ny), block(TILE, nv);
+  switch (p) {
+    case 1: k_to_nodal32<1, T><<<grid, block, 0, s>>>(src, canon, sub, dst, ms, tab, nv); break;
+    case 2: k_to_nodal32<2, T><<<grid, block, 0, s>>>(src, canon, sub, dst, ms, tab, nv); break;
+    case 3: k_to_nodal32<3, T><<<grid, block, 0, s>>>(src, canon, sub, dst, ms, tab, nv); break;
+    default: k_to_nodal32<4, T><<<grid, block, 0, s>>>(src, canon, sub, dst, ms, tab, nv); break;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_full_from_delta(const double* bg, const float* d, double* full, size_t n,
-                                   cudaStream_t s) {
-  k_full_from_delta<<<1216, 256, 0, s>>>(bg, d, full, n);
-  return cudaGetLastError();
+cudaError_t launch_to_nodal32(const double* src, int canon, const double* sub, float* dst, const Mesh& mesh,
+                              const Tables& tab, int p, int nv, int fp64, cudaStream_t s) {
+  return fp64 ? to_nodal32<double>(src, canon, sub, dst, mesh, tab, p, nv, s)
+              : to_nodal32<float>(src, canon, sub, dst, mesh, tab, p, nv, s);
 }
 
-cudaError_t launch_f64_to_f32(const double* x, float* y, size_t n, cudaStream_t s) {
-  k_f64_to_f32<<<1216, 256, 0, s>>>(x, y, n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_f32_to_f64(const float* x, double* y, size_t n, cudaStream_t s) {
-  k_f32_to_f64<<<1216, 256, 0, s>>>(x, y, n);
+cudaError_t launch_to_modal64(const float* src, const double* add, double* dst, const Mesh& ms,
+                              const Tables& tab, int p, int nv, cudaStream_t s) {
+  const dim3 grid(ms.ntx, ms.ny), block(TILE, nv);
+  switch (p) {
+    case 1: k_to_modal64<1><<<grid, block, 0, s>>>(src, add, dst, ms, tab, nv); break;
+    case 2: k_to_modal64<2><<<grid, block, 0, s>>>(src, add, dst, ms, tab, nv); break;
+    case 3: k_to_modal64<3><<<grid, block, 0, s>>>(src, add, dst, ms, tab, nv); break;
+    default: k_to_modal64<4><<<grid, block, 0, s>>>(src, add, dst, ms, tab, nv); break;
+  }
   return cudaGetLastError();
 }
 

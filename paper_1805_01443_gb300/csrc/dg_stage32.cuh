@@ -15,21 +15,34 @@
 // solid-body-core edge, where the analytic and projected backgrounds differ;
 // the box edge under periodic or copied-element boundaries, where the
 // neighbour's background is its own projection), where the projected one is
-// contracted from its FP32 modes.
+// interpolated from its FP32 values at the nodes.
+//
+// Nodal form.  delta, R_b and the projected background are held as the
+// values of their polynomials at the m x m Gauss-Legendre nodes of each
+// element, not as Legendre modes.  With the m-point rule the two are the
+// same discrete operator (Eq. 2 with the quadrature of the modal scheme): the
+// modal basis is orthonormal on the rule, so the map from modes to node values
+// is inverted by its transpose times the weights, and the operator's modal
+// result mapped to the nodes is the DG weak form in the Lagrange basis of
+// the nodes -- volume terms by the weak derivative dw along each node line,
+// source terms at the node itself, face traces and the lift by the Lagrange
+// values at the element ends.  So no stage contracts modes to nodes, the
+// volume sums cost m FMAs per node and direction instead of 2m per mode,
+// and damping acts on the node values directly.  The modes appear only where
+// the state crosses the library boundary (dg_prec.cu).
 //
 // Work decomposition: one CTA per 32-element tile of one mesh row, three warps;
-// thread (v, e) owns variable v of element e.  Its m*m modes, nodal values and
-// volume/lift accumulators stay in registers (sum-factorised contractions with
-// no shared-memory operand); shared memory only exchanges the nodal values,
-// face traces, pointwise fluxes and face fluxes between the three variable
-// threads of an element.  Pointwise and face work is dealt round-robin over
-// the three threads.  Independent evaluations that share their operation
-// sequence (two quadrature nodes, the two sides of a face, sums with a common
-// weight) run as the lanes of packed FP32x2 instructions, each lane in its
-// scalar order.  The last stage adds damping in delta form (tiles that touch
-// a zone, scheduled first so that an SM holds CTAs on one code path) and the
-// CFL minimum; the torque of the new state is a separate one-variable pass
-// (k_torque32 below).
+// thread (v, e) owns variable v of element e.  Its node values and
+// volume/lift accumulators stay in registers; shared memory only exchanges
+// the node values, face traces, pointwise fluxes and face fluxes between the
+// three variable threads of an element.  Pointwise and face work is dealt
+// round-robin over the three threads.  Independent evaluations that share
+// their operation sequence (two quadrature nodes, the two sides of a face, two
+// node lines of a sum) run as the lanes of packed FP32x2 instructions, each
+// lane in its scalar order.  The last stage adds damping in delta form (tiles
+// that touch a zone, scheduled first so that an SM holds CTAs on one code
+// path) and the CFL minimum; the torque of the new state is a separate
+// one-variable pass (k_torque32 below).
 #pragma once
 #include "dg_async.cuh"
 #include "dg_internal.cuh"
@@ -37,20 +50,31 @@
 
 namespace dg {
 
-// FP32 quadrature and basis tables of degree P (the m-point Gauss-Legendre
-// rule), one slice per degree so that one translation unit can hold kernels
-// of several degrees
+// FP32 tables of degree P for the nodal form (the m-point Gauss-Legendre
+// rule and the Lagrange basis l_q of its nodes), one slice per degree so that
+// one translation unit can hold kernels of several degrees.  The state of the
+// precision form is the polynomial's values at the m x m nodes; with the
+// mean-orthonormal modal basis phi_a and weights w_q/2 the two forms are
+// related by sum_a phi_a(xi_q) phi_a(xi) = l_q(xi) / (w_q/2), so that
+//   weak derivative  dw[q][q'] = (w_q'/2) l_q'(xi_q') / (w_q/2)
+//                              = (w_q'/2) sum_a phi_a(xi_q) phi'_a(xi_q'),
+//   lift at an end   lp[q] = l_q(+1) / (w_q/2) = sum_a phi_a(xi_q) phi_a(+1)
+//   (lm at -1), and traces at an end  bp[q] = l_q(+1), bm[q] = l_q(-1).
 struct Tab32 {
-  float phi[MAXM][MAXM];    // [q][a] sqrt(2a+1) P_a(xi_q)
-  float wphi[MAXM][MAXM];   // w_q/2 phi_a(xi_q)
-  float wdphi[MAXM][MAXM];  // w_q/2 phi'_a(xi_q)
-  float pp[MAXM], pm[MAXM], xi[MAXM], wh[MAXM];
+  float xi[MAXM], wh[MAXM];
+  float bp[MAXM], bm[MAXM];  // l_q(+1), l_q(-1)
+  float2 bpm2[MAXM];         // (bp, bm): the two traces of a node line as the lanes of packed FMAs
+  float dw[MAXM][MAXM];      // weak derivative [q][q']
+  float lp[MAXM], lm[MAXM];  // lift at +1 (its negative enters) and at -1
+  float eye[MAXM][MAXM];     // unit vectors: point values of exact-background tiles at a node line
+  // operand pairs of the packed volume/lift sums over node pairs (2k, 2k+1);
+  // the pair past an odd m has zero coefficients
+  float2 dwp[(MAXM + 1) / 2][MAXM];  // (dw[2k][q'], dw[2k+1][q'])
+  float2 lmp[(MAXM + 1) / 2], lpn[(MAXM + 1) / 2];  // (lm[2k], lm[2k+1]), (-lp[2k], -lp[2k+1])
+  float2 dw2[MAXM][MAXM], lm2[MAXM], lpn2[MAXM];     // (dw, dw), (lm, lm), (-lp, -lp): one entry, both lanes
   // low parts of the FP64 tables as float pairs (float-float torque)
-  float phil[MAXM][MAXM], xil[MAXM];
+  float xil[MAXM];
   float w2h[MAXM * MAXM], w2l[MAXM * MAXM];  // [q*m + r] (w_q/2)(w_r/2)
-  // operand pairs of the packed (two-lane) FMAs of the volume and lift sums
-  float2 wphi2[MAXM][MAXM];  // [r][b] (wphi, wphi)
-  float2 wdw2[MAXM][MAXM];   // [q][a] (wdphi, wphi)
 };
 static __constant__ Tab32 c32t[MAXP + 1];
 
@@ -166,9 +190,11 @@ __device__ __forceinline__ void dllf32(const Bg32& bL, const Bg32& bR, const flo
     h[v] = 0.5f * (fn[v].x + fn[v].y) - 0.5f * fmaf(al, dR[v] - dL[v], (al - alb) * jb[v]);
 }
 
-// Exact projected background at a point of one element from its FP32 modes
-// (stride 32 between modes): u_b = sum_ab b_ab fa[a] gb[b]; c2 from the
-// analytic sound speed of the point.
+// Exact projected background at a point of one element from its FP32 values
+// at the nodes (stride 32 between nodes): u_b = sum_qr b(q, r) fa[q] gb[r],
+// with fa, gb the Lagrange weights of the point along each node line (a unit
+// vector at a node, bp or bm at an element end); c2 from the analytic sound
+// speed of the point.
 template <int P>
 __device__ __noinline__ Bg32 bg32_poly(const float* bm, const float* fa, const float* gb, float c2) {
   constexpr int m = P + 1, M = m * m;
@@ -203,7 +229,7 @@ __device__ __noinline__ Bg32 bg32_poly(const float* bm, const float* fa, const f
 template <int P>
 struct Smem32 {
   static constexpr int m = P + 1, M = m * m;
-  // nodal values [3][M][32]; the pointwise terms fx[3], fy[3] 2/dy, src[2]
+  // nodal values [3][M][32]; the pointwise terms fx[3] 2/dx, fy[3] 2/dy, src[2]
   // [8][M][32] overwrite them in place (planes 0-2 alias U: each node's
   // values are read and replaced by the one thread that owns the node)
   static constexpr int U = 0;
@@ -212,8 +238,9 @@ struct Smem32 {
   static constexpr int XL = YT + 2 * 3 * m * 32;   // left x traces [3][m][33], slot e (in planes 3..)
   static constexpr int XR = F + 8 * M * 32;        // right x traces [3][m][33], slot e+1
   static constexpr int YN = XR + 3 * m * 33;       // neighbour traces [2][3][m][32]: 0 below's top, 1 above's bottom
-  // face fluxes overwrite the traces they are formed from (each face point's
-  // traces are read and replaced by the one thread that owns the point):
+  // face fluxes (times 1/dx, 1/dy) overwrite the traces they are formed from
+  // (each face point's traces are read and replaced by the one thread that
+  // owns the point):
   static constexpr int FX = XR;                    // x-face flux differences [3][m][33]
   static constexpr int FY = YN;                    // y-face flux differences [2][3][m][32]
   static constexpr int B0 = YN + 2 * 3 * m * 32;   // element averages of the new state [3][32]
@@ -316,68 +343,6 @@ __device__ __forceinline__ void ff_offset(float k, const float* x0p, const float
   r = f2_add(r, F2{-ph, -pl});
   hi = r.h;
   lo = r.l;
-}
-
-// modal -> nodal values of one variable of one element (registers), written to
-// u_out[n * 32] for node n = q*m + r; with xr/xl the x-face traces at the m
-// y-nodes are taken from the same first pass
-template <int P, bool TRACES>
-__device__ __forceinline__ void nodal32(const float* c, float* u_out, float* xr, float* xl) {
-  constexpr int m = P + 1;
-  float T[m][m];
-#pragma unroll
-  for (int aa = 0; aa < m; aa++)
-#pragma unroll
-    for (int r = 0; r < m; r++) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32t[P].phi[r][b], acc);
-      T[aa][r] = acc;
-    }
-#pragma unroll
-  for (int q = 0; q < m; q++)
-#pragma unroll
-    for (int r = 0; r < m; r++) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], T[aa][r], acc);
-      u_out[(q * m + r) * 32] = acc;
-    }
-  if (TRACES) {
-#pragma unroll
-    for (int r = 0; r < m; r++) {
-      float sr = 0.0f, sl = 0.0f;
-#pragma unroll
-      for (int aa = 0; aa < m; aa++) {
-        sr = fmaf(c32t[P].pp[aa], T[aa][r], sr);
-        sl = fmaf(c32t[P].pm[aa], T[aa][r], sl);
-      }
-      xr[r] = sr;
-      xl[r] = sl;
-    }
-  }
-}
-
-// y-face trace polynomial of one variable: R[a] = sum_b c_ab f[b], then its
-// values at the m x-nodes, written to out[q * 32]
-template <int P>
-__device__ __forceinline__ void ytrace32(const float* c, const float* f, float* out) {
-  constexpr int m = P + 1;
-  float R[m];
-#pragma unroll
-  for (int aa = 0; aa < m; aa++) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], f[b], acc);
-    R[aa] = acc;
-  }
-#pragma unroll
-  for (int q = 0; q < m; q++) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], R[aa], acc);
-    out[q * 32] = acc;
-  }
 }
 
 // minimum resident CTAs per SM asked of the register allocator (96
@@ -484,34 +449,57 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   const float xt0 = pc.x0 + i2f(i0) * pc.dx;
 
   // ---- P1: nodal values and face traces of this thread's variable ------------
+  // The state is the values at the m x m nodes (k = q*m + r): they go to
+  // shared memory as they are, and each face trace is one sum along a node
+  // line with the Lagrange weights of the element end.
   {
     float c[M];
 #pragma unroll
     for (int k = 0; k < M; k++) c[k] = own[k * 32];
-    // x traces: right trace of element e at slot e+1, left trace at slot e
+#pragma unroll
+    for (int k = 0; k < M; k++) sU[voff + k * 32 + lane] = c[k];
+    // x traces at the m y-nodes r: right (xi = +1) and left (xi = -1) as the
+    // lanes of one packed sum over q; right trace of element e at slot e+1,
+    // left trace at slot e
     float* xr = sXR + v * m * 33;
     float* xl = sXL + v * m * 33;
-    float tr_r[m], tr_l[m];
-    nodal32<P, true>(c, sU + voff + lane, tr_r, tr_l);
 #pragma unroll
     for (int r = 0; r < m; r++) {
-      xr[r * 33 + lane + 1] = tr_r[r];
-      if (valid) xl[r * 33 + lane] = tr_l[r];
-      if (lane == 0 && trL) xr[r * 33] = tr_l[r];  // mirror: exterior = interior
-      if (lane == nvalid - 1 && trR) xl[r * 33 + nvalid] = tr_r[r];
+      float2 t = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int q = 0; q < m; q++) t = f2(c32t[P].bpm2[q], d2(c[q * m + r]), t);
+      xr[r * 33 + lane + 1] = t.x;
+      if (valid) xl[r * 33 + lane] = t.y;
+      if (lane == 0 && trL) xr[r * 33] = t.y;  // mirror: exterior = interior
+      if (lane == nvalid - 1 && trR) xl[r * 33 + nvalid] = t.x;
     }
-    ytrace32<P>(c, c32t[P].pp, sYT + ((0 * 3 + v) * m) * 32 + lane);
-    ytrace32<P>(c, c32t[P].pm, sYT + ((1 * 3 + v) * m) * 32 + lane);
-    if (trB) ytrace32<P>(c, c32t[P].pm, sYN + ((0 * 3 + v) * m) * 32 + lane);
-    if (trT) ytrace32<P>(c, c32t[P].pp, sYN + ((1 * 3 + v) * m) * 32 + lane);
+    // y traces at the m x-nodes q: top (eta = +1, plane 0) and bottom (plane 1)
+#pragma unroll
+    for (int q = 0; q < m; q++) {
+      float2 t = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int r = 0; r < m; r++) t = f2(c32t[P].bpm2[r], d2(c[q * m + r]), t);
+      sYT[((0 * 3 + v) * m + q) * 32 + lane] = t.x;
+      sYT[((1 * 3 + v) * m + q) * 32 + lane] = t.y;
+      if (trB) sYN[((0 * 3 + v) * m + q) * 32 + lane] = t.y;
+      if (trT) sYN[((1 * 3 + v) * m + q) * 32 + lane] = t.x;
+    }
   }
   {
-    // neighbour rows: the face polynomial of the element below (top face) and above (bottom face)
+    // neighbour rows: the top trace of the element below and the bottom trace
+    // of the element above, each summed in the order of its owner's own trace
+    // (both CTAs of a face see the same values)
     float c[M];
     if (pB) {
 #pragma unroll
       for (int k = 0; k < M; k++) c[k] = pB[k * 32];
-      ytrace32<P>(c, c32t[P].pp, sYN + ((0 * 3 + v) * m) * 32 + lane);
+#pragma unroll
+      for (int q = 0; q < m; q++) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int r = 0; r < m; r++) acc = fmaf(c32t[P].bp[r], c[q * m + r], acc);
+        sYN[((0 * 3 + v) * m + q) * 32 + lane] = acc;
+      }
     } else if (zB) {
 #pragma unroll
       for (int q = 0; q < m; q++) sYN[((0 * 3 + v) * m + q) * 32 + lane] = 0.0f;
@@ -519,7 +507,13 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
     if (pT) {
 #pragma unroll
       for (int k = 0; k < M; k++) c[k] = pT[k * 32];
-      ytrace32<P>(c, c32t[P].pm, sYN + ((1 * 3 + v) * m) * 32 + lane);
+#pragma unroll
+      for (int q = 0; q < m; q++) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int r = 0; r < m; r++) acc = fmaf(c32t[P].bm[r], c[q * m + r], acc);
+        sYN[((1 * 3 + v) * m + q) * 32 + lane] = acc;
+      }
     } else if (zT) {
 #pragma unroll
       for (int q = 0; q < m; q++) sYN[((1 * 3 + v) * m + q) * 32 + lane] = 0.0f;
@@ -535,12 +529,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
         float acc = 0.0f;
         if (ph) {
 #pragma unroll
-          for (int aa = 0; aa < m; aa++) {
-            float t = 0.0f;
-#pragma unroll
-            for (int b = 0; b < m; b++) t = fmaf(ph[(aa * m + b) * 32], c32t[P].phi[r][b], t);
-            acc = fmaf(right ? c32t[P].pm[aa] : c32t[P].pp[aa], t, acc);
-          }
+          for (int q = 0; q < m; q++) acc = fmaf(right ? c32t[P].bm[q] : c32t[P].bp[q], ph[(q * m + r) * 32], acc);
         }
         if (right) sXL[(v * m + r) * 33 + nvalid] = acc;
         else sXR[(v * m + r) * 33] = acc;
@@ -567,14 +556,14 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
       Bg32 bO = bg32_at(pc, xq, side ? yTf : yBf), bN = bO;
       if (exact) {
         const float c2 = bO.c2;
-        bO = bg32_poly<P>(bgOwn, c32t[P].phi[q], side ? c32t[P].pp : c32t[P].pm, c2);
+        bO = bg32_poly<P>(bgOwn, c32t[P].eye[q], side ? c32t[P].bp : c32t[P].bm, c2);
         const float* nb = side ? bgT : bgB;
-        if (nb) bN = bg32_poly<P>(nb, c32t[P].phi[q], side ? c32t[P].pm : c32t[P].pp, c2);
+        if (nb) bN = bg32_poly<P>(nb, c32t[P].eye[q], side ? c32t[P].bm : c32t[P].bp, c2);
         else if (side ? trT : trB) bN = bO;
       }
       dllf32<1>(side ? bO : bN, side ? bN : bO, dL, dR, hf);
 #pragma unroll
-      for (int w3 = 0; w3 < 3; w3++) sFY[((side * 3 + w3) * m + q) * 32 + lane] = hf[w3];
+      for (int w3 = 0; w3 < 3; w3++) sFY[((side * 3 + w3) * m + q) * 32 + lane] = hf[w3] * pc.idy;
     }
     // x faces f = 0..nvalid of the tile row (face f between elements f-1 and f)
     for (int idx = tid; idx < m * 33; idx += 96) {
@@ -592,14 +581,14 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
           const float* eL = (f > 0) ? bgOwn - lc + (f - 1) : bgL;
           const float* eR = (f < nvalid) ? bgOwn - lc + f : bgR;
           const float c2 = bL.c2;
-          if (eL) bL = bg32_poly<P>(eL, c32t[P].pp, c32t[P].phi[r], c2);
-          if (eR) bR = bg32_poly<P>(eR, c32t[P].pm, c32t[P].phi[r], c2);
+          if (eL) bL = bg32_poly<P>(eL, c32t[P].bp, c32t[P].eye[r], c2);
+          if (eR) bR = bg32_poly<P>(eR, c32t[P].bm, c32t[P].eye[r], c2);
           if (!eL && trL && f == 0) bL = bR;
           if (!eR && trR && f == nvalid) bR = bL;
         }
         dllf32<0>(bL, bR, dL, dR, hf);
 #pragma unroll
-        for (int w3 = 0; w3 < 3; w3++) sFX[(w3 * m + r) * 33 + f] = hf[w3];
+        for (int w3 = 0; w3 < 3; w3++) sFX[(w3 * m + r) * 33 + f] = hf[w3] * pc.idx;
       }
     }
   }
@@ -625,8 +614,8 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
       float2 r2, ir;
       Bg32x2 bgn = bg32_at2(pc, xq, y, r2, ir);
       if (exact) {
-        const Bg32 b0 = bg32_poly<P>(bgOwn, c32t[P].phi[q0], c32t[P].phi[r0], bgn.c2.x);
-        const Bg32 b1 = bg32_poly<P>(bgOwn, c32t[P].phi[q1], c32t[P].phi[r1], bgn.c2.y);
+        const Bg32 b0 = bg32_poly<P>(bgOwn, c32t[P].eye[q0], c32t[P].eye[r0], bgn.c2.x);
+        const Bg32 b1 = bg32_poly<P>(bgOwn, c32t[P].eye[q1], c32t[P].eye[r1], bgn.c2.y);
         bgn.sig = make_float2(b0.sig, b1.sig);
         bgn.vx = make_float2(b0.vx, b1.vx);
         bgn.vy = make_float2(b0.vy, b1.vy);
@@ -653,8 +642,9 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
         src1 = f2(n2(f), pdx, src1);
         src2 = f2(n2(f), pdy, src2);
       }
-      const float2 s2y = d2(pc.s2y);
-      const float2 o2[8] = {fx[0], fx[1], fx[2], m2(fy[0], s2y), m2(fy[1], s2y), m2(fy[2], s2y), src1, src2};
+      const float2 s2x = d2(pc.s2x), s2y = d2(pc.s2y);
+      const float2 o2[8] = {m2(fx[0], s2x), m2(fx[1], s2x), m2(fx[2], s2x), m2(fy[0], s2y), m2(fy[1], s2y),
+                            m2(fy[2], s2y), src1, src2};
       float* o0 = sFl + n0 * 32 + lane;
 #pragma unroll
       for (int t = 0; t < 8; t++) o0[t * M * 32] = o2[t].x;
@@ -667,64 +657,68 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   }
   __syncthreads();
   // ---- P3: volume integral and surface lift of this thread's variable -------
-  // Sums that share a weight run as the two lanes of one packed FMA, each lane
-  // in the order of its scalar sum: (x-volume, y-volume) partial sums, the
-  // (x-volume, y-volume) second contractions, the (left, right) and (bottom,
-  // top) lifts.
-  float L[M];
+  // At node (q, r): L = sum_q' dw[q][q'] fx(q', r) + sum_r' dw[r][r'] fy(q, r')
+  //                   + src(q, r) + lm[q] hL(r) - lp[q] hR(r) + lm[r] hB(q) - lp[r] hT(q)
+  // (fx, fy carry 2/dx, 2/dy and the face fluxes 1/dx, 1/dy).  Node pairs
+  // (2k, 2k+1) along x are the lanes of packed FMAs: the x sums take the
+  // pair's two table rows against one value, the y sums one table entry
+  // against the pair's two values; each lane keeps its scalar order.
+  constexpr int MP = (m + 1) / 2;  // node pairs along x (the pair past an odd m has a dead lane)
+  float2 LP[MP][m];                // LP[k][r] = (L(2k, r), L(2k+1, r))
   {
-    float2 AB[m][m];  // first contraction over r, [b][q]: (x-volume, source part of the y-volume)
 #pragma unroll
-    for (int b = 0; b < m; b++)
-#pragma unroll
-      for (int q = 0; q < m; q++) AB[b][q] = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int q = 0; q < m; q++)
+    for (int k = 0; k < MP; k++)
 #pragma unroll
       for (int r = 0; r < m; r++) {
-        const int n = q * m + r;
-        const float2 xs = make_float2(sFl[(v * M + n) * 32 + lane],
-                                      (v > 0) ? sFl[((5 + v) * M + n) * 32 + lane] : 0.0f);
-        const float fyv = sFl[((3 + v) * M + n) * 32 + lane];
-#pragma unroll
-        for (int b = 0; b < m; b++) {
-          AB[b][q] = __ffma2_rn(c32t[P].wphi2[r][b], xs, AB[b][q]);
-          AB[b][q].y = fmaf(c32t[P].wdphi[r][b], fyv, AB[b][q].y);
-        }
+        const int q0 = 2 * k, q1 = 2 * k + 1;
+        LP[k][r] = make_float2(v > 0 ? sFl[((5 + v) * M + q0 * m + r) * 32 + lane] : 0.0f,
+                               (v > 0 && q1 < m) ? sFl[((5 + v) * M + q1 * m + r) * 32 + lane] : 0.0f);
       }
-#pragma unroll
-    for (int aa = 0; aa < m; aa++)
-#pragma unroll
-      for (int b = 0; b < m; b++) {
-        float2 vab = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int q = 0; q < m; q++) vab = __ffma2_rn(c32t[P].wdw2[q][aa], AB[b][q], vab);
-        L[aa * m + b] = fmaf(pc.s2x, vab.x, vab.y);
-      }
-  }
-  {
-    float2 HLR[m], HBT[m];
-#pragma unroll
-    for (int b = 0; b < m; b++) HLR[b] = HBT[b] = make_float2(0.0f, 0.0f);
+    // x: one node row r at a time, its m fluxes and its two face fluxes
 #pragma unroll
     for (int r = 0; r < m; r++) {
-      const float2 flr = make_float2(sFX[(v * m + r) * 33 + lane], sFX[(v * m + r) * 33 + lane + 1]);
-      const float2 fbt = make_float2(sFY[((0 * 3 + v) * m + r) * 32 + lane], sFY[((1 * 3 + v) * m + r) * 32 + lane]);
+      float X[m];
 #pragma unroll
-      for (int b = 0; b < m; b++) {
-        HLR[b] = __ffma2_rn(c32t[P].wphi2[r][b], flr, HLR[b]);
-        HBT[b] = __ffma2_rn(c32t[P].wphi2[r][b], fbt, HBT[b]);
+      for (int q2 = 0; q2 < m; q2++) X[q2] = sFl[(v * M + q2 * m + r) * 32 + lane];
+      const float hl = sFX[(v * m + r) * 33 + lane], hr = sFX[(v * m + r) * 33 + lane + 1];
+#pragma unroll
+      for (int k = 0; k < MP; k++) {
+        float2 acc = LP[k][r];
+#pragma unroll
+        for (int q2 = 0; q2 < m; q2++) acc = f2(c32t[P].dwp[k][q2], d2(X[q2]), acc);
+        acc = f2(c32t[P].lmp[k], d2(hl), acc);
+        LP[k][r] = f2(c32t[P].lpn[k], d2(hr), acc);
       }
     }
+    // y: one node pair (2k, 2k+1) at a time, its two node columns and their
+    // bottom and top face fluxes
 #pragma unroll
-    for (int aa = 0; aa < m; aa++)
+    for (int k = 0; k < MP; k++) {
+      const int q0 = 2 * k, q1 = 2 * k + 1;
+      float2 Y[m];
 #pragma unroll
-      for (int b = 0; b < m; b++) {
-        const float lx = fmaf(c32t[P].pm[aa], HLR[b].x, -c32t[P].pp[aa] * HLR[b].y);
-        const float ly = fmaf(c32t[P].pm[b], HBT[aa].x, -c32t[P].pp[b] * HBT[aa].y);
-        L[aa * m + b] = fmaf(pc.idx, lx, fmaf(pc.idy, ly, L[aa * m + b]));
+      for (int r2 = 0; r2 < m; r2++)
+        Y[r2] = make_float2(sFl[((3 + v) * M + q0 * m + r2) * 32 + lane],
+                            q1 < m ? sFl[((3 + v) * M + q1 * m + r2) * 32 + lane] : 0.0f);
+      const float2 hb = make_float2(sFY[((0 * 3 + v) * m + q0) * 32 + lane],
+                                    q1 < m ? sFY[((0 * 3 + v) * m + q1) * 32 + lane] : 0.0f);
+      const float2 ht = make_float2(sFY[((1 * 3 + v) * m + q0) * 32 + lane],
+                                    q1 < m ? sFY[((1 * 3 + v) * m + q1) * 32 + lane] : 0.0f);
+#pragma unroll
+      for (int r = 0; r < m; r++) {
+        float2 acc = LP[k][r];
+#pragma unroll
+        for (int r2 = 0; r2 < m; r2++) acc = f2(c32t[P].dw2[r][r2], Y[r2], acc);
+        acc = f2(c32t[P].lm2[r], hb, acc);
+        LP[k][r] = f2(c32t[P].lpn2[r], ht, acc);
       }
+    }
   }
+  float L[M];
+#pragma unroll
+  for (int q = 0; q < m; q++)
+#pragma unroll
+    for (int r = 0; r < m; r++) L[q * m + r] = (q & 1) ? LP[q >> 1][r].y : LP[q >> 1][r].x;
   // background residual R_b (only in the tiles that keep it), then the
   // Shu-Osher combination
   const size_t gbase = tile * NVM * 32 + voff;
@@ -769,7 +763,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   if (zones) {
     // the damping targets Q0 - Q_b at the nodes are copied by the TMA unit
     // into planes 3-5 of the pointwise terms, dead from here on, while the
-    // nodal values of the new state are formed in planes 0-2
+    // nodal values of the new state are stored in planes 0-2
     float* sDb = sm + S::F + 3 * M * 32;
     static_assert(3 * M * 32 <= 5 * M * 32, "damping offsets exceed the dead pointwise planes");
     fence_proxy_async_smem();
@@ -779,7 +773,8 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
       mbar_expect_tx(smd + 7, bytes);
       bulk_g2s(sDb, a.Db + tile * (size_t)(3 * M * 32), bytes, smd + 7);
     }
-    nodal32<P, false>(un, sU + voff + lane, nullptr, nullptr);
+#pragma unroll
+    for (int k = 0; k < M; k++) sU[voff + k * 32 + lane] = un[k];
     if (__syncthreads_or(!mbar_wait(smd + 7, 0))) {
       // the copy did not land in time: flag the step (it is discarded) and
       // give the copy a last bounded chance to drain before the CTA exits
@@ -814,7 +809,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
         const float itd = __fdividef(1.0f, tau + dt);
         const float kap = tau * itd, omk = dt * itd;
         Bg32 bgn = bg32_at(pc, xq, y);
-        if (exact) bgn = bg32_poly<P>(bgOwn, c32t[P].phi[q], c32t[P].phi[r], bgn.c2);
+        if (exact) bgn = bg32_poly<P>(bgOwn, c32t[P].eye[q], c32t[P].eye[r], bgn.c2);
         const float d0 = sU[(0 * M + n) * 32 + lane];
         const float d1 = sU[(1 * M + n) * 32 + lane], d2 = sU[(2 * M + n) * 32 + lane];
         const float sg = bgn.sig + d0;
@@ -832,27 +827,11 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
     }
     if (damped) sFlag[lane] = 1;
     if (__syncthreads_or(damped)) {
+      // the damped values at the nodes are the new state (the state is its
+      // nodal values: no projection back)
       if (sFlag[lane]) {
-        // back to modes by the m-point projection of the damped nodal values
-        float P1[m][m];  // [b][q] = sum_r w_r/2 phi_b(eta_r) u(q, r)
 #pragma unroll
-        for (int b = 0; b < m; b++)
-#pragma unroll
-          for (int q = 0; q < m; q++) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int r = 0; r < m; r++) acc = fmaf(c32t[P].wphi[r][b], sU[(v * M + q * m + r) * 32 + lane], acc);
-            P1[b][q] = acc;
-          }
-#pragma unroll
-        for (int aa = 0; aa < m; aa++)
-#pragma unroll
-          for (int b = 0; b < m; b++) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int q = 0; q < m; q++) acc = fmaf(c32t[P].wphi[q][aa], P1[b][q], acc);
-            un[aa * m + b] = acc;
-          }
+        for (int k = 0; k < M; k++) un[k] = sU[voff + k * 32 + lane];
       }
     }
   }
@@ -860,7 +839,13 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
 #pragma unroll
     for (int k = 0; k < M; k++) Outp[gbase + k * 32 + lane] = un[k];
   }
-  sB0[v * 32 + lane] = un[0];
+  {
+    // element average of this variable: the m x m Gauss-Legendre rule
+    float avg = 0.0f;
+#pragma unroll
+    for (int k = 0; k < M; k++) avg = fmaf(c32t[P].w2h[k], un[k], avg);
+    sB0[v * 32 + lane] = avg;
+  }
   __syncthreads();
   if (v == 0) {
     // CFL minimum of the new state from the element averages of u_b + delta
@@ -912,22 +897,17 @@ __global__ void __launch_bounds__(96, DG_STAGE32_MIN_CTAS) k_stage32(const Stage
 // spread evenly over the decades of distance from the planet, so every term
 // is evaluated, and summed over the element's nodes, in float-float
 // arithmetic (~2^-44 relative); the sums over elements are FP64: node
-// mass Sigma_b (a float pair from the FP64 background) + delta Sigma, offsets
-// from the planet as float pairs from the FP64 position, the inverse cube by
-// one float-float Newton correction.  delta Sigma at the nodes is contracted
-// in FP32 (its rounding is ~1e-7 of delta, far below the mass where delta <<
-// Sigma_b) and in float-float within sqrt(near2) of the planet, where delta ~
-// Sigma_b; it waits in this lane's column of shared memory (sD[n * 32], tail
-// at sD[(M + n) * 32]) so that no contraction operand stays live through the
-// node loop.  The x offset depends on the node row q only and the y offset on
-// the node column r only, so the force sums as sum_q dx_q (sum_r f_qr) and
-// sum_r dy_r (sum_q f_qr).  Each element's pair is rounded to a double and
-// the warp sums its elements in FP64; the finish kernel sums the tiles in
+// mass Sigma_b (a float pair from the FP64 background) + delta Sigma (the
+// state's own FP32 value at the node), offsets from the planet as float pairs
+// from the FP64 position, the inverse cube by one float-float Newton
+// correction.  The x offset depends on the node row q only and the y offset
+// on the node column r only, so the force sums as sum_q dx_q (sum_r f_qr)
+// and sum_r dy_r (sum_q f_qr).  Each element's pair is rounded to a double
+// and the warp sums its elements in FP64; the finish kernel sums the tiles in
 // FP64.
 template <int P>
 __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN, const DevState* ts,
-                                              double* part, const Mesh& ms, const Prec32& pc, int tile,
-                                              float* sD) {
+                                              double* part, const Mesh& ms, const Prec32& pc, int tile) {
   constexpr int m = P + 1, M = m * m, NVM = 3 * M;
   if (ts->status != 0) return;
   const int lane = threadIdx.x & 31;
@@ -935,64 +915,13 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
   const int i = bx * 32 + lane;
   const bool valid = i < ms.nx;
   const int lc = valid ? lane : 0;
-  const float* dsig = D + (size_t)tile * NVM * 32 + lc;  // variable 0
+  const float* sD = D + (size_t)tile * NVM * 32 + lc;  // variable 0 at the nodes
   const float* sbh = SigbN + (size_t)tile * 2 * M * 32 + lc;
   const float* sbl = sbh + M * 32;
   const float* p1 = ts->plf[2];
   F2 ox, oy;
   ff_offset(i2f(i) + 0.5f, pc.x0p, pc.dxp, p1[0], p1[1], ox.h, ox.l);
   ff_offset(i2f(j) + 0.5f, pc.y0p, pc.dyp, p1[2], p1[3], oy.h, oy.l);
-  const bool near = valid && fmaf(ox.h, ox.h, oy.h * oy.h) < pc.near2;
-  const bool ffw = __any_sync(0xffffffffu, near);  // float-float delta contraction in this warp
-  float* sDl = sD + M * 32;
-  {
-    // T[a][r] = sum_b c_ab phi_b(eta_r), then delta Sigma(q, r) = sum_a phi_a(xi_q) T[a][r]
-    float c[M];
-#pragma unroll
-    for (int k = 0; k < M; k++) c[k] = dsig[k * 32];
-    if (ffw) {
-      F2 T[m][m];
-#pragma unroll
-      for (int aa = 0; aa < m; aa++)
-#pragma unroll
-        for (int r = 0; r < m; r++) {
-          F2 acc{0.0f, 0.0f};
-#pragma unroll
-          for (int b = 0; b < m; b++) acc = f2_add(acc, f2_mulf(F2{c32t[P].phi[r][b], c32t[P].phil[r][b]}, c[aa * m + b]));
-          T[aa][r] = acc;
-        }
-#pragma unroll
-      for (int q = 0; q < m; q++)
-#pragma unroll
-        for (int r = 0; r < m; r++) {
-          F2 ds{0.0f, 0.0f};
-#pragma unroll
-          for (int aa = 0; aa < m; aa++) ds = f2_add(ds, f2_mul(F2{c32t[P].phi[q][aa], c32t[P].phil[q][aa]}, T[aa][r]));
-          sD[(q * m + r) * 32] = ds.h;
-          sDl[(q * m + r) * 32] = ds.l;
-        }
-    } else {
-      float T[m][m];
-#pragma unroll
-      for (int aa = 0; aa < m; aa++)
-#pragma unroll
-        for (int r = 0; r < m; r++) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int b = 0; b < m; b++) acc = fmaf(c[aa * m + b], c32t[P].phi[r][b], acc);
-          T[aa][r] = acc;
-        }
-#pragma unroll
-      for (int q = 0; q < m; q++)
-#pragma unroll
-        for (int r = 0; r < m; r++) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int aa = 0; aa < m; aa++) acc = fmaf(c32t[P].phi[q][aa], T[aa][r], acc);
-          sD[(q * m + r) * 32] = acc;
-        }
-    }
-  }
   const F2 hdx{0.5f * pc.dxp[0], 0.5f * pc.dxp[1]}, hdy{0.5f * pc.dyp[0], 0.5f * pc.dyp[1]};
   const F2 eps2{pc.eps2p[0], pc.eps2p[1]};
   // offsets of the node columns from the planet and their squares plus eps^2
@@ -1022,7 +951,7 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
 #pragma unroll
       for (int r = 0; r < m; r++) {
         const int n = q * m + r;
-        const F2 ds{sD[n * 32], ffw ? sDl[n * 32] : 0.0f};
+        const F2 ds{sD[n * 32], 0.0f};
         // w_n (Sigma_b + delta Sigma) / (d^2 + eps^2)^{3/2}
         const F2 mass = f2_mul_u(f2_add_u(F2{sh[r], sl[r]}, ds), F2{c32t[P].w2h[n], c32t[P].w2l[n]});
         const F2 f = f2_mul_u(mass, f2_rsqrt3_u(f2_add_u(px2, pye[r])));
@@ -1048,18 +977,15 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
   }
 }
 
-// four tiles (warps) per CTA; each lane keeps its element's nodal delta Sigma
-// (head and tail) in shared memory
+// four tiles (warps) per CTA
 template <int P>
-__global__ void __launch_bounds__(128, 7) k_torque32(const float* D, const float* SigbN, const DevState* ts,
+__global__ void __launch_bounds__(128, 8) k_torque32(const float* D, const float* SigbN, const DevState* ts,
                                                    double* part, const Mesh ms, const Prec32 pc) {
-  constexpr int M = (P + 1) * (P + 1);
-  __shared__ float sD[4][2 * M * 32];
   pdl_wait();
   pdl_trigger();
   const int w = threadIdx.x >> 5;
   const int tile = blockIdx.x * 4 + w;
-  if (tile < ms.ntx * ms.ny) torque32_tile<P>(D, SigbN, ts, part, ms, pc, tile, sD[w] + (threadIdx.x & 31));  // warp-uniform
+  if (tile < ms.ntx * ms.ny) torque32_tile<P>(D, SigbN, ts, part, ms, pc, tile);  // warp-uniform
 }
 
 template <int P, bool LAST>
@@ -1089,26 +1015,48 @@ static cudaError_t launch_torque32_impl(const float* D, const float* SigbN, cons
 
 template <int P>
 static Tab32 make_tab32(const Tables& t) {
+  constexpr int m = P + 1;
   Tab32 c{};
-  for (int q = 0; q <= P; q++) {
+  double dw[MAXM][MAXM] = {}, lp[MAXM] = {}, lm[MAXM] = {};
+  for (int q = 0; q < m; q++) {
+    for (int a = 0; a < m; a++) {
+      lp[q] += t.phi[q][a] * t.pp[a];
+      lm[q] += t.phi[q][a] * t.pm[a];
+    }
+    for (int q2 = 0; q2 < m; q2++) {
+      double s = 0.0;
+      for (int a = 0; a < m; a++) s += t.phi[q][a] * t.dphi[q2][a];
+      dw[q][q2] = t.wh[q2] * s;
+    }
+  }
+  for (int q = 0; q < m; q++) {
     c.xi[q] = (float)t.xi[q];
     c.xil[q] = (float)(t.xi[q] - (double)c.xi[q]);
     c.wh[q] = (float)t.wh[q];
-    c.pp[q] = (float)t.pp[q];
-    c.pm[q] = (float)t.pm[q];
-    for (int a = 0; a <= P; a++) {
-      c.phi[q][a] = (float)t.phi[q][a];
-      c.phil[q][a] = (float)(t.phi[q][a] - (double)c.phi[q][a]);
-      c.wphi[q][a] = (float)(t.wh[q] * t.phi[q][a]);
-      c.wdphi[q][a] = (float)(t.wh[q] * t.dphi[q][a]);
-      c.wphi2[q][a] = make_float2(c.wphi[q][a], c.wphi[q][a]);
-      c.wdw2[q][a] = make_float2(c.wdphi[q][a], c.wphi[q][a]);
+    c.bp[q] = (float)(t.wh[q] * lp[q]);
+    c.bm[q] = (float)(t.wh[q] * lm[q]);
+    c.bpm2[q] = make_float2(c.bp[q], c.bm[q]);
+    c.lp[q] = (float)lp[q];
+    c.lm[q] = (float)lm[q];
+    c.eye[q][q] = 1.0f;
+    for (int q2 = 0; q2 < m; q2++) {
+      c.dw[q][q2] = (float)dw[q][q2];
+      c.dw2[q][q2] = make_float2(c.dw[q][q2], c.dw[q][q2]);
     }
-    for (int r = 0; r <= P; r++) {
+    c.lm2[q] = make_float2(c.lm[q], c.lm[q]);
+    c.lpn2[q] = make_float2(-c.lp[q], -c.lp[q]);
+    for (int r = 0; r < m; r++) {
       const double w2 = t.wh[q] * t.wh[r];
-      c.w2h[q * (P + 1) + r] = (float)w2;
-      c.w2l[q * (P + 1) + r] = (float)(w2 - (double)c.w2h[q * (P + 1) + r]);
+      c.w2h[q * m + r] = (float)w2;
+      c.w2l[q * m + r] = (float)(w2 - (double)c.w2h[q * m + r]);
     }
+  }
+  for (int k = 0; 2 * k < m; k++) {
+    const int q0 = 2 * k, q1 = 2 * k + 1;
+    const bool two = q1 < m;
+    for (int q2 = 0; q2 < m; q2++) c.dwp[k][q2] = make_float2(c.dw[q0][q2], two ? c.dw[q1][q2] : 0.0f);
+    c.lmp[k] = make_float2(c.lm[q0], two ? c.lm[q1] : 0.0f);
+    c.lpn[k] = make_float2(-c.lp[q0], two ? -c.lp[q1] : 0.0f);
   }
   return c;
 }

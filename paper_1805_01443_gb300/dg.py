@@ -263,7 +263,8 @@ class Disc:
         self._keep.append(delta)
 
     def fetch_delta(self, out=None):
-        """dg_fetch_delta (precision form): delta = u - u_b as float32."""
+        """dg_fetch_delta (precision form): delta = u - u_b as float32 values
+        at the Gauss-Legendre nodes, index q*m + r along the mode axis."""
         if out is None:
             out = np.empty(self.shape, dtype=np.float32)
         _check(lib().dg_fetch_delta(self.h, out.ctypes.data_as(_VP)), self.h)
