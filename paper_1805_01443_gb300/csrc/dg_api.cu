@@ -433,11 +433,16 @@ int read_state(dg_handle* h, DevState* out) {
 }
 
 // CFL step of a full FP64 tiled state into the device time state
-int launch_cfl_and_dt(dg_handle* h, const double* full, const float* delta = nullptr) {
-  double wn[MAXM * MAXM];
+// weights (w_q/2)(w_r/2) of the m x m nodes (element averages of node values)
+void node_weights(const dg_handle* h, double* wn) {
   const int m = h->p + 1;
   for (int q = 0; q < m; q++)
     for (int r = 0; r < m; r++) wn[q * m + r] = h->tab.wh[q] * h->tab.wh[r];
+}
+
+int launch_cfl_and_dt(dg_handle* h, const double* full, const float* delta = nullptr) {
+  double wn[MAXM * MAXM];
+  node_weights(h, wn);
   CU(h, launch_cfl(full, delta, wn, h->ts, h->dm, h->ph, h->p, h->nv, h->stream));
   CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, 0, h->ph.r_p, h->ph.omega_p,
                       h->ph.phi0, h->stream));
@@ -1111,14 +1116,15 @@ int dg_set_state(dg_handle* h, const double* coeffs, double t, long step) {
   else
     CU(h, cudaMemcpyAsync(h->S, coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   cudaGetLastError();  // a pointer query on unregistered memory may leave an error behind
-  double* full = h->prec == 1 ? h->Z : h->B[0];
-  CU(h, launch_ingest(src, full, h->dm, h->nv, h->M, h->stream));
-  if (h->prec == 1) CU(h, launch_to_nodal32(full, 0, h->BG, h->D[0], h->dm, h->tab, h->p, h->nv, 0, h->stream));
+  // the precision form maps u - u_b (canonical modes minus the tiled
+  // background) to the nodes in one pass; its CFL step averages u_b + delta
+  if (h->prec == 1) CU(h, launch_to_nodal32(src, 1, h->BG, h->D[0], h->dm, h->tab, h->p, h->nv, 0, h->stream));
+  else CU(h, launch_ingest(src, h->B[0], h->dm, h->nv, h->M, h->stream));
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
   h->cur = h->cur0 = 0;
   h->step0 = step;
   h->series_read = 0;
-  int rc = launch_cfl_and_dt(h, full);
+  int rc = h->prec == 1 ? launch_cfl_and_dt(h, h->BG, h->D[0]) : launch_cfl_and_dt(h, h->B[0]);
   if (rc) return rc;
   DevState st;
   return read_state(h, &st);
@@ -1153,16 +1159,15 @@ int dg_set_state_async(dg_handle* h, const double* coeffs, double t, long step) 
   CU(h, cudaMemcpyAsync(h->SA[k], coeffs, n * sizeof(double), cudaMemcpyHostToDevice, h->cstream));
   CU(h, cudaEventRecord(h->ev_copied[k], h->cstream));
   CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
-  double* full = h->prec == 1 ? h->Z : h->B[0];
-  CU(h, launch_ingest(h->SA[k], full, h->dm, h->nv, h->M, h->stream));
-  if (h->prec == 1) CU(h, launch_to_nodal32(full, 0, h->BG, h->D[0], h->dm, h->tab, h->p, h->nv, 0, h->stream));
+  if (h->prec == 1) CU(h, launch_to_nodal32(h->SA[k], 1, h->BG, h->D[0], h->dm, h->tab, h->p, h->nv, 0, h->stream));
+  else CU(h, launch_ingest(h->SA[k], h->B[0], h->dm, h->nv, h->M, h->stream));
   CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
   h->cur = h->cur0 = 0;
   h->step0 = step;
   h->series_read = 0;
   h->apar = 1 - k;
-  return launch_cfl_and_dt(h, full);
+  return h->prec == 1 ? launch_cfl_and_dt(h, h->BG, h->D[0]) : launch_cfl_and_dt(h, h->B[0]);
 }
 
 int dg_set_delta_async(dg_handle* h, const float* delta, double t, long step) {
@@ -1186,14 +1191,20 @@ int dg_set_delta_async(dg_handle* h, const float* delta, double t, long step) {
   CU(h, cudaMemcpyAsync(stage, delta, n * sizeof(float), cudaMemcpyHostToDevice, h->cstream));
   CU(h, cudaEventRecord(h->ev_copied[k], h->cstream));
   CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
-  CU(h, launch_ingest_delta(stage, h->D[0], h->dm, h->nv, h->M, h->stream));
-  CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
+  // the status reset, then the layout change and the CFL step of u_b + delta
+  // in one pass over the upload, then the step's dt
   CU(h, launch_reset_state(h->ts, t, step, h->stream));
+  double wn[MAXM * MAXM];
+  node_weights(h, wn);
+  CU(h, launch_ingest_delta_cfl(stage, h->D[0], h->BG, wn, h->ts, h->dm, h->ph, h->M, h->stream));
+  CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
   h->cur = h->cur0 = 0;
   h->step0 = step;
   h->series_read = 0;
   h->apar = 1 - k;
-  return launch_cfl_and_dt(h, h->BG, h->D[0]);  // element averages of u_b + delta
+  CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, 0, h->ph.r_p, h->ph.omega_p, h->ph.phi0,
+                      h->stream));
+  return DG_OK;
 }
 
 int dg_fetch_delta(dg_handle* h, float* delta) {

@@ -29,6 +29,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// ask the L2 for `bytes` of global memory (a hint: no completion, no
+// register); address and size multiples of 16
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_test(void* bar, unsigned parity) {
   unsigned ok;
   asm volatile(

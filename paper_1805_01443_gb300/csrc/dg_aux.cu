@@ -81,11 +81,50 @@ __global__ void k_init(const InitArgs a, int count) {
 // CFL time step of Sec. 2.3 from the element averages; block minimum folded
 // into the device slot with an atomic minimum on the (positive) bit pattern.
 // CFL minimum of the element averages of U (tiled FP64), or of U + D when D
-// (tiled FP32, the precision form's delta about U = u_b, values at the nodes
-// averaged with the weights w) is given
+// (tiled FP32, the precision form's delta about U = u_b, values at the nodes)
+// is given: the average of D is sum_n w_n D_n with the weights w_n = (w_q/2)
+// (w_r/2) as float pairs (wh, wl), each product and the sum formed in
+// float-float arithmetic (~2^-44 relative to sum |w_n D_n|), then added to
+// U's FP64 average
 struct NodeW {
-  double w[MAXM * MAXM];
+  float wh[MAXM * MAXM], wl[MAXM * MAXM];
 };
+
+// one term w_n d of the float-float sum (sh, sl), in node order
+__device__ __forceinline__ void ff_acc(const NodeW& w, int n, float d, float& sh, float& sl) {
+  const float p = __fmul_rn(w.wh[n], d);
+  const float e = fmaf(w.wl[n], d, fmaf(w.wh[n], d, -p));  // w d - p, to ~2^-48 of w d
+  const float t = __fadd_rn(sh, p);                          // two-sum of sh and p
+  const float bb = __fsub_rn(t, sh);
+  sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb)), e));
+  sh = t;
+}
+
+// the CFL bound of element (i, j) from its averages (E: adiabatic only);
+// +inf (no wave speed) is no constraint, and bad is set for a NaN or
+// non-positive bound or density
+__device__ __forceinline__ double cfl_bound(double rho, double mx, double my, double E, int i, int j,
+                                            const Mesh& ms, const Phys& ph, double idx, double idy, int& bad) {
+  const double irho = 1.0 / rho;
+  const double vx = mx * irho, vy = my * irho;
+  double c;
+  if (ph.kind == 1) {
+    const double pr = (ph.gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy));
+    c = sqrt(ph.gamma * pr * irho);
+  } else if (ph.kind == 2) {
+    c = ph.h;
+  } else {
+    const double xc = ms.x0 + (i + 0.5) * ms.dx, yc = ms.y0 + (j + 0.5) * ms.dy;
+    const double r = sqrt(xc * xc + yc * yc);
+    // h v_K: h / sqrt(r) outside the softened core, h r / r_s^(3/2) inside
+    c = ph.h * (r >= ph.rs ? rsqrt(r) : sqrt(vk2_of(ph, r)));
+  }
+  double dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) * idx + (fabs(vy) + c) * idy);
+  bad = !(rho > 0.0) || !(dtk > 0.0);
+  if (bad) dtk = __longlong_as_double((long long)INF_BITS);
+  return dtk;
+}
+
 __global__ void k_cfl(const double* U, const float* D, const NodeW w, DevState* ts, const Mesh ms, const Phys ph,
                       int p, int nv, double idx, double idy) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,29 +137,11 @@ __global__ void k_cfl(const double* U, const float* D, const NodeW w, DevState* 
     auto avg = [&](int v) {
       const size_t o = base + (size_t)v * M * TILE;
       if (!D) return U[o];
-      double s = 0.0;
-      for (int n = 0; n < M; n++) s += w.w[n] * (double)D[o + (size_t)n * TILE];
-      return U[o] + s;
+      float sh = 0.0f, sl = 0.0f;
+      for (int n = 0; n < M; n++) ff_acc(w, n, D[o + (size_t)n * TILE], sh, sl);
+      return U[o] + ((double)sh + (double)sl);
     };
-    const double rho = avg(0), mx = avg(1), my = avg(2);
-    const double irho = 1.0 / rho;
-    const double vx = mx * irho, vy = my * irho;
-    double c;
-    if (ph.kind == 1) {
-      const double E = avg(3);
-      const double pr = (ph.gamma - 1.0) * (E - 0.5 * (mx * vx + my * vy));
-      c = sqrt(ph.gamma * pr * irho);
-    } else if (ph.kind == 2) {
-      c = ph.h;
-    } else {
-      const double xc = ms.x0 + (i + 0.5) * ms.dx, yc = ms.y0 + (j + 0.5) * ms.dy;
-      const double r = sqrt(xc * xc + yc * yc);
-      // h v_K: h / sqrt(r) outside the softened core, h r / r_s^(3/2) inside
-      c = ph.h * (r >= ph.rs ? rsqrt(r) : sqrt(vk2_of(ph, r)));
-    }
-    dtk = ph.cfl * ph.cfl_fac / ((fabs(vx) + c) * idx + (fabs(vy) + c) * idy);
-    bad = !(rho > 0.0) || !(dtk > 0.0);  // +inf (no wave speed) is no constraint; NaN fails
-    if (bad) dtk = __longlong_as_double((long long)INF_BITS);
+    dtk = cfl_bound(avg(0), avg(1), avg(2), ph.kind == 1 ? avg(3) : 0.0, i, j, ms, ph, idx, idy, bad);
   }
   for (int o = 16; o > 0; o >>= 1) {
     dtk = fmin(dtk, __shfl_xor_sync(0xffffffffu, dtk, o));
@@ -168,12 +189,45 @@ __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ 
         canon[((size_t)vk * ms.ny + j) * ms.nx + i];
 }
 
-// canonical FP32 delta (values at the nodes) -> tiled delta
-__global__ void k_ingest_delta(const float* __restrict__ canon, float* __restrict__ d, const Mesh ms, int nvm) {
-  const int i = blockIdx.x * TILE + threadIdx.x, j = blockIdx.y;
-  if (i >= ms.nx) return;
-  for (int vk = threadIdx.y; vk < nvm; vk += blockDim.y)
-    d[(((size_t)j * ms.ntx + blockIdx.x) * nvm + vk) * TILE + threadIdx.x] = canon[((size_t)vk * ms.ny + j) * ms.nx + i];
+// canonical FP32 delta (values at the nodes) -> tiled delta, with the CFL
+// step of u_b + delta (the precision form's upload): a block of (32, 3)
+// threads per tile, thread (lane, v) moving variable v of one element in node
+// order and summing its average as k_cfl does, warp 0 forming the bounds
+__global__ void k_ingest_delta_cfl(const float* __restrict__ canon, float* __restrict__ d,
+                                   const double* __restrict__ U, const NodeW w, DevState* ts, const Mesh ms,
+                                   const Phys ph, int M, double idx, double idy) {
+  __shared__ float s_sum[3][2][TILE];
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int i = blockIdx.x * TILE + lane, j = blockIdx.y;
+  const size_t base = ((size_t)j * ms.ntx + blockIdx.x) * 3 * M * TILE + lane;
+  float sh = 0.0f, sl = 0.0f;
+  if (i < ms.nx) {
+    for (int n = 0; n < M; n++) {
+      const float x = canon[((size_t)(v * M + n) * ms.ny + j) * ms.nx + i];
+      d[base + (size_t)(v * M + n) * TILE] = x;
+      ff_acc(w, n, x, sh, sl);
+    }
+  }
+  s_sum[v][0][lane] = sh;
+  s_sum[v][1][lane] = sl;
+  __syncthreads();
+  if (v != 0) return;
+  double dtk = __longlong_as_double((long long)INF_BITS);
+  int bad = 0;
+  if (i < ms.nx) {
+    double a[3];
+    for (int k = 0; k < 3; k++)
+      a[k] = U[base + (size_t)k * M * TILE] + ((double)s_sum[k][0][lane] + (double)s_sum[k][1][lane]);
+    dtk = cfl_bound(a[0], a[1], a[2], 0.0, i, j, ms, ph, idx, idy, bad);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dtk = fmin(dtk, __shfl_xor_sync(0xffffffffu, dtk, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (lane == 0) {
+    if (bad) atomicOr(&ts->pending, 1);
+    atomicMin(&ts->dt_bits, (unsigned long long)__double_as_longlong(dtk));
+  }
 }
 
 __global__ void k_to_canon_f32(const float* tiled, float* canon, const Mesh ms, int nvm) {
@@ -243,7 +297,10 @@ cudaError_t launch_cfl(const double* U, const float* D, const double* wn, DevSta
   const int n = mesh.nx * mesh.ny;
   NodeW w{};
   if (D)
-    for (int k = 0; k < (p + 1) * (p + 1); k++) w.w[k] = wn[k];
+    for (int k = 0; k < (p + 1) * (p + 1); k++) {
+      w.wh[k] = (float)wn[k];
+      w.wl[k] = (float)(wn[k] - (double)w.wh[k]);
+    }
   k_cfl<<<(n + 255) / 256, 256, 0, s>>>(U, D, w, ts, mesh, phys, p, nv, 1.0 / mesh.dx, 1.0 / mesh.dy);
   return cudaGetLastError();
 }
@@ -305,8 +362,15 @@ cudaError_t launch_ingest(const double* canon, double* tiled, const Mesh& mesh, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ingest_delta(const float* canon, float* d, const Mesh& mesh, int nv, int M, cudaStream_t s) {
-  k_ingest_delta<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 8), 0, s>>>(canon, d, mesh, nv * M);
+cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* U, const double* wn, DevState* ts,
+                                   const Mesh& mesh, const Phys& phys, int M, cudaStream_t s) {
+  NodeW w{};
+  for (int k = 0; k < M; k++) {
+    w.wh[k] = (float)wn[k];
+    w.wl[k] = (float)(wn[k] - (double)w.wh[k]);
+  }
+  k_ingest_delta_cfl<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 3), 0, s>>>(canon, d, U, w, ts, mesh, phys, M,
+                                                                       1.0 / mesh.dx, 1.0 / mesh.dy);
   return cudaGetLastError();
 }
 

@@ -183,8 +183,12 @@ cudaError_t launch_finish(DevState* ts, const double* part, int nparts, double* 
 cudaError_t launch_ingest(const double* canon, double* tiled, const Mesh& mesh, int nv, int M, cudaStream_t s);
 cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh, int nv, int M,
                             cudaStream_t s);
-// precision form: canonical FP32 delta (values at the nodes) -> tiled delta d
-cudaError_t launch_ingest_delta(const float* canon, float* d, const Mesh& mesh, int nv, int M, cudaStream_t s);
+// precision form (locally isothermal, 3 variables): canonical FP32 delta
+// (values at the nodes) -> tiled delta d, with the CFL minimum of U + d (U:
+// tiled FP64 u_b; wn: the node weights) folded into ts->dt_bits in the same
+// pass, as launch_cfl would
+cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* U, const double* wn, DevState* ts,
+                                   const Mesh& mesh, const Phys& phys, int M, cudaStream_t s);
 cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
                                 cudaStream_t s);
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,

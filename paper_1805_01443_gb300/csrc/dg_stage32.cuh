@@ -433,6 +433,28 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   else if (ms.bc == 1) zR = true;
   else if (ms.bc == 3) { const int ie = ms.nx - 1; pR = Dcur + ((size_t)j * ms.ntx + (ie >> 5)) * NVM * 32 + voff + (ie & 31); }
   const bool trL = !pL && !zL, trR = !pR && !zR;
+  // does any node of the tile lie in a damping zone (last stage; a
+  // conservative test on the tile's box, the per-node test decides)
+  bool zones = false;
+  if (LAST) {
+    const float xlo = pc.x0 + i2f(i0) * pc.dx, xhi = fmaf(i2f(nvalid), pc.dx, xlo);
+    const float ylo = pc.y0 + i2f(j) * pc.dy, yhi = ylo + pc.dy;
+    const float cx = fminf(fmaxf(0.0f, xlo), xhi), cy = fminf(fmaxf(0.0f, ylo), yhi);
+    const float rmin2 = fmaf(cx, cx, cy * cy);
+    const float rmax2 = fmaxf(xlo * xlo, xhi * xhi) + fmaxf(ylo * ylo, yhi * yhi);
+    zones = (pc.rd_in > 0.0f && rmin2 < 1.001f * pc.rd_in * pc.rd_in) ||
+            (pc.rd_out > 0.0f && rmax2 > 0.999f * pc.rd_out * pc.rd_out);
+  }
+  // the tile rows the update reads at the end (u^n, R_b, the damping offsets)
+  // are asked of the L2 now, one bulk request each, so that their DRAM
+  // latency passes while the tile computes
+  const int rbs = a.RbIdx[tile];
+  if (tid == 32) {
+    const unsigned tbytes = NVM * 32 * sizeof(float);
+    if (mode != 0 && alpha != 0.0f) bulk_prefetch_l2(Dn0 + tile * NVM * 32, tbytes);
+    if (rbs >= 0) bulk_prefetch_l2(a.Rb + (size_t)rbs * NVM * 32, tbytes);
+    if (LAST && zones) bulk_prefetch_l2(a.Db + tile * (size_t)(3 * M * 32), 3 * M * 32 * sizeof(float));
+  }
   // tiles near the singular centre use the exact projected background (FP32
   // modes of u_b, same tiled layout as delta, all three variables)
   const int exact = a.TileFlag[tile];
@@ -722,7 +744,6 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   // background residual R_b (only in the tiles that keep it), then the
   // Shu-Osher combination
   const size_t gbase = tile * NVM * 32 + voff;
-  const int rbs = a.RbIdx[tile];
   if (rbs >= 0) {
     const float* rb = a.Rb + (size_t)rbs * NVM * 32 + voff + lc;
 #pragma unroll
@@ -749,17 +770,6 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
     return;
   }
   // ---- P4 (last stage): damping in delta form, CFL ---------------------------
-  // does any node of the tile lie in a damping zone (a conservative test on
-  // the tile's box; the per-node test below decides)
-  bool zones;
-  {
-    const float xlo = xt0, xhi = fmaf(i2f(nvalid), pc.dx, xt0);
-    const float cx = fminf(fmaxf(0.0f, xlo), xhi), cy = fminf(fmaxf(0.0f, yBf), yTf);
-    const float rmin2 = fmaf(cx, cx, cy * cy);
-    const float rmax2 = fmaxf(xlo * xlo, xhi * xhi) + fmaxf(yBf * yBf, yTf * yTf);
-    zones = (pc.rd_in > 0.0f && rmin2 < 1.001f * pc.rd_in * pc.rd_in) ||
-            (pc.rd_out > 0.0f && rmax2 > 0.999f * pc.rd_out * pc.rd_out);
-  }
   if (zones) {
     // the damping targets Q0 - Q_b at the nodes are copied by the TMA unit
     // into planes 3-5 of the pointwise terms, dead from here on, while the
