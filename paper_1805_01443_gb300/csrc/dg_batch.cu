@@ -256,6 +256,13 @@ cudaError_t batch_upload_tables32(const Tables* const* tabs) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_batch_stage32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes());
+  // the whole unified L1 as shared memory (the occupancy the kernel is built for)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_stage32<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_stage32<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   return e;
 }
 

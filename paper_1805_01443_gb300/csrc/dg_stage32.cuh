@@ -86,30 +86,33 @@ struct Bg32 {
 // The background enters only as coefficients of perturbation terms, so the
 // hardware approximations (a few ulp) of reciprocal and square root serve; the
 // correctly rounded library forms run partly on this part's narrow FP64 unit.
-__device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrtf(x); }
+// Products that may meet a sum are written as explicitly rounded products, so
+// that no code generator fuses them into an FMA in one kernel and not in
+// another (the single-disc and batched kernels round alike).
+__device__ __forceinline__ float sqrt_fast(float x) { return __fmul_rn(x, rsqrtf(x)); }
 
 __device__ __forceinline__ Bg32 bg32_at(const Prec32& pc, float x, float y) {
   Bg32 b;
-  const float r2 = fmaxf(fmaf(x, x, y * y), 1e-24f);  // r >= 1e-12: a node at the origin
+  const float r2 = fmaxf(fmaf(x, x, __fmul_rn(y, y)), 1e-24f);  // r >= 1e-12: a node at the origin
   const float ir = rsqrtf(r2);
-  const float r = r2 * ir;
+  const float r = __fmul_rn(r2, ir);
   const float sir = sqrt_fast(ir);  // r^-1/2
-  float sig = pc.slope_half ? sir : exp2f(pc.slope * __log2f(r));
+  float sig = pc.slope_half ? sir : exp2f(__fmul_rn(pc.slope, __log2f(r)));
   sig = fmaxf(sig, pc.sig_floor);
   float om, vk2;
   if (r >= pc.rs) {
-    om = pc.sqk_out * ir * sir;        // v_phi / r = sqrt((1 + (s-1) h^2) / r) / r
+    om = __fmul_rn(__fmul_rn(pc.sqk_out, ir), sir);  // v_phi / r = sqrt((1 + (s-1) h^2) / r) / r
     vk2 = ir;
   } else {
     om = pc.om_in;                     // solid-body core
-    vk2 = r2 * pc.irs3;
+    vk2 = __fmul_rn(r2, pc.irs3);
   }
   b.sig = sig;
-  b.vx = -om * y;
-  b.vy = om * x;
-  b.mx = sig * b.vx;
-  b.my = sig * b.vy;
-  b.c2 = pc.h2 * vk2;
+  b.vx = __fmul_rn(-om, y);
+  b.vy = __fmul_rn(om, x);
+  b.mx = __fmul_rn(sig, b.vx);
+  b.my = __fmul_rn(sig, b.vy);
+  b.c2 = __fmul_rn(pc.h2, vk2);
   return b;
 }
 
@@ -187,7 +190,7 @@ __device__ __forceinline__ void dllf32(const Bg32& bL, const Bg32& bR, const flo
   const float jb[3] = {bR.sig - bL.sig, bR.mx - bL.mx, bR.my - bL.my};
 #pragma unroll
   for (int v = 0; v < 3; v++)
-    h[v] = 0.5f * (fn[v].x + fn[v].y) - 0.5f * fmaf(al, dR[v] - dL[v], (al - alb) * jb[v]);
+    h[v] = fmaf(0.5f, __fadd_rn(fn[v].x, fn[v].y), __fmul_rn(-0.5f, fmaf(al, dR[v] - dL[v], __fmul_rn(al - alb, jb[v]))));
 }
 
 // Exact projected background at a point of one element from its FP32 values
@@ -437,8 +440,8 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   // conservative test on the tile's box, the per-node test decides)
   bool zones = false;
   if (LAST) {
-    const float xlo = pc.x0 + i2f(i0) * pc.dx, xhi = fmaf(i2f(nvalid), pc.dx, xlo);
-    const float ylo = pc.y0 + i2f(j) * pc.dy, yhi = ylo + pc.dy;
+    const float xlo = fmaf(i2f(i0), pc.dx, pc.x0), xhi = fmaf(i2f(nvalid), pc.dx, xlo);
+    const float ylo = fmaf(i2f(j), pc.dy, pc.y0), yhi = ylo + pc.dy;
     const float cx = fminf(fmaxf(0.0f, xlo), xhi), cy = fminf(fmaxf(0.0f, ylo), yhi);
     const float rmin2 = fmaf(cx, cx, cy * cy);
     const float rmax2 = fmaxf(xlo * xlo, xhi * xhi) + fmaxf(ylo * ylo, yhi * yhi);
@@ -465,10 +468,9 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   const float* bgR = (exact && pR) ? a.Bmodes + (pR - Dcur) - voff : nullptr;
   // FP32 geometry of this thread's element
   const float lanef = i2f(lane);
-  const float xcf = pc.x0 + (i2f(i0 + lane) + 0.5f) * pc.dx;
-  const float ycf = pc.y0 + (i2f(j) + 0.5f) * pc.dy;
-  const float yBf = pc.y0 + i2f(j) * pc.dy, yTf = yBf + pc.dy;
-  const float xt0 = pc.x0 + i2f(i0) * pc.dx;
+  const float xcf = fmaf(i2f(i0 + lane) + 0.5f, pc.dx, pc.x0);
+  const float ycf = fmaf(i2f(j) + 0.5f, pc.dy, pc.y0);
+  const float yBf = fmaf(i2f(j), pc.dy, pc.y0), yTf = fmaf(i2f(j + 1), pc.dy, pc.y0);
 
   // ---- P1: nodal values and face traces of this thread's variable ------------
   // The state is the values at the m x m nodes (k = q*m + r): they go to
@@ -598,7 +600,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
           dR[w3] = sXL[(w3 * m + r) * 33 + f];
         }
         const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
-        Bg32 bL = bg32_at(pc, fmaf(i2f(f), pc.dx, xt0), y), bR = bL;
+        Bg32 bL = bg32_at(pc, fmaf(i2f(i0 + f), pc.dx, pc.x0), y), bR = bL;
         if (exact) {
           const float* eL = (f > 0) ? bgOwn - lc + (f - 1) : bgL;
           const float* eR = (f < nvalid) ? bgOwn - lc + f : bgR;
@@ -800,39 +802,39 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
       const int q = n / m, r = n - q * m;
       const float xq = fmaf(pc.hdx, c32t[P].xi[q], xcf);
       const float y = fmaf(pc.hdy, c32t[P].xi[r], ycf);
-      const float rr = sqrt_fast(fmaxf(fmaf(xq, xq, y * y), 1e-24f));
+      const float rr = sqrt_fast(fmaxf(fmaf(xq, xq, __fmul_rn(y, y)), 1e-24f));
       float R = 0.0f, rd = 0.0f;
       if (pc.rd_in > 0.0f && rr < pc.rd_in) {
         rd = pc.rd_in;
-        const float x = __fdividef(rr - rd, __fdividef(rd, pc.damp_ratio) - rd);
-        R = fminf(x * x, 1.0f);
+        const float x = __fdividef(__fsub_rn(rr, rd), __fsub_rn(__fdividef(rd, pc.damp_ratio), rd));
+        R = fminf(__fmul_rn(x, x), 1.0f);
       } else if (pc.rd_out > 0.0f && rr > pc.rd_out) {
         rd = pc.rd_out;
-        const float x = __fdividef(rr - rd, rd * pc.damp_ratio - rd);
-        R = fminf(x * x, 1.0f);
+        const float x = __fdividef(__fsub_rn(rr, rd), fmaf(rd, pc.damp_ratio, -rd));
+        R = fminf(__fmul_rn(x, x), 1.0f);
       }
       if (R > 0.0f) {
         damped = 1;
         // Q_new = Q0 + kappa (Q - Q0), kappa = tau / (tau + dt), written for
         // delta Q = Q - Q_b: dQ_new = kappa dQ + (1 - kappa) (Q0 - Q_b)
-        const float tau = __fdividef(6.2831853071795864769f * sqrt_fast(rd * rd * rd), R);
-        const float itd = __fdividef(1.0f, tau + dt);
-        const float kap = tau * itd, omk = dt * itd;
+        const float tau = __fdividef(__fmul_rn(6.2831853071795864769f, sqrt_fast(__fmul_rn(__fmul_rn(rd, rd), rd))), R);
+        const float itd = __fdividef(1.0f, __fadd_rn(tau, dt));
+        const float kap = __fmul_rn(tau, itd), omk = __fmul_rn(dt, itd);
         Bg32 bgn = bg32_at(pc, xq, y);
         if (exact) bgn = bg32_poly<P>(bgOwn, c32t[P].eye[q], c32t[P].eye[r], bgn.c2);
         const float d0 = sU[(0 * M + n) * 32 + lane];
         const float d1 = sU[(1 * M + n) * 32 + lane], d2 = sU[(2 * M + n) * 32 + lane];
-        const float sg = bgn.sig + d0;
+        const float sg = __fadd_rn(bgn.sig, d0);
         const float isg = __fdividef(1.0f, sg);
-        const float dvx = (d1 - bgn.vx * d0) * isg;
-        const float dvy = (d2 - bgn.vy * d0) * isg;
-        const float ds2 = fmaf(kap, d0, omk * sDb[(0 * M + n) * 32 + lc]);
-        const float dvx2 = fmaf(kap, dvx, omk * sDb[(1 * M + n) * 32 + lc]);
-        const float dvy2 = fmaf(kap, dvy, omk * sDb[(2 * M + n) * 32 + lc]);
-        const float sg2 = bgn.sig + ds2;
+        const float dvx = __fmul_rn(fmaf(-bgn.vx, d0, d1), isg);
+        const float dvy = __fmul_rn(fmaf(-bgn.vy, d0, d2), isg);
+        const float ds2 = fmaf(kap, d0, __fmul_rn(omk, sDb[(0 * M + n) * 32 + lc]));
+        const float dvx2 = fmaf(kap, dvx, __fmul_rn(omk, sDb[(1 * M + n) * 32 + lc]));
+        const float dvy2 = fmaf(kap, dvy, __fmul_rn(omk, sDb[(2 * M + n) * 32 + lc]));
+        const float sg2 = __fadd_rn(bgn.sig, ds2);
         sU[(0 * M + n) * 32 + lane] = ds2;
-        sU[(1 * M + n) * 32 + lane] = fmaf(ds2, bgn.vx, sg2 * dvx2);
-        sU[(2 * M + n) * 32 + lane] = fmaf(ds2, bgn.vy, sg2 * dvy2);
+        sU[(1 * M + n) * 32 + lane] = fmaf(ds2, bgn.vx, __fmul_rn(sg2, dvx2));
+        sU[(2 * M + n) * 32 + lane] = fmaf(ds2, bgn.vy, __fmul_rn(sg2, dvy2));
       }
     }
     if (damped) sFlag[lane] = 1;
@@ -1005,6 +1007,11 @@ static cudaError_t launch_stage32_kind(const StageArgs32& a, cudaStream_t s) {
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_stage32<P, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
+    // the whole unified L1 as shared memory: the occupancy the kernel is
+    // built for, not the carveout the driver would pick for it
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage32<P, LAST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     configured = true;
   }
