@@ -85,7 +85,7 @@ __device__ __forceinline__ void batch_torque_tile(const BatchLaunch32& L, int k,
   }
 }
 
-__global__ void __launch_bounds__(128, 8) k_batch_torque32(const __grid_constant__ BatchLaunch32 L) {
+__global__ void __launch_bounds__(128, 6) k_batch_torque32(const __grid_constant__ BatchLaunch32 L) {
   const int w = threadIdx.x >> 5;
   const int item = blockIdx.x * 4 + w;  // warp-uniform
   if (item >= L.nitems) return;

@@ -948,14 +948,31 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
     F2 C[m];  // column sums sum_q f_qr
 #pragma unroll
     for (int r = 0; r < m; r++) C[r] = F2{0.0f, 0.0f};
-    // one node row q per iteration (rolled: the float-float body is long)
+    // one node row q per iteration (rolled: the float-float body is long);
+    // the next row's values are loaded while this row computes
+    float nh[m], nl[m], nd[m];
+#pragma unroll
+    for (int r = 0; r < m; r++) {
+      nh[r] = sbh[r * 32];
+      nl[r] = sbl[r * 32];
+      nd[r] = sD[r * 32];
+    }
 #pragma unroll 1
     for (int q = 0; q < m; q++) {
-      float sh[m], sl[m];
+      float sh[m], sl[m], dd[m];
 #pragma unroll
       for (int r = 0; r < m; r++) {
-        sh[r] = sbh[(q * m + r) * 32];
-        sl[r] = sbl[(q * m + r) * 32];
+        sh[r] = nh[r];
+        sl[r] = nl[r];
+        dd[r] = nd[r];
+      }
+      if (q + 1 < m) {
+#pragma unroll
+        for (int r = 0; r < m; r++) {
+          nh[r] = sbh[((q + 1) * m + r) * 32];
+          nl[r] = sbl[((q + 1) * m + r) * 32];
+          nd[r] = sD[((q + 1) * m + r) * 32];
+        }
       }
       const F2 px = f2_add(ox, f2_mul(hdx, F2{c32t[P].xi[q], c32t[P].xil[q]}));
       const F2 px2 = f2_mul_u(px, px);
@@ -963,7 +980,7 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
 #pragma unroll
       for (int r = 0; r < m; r++) {
         const int n = q * m + r;
-        const F2 ds{sD[n * 32], 0.0f};
+        const F2 ds{dd[r], 0.0f};
         // w_n (Sigma_b + delta Sigma) / (d^2 + eps^2)^{3/2}
         const F2 mass = f2_mul_u(f2_add_u(F2{sh[r], sl[r]}, ds), F2{c32t[P].w2h[n], c32t[P].w2l[n]});
         const F2 f = f2_mul_u(mass, f2_rsqrt3_u(f2_add_u(px2, pye[r])));
@@ -991,7 +1008,7 @@ __device__ __forceinline__ void torque32_tile(const float* D, const float* SigbN
 
 // four tiles (warps) per CTA
 template <int P>
-__global__ void __launch_bounds__(128, 8) k_torque32(const float* D, const float* SigbN, const DevState* ts,
+__global__ void __launch_bounds__(128, 6) k_torque32(const float* D, const float* SigbN, const DevState* ts,
                                                    double* part, const Mesh ms, const Prec32 pc) {
   pdl_wait();
   pdl_trigger();
