@@ -383,3 +383,35 @@ def test_delta_upload_matches_the_fp64_upload():
         with pytest.raises(dg.DgError) as e:
             f64.fetch_delta()
         assert e.value.code == dg.DG_ERR_UNSUPPORTED
+
+
+def test_delta_exchange_is_the_node_values():
+    """dg_fetch_delta returns delta = u - u_b as its values at the m x m
+    Gauss-Legendre nodes of each element (index q*m + r), the documented
+    exchange format of the precision form: the fetched FP64 modes minus the
+    noise-free background (the oracle's projection), mapped to the nodes with
+    the basis values sqrt(2a+1) P_a(xi_q) sqrt(2b+1) P_b(xi_r), give the same
+    numbers to the FP32 rounding of delta."""
+    from numpy.polynomial import legendre
+    p = 3
+    m = p + 1
+    cfg = inputs.disc_planet(40, p)
+    bg = {k: (dict(v) if isinstance(v, dict) else v) for k, v in cfg.items()}
+    bg["disc"]["noise_amp"] = 0.0
+    ob = oracle.Oracle(bg)
+    try:
+        ub = ob.fetch()
+    finally:
+        ob.close()
+    with dg.Disc(prec_cfg(cfg)) as g:
+        g.step(3)
+        u = g.fetch()
+        d = g.fetch_delta()
+    xi, _ = legendre.leggauss(m)
+    phi = np.array([[np.sqrt(2 * a + 1) * legendre.legval(x, [0] * a + [1]) for a in range(m)] for x in xi])
+    V = np.einsum("qa,rb->qrab", phi, phi).reshape(m * m, m * m)
+    dn = np.einsum("nk,vkji->vnji", V, u - ub)
+    for v in range(3):
+        scale = np.abs(dn[v]).max()
+        # FP32 rounding of delta (2^-24 of a value) and the FP64 rounding of u_b
+        assert np.abs(d[v] - dn[v]).max() <= 2e-7 * scale + 1e-13 * np.abs(u[v]).max(), v
