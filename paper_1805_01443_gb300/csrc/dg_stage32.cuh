@@ -232,14 +232,21 @@ __device__ __noinline__ Bg32 bg32_poly(const float* bm, const float* fa, const f
 template <int P>
 struct Smem32 {
   static constexpr int m = P + 1, M = m * m;
-  // nodal values [3][M][32]; the pointwise terms fx[3] 2/dx, fy[3] 2/dy, src[2]
-  // [8][M][32] overwrite them in place (planes 0-2 alias U: each node's
-  // values are read and replaced by the one thread that owns the node)
+  // nodal values [3][M][32]; the pointwise terms of the momentum rows fx1,
+  // fx2 (times 2/dx), fy1, fy2 (times 2/dy) and the sources src1, src2,
+  // [6][M][32], overwrite them in place (planes 0-2 alias U: each node's
+  // values are read and replaced by the one thread that owns the node).  The
+  // density's fluxes are the momentum perturbations themselves, which its
+  // thread reads from the state in global memory, so they need no plane.
   static constexpr int U = 0;
   static constexpr int F = 0;
+  static constexpr int PFX = 0;                    // planes of fx_v, fy_v, src_v for v = 1, 2: PFX + v - 1, ...
+  static constexpr int PFY = 2;
+  static constexpr int PSRC = 4;
   static constexpr int YT = F + 3 * M * 32;        // own y traces [2][3][m][32]: 0 top, 1 bottom (in planes 3..)
   static constexpr int XL = YT + 2 * 3 * m * 32;   // left x traces [3][m][33], slot e (in planes 3..)
-  static constexpr int XR = F + 8 * M * 32;        // right x traces [3][m][33], slot e+1
+  static constexpr int XR0 = F + 6 * M * 32;
+  static constexpr int XR = XL + 3 * m * 33 > XR0 ? XL + 3 * m * 33 : XR0;  // right x traces [3][m][33], slot e+1
   static constexpr int YN = XR + 3 * m * 33;       // neighbour traces [2][3][m][32]: 0 below's top, 1 above's bottom
   // face fluxes (times 1/dx, 1/dy) overwrite the traces they are formed from
   // (each face point's traces are read and replaced by the one thread that
@@ -251,7 +258,7 @@ struct Smem32 {
   static constexpr int TOTAL = FLAGS + 32;
   static constexpr int ND = 8;                     // 8-byte words: offsets, dt, mbarrier
   static constexpr size_t BYTES = (size_t)ND * sizeof(double) + (size_t)TOTAL * sizeof(float);
-  static_assert(XL + 3 * m * 33 <= F + 8 * M * 32, "traces exceed the pointwise planes");
+  static_assert(F + 6 * M * 32 <= XR, "damping offsets (planes 3-5) overlap the x traces");
 };
 
 // exact int -> float for 0 <= x < 2^23 on the integer and FP32 pipes (this
@@ -348,10 +355,10 @@ __device__ __forceinline__ void ff_offset(float k, const float* x0p, const float
   lo = r.l;
 }
 
-// minimum resident CTAs per SM asked of the register allocator (96
-// registers and 32.0 KB of shared memory at P4 fit seven)
+// minimum resident CTAs per SM asked of the register allocator (80
+// registers and 25.6 KB of shared memory at P4 fit eight)
 #ifndef DG_STAGE32_MIN_CTAS
-#define DG_STAGE32_MIN_CTAS 7
+#define DG_STAGE32_MIN_CTAS 8
 #endif
 
 
@@ -666,16 +673,16 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
         src1 = f2(n2(f), pdx, src1);
         src2 = f2(n2(f), pdy, src2);
       }
+      // the momentum rows' terms in planes 0-5 (fx1, fx2, fy1, fy2, src1, src2)
       const float2 s2x = d2(pc.s2x), s2y = d2(pc.s2y);
-      const float2 o2[8] = {m2(fx[0], s2x), m2(fx[1], s2x), m2(fx[2], s2x), m2(fy[0], s2y), m2(fy[1], s2y),
-                            m2(fy[2], s2y), src1, src2};
+      const float2 o2[6] = {m2(fx[1], s2x), m2(fx[2], s2x), m2(fy[1], s2y), m2(fy[2], s2y), src1, src2};
       float* o0 = sFl + n0 * 32 + lane;
 #pragma unroll
-      for (int t = 0; t < 8; t++) o0[t * M * 32] = o2[t].x;
+      for (int t = 0; t < 6; t++) o0[t * M * 32] = o2[t].x;
       if (two) {
         float* o1 = sFl + n1 * 32 + lane;
 #pragma unroll
-        for (int t = 0; t < 8; t++) o1[t * M * 32] = o2[t].y;
+        for (int t = 0; t < 6; t++) o1[t * M * 32] = o2[t].y;
       }
     }
   }
@@ -687,23 +694,34 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   // (2k, 2k+1) along x are the lanes of packed FMAs: the x sums take the
   // pair's two table rows against one value, the y sums one table entry
   // against the pair's two values; each lane keeps its scalar order.
+  // The density row's fluxes are the momentum perturbations (times 2/dx,
+  // 2/dy), read from the state in global memory (the tile loaded in P1, at
+  // hand in the caches); the momentum rows read their terms from planes 0-5.
   constexpr int MP = (m + 1) / 2;  // node pairs along x (the pair past an odd m has a dead lane)
   float2 LP[MP][m];                // LP[k][r] = (L(2k, r), L(2k+1, r))
   {
+    const int pfx = S::PFX + v - 1, pfy = S::PFY + v - 1, psrc = S::PSRC + v - 1;
+    const float* gmx = Dcur + tile * NVM * 32 + 1 * M * 32 + lc;  // delta m_x, delta m_y of this element
+    const float* gmy = gmx + M * 32;
 #pragma unroll
     for (int k = 0; k < MP; k++)
 #pragma unroll
       for (int r = 0; r < m; r++) {
         const int q0 = 2 * k, q1 = 2 * k + 1;
-        LP[k][r] = make_float2(v > 0 ? sFl[((5 + v) * M + q0 * m + r) * 32 + lane] : 0.0f,
-                               (v > 0 && q1 < m) ? sFl[((5 + v) * M + q1 * m + r) * 32 + lane] : 0.0f);
+        LP[k][r] = make_float2(v > 0 ? sFl[(psrc * M + q0 * m + r) * 32 + lane] : 0.0f,
+                               (v > 0 && q1 < m) ? sFl[(psrc * M + q1 * m + r) * 32 + lane] : 0.0f);
       }
     // x: one node row r at a time, its m fluxes and its two face fluxes
 #pragma unroll
     for (int r = 0; r < m; r++) {
       float X[m];
+      if (v > 0) {
 #pragma unroll
-      for (int q2 = 0; q2 < m; q2++) X[q2] = sFl[(v * M + q2 * m + r) * 32 + lane];
+        for (int q2 = 0; q2 < m; q2++) X[q2] = sFl[(pfx * M + q2 * m + r) * 32 + lane];
+      } else {
+#pragma unroll
+        for (int q2 = 0; q2 < m; q2++) X[q2] = __fmul_rn(pc.s2x, gmx[(q2 * m + r) * 32]);
+      }
       const float hl = sFX[(v * m + r) * 33 + lane], hr = sFX[(v * m + r) * 33 + lane + 1];
 #pragma unroll
       for (int k = 0; k < MP; k++) {
@@ -720,10 +738,17 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
     for (int k = 0; k < MP; k++) {
       const int q0 = 2 * k, q1 = 2 * k + 1;
       float2 Y[m];
+      if (v > 0) {
 #pragma unroll
-      for (int r2 = 0; r2 < m; r2++)
-        Y[r2] = make_float2(sFl[((3 + v) * M + q0 * m + r2) * 32 + lane],
-                            q1 < m ? sFl[((3 + v) * M + q1 * m + r2) * 32 + lane] : 0.0f);
+        for (int r2 = 0; r2 < m; r2++)
+          Y[r2] = make_float2(sFl[(pfy * M + q0 * m + r2) * 32 + lane],
+                              q1 < m ? sFl[(pfy * M + q1 * m + r2) * 32 + lane] : 0.0f);
+      } else {
+#pragma unroll
+        for (int r2 = 0; r2 < m; r2++)
+          Y[r2] = make_float2(__fmul_rn(pc.s2y, gmy[(q0 * m + r2) * 32]),
+                              q1 < m ? __fmul_rn(pc.s2y, gmy[(q1 * m + r2) * 32]) : 0.0f);
+      }
       const float2 hb = make_float2(sFY[((0 * 3 + v) * m + q0) * 32 + lane],
                                     q1 < m ? sFY[((0 * 3 + v) * m + q1) * 32 + lane] : 0.0f);
       const float2 ht = make_float2(sFY[((1 * 3 + v) * m + q0) * 32 + lane],
@@ -777,7 +802,7 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
     // into planes 3-5 of the pointwise terms, dead from here on, while the
     // nodal values of the new state are stored in planes 0-2
     float* sDb = sm + S::F + 3 * M * 32;
-    static_assert(3 * M * 32 <= 5 * M * 32, "damping offsets exceed the dead pointwise planes");
+    static_assert(S::F + 6 * M * 32 <= S::XR, "damping offsets exceed the dead pointwise planes 3-5");
     fence_proxy_async_smem();
     __syncthreads();  // every read of the pointwise terms and face fluxes by P3 is done
     if (tid == 0) {
