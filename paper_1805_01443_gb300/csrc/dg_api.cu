@@ -1581,7 +1581,7 @@ int dg_set_indicator(dg_handle* h, const dg_mlp* net, float threshold) {
   std::vector<unsigned char> w(mlp_pack_bytes(h->nv, h->M));
   mlp_pack(p.data(), h->nv, h->M, w.data());
   h->ind_work = (w.size() + 255) / 256 * 256;
-  if (!h->ind_w) CU(h, cudaMalloc((void**)&h->ind_w, h->ind_work + mlp_work_bytes(h->dm, h->nv)));
+  if (!h->ind_w) CU(h, cudaMalloc((void**)&h->ind_w, h->ind_work + mlp_work_bytes(h->dm, h->nv, h->M)));
   CU(h, cudaMemcpy(h->ind_w, w.data(), w.size(), cudaMemcpyHostToDevice));
   h->ind_thr = threshold;
   return DG_OK;

@@ -238,11 +238,12 @@ cudaError_t launch_features(const double* U, const double* GL, const double* GR,
                             cudaStream_t s);
 // flags (logit > threshold) and optionally logits of every element, on the
 // tensor cores; wpack holds the weights in the layout mlp_pack writes, work
-// is scratch of mlp_work_bytes (per-element maxima of |c|)
+// is scratch of mlp_work_bytes (per-element maxima of |c| and the
+// coefficients as BF16 pairs)
 cudaError_t launch_mlp_flags(const double* U, const double* GL, const double* GR, const double* GB,
                              const double* GT, const Mesh& ms, int p, int nv, const void* wpack, void* work,
                              float threshold, DevState* ts, unsigned char* flags, float* logits, cudaStream_t s);
-size_t mlp_work_bytes(const Mesh& ms, int nv);
+size_t mlp_work_bytes(const Mesh& ms, int nv, int M);
 // host: the flat FP32 parameters as the inference kernel's operands (W1 in
 // 64-input chunks and W2 as BF16 tensor-core tiles, then b1, b2, w3, b3 as the
 // FP32 values of their BF16 roundings)

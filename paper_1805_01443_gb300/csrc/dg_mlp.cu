@@ -8,9 +8,10 @@
 // largest |c_s[v][k]| over the stencil and the modes (1 when all vanish): the
 // reciprocal and the product in FP64, the product rounded once to FP32
 // (dg_features, the training inputs).  The inference kernel on the tensor
-// cores forms the same inputs in FP32 -- the coefficient truncated and the
-// reciprocal rounded to FP32, then their FP32 product -- within 2^-22
-// relative of those and without an FP64 instruction per input.
+// cores applies the scale after the first layer's sums instead: the
+// coefficients, truncated to FP32 and held as BF16 pairs hi + lo (2^-17
+// relative), enter the products unscaled, and the sums of each variable are
+// multiplied by 1 / S_v rounded to FP32 -- no FP64 instruction per input.
 //
 // Parameters (FP32 master copy, flat): W1 [64][nin], b1 [64], W2 [64][64],
 // b2 [64], w3 [64], b3.  The products use the weights rounded to BF16
@@ -223,28 +224,36 @@ __global__ void k_features(const FeatArgs a, const int* __restrict__ elems, int 
 
 // ---- fused inference on the tensor cores ----------------------------------
 // One CTA of 256 threads per 128 elements (4 mesh tiles); element row r is
-// the MMA row r.  Layer 1 runs over the inputs in chunks of 64: the 256
-// threads form the chunk's features (two threads per row, 32 inputs each),
-// split each into BF16 hi + lo (x = hi + lo to 2^-16 relative; the weights are
-// BF16 already, so the two MMAs reproduce the FP32 products), and one thread
-// issues the chunk's MMAs (M 128, N 64, K 16) into tensor memory.  The next
-// chunk's coefficients are loaded and scaled while those MMAs run; its
-// features are stored once they are done (one A buffer: the MMAs take a
-// small fraction of the feature time, and the smaller footprint lets three
-// CTAs share an SM).  The W1 chunks arrive by bulk copies into a two-stage
-// ring.  The epilogue reads the accumulators back (warp w: lanes 32 (w mod 4)..,
-// columns 32 (w / 4)..), adds the bias, applies GELU and splits the hidden
-// units into BF16 hi + lo, the A operand of layer 2 (64 -> 64, same scheme);
-// the last epilogue forms the logit.
-constexpr int TC_ROWS = 128, TC_KC = 64, TC_THREADS = 256;
-constexpr int TC_A = 0;                          // [hi, lo][128 x 64] BF16, 16 KB each
-constexpr int TC_B = TC_A + 2 * 16384;           // W1 chunks [2 stages][64 x 64] BF16
-constexpr int TC_W2 = TC_B + 2 * 8192;           // W2 [64 x 64] BF16
-constexpr int TC_PAR = TC_W2 + 8192;             // b1, b2, w3 [64] and b3, FP32 (1 KB); then partial logits
-constexpr int TC_BAR = TC_PAR + 1024;            // mbarriers: MMA done, (unused), W1 chunk [2], W2, layer 2
+// the MMA row r.  The scale 1/S_v of a feature depends only on the element's
+// stencil and the variable, so layer 1 is sum_v (1/S_v) (W1_v c_v): the
+// unscaled coefficients enter the MMAs and four accumulators in tensor memory
+// (one per variable, 64 columns each) are scaled and summed in the epilogue.
+// Each element's coefficients are then converted once, not once per stencil
+// they enter: a pre-pass (k_elem_prep) writes every coefficient as a BF16
+// pair hi + lo of its FP32 truncation (x = hi + lo to 2^-16 relative; the
+// weights are BF16 already, so the two MMAs reproduce the FP32 products) and
+// every element's max |c| per variable.  Layer 1 runs over the inputs in
+// chunks of 64, ordered by variable (each variable's stencil groups of 8
+// modes, padded to an even count so that an MMA's K = 16 never spans two
+// variables): the 256 threads gather the chunk's pairs (two threads per row,
+// 32 inputs each) into the hi and lo operands, and one thread issues the
+// chunk's MMAs (M 128, N 64, K 16) into the accumulator of their variable.
+// The next chunk's pairs are loaded while those MMAs run; they are stored
+// once the MMAs are done (one A buffer).  The W1 chunks arrive by bulk copies
+// into a two-stage ring.  The epilogue reads the four accumulators back
+// (warp w: lanes 32 (w mod 4).., columns 32 (w / 4)..), forms
+// sum_v (1/S_v) D1_v + b1, applies GELU and splits the hidden units into BF16
+// hi + lo, the A operand of layer 2 (64 -> 64, same scheme, its accumulator
+// in the first variable's columns); the last epilogue forms the logit.
+constexpr int TC_ROWS = 128, TC_KC = 64, TC_THREADS = 256, TC_WST = 4;
+constexpr int TC_A = 0;                          // [2 buffers][hi, lo][128 x 64] BF16, 16 KB each
+constexpr int TC_B = TC_A + 4 * 16384;           // W1 chunks [TC_WST stages][64 x 64] BF16
+constexpr int TC_W2 = TC_B + TC_WST * 8192;      // W2 [64 x 64] BF16
+constexpr int TC_PAR = TC_W2 + 8192;             // b1, b2, w3 [64] and b3, FP32 (1 KB)
+constexpr int TC_PZ = TC_PAR + 1024;             // partial logits [128] FP32
+constexpr int TC_BAR = TC_PZ + 512;              // mbarriers: A buffer [2], W1 stage [4], W2, layer 2
 constexpr int TC_TM = TC_BAR + 64;               // tensor-memory base address
-constexpr int TC_SMEM = TC_TM + 16;
-constexpr int TC_PZ = TC_A + 8192;               // partial logits [128] (A is dead by then)
+constexpr int TC_SMEM = TC_TM + 16;              // 105.6 KB: two CTAs per SM, 2 x 256 tensor-memory columns
 
 // byte offset of (row, k) in a K-major no-swizzle operand of `rows` rows
 __host__ __device__ inline int tc_off(int rows, int row, int k) {
@@ -301,6 +310,33 @@ __device__ __forceinline__ float d2f_rz(double x) {
   return __uint_as_float(f | (hi & 0x80000000u));
 }
 
+// GELU a Phi(a) of a pair, for the inference epilogues, in packed FP32x2
+// arithmetic.  Phi(a) = (1 + erf(a / sqrt 2)) / 2 with erf from Abramowitz &
+// Stegun 7.1.26 (Hastings' rational form, |error| <= 1.5e-7): for x >= 0,
+// erf x = 1 - q, q = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+// t = 1 / (1 + p x).  With x = |a| / sqrt 2 and h = a q / 2, a Phi(a) is
+// a - h for a >= 0 and h for a < 0.  exp(-a^2 / 2) = 2^(-a^2 log2(e) / 2) by
+// the hardware base-2 exponential (zero for |a| > 13).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float2 gelu_pair(float2 a) {
+  const float2 x = make_float2(fabsf(a.x) * 0.70710678118654752f, fabsf(a.y) * 0.70710678118654752f);
+  const float2 d = __ffma2_rn(x, make_float2(0.3275911f, 0.3275911f), make_float2(1.0f, 1.0f));
+  const float2 t = make_float2(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y));
+  float2 q = __ffma2_rn(t, make_float2(1.061405429f, 1.061405429f), make_float2(-1.453152027f, -1.453152027f));
+  q = __ffma2_rn(q, t, make_float2(1.421413741f, 1.421413741f));
+  q = __ffma2_rn(q, t, make_float2(-0.284496736f, -0.284496736f));
+  q = __ffma2_rn(q, t, make_float2(0.254829592f, 0.254829592f));
+  q = __fmul2_rn(q, t);
+  const float2 g = __fmul2_rn(__fmul2_rn(a, a), make_float2(-0.72134752044448170f, -0.72134752044448170f));
+  q = __fmul2_rn(q, make_float2(ex2_approx(g.x), ex2_approx(g.y)));
+  const float2 h = __fmul2_rn(__fmul2_rn(a, make_float2(0.5f, 0.5f)), q);
+  return make_float2(a.x >= 0.0f ? a.x - h.x : h.x, a.y >= 0.0f ? a.y - h.y : h.y);
+}
+
 // the mesh element standing for stencil element (ii, jj) of element (ci, cj):
 // false for a fixed ghost element (bc 1)
 __device__ __forceinline__ bool mesh_elem(const Mesh& ms, int ii, int jj, int ci, int cj, long long& tile,
@@ -321,37 +357,137 @@ __device__ __forceinline__ bool mesh_elem(const Mesh& ms, int ii, int jj, int ci
   return true;
 }
 
-// bits of max |c| over the modes of variable v of every element, [tile][v][32]
-template <int NV, int M>
-__global__ void k_elem_max(const double* __restrict__ U, unsigned long long* __restrict__ mx, long long n) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const double* p = U + (t >> 5) * (M * 32) + (t & 31);
-  unsigned long long m = 0ull;
-#pragma unroll
-  for (int k = 0; k < M; k++) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(p[k * 32]) & 0x7fffffffffffffffull;
-    m = b > m ? b : m;
-  }
-  mx[t] = m;
+// an FP64 coefficient as the BF16 pair of its FP32 truncation: hi in the low
+// half, lo = the BF16 rounding of x - hi in the high half
+__device__ __forceinline__ unsigned bf16_pair(double c) {
+  const float x = d2f_rz(c);
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  return (unsigned)__bfloat16_as_ushort(h) | ((unsigned)__bfloat16_as_ushort(l) << 16);
 }
 
-#ifdef DG_TC_SWAP_LBO
-#define TC_DESC(addr, lbo, sbo) tc_sdesc(addr, sbo, lbo)
-#else
-#define TC_DESC(addr, lbo, sbo) tc_sdesc(addr, lbo, sbo)
-#endif
+// input groups of 8 modes of one (variable, stencil element): per variable
+// 5 * GPB groups padded to an even count GPV (an MMA's K = 16 is two groups),
+// group G = v * GPV + s * GPB + g holding modes 8 g .. 8 g + 7 of variable v
+// of stencil element s (zero past M)
+__host__ __device__ constexpr int tc_gpb(int M) { return (M + 7) / 8; }
+__host__ __device__ constexpr int tc_gpv(int M) { return (5 * tc_gpb(M) + 1) / 2 * 2; }
+
+// The BF16 pairs of an element's variable as GPB groups of 8 words (zero past
+// mode M), so that a thread loads a group with two 16-byte loads:
+//   mesh elements   [tile][v][g][lane][8]   (32 elements of a tile row side by side)
+//   bc 1 ghosts     GL, GR: [j][v][g][8];  GB, GT: [x tile][v][g][lane][8]
+// Per element and variable the prep pass also writes the bits of max |c| over
+// the modes, [tile][v][32] (the order of non-negative doubles as integers).
+template <int M>
+__device__ __forceinline__ void put_groups(const double* __restrict__ src, int stride, unsigned* __restrict__ dst,
+                                           int gstride, unsigned long long* mx) {
+  constexpr int GPB = tc_gpb(M);
+  unsigned long long m = 0ull;
+#pragma unroll
+  for (int g = 0; g < GPB; g++) {
+    unsigned w[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      const int k = g * 8 + e;
+      double x = 0.0;
+      if (k < M) x = src[k * stride];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+      m = b > m ? b : m;
+      w[e] = bf16_pair(x);
+    }
+    uint4* q = reinterpret_cast<uint4*>(dst + (size_t)g * gstride);
+    q[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    q[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+  if (mx) *mx = m;
+}
+
+// one thread per (tile, variable, lane) of the state: t = (tile * NV + v) * 32 + lane
+template <int NV, int M>
+__global__ void k_elem_prep(const double* __restrict__ U, unsigned long long* __restrict__ mx,
+                            unsigned* __restrict__ img, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  put_groups<M>(U + (size_t)(t >> 5) * (M * 32) + (t & 31), 32,
+                img + ((size_t)(t >> 5) * tc_gpb(M) * 32 + (t & 31)) * 8, 256, mx + t);
+}
+
+// the fixed ghost elements (bc 1): GL, GR ([j][v][k], ny * NV rows each), then
+// GB, GT ([x tile][v][k][32], ntx * NV * 32 columns each)
+template <int NV, int M>
+__global__ void k_ghost_prep(const double* __restrict__ GL, const double* __restrict__ GR,
+                             const double* __restrict__ GB, const double* __restrict__ GT, unsigned* __restrict__ gl,
+                             unsigned* __restrict__ gr, unsigned* __restrict__ gb, unsigned* __restrict__ gt, int ny,
+                             int ntx) {
+  constexpr int GPB = tc_gpb(M);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nside = (long long)ny * NV, ntop = (long long)ntx * NV * 32;
+  if (t < 2 * nside) {
+    const bool r = t >= nside;
+    const long long q = t - (r ? nside : 0);  // j * NV + v
+    put_groups<M>((r ? GR : GL) + (size_t)q * M, 1, (r ? gr : gl) + (size_t)q * GPB * 8, 8, nullptr);
+  } else if (t < 2 * nside + 2 * ntop) {
+    const long long u = t - 2 * nside;
+    const bool top = u >= ntop;
+    const long long q = u - (top ? ntop : 0);  // (x tile * NV + v) * 32 + lane
+    put_groups<M>((top ? GT : GB) + (size_t)(q >> 5) * (M * 32) + (q & 31), 32,
+                  (top ? gt : gb) + ((size_t)(q >> 5) * GPB * 32 + (q & 31)) * 8, 256, nullptr);
+  }
+}
+
+// the inference's scratch: per-element maxima, then the BF16 pair images of
+// the state and of the four ghost arrays (byte offsets, 256-byte aligned)
+struct WorkPlan {
+  size_t img, gl, gr, gb, gt, total;
+};
+inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+inline WorkPlan work_plan(const Mesh& ms, int nv, int M) {
+  const size_t nt = (size_t)ms.ntx * ms.ny, grp = (size_t)nv * tc_gpb(M) * 8 * sizeof(unsigned);
+  WorkPlan w;
+  w.img = al256(nt * nv * 32 * sizeof(unsigned long long));
+  w.gl = w.img + al256(nt * 32 * grp);
+  w.gr = w.gl + al256((size_t)ms.ny * grp);
+  w.gb = w.gr + al256((size_t)ms.ny * grp);
+  w.gt = w.gb + al256((size_t)ms.ntx * 32 * grp);
+  w.total = w.gt + al256((size_t)ms.ntx * 32 * grp);
+  return w;
+}
+
+struct ImgArgs {
+  const unsigned long long* emax;
+  const unsigned *img, *gl, *gr, *gb, *gt;
+};
+
+// words of a group of 8 modes of stencil element s of this row (zeros for an
+// invalid row, a padding group or one past the last)
+template <int NV, int M>
+__device__ __forceinline__ void tc_load_group(const unsigned* const* sp, const int* sst, bool valid, int G,
+                                              uint4& w0, uint4& w1) {
+  constexpr int GPB = tc_gpb(M), GPV = tc_gpv(M);
+  const int v = G / GPV, r = G - v * GPV, s = r / GPB, g = r - s * GPB;
+  w0 = w1 = make_uint4(0u, 0u, 0u, 0u);
+  if (valid && v < NV && s < 5) {
+    const uint4* q = reinterpret_cast<const uint4*>(sp[s] + (v * GPB + g) * sst[s]);
+    w0 = __ldg(q);
+    w1 = __ldg(q + 1);
+  }
+}
+
+// a group's 8 pairs as the hi and lo operand rows (low halves, high halves)
+__device__ __forceinline__ void tc_unpair(const uint4& w0, const uint4& w1, uint4& hi, uint4& lo) {
+  hi = make_uint4(__byte_perm(w0.x, w0.y, 0x5410), __byte_perm(w0.z, w0.w, 0x5410), __byte_perm(w1.x, w1.y, 0x5410),
+                  __byte_perm(w1.z, w1.w, 0x5410));
+  lo = make_uint4(__byte_perm(w0.x, w0.y, 0x7632), __byte_perm(w0.z, w0.w, 0x7632), __byte_perm(w1.x, w1.y, 0x7632),
+                  __byte_perm(w1.z, w1.w, 0x7632));
+}
 
 template <int NV, int M>
-__global__ void __launch_bounds__(TC_THREADS, 3)
-    k_mlp_tc(const FeatArgs a, const unsigned char* __restrict__ wp, const unsigned long long* __restrict__ emax,
-             float threshold, DevState* ts, unsigned char* __restrict__ flags, float* __restrict__ logits,
-             long long ntiles) {
-  // inputs in groups of 8 modes of one (stencil element, variable), the modes
-  // of a variable padded to a multiple of 8 (zero weights): a group has one
-  // base address, one stride and one scale
-  constexpr int GPB = (M + 7) / 8, NG = 5 * NV * GPB, NC = (NG + 7) / 8, H2 = MLP_HIDDEN;
-  static_assert(MLP_HIDDEN == 64 && NV <= 4, "tile plan");
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_mlp_tc(const FeatArgs a, const ImgArgs im, const unsigned char* __restrict__ wp, float threshold,
+             DevState* ts, unsigned char* __restrict__ flags, float* __restrict__ logits, long long ntiles) {
+  constexpr int GPB = tc_gpb(M), GPV = tc_gpv(M), NGT = NV * GPV, NC = (NGT + 7) / 8, H2 = MLP_HIDDEN;
+  static_assert(MLP_HIDDEN == 64 && NV <= 4, "tile plan: NV accumulators of 64 columns in 256");
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TC_BAR);
   unsigned* s_taddr = reinterpret_cast<unsigned*>(sm + TC_TM);
@@ -359,16 +495,16 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
   const int tid = threadIdx.x, warp = tid >> 5, row = tid & (TC_ROWS - 1), half = tid >> 7;
   const unsigned idesc = tc_idesc_bf16(TC_ROWS, H2);
 
-  if (warp == 0) tmem_alloc(s_taddr, 128);  // D1: columns 0..63, D2: 64..127
+  if (warp == 0) tmem_alloc(s_taddr, 256);  // variable v's layer-1 sums: columns 64 v ..; layer 2: 0..63
   if (tid == 0) {
 #pragma unroll
-    for (int b = 0; b < 6; b++) mbar_init(&bar[b], 1);
+    for (int b = 0; b < 8; b++) mbar_init(&bar[b], 1);
     fence_proxy_async_smem();
-    mbar_expect_tx(&bar[4], 8192 + 1024);
-    bulk_g2s(sm + TC_W2, wp + (size_t)NC * 8192, 8192, &bar[4]);
-    bulk_g2s(sm + TC_PAR, wp + (size_t)NC * 8192 + 8192, 1024, &bar[4]);
+    mbar_expect_tx(&bar[6], 8192 + 1024);
+    bulk_g2s(sm + TC_W2, wp + (size_t)NC * 8192, 8192, &bar[6]);
+    bulk_g2s(sm + TC_PAR, wp + (size_t)NC * 8192 + 8192, 1024, &bar[6]);
 #pragma unroll
-    for (int c = 0; c < (NC < 2 ? NC : 2); c++) {
+    for (int c = 0; c < (NC < TC_WST ? NC : TC_WST); c++) {
       mbar_expect_tx(&bar[2 + c], 8192);
       bulk_g2s(sm + TC_B + c * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + c]);
     }
@@ -388,157 +524,166 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     i = (int)(tile - (long long)j * a.ms.ntx) * 32 + (row & 31);
     valid = i < a.ms.nx;
   }
-  // 1 / S_v over the stencil, from the per-element maxima (fixed ghost elements
-  // scanned here), rounded to FP32
+  // 1 / S_v over the stencil, from the per-element maxima (fixed ghost
+  // elements scanned here), rounded to FP32; and where each stencil
+  // element's pairs are: the first word of its group 0 of variable 0 and the
+  // words from one group to the next
   float R[NV];
+  const unsigned* sp[5];
+  int sst[5];
   {
     unsigned long long mx[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) mx[v] = 0ull;
-    if (valid) {
 #pragma unroll
-      for (int s = 0; s < 5; s++) {
-        const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
-        long long te;
-        int le;
-        if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
+    for (int s = 0; s < 5; s++) {
+      const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
+      long long te;
+      int le;
+      sp[s] = im.img;
+      sst[s] = 0;
+      if (!valid) continue;
+      if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
 #pragma unroll
-          for (int v = 0; v < NV; v++) {
-            const unsigned long long b = emax[((size_t)te * NV + v) * 32 + le];
+        for (int v = 0; v < NV; v++) {
+          const unsigned long long b = im.emax[((size_t)te * NV + v) * 32 + le];
+          mx[v] = b > mx[v] ? b : mx[v];
+        }
+        sp[s] = im.img + ((size_t)te * NV * GPB * 32 + le) * 8;
+        sst[s] = 256;
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+          for (int k = 0; k < M; k++) {
+            const unsigned long long b =
+                (unsigned long long)__double_as_longlong(coef<NV, M>(a, ii, jj, i, j, v, k)) & 0x7fffffffffffffffull;
             mx[v] = b > mx[v] ? b : mx[v];
           }
-        } else {
-#pragma unroll
-          for (int v = 0; v < NV; v++)
-            for (int k = 0; k < M; k++) {
-              const unsigned long long b =
-                  (unsigned long long)__double_as_longlong(coef<NV, M>(a, ii, jj, i, j, v, k)) & 0x7fffffffffffffffull;
-              mx[v] = b > mx[v] ? b : mx[v];
-            }
+        if (ii < 0 || ii >= a.ms.nx) {  // [j][v][g][8]
+          sp[s] = (ii < 0 ? im.gl : im.gr) + (size_t)j * NV * GPB * 8;
+          sst[s] = 8;
+        } else {  // [x tile][v][g][lane][8]
+          sp[s] = (jj < 0 ? im.gb : im.gt) + ((size_t)(i >> 5) * NV * GPB * 32 + (i & 31)) * 8;
+          sst[s] = 256;
         }
       }
     }
+    // S_v rounded to FP32, its FP32 reciprocal (1 where S_v vanishes or is
+    // below the FP32 normal range, whose coefficients truncate to zero)
 #pragma unroll
-    for (int v = 0; v < NV; v++) R[v] = mx[v] ? d2f_rn(1.0 / __longlong_as_double((long long)mx[v])) : 1.0f;
-  }
-
-  // base address and stride (elements) of each stencil element's coefficients
-  const double* sp[5];
-  int sst[5];
-#pragma unroll
-  for (int s = 0; s < 5; s++) {
-    const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
-    long long te;
-    int le;
-    sp[s] = a.U;
-    sst[s] = 0;
-    if (!valid) continue;
-    if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
-      sp[s] = a.U + (size_t)te * NV * M * 32 + le;
-      sst[s] = 32;
-    } else if (ii < 0 || ii >= a.ms.nx) {  // fixed ghost elements [j][v][k]
-      sp[s] = (ii < 0 ? a.GL : a.GR) + (size_t)j * NV * M;
-      sst[s] = 1;
-    } else {  // [tile][v][k][32]
-      sp[s] = (jj < 0 ? a.GB : a.GT) + (size_t)(i >> 5) * NV * M * 32 + (i & 31);
-      sst[s] = 32;
+    for (int v = 0; v < NV; v++) {
+      const float m = d2f_rn(__longlong_as_double((long long)mx[v]));
+      R[v] = m >= 1.17549435e-38f ? __frcp_rn(m) : 1.0f;
     }
   }
 
   // ---- layer 1 over the input chunks ----
-  unsigned char* Ahi = sm + TC_A;
-  unsigned char* Alo = Ahi + 16384;
-  for (int c = 0; c < NC; c++) {
-    const int st = c & 1;
-    if (c >= 2 && tid == 0) {
-      // the MMAs of chunk c - 2, the last readers of this W1 stage, are done:
-      // every thread saw their commit before it wrote chunk c - 1
-      mbar_expect_tx(&bar[2 + st], 8192);
-      bulk_g2s(sm + TC_B + st * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + st]);
+  // this thread's four groups of chunk c, at K positions 8 kg(g): with an even
+  // GPB the groups c * 8 + 2 g + half (a group pair shares its variable and
+  // stencil element, so one code serves both halves); else c * 8 + 4 half + g,
+  // the branch on the warp-uniform half making every group index a constant
+  auto kg = [&](int g) { return GPB % 2 == 0 ? 2 * g + half : 4 * half + g; };
+  auto load4 = [&](int c, uint4* w) {
+    if constexpr (GPB % 2 == 0) {
+#pragma unroll
+      for (int g = 0; g < 4; g++) {
+        const int G0 = c * 8 + 2 * g, v = G0 / GPV, r = G0 - v * GPV, s = r / GPB, gg = r - s * GPB + half;
+        w[2 * g] = w[2 * g + 1] = make_uint4(0u, 0u, 0u, 0u);
+        if (valid && v < NV) {
+          const uint4* q = reinterpret_cast<const uint4*>(sp[s] + (v * GPB + gg) * sst[s]);
+          w[2 * g] = __ldg(q);
+          w[2 * g + 1] = __ldg(q + 1);
+        }
+      }
+    } else if (half == 0) {
+#pragma unroll
+      for (int g = 0; g < 4; g++) tc_load_group<NV, M>(sp, sst, valid, c * 8 + g, w[2 * g], w[2 * g + 1]);
+    } else {
+#pragma unroll
+      for (int g = 0; g < 4; g++) tc_load_group<NV, M>(sp, sst, valid, c * 8 + 4 + g, w[2 * g], w[2 * g + 1]);
     }
-#pragma unroll 1
-    for (int g = 0; g < 4; g += 2) {
-      // the two groups' 16 coefficients are loaded first (all in flight at
-      // once), then scaled and rounded
-      double cv[16];
-      float rv2[2];
+  };
+  uint4 cur[8];
+  load4(0, cur);
 #pragma unroll
-      for (int h8 = 0; h8 < 2; h8++) {
-        const int G = c * 8 + half * 4 + g + h8;
-        const int sv = G / GPB, kk0 = (G - sv * GPB) * 8, s = sv / NV, v = sv - s * NV;
-        const double* q = sp[0];
-        int qs = sst[0];
-#pragma unroll
-        for (int w = 1; w < 5; w++)
-          if (s == w) {
-            q = sp[w];
-            qs = sst[w];
-          }
-        float rv = R[0];
-#pragma unroll
-        for (int w = 1; w < NV; w++) rv = (v == w) ? R[w] : rv;
-        rv2[h8] = rv;
-        const bool on = valid && G < NG;
-        q += (size_t)(v * M + kk0) * qs;
-#pragma unroll
-        for (int e = 0; e < 8; e++) cv[h8 * 8 + e] = (on && kk0 + e < M) ? q[e * qs] : 0.0;
+  for (int c = 0; c < NC; c++) {
+    // the next chunk's pairs are in flight while this one is stored and multiplied
+    uint4 nxt[8];
+    if (c + 1 < NC) load4(c + 1, nxt);
+    unsigned char* Ahi = sm + TC_A + (c & 1) * 32768;
+    unsigned char* Alo = Ahi + 16384;
+    if (c >= 2) {
+      // the MMAs of chunk c - 2, the last readers of this A buffer and of W1
+      // stage (c + 2) mod 4, are done
+      ok &= mbar_wait(&bar[c & 1], ((c - 2) >> 1) & 1);
+      if (tid == 0 && c + 2 < NC) {
+        const int st = (c + 2) & 3;
+        mbar_expect_tx(&bar[2 + st], 8192);
+        bulk_g2s(sm + TC_B + st * 8192, wp + (size_t)(c + 2) * 8192, 8192, &bar[2 + st]);
       }
-      // each coefficient truncated to FP32 on the integer pipe, then scaled
-      // in FP32: within 2^-22 of the features of the FP64 product
-      // (dg_features), and no FP64 instruction per input
-      float x[16];
+    }
 #pragma unroll
-      for (int t = 0; t < 16; t++) x[t] = d2f_rz(cv[t]) * rv2[t >> 3];
-      // the previous chunk's MMAs have read the A buffer
-      if (c > 0 && g == 0) ok &= mbar_wait(&bar[0], (c - 1) & 1);
-#pragma unroll
-      for (int h8 = 0; h8 < 2; h8++) {
-        uint4 hi, lo;
-        split8(x + 8 * h8, hi, lo);
-        const int off = tc_off(TC_ROWS, row, half * 32 + (g + h8) * 8);
-        *reinterpret_cast<uint4*>(Ahi + off) = hi;
-        *reinterpret_cast<uint4*>(Alo + off) = lo;
-      }
+    for (int g = 0; g < 4; g++) {
+      uint4 hi, lo;
+      tc_unpair(cur[2 * g], cur[2 * g + 1], hi, lo);
+      const int off = tc_off(TC_ROWS, row, kg(g) * 8);
+      *reinterpret_cast<uint4*>(Ahi + off) = hi;
+      *reinterpret_cast<uint4*>(Alo + off) = lo;
     }
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
-      ok &= mbar_wait(&bar[2 + st], (c >> 1) & 1);
+      ok &= mbar_wait(&bar[2 + (c & 3)], (c >> 2) & 1);
       tc_fence_after();
-      const unsigned aH = smem_addr(Ahi), aL = smem_addr(Alo), bB = smem_addr(sm + TC_B + st * 8192);
+      const unsigned aH = smem_addr(Ahi), aL = smem_addr(Alo), bB = smem_addr(sm + TC_B + (c & 3) * 8192);
 #pragma unroll
       for (int ks = 0; ks < TC_KC / 16; ks++) {
-        const uint64_t db = TC_DESC(bB + ks * 2048, 1024, 128);
-        tc_mma(taddr, TC_DESC(aH + ks * 4096, 2048, 128), db, idesc, (c > 0 || ks > 0) ? 1 : 0);
-        tc_mma(taddr, TC_DESC(aL + ks * 4096, 2048, 128), db, idesc, 1);
+        // K step ks: groups c * 8 + 2 ks and + 1, both of variable v; its
+        // first K step of a variable starts that variable's sums
+        const int G0 = c * 8 + 2 * ks, v = G0 / GPV;
+        if (G0 < NGT) {
+          const unsigned d = taddr + 64 * v;
+          const uint64_t db = tc_sdesc(bB + ks * 2048, 1024, 128);
+          tc_mma(d, tc_sdesc(aH + ks * 4096, 2048, 128), db, idesc, G0 > v * GPV ? 1 : 0);
+          tc_mma(d, tc_sdesc(aL + ks * 4096, 2048, 128), db, idesc, 1);
+        }
       }
-      tc_commit(&bar[0]);
+      tc_commit(&bar[c & 1]);
+    }
+    if (c + 1 < NC) {
+#pragma unroll
+      for (int q = 0; q < 8; q++) cur[q] = nxt[q];
     }
   }
-  // the last commit covers every earlier MMA
-  ok &= mbar_wait(&bar[0], (NC - 1) & 1);
-  ok &= mbar_wait(&bar[4], 0);
+  // the commits of the last two chunks (each covers every earlier MMA)
+  ok &= mbar_wait(&bar[(NC - 1) & 1], ((NC - 1) >> 1) & 1);
+  if (NC >= 2) ok &= mbar_wait(&bar[NC & 1], ((NC - 2) >> 1) & 1);
+  ok &= mbar_wait(&bar[6], 0);
   tc_fence_after();
   const float* par = reinterpret_cast<const float*>(sm + TC_PAR);  // b1, b2, w3, b3
   const int quarter = warp & 3, ch = warp >> 2;
   const unsigned tl = taddr + ((unsigned)(quarter * 32) << 16);
-  float acc[32];
-  // ---- epilogue 1: h1 = GELU(D1 + b1) as the layer-2 A operand (the A buffer) ----
-  tmem_ld32(tl + ch * 32, acc);
-  {
-    unsigned char* Hhi = sm + TC_A;
-    unsigned char* Hlo = Hhi + 16384;
+  // ---- epilogue 1: h1 = GELU(sum_v (1 / S_v) D1_v + b1) as the layer-2 A operand ----
+  // (8 hidden units at a time: the loop is not unrolled, to keep the code small)
+#pragma unroll 1
+  for (int g = 0; g < 4; g++) {
+    const int col = ch * 32 + g * 8;
+    float d[32], x[8];
+    tmem_ld8x4(tl + col, tl + 64 + col, tl + (NV > 2 ? 128 : 0) + col, tl + (NV > 3 ? 192 : 0) + col, d);
 #pragma unroll
-    for (int g = 0; g < 4; g++) {
-      float x[8];
+    for (int e = 0; e < 8; e += 2) {
+      float2 h = make_float2(par[col + e], par[col + e + 1]);
 #pragma unroll
-      for (int e = 0; e < 8; e++) x[e] = gelu(acc[g * 8 + e] + par[ch * 32 + g * 8 + e]);
-      uint4 hi, lo;
-      split8(x, hi, lo);
-      const int off = tc_off(TC_ROWS, row, ch * 32 + g * 8);
-      *reinterpret_cast<uint4*>(Hhi + off) = hi;
-      *reinterpret_cast<uint4*>(Hlo + off) = lo;
+      for (int v = 0; v < NV; v++) h = __ffma2_rn(make_float2(R[v], R[v]), make_float2(d[8 * v + e], d[8 * v + e + 1]), h);
+      h = gelu_pair(h);
+      x[e] = h.x;
+      x[e + 1] = h.y;
     }
+    uint4 hi, lo;
+    split8(x, hi, lo);
+    const int off = tc_off(TC_ROWS, row, col);
+    *reinterpret_cast<uint4*>(sm + TC_A + off) = hi;
+    *reinterpret_cast<uint4*>(sm + TC_A + 16384 + off) = lo;
   }
   fence_proxy_async_smem();
   tc_fence_before();
@@ -548,19 +693,28 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     const unsigned aH = smem_addr(sm + TC_A), aL = aH + 16384, bW = smem_addr(sm + TC_W2);
 #pragma unroll
     for (int ks = 0; ks < H2 / 16; ks++) {
-      const uint64_t db = TC_DESC(bW + ks * 2048, 1024, 128);
-      tc_mma(taddr + H2, TC_DESC(aH + ks * 4096, 2048, 128), db, idesc, ks > 0 ? 1 : 0);
-      tc_mma(taddr + H2, TC_DESC(aL + ks * 4096, 2048, 128), db, idesc, 1);
+      const uint64_t db = tc_sdesc(bW + ks * 2048, 1024, 128);
+      tc_mma(taddr, tc_sdesc(aH + ks * 4096, 2048, 128), db, idesc, ks > 0 ? 1 : 0);
+      tc_mma(taddr, tc_sdesc(aL + ks * 4096, 2048, 128), db, idesc, 1);
     }
-    tc_commit(&bar[5]);
+    tc_commit(&bar[7]);
   }
-  ok &= mbar_wait(&bar[5], 0);
+  ok &= mbar_wait(&bar[7], 0);
   tc_fence_after();
   // ---- epilogue 2: z = w3 . GELU(D2 + b2) + b3 ----
-  tmem_ld32(tl + H2 + ch * 32, acc);
-  float zp = 0.0f;
+  float2 zp2 = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+  for (int g = 0; g < 4; g++) {
+    const int col = ch * 32 + g * 8;
+    float d[8];
+    tmem_ld8(tl + col, d);
 #pragma unroll
-  for (int e = 0; e < 32; e++) zp = fmaf(gelu(acc[e] + par[H2 + ch * 32 + e]), par[2 * H2 + ch * 32 + e], zp);
+    for (int e = 0; e < 8; e += 2) {
+      const float2 h = gelu_pair(__fadd2_rn(make_float2(d[e], d[e + 1]), make_float2(par[H2 + col + e], par[H2 + col + e + 1])));
+      zp2 = __ffma2_rn(h, make_float2(par[2 * H2 + col + e], par[2 * H2 + col + e + 1]), zp2);
+    }
+  }
+  const float zp = zp2.x + zp2.y;
   float* szp = reinterpret_cast<float*>(sm + TC_PZ);
   if (ch == 1) szp[row] = zp;
   tc_fence_before();
@@ -573,26 +727,38 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
   }
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(taddr, 128);
+    tmem_dealloc(taddr, 256);
   }
   if (!ok) atomicOr(&ts->pending, 2);
 }
 
 template <int NV, int M>
-cudaError_t launch_flags_t(const FeatArgs& fa, const void* wpack, unsigned long long* emax, float threshold,
-                           DevState* ts, unsigned char* flags, float* logits, cudaStream_t s) {
+cudaError_t launch_flags_t(const FeatArgs& fa, const void* wpack, void* work, float threshold, DevState* ts,
+                           unsigned char* flags, float* logits, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<NV, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const long long ntiles = (long long)fa.ms.ntx * fa.ms.ny;
-  const long long nmax = ntiles * NV * 32;
-  k_elem_max<NV, M><<<blocks(nmax, 256), 256, 0, s>>>(fa.U, emax, nmax);
+  const Mesh& ms = fa.ms;
+  const WorkPlan wl = work_plan(ms, NV, M);
+  unsigned char* w = static_cast<unsigned char*>(work);
+  unsigned long long* emax = reinterpret_cast<unsigned long long*>(w);
+  unsigned* img = reinterpret_cast<unsigned*>(w + wl.img);
+  unsigned *gl = reinterpret_cast<unsigned*>(w + wl.gl), *gr = reinterpret_cast<unsigned*>(w + wl.gr);
+  unsigned *gb = reinterpret_cast<unsigned*>(w + wl.gb), *gt = reinterpret_cast<unsigned*>(w + wl.gt);
+  const long long ntiles = (long long)ms.ntx * ms.ny;
+  const long long n = ntiles * NV * 32;
+  k_elem_prep<NV, M><<<blocks(n, 128), 128, 0, s>>>(fa.U, emax, img, n);
+  if (ms.bc == 1) {
+    const long long ng = 2LL * ms.ny * NV + 2LL * ms.ntx * NV * 32;
+    k_ghost_prep<NV, M><<<blocks(ng, 128), 128, 0, s>>>(fa.GL, fa.GR, fa.GB, fa.GT, gl, gr, gb, gt, ms.ny, ms.ntx);
+  }
+  const ImgArgs im = {emax, img, gl, gr, gb, gt};
   const long long nblk = (ntiles + 3) / 4;
-  k_mlp_tc<NV, M><<<(unsigned)nblk, TC_THREADS, TC_SMEM, s>>>(
-      fa, static_cast<const unsigned char*>(wpack), emax, threshold, ts, flags, logits, ntiles);
+  k_mlp_tc<NV, M><<<(unsigned)nblk, TC_THREADS, TC_SMEM, s>>>(fa, im, static_cast<const unsigned char*>(wpack),
+                                                              threshold, ts, flags, logits, ntiles);
   return cudaGetLastError();
 }
 
@@ -649,17 +815,13 @@ cudaError_t launch_mlp_flags(const double* U, const double* GL, const double* GR
                              const double* GT, const Mesh& ms, int p, int nv, const void* wpack, void* work,
                              float threshold, DevState* ts, unsigned char* flags, float* logits, cudaStream_t s) {
   const FeatArgs fa = feat_args(U, GL, GR, GB, GT, ms);
-  unsigned long long* emax = static_cast<unsigned long long*>(work);
-#define CALL(a, b) launch_flags_t<a, b>(fa, wpack, emax, threshold, ts, flags, logits, s)
+#define CALL(a, b) launch_flags_t<a, b>(fa, wpack, work, threshold, ts, flags, logits, s)
   DG_MLP_DISPATCH(nv, p, CALL);
 #undef CALL
 }
 
-size_t mlp_pack_bytes(int nv, int M) {
-  const int ng = 5 * nv * ((M + 7) / 8);
-  return (size_t)((ng + 7) / 8) * 8192 + 8192 + 1024;
-}
-size_t mlp_work_bytes(const Mesh& ms, int nv) { return (size_t)ms.ntx * ms.ny * nv * 32 * sizeof(unsigned long long); }
+size_t mlp_pack_bytes(int nv, int M) { return (size_t)((nv * tc_gpv(M) + 7) / 8) * 8192 + 8192 + 1024; }
+size_t mlp_work_bytes(const Mesh& ms, int nv, int M) { return work_plan(ms, nv, M).total; }
 
 namespace {
 unsigned short bf16_bits(float f) {  // round to nearest even, as __float2bfloat16_rn
@@ -682,18 +844,19 @@ void put_bf16(unsigned char* base, int off, float f) {
 }  // namespace
 
 void mlp_pack(const float* prm, int nv, int M, unsigned char* out) {
-  const int nin = 5 * nv * M, gpb = (M + 7) / 8, ng = 5 * nv * gpb, nc = (ng + 7) / 8;
+  const int nin = 5 * nv * M, gpb = tc_gpb(M), gpv = tc_gpv(M), ng = nv * gpv, nc = (ng + 7) / 8;
   const Offs o = offs(nin);
   memset(out, 0, mlp_pack_bytes(nv, M));
-  // input k' = (sv * gpb + kk / 8) * 8 + kk % 8 of group sv = s * nv + v is
-  // input (s * nv + v) * M + kk of the network (zero for the padding kk >= M)
+  // input k' = G * 8 + e of group G = v * gpv + s * gpb + g is input
+  // (s * nv + v) * M + 8 g + e of the network (zero for the padding group
+  // s = 5 and the padding modes 8 g + e >= M)
   for (int c = 0; c < nc; c++)
     for (int kc = 0; kc < TC_KC; kc++) {
       const int kp = c * TC_KC + kc, G = kp / 8;
       if (G >= ng) continue;
-      const int sv = G / gpb, kk = (G - sv * gpb) * 8 + kp % 8;
-      if (kk >= M) continue;
-      const int in = sv * M + kk;
+      const int v = G / gpv, r = G - v * gpv, s = r / gpb, kk = (r - s * gpb) * 8 + kp % 8;
+      if (s >= 5 || kk >= M) continue;
+      const int in = (s * nv + v) * M + kk;
       for (int n = 0; n < H; n++) put_bf16(out + (size_t)c * 8192, tc_off(H, n, kc), prm[o.W1 + (size_t)n * nin + in]);
     }
   unsigned char* w2 = out + (size_t)nc * 8192;
