@@ -239,7 +239,7 @@ cudaError_t launch_features(const double* U, const double* GL, const double* GR,
 // flags (logit > threshold) and optionally logits of every element, on the
 // tensor cores; wpack holds the weights in the layout mlp_pack writes, work
 // is scratch of mlp_work_bytes (per-element maxima of |c| and the
-// coefficients as BF16 pairs)
+// coefficients as BF16 pairs, the stencil scales)
 cudaError_t launch_mlp_flags(const double* U, const double* GL, const double* GR, const double* GB,
                              const double* GT, const Mesh& ms, int p, int nv, const void* wpack, void* work,
                              float threshold, DevState* ts, unsigned char* flags, float* logits, cudaStream_t s);

@@ -238,13 +238,15 @@ __global__ void k_features(const FeatArgs a, const int* __restrict__ elems, int 
 // variables): the 256 threads gather the chunk's pairs (two threads per row,
 // 32 inputs each) into the hi and lo operands, and one thread issues the
 // chunk's MMAs (M 128, N 64, K 16) into the accumulator of their variable.
-// The next chunk's pairs are loaded while those MMAs run; they are stored
-// once the MMAs are done (one A buffer).  The W1 chunks arrive by bulk copies
-// into a two-stage ring.  The epilogue reads the four accumulators back
-// (warp w: lanes 32 (w mod 4).., columns 32 (w / 4)..), forms
-// sum_v (1/S_v) D1_v + b1, applies GELU and splits the hidden units into BF16
-// hi + lo, the A operand of layer 2 (64 -> 64, same scheme, its accumulator
-// in the first variable's columns); the last epilogue forms the logit.
+// The A operand is double-buffered: the next chunk's pairs are loaded while
+// this one is stored and its MMAs run.  The W1 chunks arrive by bulk copies
+// into a four-stage ring, two chunks ahead.  1/S_v of every element's stencil
+// comes from its own pass (k_stencil_scale).  The epilogue reads the four
+// accumulators back (warp w: lanes 32 (w mod 4).., columns 32 (w / 4)..),
+// forms sum_v (1/S_v) D1_v + b1, applies GELU and splits the hidden units into
+// BF16 hi + lo, the A operand of layer 2 (64 -> 64, same scheme, its
+// accumulator in the first variable's columns); the last epilogue forms the
+// logit.
 constexpr int TC_ROWS = 128, TC_KC = 64, TC_THREADS = 256, TC_WST = 4;
 constexpr int TC_A = 0;                          // [2 buffers][hi, lo][128 x 64] BF16, 16 KB each
 constexpr int TC_B = TC_A + 4 * 16384;           // W1 chunks [TC_WST stages][64 x 64] BF16
@@ -436,10 +438,58 @@ __global__ void k_ghost_prep(const double* __restrict__ GL, const double* __rest
   }
 }
 
-// the inference's scratch: per-element maxima, then the BF16 pair images of
-// the state and of the four ghost arrays (byte offsets, 256-byte aligned)
+// 1 / S_v of every element's stencil, FP32, [tile][lane] as 4 floats (the
+// fourth unused for 3 variables): S_v from the per-element maxima (the fixed
+// ghost elements of bc 1 scanned here) rounded to FP32, its FP32 reciprocal,
+// 1 where S_v vanishes or is below the FP32 normal range (its coefficients
+// truncate to zero)
+template <int NV, int M>
+__global__ void k_stencil_scale(const FeatArgs a, const unsigned long long* __restrict__ emax,
+                                float4* __restrict__ rs, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int tile = (int)(t >> 5);  // ntiles < 2^31
+  const int j = tile / a.ms.ntx, i = (tile - j * a.ms.ntx) * 32 + (int)(t & 31);
+  float R[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+  if (i < a.ms.nx) {
+    unsigned long long mx[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) mx[v] = 0ull;
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+      const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
+      long long te;
+      int le;
+      if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          const unsigned long long b = emax[((size_t)te * NV + v) * 32 + le];
+          mx[v] = b > mx[v] ? b : mx[v];
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; v++)
+          for (int k = 0; k < M; k++) {
+            const unsigned long long b =
+                (unsigned long long)__double_as_longlong(coef<NV, M>(a, ii, jj, i, j, v, k)) & 0x7fffffffffffffffull;
+            mx[v] = b > mx[v] ? b : mx[v];
+          }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const float m = d2f_rn(__longlong_as_double((long long)mx[v]));
+      R[v] = m >= 1.17549435e-38f ? __frcp_rn(m) : 1.0f;
+    }
+  }
+  rs[t] = make_float4(R[0], R[1], R[2], R[3]);
+}
+
+// the inference's scratch: per-element maxima, the BF16 pair images of
+// the state and of the four ghost arrays, the stencil scales (byte offsets,
+// 256-byte aligned)
 struct WorkPlan {
-  size_t img, gl, gr, gb, gt, total;
+  size_t img, gl, gr, gb, gt, rs, total;
 };
 inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 inline WorkPlan work_plan(const Mesh& ms, int nv, int M) {
@@ -450,12 +500,13 @@ inline WorkPlan work_plan(const Mesh& ms, int nv, int M) {
   w.gr = w.gl + al256((size_t)ms.ny * grp);
   w.gb = w.gr + al256((size_t)ms.ny * grp);
   w.gt = w.gb + al256((size_t)ms.ntx * 32 * grp);
-  w.total = w.gt + al256((size_t)ms.ntx * 32 * grp);
+  w.rs = w.gt + al256((size_t)ms.ntx * 32 * grp);
+  w.total = w.rs + al256(nt * 32 * sizeof(float4));
   return w;
 }
 
 struct ImgArgs {
-  const unsigned long long* emax;
+  const float4* rs;
   const unsigned *img, *gl, *gr, *gb, *gt;
 };
 
@@ -485,95 +536,51 @@ __device__ __forceinline__ void tc_unpair(const uint4& w0, const uint4& w1, uint
 template <int NV, int M>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     k_mlp_tc(const FeatArgs a, const ImgArgs im, const unsigned char* __restrict__ wp, float threshold,
-             DevState* ts, unsigned char* __restrict__ flags, float* __restrict__ logits, long long ntiles) {
+             DevState* ts, unsigned char* __restrict__ flags, float* __restrict__ logits, long long ntiles,
+             int ahead) {
   constexpr int GPB = tc_gpb(M), GPV = tc_gpv(M), NGT = NV * GPV, NC = (NGT + 7) / 8, H2 = MLP_HIDDEN;
   static_assert(MLP_HIDDEN == 64 && NV <= 4, "tile plan: NV accumulators of 64 columns in 256");
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TC_BAR);
   unsigned* s_taddr = reinterpret_cast<unsigned*>(sm + TC_TM);
-  if (ts->status != 0) return;
+  // this row's element and where its stencil's pairs are are found first,
+  // so that the first chunk's loads are in flight during the set-up; the
+  // status is read here too and decides only whether the CTA writes (a set
+  // status leaves every output as it was), so that no CTA waits for it
+  const int status = *(volatile const int*)&ts->status;
   const int tid = threadIdx.x, warp = tid >> 5, row = tid & (TC_ROWS - 1), half = tid >> 7;
   const unsigned idesc = tc_idesc_bf16(TC_ROWS, H2);
 
-  if (warp == 0) tmem_alloc(s_taddr, 256);  // variable v's layer-1 sums: columns 64 v ..; layer 2: 0..63
-  if (tid == 0) {
-#pragma unroll
-    for (int b = 0; b < 8; b++) mbar_init(&bar[b], 1);
-    fence_proxy_async_smem();
-    mbar_expect_tx(&bar[6], 8192 + 1024);
-    bulk_g2s(sm + TC_W2, wp + (size_t)NC * 8192, 8192, &bar[6]);
-    bulk_g2s(sm + TC_PAR, wp + (size_t)NC * 8192 + 8192, 1024, &bar[6]);
-#pragma unroll
-    for (int c = 0; c < (NC < TC_WST ? NC : TC_WST); c++) {
-      mbar_expect_tx(&bar[2 + c], 8192);
-      bulk_g2s(sm + TC_B + c * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + c]);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const unsigned taddr = *s_taddr;
-  bool ok = true;
-
   // this row's element and its stencil (s = 0 own, 1 left, 2 right, 3 below, 4 above)
-  const long long tile = (long long)blockIdx.x * 4 + (row >> 5);
+  const int tile = (int)blockIdx.x * 4 + (row >> 5);  // ntiles < 2^31
   int i = 0, j = 0;
   bool valid = false;
   if (tile < ntiles) {
-    j = (int)(tile / a.ms.ntx);
-    i = (int)(tile - (long long)j * a.ms.ntx) * 32 + (row & 31);
+    j = tile / a.ms.ntx;
+    i = (tile - j * a.ms.ntx) * 32 + (row & 31);
     valid = i < a.ms.nx;
   }
-  // 1 / S_v over the stencil, from the per-element maxima (fixed ghost
-  // elements scanned here), rounded to FP32; and where each stencil
-  // element's pairs are: the first word of its group 0 of variable 0 and the
-  // words from one group to the next
-  float R[NV];
+  // each stencil element's pairs: the first word of its group 0 of variable
+  // 0 and the words from one group to the next
   const unsigned* sp[5];
   int sst[5];
-  {
-    unsigned long long mx[NV];
 #pragma unroll
-    for (int v = 0; v < NV; v++) mx[v] = 0ull;
-#pragma unroll
-    for (int s = 0; s < 5; s++) {
-      const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
-      long long te;
-      int le;
-      sp[s] = im.img;
-      sst[s] = 0;
-      if (!valid) continue;
-      if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-          const unsigned long long b = im.emax[((size_t)te * NV + v) * 32 + le];
-          mx[v] = b > mx[v] ? b : mx[v];
-        }
-        sp[s] = im.img + ((size_t)te * NV * GPB * 32 + le) * 8;
-        sst[s] = 256;
-      } else {
-#pragma unroll
-        for (int v = 0; v < NV; v++)
-          for (int k = 0; k < M; k++) {
-            const unsigned long long b =
-                (unsigned long long)__double_as_longlong(coef<NV, M>(a, ii, jj, i, j, v, k)) & 0x7fffffffffffffffull;
-            mx[v] = b > mx[v] ? b : mx[v];
-          }
-        if (ii < 0 || ii >= a.ms.nx) {  // [j][v][g][8]
-          sp[s] = (ii < 0 ? im.gl : im.gr) + (size_t)j * NV * GPB * 8;
-          sst[s] = 8;
-        } else {  // [x tile][v][g][lane][8]
-          sp[s] = (jj < 0 ? im.gb : im.gt) + ((size_t)(i >> 5) * NV * GPB * 32 + (i & 31)) * 8;
-          sst[s] = 256;
-        }
-      }
-    }
-    // S_v rounded to FP32, its FP32 reciprocal (1 where S_v vanishes or is
-    // below the FP32 normal range, whose coefficients truncate to zero)
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-      const float m = d2f_rn(__longlong_as_double((long long)mx[v]));
-      R[v] = m >= 1.17549435e-38f ? __frcp_rn(m) : 1.0f;
+  for (int s = 0; s < 5; s++) {
+    const int ii = i + (s == 1 ? -1 : s == 2 ? 1 : 0), jj = j + (s == 3 ? -1 : s == 4 ? 1 : 0);
+    long long te;
+    int le;
+    sp[s] = im.img;
+    sst[s] = 0;
+    if (!valid) continue;
+    if (mesh_elem(a.ms, ii, jj, i, j, te, le)) {
+      sp[s] = im.img + ((size_t)te * NV * GPB * 32 + le) * 8;
+      sst[s] = 256;
+    } else if (ii < 0 || ii >= a.ms.nx) {  // [j][v][g][8]
+      sp[s] = (ii < 0 ? im.gl : im.gr) + (size_t)j * NV * GPB * 8;
+      sst[s] = 8;
+    } else {  // [x tile][v][g][lane][8]
+      sp[s] = (jj < 0 ? im.gb : im.gt) + ((size_t)(i >> 5) * NV * GPB * 32 + (i & 31)) * 8;
+      sst[s] = 256;
     }
   }
 
@@ -605,6 +612,38 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   };
   uint4 cur[8];
   load4(0, cur);
+  // 1 / S_v of this row's stencil (used by the first epilogue)
+  const float4 r4 = valid ? im.rs[(size_t)tile * 32 + (row & 31)] : make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+  const float R[4] = {r4.x, r4.y, r4.z, r4.w};
+  if (warp == 0) tmem_alloc(s_taddr, 256);  // variable v's layer-1 sums: columns 64 v ..; layer 2: 0..63
+  if (tid == 64) {
+    // the CTA `ahead` places on (one wave later) first touches the pairs of
+    // the tile row above its own and its scales: ask the L2 for them now
+    const long long nb = (long long)blockIdx.x + ahead, t0 = nb * 4 + a.ms.ntx;
+    const long long t1 = t0 + 4 < ntiles ? t0 + 4 : ntiles;
+    if (t0 < t1) bulk_prefetch_l2(im.img + (size_t)t0 * NV * GPB * 256, (unsigned)(t1 - t0) * NV * GPB * 1024);
+    if (nb * 4 < ntiles)
+      bulk_prefetch_l2(im.rs + nb * 128, (unsigned)((ntiles - nb * 4 < 4 ? ntiles - nb * 4 : 4) * 32 * sizeof(float4)));
+  }
+  if (tid == 32) {  // warp 1, while warp 0 allocates
+#pragma unroll
+    for (int b = 0; b < 8; b++) mbar_init(&bar[b], 1);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[6], 8192 + 1024);
+    bulk_g2s(sm + TC_W2, wp + (size_t)NC * 8192, 8192, &bar[6]);
+    bulk_g2s(sm + TC_PAR, wp + (size_t)NC * 8192 + 8192, 1024, &bar[6]);
+#pragma unroll
+    for (int c = 0; c < (NC < TC_WST ? NC : TC_WST); c++) {
+      mbar_expect_tx(&bar[2 + c], 8192);
+      bulk_g2s(sm + TC_B + c * 8192, wp + (size_t)c * 8192, 8192, &bar[2 + c]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = *s_taddr;
+  bool ok = true;
+
 #pragma unroll
   for (int c = 0; c < NC; c++) {
     // the next chunk's pairs are in flight while this one is stored and multiplied
@@ -719,7 +758,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   if (ch == 1) szp[row] = zp;
   tc_fence_before();
   __syncthreads();
-  if (ch == 0 && valid) {
+  if (ch == 0 && valid && status == 0) {
     const float z = zp + szp[row] + par[3 * H2];
     const size_t e = (size_t)j * a.ms.nx + i;
     flags[e] = (unsigned char)(z > threshold);
@@ -729,7 +768,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     tc_fence_after();
     tmem_dealloc(taddr, 256);
   }
-  if (!ok) atomicOr(&ts->pending, 2);
+  if (!ok && status == 0) atomicOr(&ts->pending, 2);
 }
 
 template <int NV, int M>
@@ -749,16 +788,28 @@ cudaError_t launch_flags_t(const FeatArgs& fa, const void* wpack, void* work, fl
   unsigned *gl = reinterpret_cast<unsigned*>(w + wl.gl), *gr = reinterpret_cast<unsigned*>(w + wl.gr);
   unsigned *gb = reinterpret_cast<unsigned*>(w + wl.gb), *gt = reinterpret_cast<unsigned*>(w + wl.gt);
   const long long ntiles = (long long)ms.ntx * ms.ny;
+  if (ntiles >= (1ll << 29)) return cudaErrorInvalidValue;  // tile indices in int, CTA indices * 4 too
   const long long n = ntiles * NV * 32;
   k_elem_prep<NV, M><<<blocks(n, 128), 128, 0, s>>>(fa.U, emax, img, n);
   if (ms.bc == 1) {
     const long long ng = 2LL * ms.ny * NV + 2LL * ms.ntx * NV * 32;
     k_ghost_prep<NV, M><<<blocks(ng, 128), 128, 0, s>>>(fa.GL, fa.GR, fa.GB, fa.GT, gl, gr, gb, gt, ms.ny, ms.ntx);
   }
-  const ImgArgs im = {emax, img, gl, gr, gb, gt};
+  float4* rs = reinterpret_cast<float4*>(w + wl.rs);
+  const long long ne = ntiles * 32;
+  k_stencil_scale<NV, M><<<blocks(ne, 128), 128, 0, s>>>(fa, emax, rs, ne);
+  const ImgArgs im = {rs, img, gl, gr, gb, gt};
+  static int resident = 0;  // CTAs in one wave: two per SM
+  if (!resident) {
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    resident = 2 * nsm;
+  }
   const long long nblk = (ntiles + 3) / 4;
   k_mlp_tc<NV, M><<<(unsigned)nblk, TC_THREADS, TC_SMEM, s>>>(fa, im, static_cast<const unsigned char*>(wpack),
-                                                              threshold, ts, flags, logits, ntiles);
+                                                              threshold, ts, flags, logits, ntiles, resident);
   return cudaGetLastError();
 }
 
