@@ -483,10 +483,20 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
   // The state is the values at the m x m nodes (k = q*m + r): they go to
   // shared memory as they are, and each face trace is one sum along a node
   // line with the Lagrange weights of the element end.
+  // the element below is loaded with the own element and the element above
+  // before the traces below are summed, so that each load's latency passes
+  // under the sums before it (a missing neighbour reads the own element,
+  // unused)
+  float cb[M];
   {
     float c[M];
 #pragma unroll
     for (int k = 0; k < M; k++) c[k] = own[k * 32];
+    {
+      const float* qB = pB ? pB : own;
+#pragma unroll
+      for (int k = 0; k < M; k++) cb[k] = qB[k * 32];
+    }
 #pragma unroll
     for (int k = 0; k < M; k++) sU[voff + k * 32 + lane] = c[k];
     // x traces at the m y-nodes r: right (xi = +1) and left (xi = -1) as the
@@ -521,14 +531,17 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
     // of the element above, each summed in the order of its owner's own trace
     // (both CTAs of a face see the same values)
     float c[M];
-    if (pB) {
+    {
+      const float* qT = pT ? pT : own;
 #pragma unroll
-      for (int k = 0; k < M; k++) c[k] = pB[k * 32];
+      for (int k = 0; k < M; k++) c[k] = qT[k * 32];
+    }
+    if (pB) {
 #pragma unroll
       for (int q = 0; q < m; q++) {
         float acc = 0.0f;
 #pragma unroll
-        for (int r = 0; r < m; r++) acc = fmaf(c32t[P].bp[r], c[q * m + r], acc);
+        for (int r = 0; r < m; r++) acc = fmaf(c32t[P].bp[r], cb[q * m + r], acc);
         sYN[((0 * 3 + v) * m + q) * 32 + lane] = acc;
       }
     } else if (zB) {
@@ -536,8 +549,6 @@ __device__ __forceinline__ void stage32_tile(const StageArgs32& a, const float* 
       for (int q = 0; q < m; q++) sYN[((0 * 3 + v) * m + q) * 32 + lane] = 0.0f;
     }
     if (pT) {
-#pragma unroll
-      for (int k = 0; k < M; k++) c[k] = pT[k * 32];
 #pragma unroll
       for (int q = 0; q < m; q++) {
         float acc = 0.0f;
