@@ -58,8 +58,8 @@ def design_bytes(ntiles, rb_tiles, zone_tiles):
 BYTES_PER_ELEM_TORQUE_PREC = 300.0
 # DRAM bytes (read + write) per stage launch of k_stage32<4> at 512^2, the mean
 # over the three stages of one step from one ncu capture of the current kernel
-# (137.7, 229.3 and 294.4 MB)
-TRAFFIC_PER_STAGE_PREC = 220.5e6
+# (135.5, 227.3 and 294.7 MB)
+TRAFFIC_PER_STAGE_PREC = 219.2e6
 # FP64 peak of GB300 derived from unit counts and clock: 2 FP64 FMA / clk / SM
 # x 152 SMs x 2 flop x 2.07 GHz = 1.26 TFLOP/s
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
