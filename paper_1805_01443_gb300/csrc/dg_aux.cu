@@ -153,8 +153,12 @@ __global__ void k_cfl(const double* U, const float* D, const NodeW w, DevState* 
   }
 }
 
+// the three stage-time positions, one per thread (FP64 sincos each)
 __global__ void k_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0) {
-  store_planet32(ts, fixed_dt > 0.0 ? fixed_dt : ts->dt, r_p, omega_p, phi0);
+  const int k = threadIdx.x;
+  const double dt = fixed_dt > 0.0 ? fixed_dt : ts->dt;
+  if (k < 3) store_planet32_k(ts, k, ts->t, dt, r_p, omega_p, phi0);
+  if (k == 0) ts->dtf = (float)dt;
 }
 
 __global__ void k_finish(DevState* ts, const double* part, int nparts, double* series,
@@ -192,20 +196,25 @@ __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ 
 // canonical FP32 delta (values at the nodes) -> tiled delta, with the CFL
 // step of u_b + delta (the precision form's upload): a block of (32, 3)
 // threads per tile, thread (lane, v) moving variable v of one element in node
-// order and summing its average as k_cfl does, warp 0 forming the bounds
+// order and summing its average as k_cfl does, warp 0 forming the bounds; the
+// M loads of a thread are issued before any is used
+template <int M>
 __global__ void k_ingest_delta_cfl(const float* __restrict__ canon, float* __restrict__ d,
                                    const double* __restrict__ U, const NodeW w, DevState* ts, const Mesh ms,
-                                   const Phys ph, int M, double idx, double idy) {
+                                   const Phys ph, double idx, double idy) {
   __shared__ float s_sum[3][2][TILE];
   const int lane = threadIdx.x, v = threadIdx.y;
   const int i = blockIdx.x * TILE + lane, j = blockIdx.y;
   const size_t base = ((size_t)j * ms.ntx + blockIdx.x) * 3 * M * TILE + lane;
   float sh = 0.0f, sl = 0.0f;
   if (i < ms.nx) {
+    float x[M];
+#pragma unroll
+    for (int n = 0; n < M; n++) x[n] = __ldg(canon + ((size_t)(v * M + n) * ms.ny + j) * ms.nx + i);
+#pragma unroll
     for (int n = 0; n < M; n++) {
-      const float x = canon[((size_t)(v * M + n) * ms.ny + j) * ms.nx + i];
-      d[base + (size_t)(v * M + n) * TILE] = x;
-      ff_acc(w, n, x, sh, sl);
+      d[base + (size_t)(v * M + n) * TILE] = x[n];
+      ff_acc(w, n, x[n], sh, sl);
     }
   }
   s_sum[v][0][lane] = sh;
@@ -348,7 +357,7 @@ cudaError_t launch_combine(double* out, const double* u0, const double* const* k
 
 cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double omega_p, double phi0,
                             cudaStream_t s) {
-  k_planet32<<<1, 1, 0, s>>>(ts, fixed_dt, r_p, omega_p, phi0);
+  k_planet32<<<1, 32, 0, s>>>(ts, fixed_dt, r_p, omega_p, phi0);
   return cudaGetLastError();
 }
 
@@ -369,8 +378,15 @@ cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* 
     w.wh[k] = (float)wn[k];
     w.wl[k] = (float)(wn[k] - (double)w.wh[k]);
   }
-  k_ingest_delta_cfl<<<dim3(mesh.ntx, mesh.ny), dim3(TILE, 3), 0, s>>>(canon, d, U, w, ts, mesh, phys, M,
-                                                                       1.0 / mesh.dx, 1.0 / mesh.dy);
+  const dim3 g(mesh.ntx, mesh.ny), b(TILE, 3);
+  const double idx = 1.0 / mesh.dx, idy = 1.0 / mesh.dy;
+  switch (M) {
+    case 4: k_ingest_delta_cfl<4><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
+    case 9: k_ingest_delta_cfl<9><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
+    case 16: k_ingest_delta_cfl<16><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
+    case 25: k_ingest_delta_cfl<25><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
