@@ -158,7 +158,9 @@ int dg_workspace_bytes(const dg_mesh *mesh, int order, const dg_eos *eos, const 
 /* As dg_init, but all device memory of the handle is carved out of the
    caller's device buffer `workspace` (>= dg_workspace_bytes, 256-byte aligned,
    owned by the caller and valid until dg_destroy), and work is issued on
-   `stream` (a cudaStream_t, NULL for the legacy default stream). */
+   `stream` (a cudaStream_t, NULL for the legacy default stream).  A workspace
+   that is not device memory of the current device is refused with
+   DG_ERR_ARG; a smaller one with DG_ERR_NOMEM. */
 int dg_init_ex(dg_handle **h, const dg_mesh *mesh, int order, const dg_eos *eos,
                const dg_planet *planet, const dg_disc *disc, void *workspace,
                size_t workspace_bytes, void *stream);
@@ -363,7 +365,11 @@ int dg_last_flags(dg_handle *h, unsigned char *flags);
    rounded once; index (s nv + v) m^2 + k.
    x, y, z and grad pointers marked _dev are device pointers; host pointers are
    caller-owned; `stream` is a cudaStream_t (NULL: legacy default).  The
-   network calls synchronise their stream before returning. */
+   network calls synchronise their stream before returning.  A _dev pointer
+   that is not device (or managed) memory of the current device is refused
+   with DG_ERR_ARG before any launch; the sizes of the buffers behind them
+   (B rows of nin, B labels, B logits; n indices, n rows of features) are
+   the caller's to guarantee. */
 typedef struct dg_mlp dg_mlp;
 
 /* Weights uniform in +-1/sqrt(fan_in) (counter-based SplitMix64 of seed), biases 0. */

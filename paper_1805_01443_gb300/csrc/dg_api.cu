@@ -107,6 +107,29 @@ int fail(dg_handle* h, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(h, DG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// DG_OK if p is device (or managed) memory that kernels on the current device
+// can read and write.  Host memory (pageable or page-locked), memory of
+// another device, addresses the runtime does not know and calls without a
+// current device are refused with DG_ERR_ARG before any kernel could fault.
+int device_pointer(dg_handle* h, const void* p, const char* what) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0) {
+    cudaGetLastError();
+    return fail(h, DG_ERR_ARG, "%s: no current CUDA device", what);
+  }
+  cudaPointerAttributes at;
+  e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // the failed query is this call's own; leave no error behind
+    return fail(h, DG_ERR_ARG, "%s: pointer attributes unavailable (%s)", what, cudaGetErrorString(e));
+  }
+  const bool device_mem = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (!device_mem || (at.type == cudaMemoryTypeDevice && at.device != dev))
+    return fail(h, DG_ERR_ARG, "%s is not device memory of the current device %d", what, dev);
+  return DG_OK;
+}
+
 // Legendre P_n and P'_n at x (three-term recurrence; derivative from the
 // identity (x^2 - 1) P'_n = n (x P_n - P_{n-1}), with the endpoint limits).
 void leg(int n, double x, double* Pn, double* dPn, double* Pn1) {
@@ -709,6 +732,7 @@ int dg_init_ex(dg_handle** out, const dg_mesh* mesh, int order, const dg_eos* eo
     return fail(nullptr, DG_ERR_ARG, "workspace must be 256-byte aligned");
   if (workspace && workspace_bytes < L.total)
     return fail(nullptr, DG_ERR_NOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, L.total);
+  if (workspace && device_pointer(nullptr, workspace, "workspace")) return DG_ERR_ARG;
   dg_handle* h = new (std::nothrow) dg_handle();  // value-initialised: every pointer starts null
   if (!h) return fail(nullptr, DG_ERR_NOMEM, "host allocation failed");
   memset(h, 0, sizeof(*h));
@@ -1508,6 +1532,7 @@ int dg_mlp_set_params(dg_mlp* net, const float* host) {
 
 int dg_mlp_forward(dg_mlp* net, const float* x, int B, float* z, void* stream) {
   if (!net || !x || !z || B < 1) return fail(nullptr, DG_ERR_ARG, "bad argument");
+  if (device_pointer(nullptr, x, "x_dev") || device_pointer(nullptr, z, "z_dev")) return DG_ERR_ARG;
   int rc = mlp_reserve(net, B);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1520,6 +1545,7 @@ int dg_mlp_forward(dg_mlp* net, const float* x, int B, float* z, void* stream) {
 int dg_mlp_grad(dg_mlp* net, const float* x, const float* y, int B, float pos_weight, float* grad_host,
                 double* loss, void* stream) {
   if (!net || !x || !y || B < 1 || !(pos_weight > 0.0f)) return fail(nullptr, DG_ERR_ARG, "bad argument");
+  if (device_pointer(nullptr, x, "x_dev") || device_pointer(nullptr, y, "y_dev")) return DG_ERR_ARG;
   int rc = mlp_reserve(net, B);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1538,6 +1564,7 @@ int dg_mlp_train_step(dg_mlp* net, const float* x, const float* y, int B, float 
                       double* loss, void* stream) {
   if (!net || !x || !y || B < 1 || !(pos_weight > 0.0f) || !(lr > 0.0f))
     return fail(nullptr, DG_ERR_ARG, "bad argument");
+  if (device_pointer(nullptr, x, "x_dev") || device_pointer(nullptr, y, "y_dev")) return DG_ERR_ARG;
   int rc = mlp_reserve(net, B);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1556,6 +1583,7 @@ int dg_mlp_train_step(dg_mlp* net, const float* x, const float* y, int B, float 
 int dg_features(dg_handle* h, const int* elems, int n, float* out) {
   if (!h || !elems || !out || n < 0) return fail(h, DG_ERR_ARG, "bad argument");
   if (h->prec != 0) return fail(h, DG_ERR_UNSUPPORTED, "features of the FP64 form only");
+  if (n > 0 && (device_pointer(h, elems, "elems_dev") || device_pointer(h, out, "out_dev"))) return DG_ERR_ARG;
   DevState st;
   int rc = read_state(h, &st);
   if (rc) return rc;

@@ -322,6 +322,7 @@ class Disc:
         """FP32 features [n, 5 nv M] (a torch CUDA tensor) of the elements
         `elems` (a torch int32 CUDA tensor of indices j*nx + i)."""
         import torch
+        _device_tensor(elems, torch.int32, (elems.numel(),), "elems")
         nin = 5 * self.nv * self.M
         out = torch.empty((elems.numel(), nin), dtype=torch.float32, device=elems.device)
         _check(lib().dg_features(self.h, _VP(elems.data_ptr()), elems.numel(), _VP(out.data_ptr())), self.h)
@@ -509,6 +510,17 @@ class Batch:
         self.close()
 
 
+def _device_tensor(t, dtype, shape, name):
+    """The kernels read a tensor through its data pointer alone: refuse one of
+    another dtype, shape or device, or one that is not contiguous, before its
+    pointer is passed on."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+
+
 class Mlp:
     """The learned troubled-cell indicator's network (a dg_mlp): training and
     inference run in libdg's kernels; batches are torch CUDA tensors."""
@@ -527,6 +539,11 @@ class Mlp:
         import torch
         return _VP(torch.cuda.current_stream().cuda_stream)
 
+    def _check_batch(self, x, y):
+        import torch
+        _device_tensor(x, torch.float32, (x.shape[0], self.nin), "x")
+        _device_tensor(y, torch.float32, (x.shape[0],), "y")
+
     def get_params(self):
         p = np.zeros(self.nparams, dtype=np.float32)
         _check(lib().dg_mlp_get_params(self.net, p.ctypes.data_as(_VP)))
@@ -539,11 +556,13 @@ class Mlp:
 
     def forward(self, x):
         import torch
+        _device_tensor(x, torch.float32, (x.shape[0], self.nin), "x")
         z = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
         _check(lib().dg_mlp_forward(self.net, _VP(x.data_ptr()), x.shape[0], _VP(z.data_ptr()), self._stream()))
         return z
 
     def grad(self, x, y, pos_weight=1.0):
+        self._check_batch(x, y)
         g = np.zeros(self.nparams, dtype=np.float32)
         loss = ctypes.c_double()
         _check(lib().dg_mlp_grad(self.net, _VP(x.data_ptr()), _VP(y.data_ptr()), x.shape[0], pos_weight,
@@ -551,6 +570,7 @@ class Mlp:
         return g, loss.value
 
     def train_step(self, x, y, pos_weight=1.0, lr=1e-3):
+        self._check_batch(x, y)
         loss = ctypes.c_double()
         _check(lib().dg_mlp_train_step(self.net, _VP(x.data_ptr()), _VP(y.data_ptr()), x.shape[0], pos_weight,
                                        lr, ctypes.byref(loss), self._stream()))

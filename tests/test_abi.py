@@ -131,3 +131,26 @@ def test_no_cpu_fallback_without_a_device(L):
     with pytest.raises(dg.DgError) as e:
         dg.Disc(cfg, torch_memory=False)
     assert e.value.code in (dg.DG_ERR_NOMEM, dg.DG_ERR_CUDA)
+
+
+def test_init_ex_refuses_a_host_workspace(L):
+    """A caller workspace in host memory (aligned and large enough) is refused
+    with DG_ERR_ARG before any allocation or launch: with a GPU it is not
+    device memory, without one there is no current device."""
+    import ctypes
+
+    import numpy as np
+    from paper_1805_01443_gb300 import inputs
+    cfg = inputs.disc_small(8, 2)
+    nbytes = dg.dg_workspace_bytes(cfg)
+    raw = np.zeros(nbytes + 256, dtype=np.uint8)
+    off = (-raw.ctypes.data) % 256
+    ws = raw[off:off + nbytes]
+    mesh, order, eos, planet, disc = dg.structs(cfg)
+    h = ctypes.c_void_p()
+    rc = L.dg_init_ex(ctypes.byref(h), ctypes.byref(mesh), order, ctypes.byref(eos), ctypes.byref(planet),
+                      ctypes.byref(disc), ctypes.c_void_p(ws.ctypes.data), nbytes, None)
+    assert rc == dg.DG_ERR_ARG
+    assert not h.value
+    assert b"workspace" in L.dg_last_error(None)
+    assert not ws.any()

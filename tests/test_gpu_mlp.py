@@ -157,3 +157,45 @@ def test_limiter2_without_network_is_tvb_and_with_network_runs():
         net.close()
         a.close()
         b.close()
+
+
+def test_network_calls_refuse_host_memory_and_bad_tensors():
+    """dg_mlp_forward / grad / train_step and dg_features refuse host arrays
+    with DG_ERR_ARG before any launch; the binding refuses tensors of the wrong
+    dtype, shape or device before their pointers reach the library."""
+    import ctypes
+    L = dg.lib()
+    nin, B = 320, 8
+    net = dg.Mlp(nin, seed=4)
+    g = dg.Disc(inputs.shock_ring(16, 3))
+    try:
+        x = np.zeros((B, nin), dtype=np.float32)
+        y = np.zeros(B, dtype=np.float32)
+        z = np.full(B, 7.0, dtype=np.float32)
+        xp, yp, zp = (ctypes.c_void_p(a.ctypes.data) for a in (x, y, z))
+        assert L.dg_mlp_forward(net.net, xp, B, zp, None) == dg.DG_ERR_ARG
+        assert L.dg_mlp_grad(net.net, xp, yp, B, 1.0, None, None, None) == dg.DG_ERR_ARG
+        assert L.dg_mlp_train_step(net.net, xp, yp, B, 1.0, 1e-3, None, None) == dg.DG_ERR_ARG
+        assert np.all(z == 7.0)
+        elems = np.arange(4, dtype=np.int32)
+        out = np.zeros((4, nin), dtype=np.float32)
+        assert L.dg_features(g.h, ctypes.c_void_p(elems.ctypes.data), 4,
+                             ctypes.c_void_p(out.ctypes.data)) == dg.DG_ERR_ARG
+        assert not out.any()
+        xd = torch.zeros((B, nin), dtype=torch.float32, device="cuda")
+        with pytest.raises(ValueError):
+            net.forward(xd[:, :100])                       # too few inputs per row
+        with pytest.raises(ValueError):
+            net.forward(xd.double())                       # wrong dtype
+        with pytest.raises(ValueError):
+            net.forward(torch.zeros((B, nin)))             # host tensor
+        with pytest.raises(ValueError):
+            net.train_step(xd, torch.zeros(B - 1, device="cuda"))
+        with pytest.raises(ValueError):
+            g.features(torch.arange(4, dtype=torch.int64, device="cuda"))
+        # the refusals left the handle and the network usable
+        assert net.forward(xd).shape == (B,)
+        assert g.features(torch.arange(4, dtype=torch.int32, device="cuda")).shape == (4, nin)
+    finally:
+        net.close()
+        g.close()
