@@ -85,12 +85,24 @@ struct dg_handle {
   double* SA[2];
   cudaEvent_t ev_copied[2], ev_consumed[2];
   int apar;
+  // pipelined delta upload (precision form, handle in no batch): the
+  // conversion runs on its own stream into a spare state buffer, which then
+  // trades places with D[0]; the CFL slots keep its time step apart from the
+  // time state of the steps in flight (own allocations, null until the first
+  // dg_set_delta_async)
+  cudaStream_t istream;
+  float* DS;      // the spare state buffer (one of DSmem, D[0], D[1] after trades)
+  float* DSmem;   // the spare buffer's own allocation, whichever role it has now
+  UpSlot* up;
+  cudaEvent_t ev_ingested, ev_spare_free;
+  int in_batch;  // batches this handle belongs to (they hold D[0] and D[1])
   char err[256];
 };
 
 namespace {
 
 thread_local char g_err[256] = "";
+constexpr unsigned long long kEmptySlotBits = 0x7ff0000000000000ULL;  // +inf: an empty CFL slot
 
 int fail(dg_handle* h, int code, const char* fmt, ...) {
   char* dst = h ? h->err : g_err;
@@ -1155,6 +1167,68 @@ int dg_set_state(dg_handle* h, const double* coeffs, double t, long step) {
 }
 
 namespace {
+// The upload's copy stream, two staging buffers of n doubles and their
+// events, all or none: on a failure whatever was made is released again.
+int create_staging(dg_handle* h, size_t n) {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ec[2] = {nullptr, nullptr}, eu[2] = {nullptr, nullptr};
+  double* sa[2] = {nullptr, nullptr};
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    e = cudaEventCreateWithFlags(&ec[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&eu[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sa[k], n * sizeof(double));
+  }
+  if (e != cudaSuccess) {
+    for (int k = 0; k < 2; k++) {
+      if (ec[k]) cudaEventDestroy(ec[k]);
+      if (eu[k]) cudaEventDestroy(eu[k]);
+      cudaFree(sa[k]);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    return fail(h, DG_ERR_CUDA, "upload staging: %s", cudaGetErrorString(e));
+  }
+  for (int k = 0; k < 2; k++) {
+    h->ev_copied[k] = ec[k];
+    h->ev_consumed[k] = eu[k];
+    h->SA[k] = sa[k];
+  }
+  h->cstream = cs;
+  return DG_OK;
+}
+
+// The pipelined delta upload's conversion stream, its two events, the spare
+// state buffer and the two CFL slots (set empty), all or none.
+int create_pipeline(dg_handle* h) {
+  cudaStream_t is = nullptr;
+  cudaEvent_t ei = nullptr, ef = nullptr;
+  float* ds = nullptr;
+  UpSlot* up = nullptr;
+  const UpSlot empty[2] = {{kEmptySlotBits, 0, 0}, {kEmptySlotBits, 0, 0}};
+  cudaError_t e = cudaStreamCreateWithFlags(&is, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ei, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ef, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&ds, (size_t)h->dm.ntx * h->dm.ny * h->nv * h->M * TILE * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&up, sizeof(empty));
+  if (e == cudaSuccess) e = cudaMemcpy(up, empty, sizeof(empty), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (ei) cudaEventDestroy(ei);
+    if (ef) cudaEventDestroy(ef);
+    cudaFree(ds);
+    cudaFree(up);
+    if (is) cudaStreamDestroy(is);
+    return fail(h, DG_ERR_CUDA, "delta upload pipeline: %s", cudaGetErrorString(e));
+  }
+  h->ev_ingested = ei;
+  h->ev_spare_free = ef;
+  h->DS = ds;
+  h->DSmem = ds;
+  h->up = up;
+  h->istream = is;
+  return DG_OK;
+}
+
 bool page_locked(const void* p) {
   cudaPointerAttributes at;
   const bool ok = cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost;
@@ -1169,12 +1243,8 @@ int dg_set_state_async(dg_handle* h, const double* coeffs, double t, long step) 
   if (!page_locked(coeffs)) return fail(h, DG_ERR_ARG, "dg_set_state_async needs page-locked host memory");
   const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
   if (!h->cstream) {
-    CU(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
-    for (int k = 0; k < 2; k++) {
-      CU(h, cudaEventCreateWithFlags(&h->ev_copied[k], cudaEventDisableTiming));
-      CU(h, cudaEventCreateWithFlags(&h->ev_consumed[k], cudaEventDisableTiming));
-      CU(h, cudaMalloc((void**)&h->SA[k], n * sizeof(double)));
-    }
+    const int rc = create_staging(h, n);
+    if (rc) return rc;
   }
   // the copy into this staging buffer waits for the conversion that read it
   // last; the conversion waits for the copy
@@ -1201,12 +1271,12 @@ int dg_set_delta_async(dg_handle* h, const float* delta, double t, long step) {
   if (!page_locked(delta)) return fail(h, DG_ERR_ARG, "dg_set_delta_async needs page-locked host memory");
   const size_t n = (size_t)h->nv * h->M * h->mesh.nx * h->mesh.ny;
   if (!h->cstream) {
-    CU(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
-    for (int k = 0; k < 2; k++) {
-      CU(h, cudaEventCreateWithFlags(&h->ev_copied[k], cudaEventDisableTiming));
-      CU(h, cudaEventCreateWithFlags(&h->ev_consumed[k], cudaEventDisableTiming));
-      CU(h, cudaMalloc((void**)&h->SA[k], n * sizeof(double)));
-    }
+    const int rc = create_staging(h, n);
+    if (rc) return rc;
+  }
+  if (!h->istream && !h->in_batch) {
+    const int rc = create_pipeline(h);
+    if (rc) return rc;
   }
   // the staging buffers hold n doubles; the FP32 delta takes half of one
   const int k = h->apar;
@@ -1214,20 +1284,44 @@ int dg_set_delta_async(dg_handle* h, const float* delta, double t, long step) {
   CU(h, cudaStreamWaitEvent(h->cstream, h->ev_consumed[k], 0));
   CU(h, cudaMemcpyAsync(stage, delta, n * sizeof(float), cudaMemcpyHostToDevice, h->cstream));
   CU(h, cudaEventRecord(h->ev_copied[k], h->cstream));
-  CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
-  // the status reset, then the layout change and the CFL step of u_b + delta
-  // in one pass over the upload, then the step's dt
-  CU(h, launch_reset_state(h->ts, t, step, h->stream));
   double wn[MAXM * MAXM];
   node_weights(h, wn);
-  CU(h, launch_ingest_delta_cfl(stage, h->D[0], h->BG, wn, h->ts, h->dm, h->ph, h->M, h->stream));
-  CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
+  if (h->in_batch) {
+    // a batch holds this handle's state buffers: convert in place on the
+    // handle's stream (the status reset, then the layout change and the CFL
+    // step of u_b + delta in one pass over the upload, then the step's dt)
+    CU(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
+    CU(h, launch_reset_state(h->ts, t, step, h->stream));
+    CU(h, launch_ingest_delta_cfl(stage, h->D[0], h->BG, wn, &h->ts->dt_bits, &h->ts->pending, h->dm, h->ph,
+                                  h->M, h->stream));
+    CU(h, cudaEventRecord(h->ev_consumed[k], h->stream));
+    CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, 0, h->ph.r_p, h->ph.omega_p,
+                        h->ph.phi0, h->stream));
+  } else {
+    // the layout change and the CFL step of u_b + delta run on the handle's
+    // conversion stream, into the spare state buffer and CFL slot k, as soon
+    // as the upload has landed and the steps that last used the spare buffer
+    // are done -- so that they overlap the steps queued before this call
+    CU(h, cudaStreamWaitEvent(h->istream, h->ev_copied[k], 0));
+    CU(h, cudaStreamWaitEvent(h->istream, h->ev_spare_free, 0));
+    CU(h, launch_ingest_delta_cfl(stage, h->DS, h->BG, wn, &h->up[k].dt_bits, &h->up[k].pending, h->dm, h->ph,
+                                  h->M, h->istream));
+    CU(h, cudaEventRecord(h->ev_consumed[k], h->istream));
+    CU(h, cudaEventRecord(h->ev_ingested, h->istream));
+    // the handle's stream takes it as its state behind the work queued so
+    // far: time state, dt from the slot; the spare buffer becomes D[0] and the
+    // old D[0] the spare, free once that queued work is done
+    CU(h, cudaStreamWaitEvent(h->stream, h->ev_ingested, 0));
+    CU(h, launch_adopt_upload(h->ts, h->up + k, t, step, h->stream));
+    float* d0 = h->D[0];
+    h->D[0] = h->DS;
+    h->DS = d0;
+    CU(h, cudaEventRecord(h->ev_spare_free, h->stream));
+  }
   h->cur = h->cur0 = 0;
   h->step0 = step;
   h->series_read = 0;
   h->apar = 1 - k;
-  CU(h, launch_finish(h->ts, h->part, h->nparts, h->series, 0.0, 0, 0, h->ph.r_p, h->ph.omega_p, h->ph.phi0,
-                      h->stream));
   return DG_OK;
 }
 
@@ -1337,6 +1431,14 @@ int dg_destroy(dg_handle* h) {
       cudaFree(h->SA[k]);
     }
     cudaStreamDestroy(h->cstream);
+  }
+  if (h->istream) {
+    cudaStreamSynchronize(h->istream);
+    cudaEventDestroy(h->ev_ingested);
+    cudaEventDestroy(h->ev_spare_free);
+    cudaFree(h->DSmem);
+    cudaFree(h->up);
+    cudaStreamDestroy(h->istream);
   }
   if (h->ind_w) cudaFree(h->ind_w);
   if (h->ev) {
@@ -1639,6 +1741,7 @@ int dg_indicator_logits(dg_handle* h, float* logits, unsigned char* flags) {
 struct dg_batch {
   int n;
   dg_handle* h[BATCH_MAX];
+  bool registered;       // the handles count this batch in their in_batch
   cudaStream_t hstream;  // the handles' stream
   cudaStream_t stream;   // the batch's own stream (capturable), joined to hstream by events
   cudaEvent_t ev_in, ev_out;
@@ -1931,6 +2034,10 @@ int dg_batch_create(dg_batch** out, dg_handle* const* hs, int n) {
     dg_batch_destroy(b);
     return rc;
   }
+  // the batch holds the handles' state buffers from here on: their delta
+  // uploads convert in place instead of trading buffers
+  for (int k = 0; k < n; k++) b->h[k]->in_batch++;
+  b->registered = true;
   *out = b;
   return DG_OK;
 }
@@ -2068,6 +2175,8 @@ int dg_batch_tune(dg_batch* b, int steps, int* policy, int* dynamic, int* ctas_p
 int dg_batch_destroy(dg_batch* b) {
   if (!b) return DG_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->registered)
+    for (int k = 0; k < b->n; k++) b->h[k]->in_batch--;
   if (b->graph_ok) cudaGraphExecDestroy(b->exec);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);

@@ -200,8 +200,8 @@ __global__ void k_ingest(const double* __restrict__ canon, double* __restrict__ 
 // M loads of a thread are issued before any is used
 template <int M>
 __global__ void k_ingest_delta_cfl(const float* __restrict__ canon, float* __restrict__ d,
-                                   const double* __restrict__ U, const NodeW w, DevState* ts, const Mesh ms,
-                                   const Phys ph, double idx, double idy) {
+                                   const double* __restrict__ U, const NodeW w, unsigned long long* dt_bits,
+                                   int* pending, const Mesh ms, const Phys ph, double idx, double idy) {
   __shared__ float s_sum[3][2][TILE];
   const int lane = threadIdx.x, v = threadIdx.y;
   const int i = blockIdx.x * TILE + lane, j = blockIdx.y;
@@ -234,9 +234,34 @@ __global__ void k_ingest_delta_cfl(const float* __restrict__ canon, float* __res
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
   if (lane == 0) {
-    if (bad) atomicOr(&ts->pending, 1);
-    atomicMin(&ts->dt_bits, (unsigned long long)__double_as_longlong(dtk));
+    if (bad) atomicOr(pending, 1);
+    atomicMin(dt_bits, (unsigned long long)__double_as_longlong(dtk));
   }
+}
+
+// what k_reset, the CFL pass into ts and k_finish without advance leave in the
+// time state, from a CFL slot filled apart from it
+__global__ void k_adopt_upload(DevState* ts, UpSlot* up, double t, long long step) {
+  const unsigned long long bits = up->dt_bits;
+  const int pend = up->pending;
+  up->dt_bits = INF_BITS;
+  up->pending = 0;
+  ts->t = t;
+  ts->dt = 0.0;
+  ts->torque = 0.0;
+  ts->step = step;
+  ts->series_count = 0;
+  ts->pending = pend;
+  ts->status = 0;
+  if (pend) {
+    ts->status = (pend & 2) ? DG_ERR_TIMEOUT : DG_ERR_NUMERIC;
+    ts->dt_bits = bits;
+    return;
+  }
+  const double dtn = __longlong_as_double((long long)bits);
+  if (!(dtn > 0.0) || !isfinite(dtn)) ts->status = DG_ERR_NUMERIC;
+  else ts->dt = dtn;
+  ts->dt_bits = INF_BITS;
 }
 
 __global__ void k_to_canon_f32(const float* tiled, float* canon, const Mesh ms, int nvm) {
@@ -361,6 +386,11 @@ cudaError_t launch_planet32(DevState* ts, double fixed_dt, double r_p, double om
   return cudaGetLastError();
 }
 
+cudaError_t launch_adopt_upload(DevState* ts, UpSlot* up, double t, long long step, cudaStream_t s) {
+  k_adopt_upload<<<1, 1, 0, s>>>(ts, up, t, step);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reset_state(DevState* ts, double t, long long step, cudaStream_t s) {
   k_reset<<<1, 1, 0, s>>>(ts, t, step);
   return cudaGetLastError();
@@ -371,8 +401,9 @@ cudaError_t launch_ingest(const double* canon, double* tiled, const Mesh& mesh, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* U, const double* wn, DevState* ts,
-                                   const Mesh& mesh, const Phys& phys, int M, cudaStream_t s) {
+cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* U, const double* wn,
+                                   unsigned long long* dt_bits, int* pending, const Mesh& mesh, const Phys& phys,
+                                   int M, cudaStream_t s) {
   NodeW w{};
   for (int k = 0; k < M; k++) {
     w.wh[k] = (float)wn[k];
@@ -381,10 +412,10 @@ cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* 
   const dim3 g(mesh.ntx, mesh.ny), b(TILE, 3);
   const double idx = 1.0 / mesh.dx, idy = 1.0 / mesh.dy;
   switch (M) {
-    case 4: k_ingest_delta_cfl<4><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
-    case 9: k_ingest_delta_cfl<9><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
-    case 16: k_ingest_delta_cfl<16><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
-    case 25: k_ingest_delta_cfl<25><<<g, b, 0, s>>>(canon, d, U, w, ts, mesh, phys, idx, idy); break;
+    case 4: k_ingest_delta_cfl<4><<<g, b, 0, s>>>(canon, d, U, w, dt_bits, pending, mesh, phys, idx, idy); break;
+    case 9: k_ingest_delta_cfl<9><<<g, b, 0, s>>>(canon, d, U, w, dt_bits, pending, mesh, phys, idx, idy); break;
+    case 16: k_ingest_delta_cfl<16><<<g, b, 0, s>>>(canon, d, U, w, dt_bits, pending, mesh, phys, idx, idy); break;
+    case 25: k_ingest_delta_cfl<25><<<g, b, 0, s>>>(canon, d, U, w, dt_bits, pending, mesh, phys, idx, idy); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

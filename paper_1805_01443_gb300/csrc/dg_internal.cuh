@@ -185,10 +185,23 @@ cudaError_t launch_to_canon(const double* tiled, double* canon, const Mesh& mesh
                             cudaStream_t s);
 // precision form (locally isothermal, 3 variables): canonical FP32 delta
 // (values at the nodes) -> tiled delta d, with the CFL minimum of U + d (U:
-// tiled FP64 u_b; wn: the node weights) folded into ts->dt_bits in the same
-// pass, as launch_cfl would
-cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* U, const double* wn, DevState* ts,
-                                   const Mesh& mesh, const Phys& phys, int M, cudaStream_t s);
+// tiled FP64 u_b; wn: the node weights) folded into *dt_bits (atomic minimum
+// of the bits of a double > 0) and a non-finite or non-positive state into
+// *pending (bit 0) in the same pass, as launch_cfl would
+cudaError_t launch_ingest_delta_cfl(const float* canon, float* d, const double* U, const double* wn,
+                                   unsigned long long* dt_bits, int* pending, const Mesh& mesh, const Phys& phys,
+                                   int M, cudaStream_t s);
+// The CFL slot of an upload converted on its own stream, apart from the time
+// state that steps still in flight read and write.
+struct UpSlot {
+  unsigned long long dt_bits;  // +inf bits when empty
+  int pending;                 // 0 when empty
+  int pad;
+};
+// Make the converted upload the handle's state: the time state as
+// launch_reset_state(t, step) leaves it, then the step's dt (or the error
+// status) from the slot, which is emptied for the upload after next.
+cudaError_t launch_adopt_upload(DevState* ts, UpSlot* up, double t, long long step, cudaStream_t s);
 cudaError_t launch_to_canon_f32(const float* tiled, float* canon, const Mesh& mesh, int nv, int M,
                                 cudaStream_t s);
 cudaError_t launch_conserved(const double* U, double* part, double* out, const Mesh& mesh, int nv,

@@ -385,6 +385,61 @@ def test_delta_upload_matches_the_fp64_upload():
         assert e.value.code == dg.DG_ERR_UNSUPPORTED
 
 
+def test_pipelined_delta_uploads_match_in_place_conversion():
+    """dg_set_delta_async converts each upload on its own stream into a spare
+    state buffer, which trades places with the current one, so that the
+    conversion overlaps the steps queued before it.  A loop of uploads, steps
+    and torque reads queued without waiting, with two steps between some
+    uploads and an FP64 upload among them, gives the torques, state and time
+    of the in-place conversion on the handle's stream (the path of a handle
+    held by a batch) bit for bit."""
+    cfg = prec_cfg(inputs.disc_planet(64, 4, q=3e-5))
+    with dg.Disc(cfg) as a, dg.Disc(cfg) as b, dg.Disc(cfg) as src:
+        src.step(3)
+        d0 = src.fetch_delta()
+        t, _, st = src.get_time()
+        pins = []
+        for k in range(5):
+            pin = torch.empty(d0.shape, dtype=torch.float32, pin_memory=True).numpy()
+            pin[...] = d0 * np.float32(1.0 + 1e-3 * k)
+            pins.append(pin)
+        full = torch.empty(src.shape, dtype=torch.float64, pin_memory=True).numpy()
+        full[...] = src.fetch()
+        nsteps = [1, 2, 1, 1, 2]
+        tq = torch.empty(8, dtype=torch.float64, pin_memory=True).numpy()
+        tr = torch.empty(8, dtype=torch.float64, pin_memory=True).numpy()
+        held = dg.Batch([b])  # b's uploads now convert in place
+        try:
+            for d, rec in ((a, tq), (b, tr)):
+                i = 0
+                for k in range(5):
+                    if k == 3:
+                        d.set_state_async(full, t, st)
+                        d.step(1)
+                        d.torque_async(rec, i)
+                        i += 1
+                    d.set_delta_async(pins[k], t + k, st + k)
+                    for _ in range(nsteps[k]):
+                        d.step(1)
+                        d.torque_async(rec, i)
+                        i += 1
+                    if d is b:
+                        d.sync()  # nothing of b overlaps
+                d.sync()
+            np.testing.assert_array_equal(tq, tr)
+            np.testing.assert_array_equal(a.fetch_delta(), b.fetch_delta())
+            assert a.get_time() == b.get_time()
+        finally:
+            held.close()
+        # out of the batch, b's next upload takes the pipelined path as well
+        a.set_delta_async(pins[0], t, st)
+        b.set_delta_async(pins[0], t, st)
+        a.step(2)
+        b.step(2)
+        np.testing.assert_array_equal(a.fetch_delta(), b.fetch_delta())
+        assert a.get_time() == b.get_time()
+
+
 def test_delta_exchange_is_the_node_values():
     """dg_fetch_delta returns delta = u - u_b as its values at the m x m
     Gauss-Legendre nodes of each element (index q*m + r), the documented
