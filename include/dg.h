@@ -127,7 +127,10 @@ typedef struct {
                          projected equilibrium u_b, with R_b = L(u_b) evaluated
                          in FP64 once, FP64 torque reduction and sums; delta is
                          held as its values at the Gauss-Legendre nodes and the
-                         state is exchanged as FP64 modes u = u_b + delta */
+                         state is exchanged as FP64 modes u = u_b + delta.
+                         2 (3xTF32) and 3 (split-BF16 tensor-core contractions)
+                         are not built: DG_ERR_UNSUPPORTED (the nodal form's
+                         contractions are ~8 % of a stage's instructions) */
   double amp, vx0, vy0;
   int limiter;        /* troubled-cell limiting after every RK stage (FP64 form,
                          SSP(3,3)): 0 none; 1 the TVB-modified minmod test
