@@ -154,3 +154,15 @@ def test_init_ex_refuses_a_host_workspace(L):
     assert not h.value
     assert b"workspace" in L.dg_last_error(None)
     assert not ws.any()
+
+
+def test_binding_refuses_tensors_it_cannot_pass_on():
+    """The binding hands the network calls and dg_features bare data pointers:
+    a host tensor, or one of another dtype, shape or layout, is refused before
+    any pointer reaches the library (host logic, no device needed)."""
+    torch = pytest.importorskip("torch")
+    x = torch.zeros((4, 8), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dg._device_tensor(x, torch.float32, (4, 8), "x")
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        dg._device_tensor(x.numpy(), torch.float32, (4, 8), "x")
